@@ -1,0 +1,265 @@
+"""Seeded synthetic game inputs shared by the CUDA path's tests/bench and the oracle's tests.
+
+This package builds inputs only: finite extensive-form games in the array form of the
+Definition in Section 2.1 (parent function, action partition, information partition,
+player partition, chance probabilities, utilities).  It performs none of the CFR
+arithmetic.  The heavy lifting (trees up to ~1e8 nodes) is in ``gamegen.c``.
+
+Families
+--------
+``public_private``   a seeded public tree hung below a root chance deal of private
+                     buckets; infoset = (acting player, own bucket, public node).
+``matrix_game``      a normal-form game written as a one-level tree (player 2 does not
+                     observe player 1's action).
+``config``           the three named workload shapes used throughout the repository:
+                     ``bucket3_depth6`` (~1e3 nodes, vanilla CFR in FP64),
+                     ``rank13_depth10`` (~2e6 nodes, 156-way deal, fold/showdown payoffs),
+                     ``holdem169_depth12`` (~1e8 nodes, 1326-way deal bucketed to 169).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libgamegen.so")
+
+DEAL_BUCKET_PAIRS = 0
+DEAL_HOLDEM_169 = 1
+PAY_UNIFORM = 0
+PAY_FOLD_SHOWDOWN = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile gamegen.c into libgamegen.so next to it (gcc, OpenMP)."""
+    src = os.path.join(_HERE, "gamegen.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", src, "-o", tmp])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("deal_kind", ctypes.c_int32),
+        ("num_buckets", ctypes.c_int32),
+        ("depth", ctypes.c_int32),
+        ("amin", ctypes.c_int32),
+        ("amax", ctypes.c_int32),
+        ("p_cont", ctypes.c_double),
+        ("p_chance", ctypes.c_double),
+        ("payoff_kind", ctypes.c_int32),
+        ("umax", ctypes.c_double),
+        ("general_sum", ctypes.c_int32),
+        ("first_actor", ctypes.c_int32),
+    ]
+
+
+_lib_handle = None
+
+
+def _lib():
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(_SO):
+            build()
+        lib = ctypes.CDLL(_SO)
+        lib.gg_make_plan.restype = ctypes.c_void_p
+        lib.gg_make_plan.argtypes = [ctypes.POINTER(_Params)]
+        lib.gg_free_plan.argtypes = [ctypes.c_void_p]
+        lib.gg_plan_counts.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        lib.gg_fill.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 7
+        _lib_handle = lib
+    return _lib_handle
+
+
+@dataclass
+class GameDesc:
+    """A finite extensive-form game as flat arrays (node order is arbitrary)."""
+
+    parent: np.ndarray               # int32 [N]; -1 at the root
+    action: np.ndarray               # int32 [N]; index in [0, |A(f_h(parent))|); -1 at the root
+    infoset: np.ndarray              # int32 [N]; -1 at terminals
+    infoset_player: np.ndarray       # int8  [H]; 0 = chance, 1, 2
+    infoset_num_actions: np.ndarray  # int32 [H]
+    chance_prob: np.ndarray          # float64, chance infosets in id order, actions in order
+    utility: np.ndarray              # float64 [N, 2]; read at terminals only
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def num_nodes(self) -> int:
+        return int(self.parent.shape[0])
+
+    @property
+    def num_infosets(self) -> int:
+        return int(self.infoset_player.shape[0])
+
+    @property
+    def num_q(self) -> int:
+        return int(self.infoset_num_actions.sum())
+
+
+def _counts(plan) -> np.ndarray:
+    out = (ctypes.c_int64 * 7)()
+    _lib().gg_plan_counts(plan, out)
+    return np.array(out[:], dtype=np.int64)
+
+
+def _params(seed, deal_kind, num_buckets, depth, amin, amax, p_cont, p_chance, payoff_kind, umax,
+            general_sum, first_actor) -> _Params:
+    return _Params(int(seed) & 0xFFFFFFFFFFFFFFFF, deal_kind, num_buckets, depth, amin, amax, float(p_cont),
+                   float(p_chance), payoff_kind, float(umax), int(bool(general_sum)), first_actor)
+
+
+def public_size(**kw) -> int:
+    """Number of game nodes the parameters produce, without writing the game."""
+    prm = _params(**kw)
+    plan = _lib().gg_make_plan(ctypes.byref(prm))
+    if not plan:
+        raise ValueError("invalid generator parameters")
+    try:
+        return int(_counts(plan)[0])
+    finally:
+        _lib().gg_free_plan(plan)
+
+
+def public_private(seed: int = 0, deal_kind: int = DEAL_BUCKET_PAIRS, num_buckets: int = 3, depth: int = 6,
+                   amin: int = 2, amax: int = 3, p_cont: float = 1.0, p_chance: float = 0.0,
+                   payoff_kind: int = PAY_UNIFORM, umax: float = 2.0, general_sum: bool = False,
+                   first_actor: int = 1) -> GameDesc:
+    prm = _params(seed, deal_kind, num_buckets, depth, amin, amax, p_cont, p_chance, payoff_kind, umax,
+                  general_sum, first_actor)
+    lib = _lib()
+    plan = lib.gg_make_plan(ctypes.byref(prm))
+    if not plan:
+        raise ValueError("invalid generator parameters")
+    try:
+        n, h, cq, k, pub, pdec, pterm = (int(x) for x in _counts(plan))
+        parent = np.empty(n, np.int32)
+        action = np.empty(n, np.int32)
+        infoset = np.empty(n, np.int32)
+        player = np.empty(h, np.int8)
+        nact = np.empty(h, np.int32)
+        cprob = np.empty(cq, np.float64)
+        util = np.empty((n, 2), np.float64)
+        lib.gg_fill(plan, *(a.ctypes.data for a in (parent, action, infoset, player, nact, cprob, util)))
+    finally:
+        lib.gg_free_plan(plan)
+    meta = dict(seed=seed, deals=k, public_nodes=pub, public_decisions=pdec, public_terminals=pterm,
+                depth=depth, amin=amin, amax=amax, p_cont=p_cont, p_chance=p_chance)
+    return GameDesc(parent, action, infoset, player, nact, cprob, util, meta)
+
+
+def fit_p_cont(target_nodes: int, tol: float = 0.1, **kw) -> float:
+    """Bisection on the continuation probability so the game lands within +-tol of target_nodes."""
+    lo, hi = 0.0, 1.0
+    best, best_err = 0.5, float("inf")
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        n = public_size(p_cont=mid, **kw)
+        err = abs(n - target_nodes) / target_nodes
+        if err < best_err:
+            best, best_err = mid, err
+        if err <= tol * 0.25:
+            break
+        if n < target_nodes:
+            lo = mid
+        else:
+            hi = mid
+    if best_err > tol:
+        raise ValueError(f"could not reach {target_nodes} nodes within {tol:.0%} (best {best_err:.1%})")
+    return best
+
+
+# Named workload shapes.  Sizes are realised counts of the seeded generator; callers report them.
+CONFIGS = {
+    # 6 ordered deals of 2 distinct buckets out of 3; depth 6 (deal + 5 decision levels); |A| in {2,3};
+    # no early termination; u1 ~ U[-2, 2].
+    "bucket3_depth6": dict(deal_kind=DEAL_BUCKET_PAIRS, num_buckets=3, depth=6, amin=2, amax=3,
+                           payoff_kind=PAY_UNIFORM, umax=2.0, p_cont=1.0),
+    # 156 ordered deals of 2 distinct ranks out of 13; depth 10; |A| in {3,4}; early cuts are folds,
+    # last-level leaves showdowns; pot in {1,2,4,8}; ~2e6 nodes.
+    "rank13_depth10": dict(deal_kind=DEAL_BUCKET_PAIRS, num_buckets=13, depth=10, amin=3, amax=4,
+                           payoff_kind=PAY_FOLD_SHOWDOWN, umax=8.0, target_nodes=2_000_000),
+    # 1326-way deal of 2-card combos bucketed to 169 classes; depth 12; |A| in {4,5}; u1 ~ U[-100, 100];
+    # ~1e8 nodes.
+    "holdem169_depth12": dict(deal_kind=DEAL_HOLDEM_169, depth=12, amin=4, amax=5,
+                              payoff_kind=PAY_UNIFORM, umax=100.0, target_nodes=100_000_000),
+}
+
+
+def config(name: str, seed: int = 0, target_nodes: int | None = None, **override) -> GameDesc:
+    """Build a named workload; ``target_nodes`` rescales the public tree (same family, other size)."""
+    kw = dict(CONFIGS[name])
+    kw.update(override)
+    tgt = target_nodes if target_nodes is not None else kw.pop("target_nodes", None)
+    kw.pop("target_nodes", None)
+    if tgt is not None:
+        kw["p_cont"] = fit_p_cont(tgt, seed=seed, **{k: v for k, v in _defaults(kw).items() if k != "p_cont"})
+    g = public_private(seed=seed, **kw)
+    g.meta["config"] = name
+    return g
+
+
+def _defaults(kw: dict) -> dict:
+    d = dict(deal_kind=DEAL_BUCKET_PAIRS, num_buckets=3, depth=6, amin=2, amax=3, p_cont=1.0, p_chance=0.0,
+             payoff_kind=PAY_UNIFORM, umax=2.0, general_sum=False, first_actor=1)
+    d.update(kw)
+    return d
+
+
+def matrix_game(payoff: np.ndarray) -> GameDesc:
+    """Zero-sum normal-form game (player-1 payoff matrix) as a one-level tree.
+
+    Player 1 acts at the root (infoset 0); player 2 acts at one infoset (1) that holds every
+    player-1 action, so player 2 does not observe it.  Node ids: 0 root, 1..m the player-2 nodes,
+    then the m*n terminals.
+    """
+    A = np.asarray(payoff, dtype=np.float64)
+    m, n = A.shape
+    N = 1 + m + m * n
+    parent = np.full(N, -1, np.int32)
+    action = np.full(N, -1, np.int32)
+    infoset = np.full(N, -1, np.int32)
+    util = np.zeros((N, 2))
+    infoset[0] = 0
+    for i in range(m):
+        parent[1 + i] = 0
+        action[1 + i] = i
+        infoset[1 + i] = 1
+        for j in range(n):
+            t = 1 + m + i * n + j
+            parent[t] = 1 + i
+            action[t] = j
+            util[t] = (A[i, j], -A[i, j])
+    return GameDesc(parent, action, infoset, np.array([1, 2], np.int8), np.array([m, n], np.int32),
+                    np.zeros(0), util, dict(kind="matrix", shape=(m, n)))
+
+
+def permute_nodes(g: GameDesc, seed: int) -> GameDesc:
+    """Same game with node ids relabelled by a seeded permutation (tests order independence)."""
+    rng = np.random.default_rng(seed)
+    n = g.num_nodes
+    perm = rng.permutation(n).astype(np.int64)       # new id of old node i is perm[i]
+    parent = np.full(n, -1, np.int32)
+    action = np.empty(n, np.int32)
+    infoset = np.empty(n, np.int32)
+    util = np.empty_like(g.utility)
+    old_par = g.parent.astype(np.int64)
+    newpar = np.where(old_par >= 0, perm[np.maximum(old_par, 0)], -1)
+    parent[perm] = newpar.astype(np.int32)
+    action[perm] = g.action
+    infoset[perm] = g.infoset
+    util[perm] = g.utility
+    meta = dict(g.meta)
+    meta["permutation_seed"] = seed
+    meta["perm"] = perm
+    return GameDesc(parent, action, infoset, g.infoset_player.copy(), g.infoset_num_actions.copy(),
+                    g.chance_prob.copy(), util, meta)
