@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: one full-tree CFR+ iteration per step on the holdem169_depth12 workload.
+
+Workload: seeded synthetic two-player zero-sum tree, ~1.0e8 nodes (1326-way root deal of 2-card
+combos bucketed to 169 classes, depth 12, 4-5 actions, u1 ~ U[-100, 100]); CFR+ with linear
+averaging, FP32 reach/values/regrets with FP64 cumulative regrets and strategy sums.  The resident
+state (~1.7 GB) is larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the plain recursive FP64 CPU oracle on
+the host cores over a bounded sample of the same workload (its first deals).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tree-node updates/sec and CFR iterations/sec (HBM roofline %); time to exploitability 1e-3"
+UNIT = "node-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="holdem169_depth12")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--variant", choices=["plus", "vanilla"], default="plus")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[4]),
+                                 reasons=[n for n, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                                             "sw_power_cap"), parts[6:10]) if v == "Active"]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        loaded = [r for r in rows if r["util"] > 0] or rows
+        sm = sorted(r["sm"] for r in loaded)
+        reasons = sorted({x for r in loaded for x in r["reasons"]})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r["smax"] for r in rows), "reasons": reasons,
+                "samples": len(loaded)}
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = json.load(open(p)).get("hbm_gbs")
+        if v:
+            return float(v), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2408_14778_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, precision: str):
+    """DRAM bytes per iteration from the committed ncu summary, if taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    want = kernel_source_hash()
+    for line in open(p):
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernels_sha") == want and kv.get("workload") == workload and kv.get("precision") == precision:
+            return float(kv["dram_bytes_per_iteration"])
+    return None
+
+
+def oracle_sample(g, budget_s: float):
+    """First-deals sub-game sized so one oracle iteration takes about budget_s seconds."""
+    import gamegen
+
+    per_deal = int(g.meta["public_nodes"])
+    rate = 1.0e7                               # oracle node-updates/s, order of magnitude, sizing only
+    k = max(1, min(int(g.meta["deals"]), int(budget_s * rate / per_deal)))
+    return gamegen.first_deals(g, k)
+
+
+def cpu_baseline(g, variant: int, seconds: float = 12.0) -> dict:
+    import oracle
+
+    sub = oracle_sample(g, 0.5)
+    o = oracle.Oracle(sub)
+    o.iterate(1, variant=variant, avg=variant)
+    iters, t0 = 0, time.perf_counter()
+    while True:
+        o.iterate(1, variant=variant, avg=variant)
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and iters >= 2:
+            break
+    return {"value": sub.num_nodes * iters / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {sub.meta['deals']} of {g.meta['deals']} deals ({sub.num_nodes} of {g.num_nodes} nodes), "
+                      f"{iters} full iterations in {el:.1f} s, single-threaded recursive FP64 oracle"}
+
+
+def workload_config(args, g, info=None):
+    c = {"workload": f"{args.workload} (seed {args.seed}): 1326-way deal bucketed to 169, depth 12, |A| 4-5, "
+                     "u1~U[-100,100]",
+         "nodes": g.num_nodes, "variant": "cfr+" if args.variant == "plus" else "vanilla",
+         "averaging": "linear" if args.variant == "plus" else "uniform",
+         "precision": "fp32 reach/values/regrets, fp64 cumulative sums" if args.precision == "fp32" else "fp64",
+         "update": "simultaneous", "l2": "resident state larger than L2 (no flush needed)"}
+    if info:
+        c.update(decision_nodes=info["num_decision"], terminals=info["num_terminal"], infosets=info["num_infosets"],
+                 infoset_actions=info["num_q"], levels=info["num_levels"], device_bytes=info["device_bytes"])
+    return c
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import gamegen
+    import oracle
+
+    variant = 1 if args.variant == "plus" else 0
+    g = gamegen.config(args.workload, seed=args.seed)
+    budget = max(0.05, 90.0 / max(args.steps + args.warmup, 1))
+    sub = oracle_sample(g, budget)
+    o = oracle.Oracle(sub)
+    o.iterate(args.warmup, variant=variant, avg=variant)
+    t0 = time.perf_counter()
+    o.iterate(args.steps, variant=variant, avg=variant)
+    el = time.perf_counter() - t0
+    value = sub.num_nodes * args.steps / el
+    sample = (f"first {sub.meta['deals']} of {g.meta['deals']} deals ({sub.num_nodes} of {g.num_nodes} nodes) per "
+              f"step; single-threaded recursive FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, g),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import gamegen
+    import paper_2408_14778_gb300 as cfr
+
+    cfr.build()
+    torch.cuda.set_device(local)
+    variant = cfr.CFR_PLUS if args.variant == "plus" else cfr.CFR_VANILLA
+    precision = cfr.CFR_FP32 if args.precision == "fp32" else cfr.CFR_FP64
+    g = gamegen.config(args.workload, seed=args.seed)
+    s = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local)
+    info = cfr.cfr_get_info(s)
+    stream = torch.cuda.current_stream(local)
+    cfr.cfr_iterate(s, args.warmup)
+    cfr.cfr_synchronize(s)
+
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cfr.cfr_iterate(s, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier(world)
+    t = e0.elapsed_time(e1) / 1e3
+    t_max = max_over_ranks(t, world, device=f"cuda:{local}")
+    N = info["num_nodes"]
+    value = world * N * args.steps / t_max
+    iter_s = t / args.steps
+    achieved = info["bytes_per_iteration"] / iter_s / 1e9
+    peak, peak_src = measured_hbm_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(args.workload, args.precision),
+                "kernel": "one full CFR iteration (graph of per-depth kernels)",
+                "algorithmic_bytes_per_launch": info["bytes_per_iteration"], "peak_source": peak_src}
+
+    e2e = None
+    if not args.no_e2e:
+        # End to end through the C ABI from host arrays: load (validate, lay out, upload the tree), then per
+        # step one iteration and a device->host read of its root value, then the average strategy.
+        s.close()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        s2 = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local)
+        for _ in range(args.steps):
+            cfr.cfr_iterate(s2, 1)
+            cfr.cfr_root_value(s2)
+        avg = cfr.cfr_average_strategy(s2)
+        el = time.perf_counter() - t0
+        el = max_over_ranks(el, world, device=f"cuda:{local}")
+        inputs = sum(a.nbytes for a in (g.parent, g.action, g.infoset, g.infoset_player, g.infoset_num_actions,
+                                        g.chance_prob, g.utility))
+        e2e = {"value": world * N * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": inputs / args.steps,
+               "d2h_bytes_per_step": 8 + avg.nbytes / args.steps,
+               "includes": "cfr_load_tree from host arrays (validation, layout, upload) + per step cfr_iterate(1) + "
+                           "cfr_root_value, then cfr_average_strategy",
+               "seconds": el}
+        s2.close()
+        del avg
+    else:
+        s.close()
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(g, 1 if args.variant == "plus" else 0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+                "data": "synthetic", "config": workload_config(args, g, info),
+                "iterations_per_s": args.steps / t_max, "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
+                "gpu_launches": info["kernels_per_iteration"] * args.steps, "clocks": clocks,
+                "parallelism": "replicas" if world > 1 else "single GPU"}
+        print(json.dumps(line), flush=True)
+    del np
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -243,6 +243,25 @@ def matrix_game(payoff: np.ndarray) -> GameDesc:
                     np.zeros(0), util, dict(kind="matrix", shape=(m, n)))
 
 
+def first_deals(g: GameDesc, k: int) -> GameDesc:
+    """The sub-game of a ``public_private`` game holding only its first k deals.
+
+    Nodes are emitted deal-major (root, then each deal's copy of the public tree), so the sub-game
+    is the node prefix [0, 1 + k * P).  The root's chance infoset keeps k outcomes with probability
+    1/k each; every other infoset keeps its id (some are left without nodes).
+    """
+    K, P = int(g.meta["deals"]), int(g.meta["public_nodes"])
+    k = max(1, min(int(k), K))
+    n = 1 + k * P
+    nact = g.infoset_num_actions.copy()
+    nact[0] = k
+    cprob = np.concatenate([np.full(k, 1.0 / k), g.chance_prob[K:]])
+    meta = dict(g.meta)
+    meta.update(deals=k, sample_of=g.num_nodes)
+    return GameDesc(g.parent[:n].copy(), g.action[:n].copy(), g.infoset[:n].copy(), g.infoset_player.copy(), nact,
+                    cprob, g.utility[:n].copy(), meta)
+
+
 def permute_nodes(g: GameDesc, seed: int) -> GameDesc:
     """Same game with node ids relabelled by a seeded permutation (tests order independence)."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,179 @@
+/*
+ * cfr_gb300.h - C ABI of a GB300-native (sm_103a) counterfactual regret minimization solver.
+ *
+ * One solver holds one finite extensive-form game <T, H, f_h, A, f_a, I, f_i, sigma_0, u>
+ * (Definition in Section 2.1) on the GPU and runs full-tree CFR iterations (Section 2.3; the
+ * matrix form of Section 3, Eq. 11-15) as hand-written CUDA kernels over a level-ordered layout of
+ * the tree.  Two-player zero-sum games only (u_2 = -u_1).
+ *
+ * Conventions shared by every entry point
+ *   - Node ids, infoset ids and action indices are the caller's.  "Q arrays" are infoset-major
+ *     over ALL infosets (chance infosets included), actions 0..|A(h)|-1 in order; their length is
+ *     num_q = sum_h |A(h)|.  Regret and strategy-sum entries of chance infosets are 0; strategy
+ *     entries of chance infosets hold sigma_0.
+ *   - Host pointers only.  The library copies every input before returning; outputs go to
+ *     caller-owned host buffers whose length is passed and checked (too short -> CFR_ERR_INVALID).
+ *   - The library owns its device memory.  It allocates through cfr_config.dev_alloc/dev_free when
+ *     given (e.g. a framework's caching allocator), otherwise through cudaMalloc/cudaFree.
+ *   - Work is queued on cfr_config.cuda_stream (borrowed, never destroyed).  Entry points that
+ *     return data to host buffers synchronise that stream first.
+ *   - Nothing throws across the ABI.  Every call returns a cfr_status; cfr_last_error() gives a
+ *     message.  A CUDA error poisons the solver: later calls return CFR_ERR_STATE; free it.
+ *   - One solver must not be used from two threads at once.
+ */
+#ifndef CFR_GB300_H
+#define CFR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CFR_OK = 0,
+    CFR_ERR_INVALID = 1,     /* malformed arguments or game description */
+    CFR_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    CFR_ERR_OOM = 3,         /* device allocation failed */
+    CFR_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired */
+    CFR_ERR_STATE = 5,       /* solver poisoned by an earlier error, or called out of order */
+    CFR_ERR_UNSUPPORTED = 6  /* valid game the solver does not handle (see each call) */
+} cfr_status;
+
+/* Variants.  CFR+ is named in Section 1 without formulas; it is read as regret-matching+
+ * (cumulative regrets clipped at 0 after every iteration) with linear averaging. */
+enum { CFR_VANILLA = 0, CFR_PLUS = 1 };
+/* Precision (Section 4.1 runs FP32 and FP64).  CFR_FP32: reach, node values and instantaneous
+ * regrets in FP32, cumulative regrets and strategy sums in FP64.  CFR_FP64: everything FP64. */
+enum { CFR_FP32 = 0, CFR_FP64 = 1 };
+/* Both players update from the same iteration (the paper's vector form, Section 3.2). */
+enum { CFR_SIMULTANEOUS = 0, CFR_ALTERNATING = 1 };
+/* Weight of iteration T in the average strategy: 1 (Eq. 10) or T.  DEFAULT = UNIFORM for vanilla
+ * and LINEAR for CFR+. */
+enum { CFR_AVG_DEFAULT = -1, CFR_AVG_UNIFORM = 0, CFR_AVG_LINEAR = 1 };
+
+typedef struct cfr_solver cfr_solver;   /* opaque; owned by the library */
+
+/* The game of the Definition in Section 2.1, as flat arrays in any node order. */
+typedef struct {
+    int64_t num_nodes;                  /* |V| >= 1; must be < 2^31 - 1 */
+    const int32_t *parent;              /* [num_nodes] f_Pa; exactly one -1 (the root v_0) */
+    const int32_t *action;              /* [num_nodes] f_a: index in [0, |A(f_h(parent))|); ignored at the root */
+    const int32_t *infoset;             /* [num_nodes] f_h for decision nodes, -1 for terminals */
+    int32_t num_infosets;               /* |H|, chance infosets included */
+    const int8_t *infoset_player;       /* [num_infosets] f_i: 0 = chance (i_0), 1, 2 */
+    const int32_t *infoset_num_actions; /* [num_infosets] |A(h)| >= 1 */
+    const double *chance_prob;          /* sigma_0: chance infosets in id order, actions in order */
+    int64_t num_chance_prob;            /* length of chance_prob = sum of |A(h)| over chance infosets */
+    const double *utility;              /* [num_nodes x 2] u(t, 1), u(t, 2) row-major; read at terminals */
+} cfr_game_desc;
+
+typedef void *(*cfr_alloc_fn)(size_t bytes, void *ctx);   /* returns NULL on failure */
+typedef void (*cfr_free_fn)(void *ptr, void *ctx);
+
+typedef struct {
+    int32_t variant;        /* CFR_VANILLA | CFR_PLUS */
+    int32_t precision;      /* CFR_FP32 | CFR_FP64 */
+    int32_t update_mode;    /* CFR_SIMULTANEOUS | CFR_ALTERNATING */
+    int32_t avg_weight;     /* CFR_AVG_DEFAULT | CFR_AVG_UNIFORM | CFR_AVG_LINEAR */
+    int32_t device;         /* CUDA device ordinal; -1 = the calling thread's current device */
+    void *cuda_stream;      /* cudaStream_t to run on (borrowed); NULL = the legacy default stream */
+    cfr_alloc_fn dev_alloc; /* optional device allocator (both or neither) */
+    cfr_free_fn dev_free;
+    void *alloc_ctx;
+} cfr_config;
+
+/* Sizes and accounting of a loaded solver. */
+typedef struct {
+    int64_t num_nodes, num_decision, num_terminal;
+    int64_t num_q;
+    int32_t num_infosets;
+    int32_t num_levels;           /* depth levels holding decision nodes */
+    int32_t max_depth;            /* deepest node (root at depth 0) */
+    int32_t max_actions;
+    int32_t single_level_infosets;/* 1 if every infoset's nodes share one depth (needed by cfr_exploitability) */
+    int32_t variant, precision, update_mode, avg_weight;
+    int64_t iteration;            /* completed iterations T */
+    int64_t device_bytes;         /* device memory held by the solver */
+    int64_t bytes_per_iteration;  /* algorithmic bytes of one iteration: 56 Nd + 4 Nt + 44 Q (FP32 mode) or
+                                     96 Nd + 8 Nt + 56 Q (FP64 mode) */
+    int32_t kernels_per_iteration;/* kernel launches of one iteration */
+} cfr_info;
+
+/* Fills *c with defaults: vanilla, FP32, simultaneous, default averaging, current device,
+ * legacy default stream, cudaMalloc. */
+void cfr_config_init(cfr_config *c);
+
+/* Checks a game description without touching the GPU.  CFR_OK, CFR_ERR_INVALID (malformed: bad
+ * sizes or ids, not a single rooted tree, children not a bijection onto 0..|A(h)|-1, sigma_0
+ * negative or not summing to 1 +- 1e-9 per chance infoset, non-finite utility, imperfect recall:
+ * two nodes of one infoset whose acting player's own (infoset, action) history differs), or
+ * CFR_ERR_UNSUPPORTED (valid but not two-player zero-sum, or sizes beyond 32-bit ids).  If msg is
+ * non-NULL, a NUL-terminated reason of at most msg_len bytes is written. */
+cfr_status cfr_validate(const cfr_game_desc *g, char *msg, size_t msg_len);
+
+/* Validates the game (as cfr_validate), builds the level-ordered layout on the host (nodes sorted
+ * by depth, children of a node contiguous and in action order - the level graphs L^(l) of
+ * Section 3.1 made implicit), uploads it once and sets sigma^(1) to uniform (Section 3.1).
+ * On success *out owns the solver; on failure *out is NULL and cfr_last_error(NULL) explains.
+ * c may be NULL (defaults). */
+cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver **out);
+
+/* Queues n >= 0 full-tree CFR iterations (Section 3.2): top-down reach (Eq. 2, 4, 13), bottom-up
+ * node values with the instantaneous-regret scatter (Eq. 1, 7, 11), then per infoset the
+ * cumulative regret (Eq. 8/15, CFR+ clipping), strategy sum (Eq. 10/14) and regret matching
+ * (Eq. 9).  Asynchronous on the solver's stream. */
+cfr_status cfr_iterate(cfr_solver *s, int32_t n);
+
+/* Waits for all queued work of the solver. */
+cfr_status cfr_synchronize(cfr_solver *s);
+
+/* Average strategy sigma-bar^(T) (Eq. 10, normalised; uniform where the strategy sum is 0) into
+ * out[num_q]. */
+cfr_status cfr_average_strategy(cfr_solver *s, double *out, int64_t len);
+
+/* Current strategy sigma^(T+1) (Eq. 9) into out[num_q]. */
+cfr_status cfr_current_strategy(cfr_solver *s, double *out, int64_t len);
+
+/* NashConv = sum_i max_{sigma'_i} u_i(sigma'_i, sigma-bar_-i) - u_i(sigma-bar) of the average
+ * strategy (Section 2.2, epsilon-Nash; used for sanity testing in Appendix A), computed on the GPU
+ * in FP64 by one top-down and one bottom-up best-response pass per player; exploitability =
+ * NashConv / 2.  Either pointer may be NULL.  CFR_ERR_UNSUPPORTED if some infoset spans two depths. */
+cfr_status cfr_exploitability(cfr_solver *s, double *nash_conv, double *exploitability);
+
+/* Copies the FP64 cumulative regrets R (R = T * r-bar of Eq. 8), strategy sums S (numerator of
+ * Eq. 10 with one node's own reach per infoset), the last iteration's instantaneous regrets (Eq. 7)
+ * into [len_q] buffers, the last iteration's own reach per infoset (Eq. 4) into own_reach[len_h],
+ * and T into *iteration.  Any pointer may be NULL.  Checkpoint and test hook. */
+cfr_status cfr_get_state(cfr_solver *s, double *cum_regret, double *strat_sum, double *inst_regret,
+                         int64_t len_q, double *own_reach, int64_t len_h, int64_t *iteration);
+
+/* Replaces R, S (each [len_q], len_q == num_q) and T, then sets the current strategy to the regret
+ * matching of R (Eq. 9).  Entries of chance infosets are ignored.  Checkpoint restore / test hook. */
+cfr_status cfr_set_state(cfr_solver *s, const double *cum_regret, const double *strat_sum, int64_t len_q,
+                         int64_t iteration);
+
+/* Per node of the last iteration, in caller node order ([len] each, len == num_nodes; any pointer
+ * may be NULL): u1 = u-check(v, 1) (Eq. 1; the utility at terminals), cf_reach1 = pi-check(v, 1)
+ * and cf_reach2 = pi-check(v, 2) (Eq. 2) at decision nodes, NaN at terminals.  Test hook. */
+cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *cf_reach2, int64_t len);
+
+/* Expected payoff of player 1 under the last iteration's profile sigma^(T): u-check(sigma^(T), v_0, 1)
+ * of Eq. 1 at the root, which equals u-hat(sigma^(T), 1) of Section 2.2.  One scalar; synchronises
+ * the stream (a per-iteration progress read).  0 before the first iteration. */
+cfr_status cfr_root_value(cfr_solver *s, double *u1);
+
+cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info);
+
+/* Message of the last failed call on s, or of the calling thread's last failed cfr_load_tree /
+ * cfr_validate when s is NULL.  Valid until the next call on the same solver / thread. */
+const char *cfr_last_error(const cfr_solver *s);
+
+/* Releases the solver and its device memory (waits for its queued work).  NULL is a no-op. */
+void cfr_free(cfr_solver *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CFR_GB300_H */

@@ -1,0 +1,313 @@
+"""Python binding of libcfr_gb300.so (include/cfr_gb300.h): argument marshalling only.
+
+Every step of a CFR iteration runs in the library's CUDA kernels; this module converts numpy
+arrays to the C structures, passes PyTorch's current CUDA stream and (optionally) PyTorch's
+caching allocator to the library, and turns status codes into exceptions.  There is no CPU
+fallback: if the shared library is missing, importing the binding's entry points raises.
+
+Functions carry the C names (``cfr_load_tree``, ``cfr_iterate``, ...).  ``Solver`` bundles them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+from ._build import build as _build_library
+
+CFR_OK, CFR_ERR_INVALID, CFR_ERR_CUDA, CFR_ERR_OOM, CFR_ERR_TIMEOUT, CFR_ERR_STATE, CFR_ERR_UNSUPPORTED = range(7)
+CFR_VANILLA, CFR_PLUS = 0, 1
+CFR_FP32, CFR_FP64 = 0, 1
+CFR_SIMULTANEOUS, CFR_ALTERNATING = 0, 1
+CFR_AVG_DEFAULT, CFR_AVG_UNIFORM, CFR_AVG_LINEAR = -1, 0, 1
+
+_STATUS_NAMES = {0: "CFR_OK", 1: "CFR_ERR_INVALID", 2: "CFR_ERR_CUDA", 3: "CFR_ERR_OOM", 4: "CFR_ERR_TIMEOUT",
+                 5: "CFR_ERR_STATE", 6: "CFR_ERR_UNSUPPORTED"}
+
+
+class CfrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class _GameDesc(ctypes.Structure):
+    _fields_ = [
+        ("num_nodes", ctypes.c_int64),
+        ("parent", ctypes.c_void_p),
+        ("action", ctypes.c_void_p),
+        ("infoset", ctypes.c_void_p),
+        ("num_infosets", ctypes.c_int32),
+        ("infoset_player", ctypes.c_void_p),
+        ("infoset_num_actions", ctypes.c_void_p),
+        ("chance_prob", ctypes.c_void_p),
+        ("num_chance_prob", ctypes.c_int64),
+        ("utility", ctypes.c_void_p),
+    ]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("variant", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("update_mode", ctypes.c_int32),
+        ("avg_weight", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+        ("dev_alloc", _ALLOC_FN),
+        ("dev_free", _FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [
+        ("num_nodes", ctypes.c_int64), ("num_decision", ctypes.c_int64), ("num_terminal", ctypes.c_int64),
+        ("num_q", ctypes.c_int64), ("num_infosets", ctypes.c_int32), ("num_levels", ctypes.c_int32),
+        ("max_depth", ctypes.c_int32), ("max_actions", ctypes.c_int32), ("single_level_infosets", ctypes.c_int32),
+        ("variant", ctypes.c_int32), ("precision", ctypes.c_int32), ("update_mode", ctypes.c_int32),
+        ("avg_weight", ctypes.c_int32), ("iteration", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("bytes_per_iteration", ctypes.c_int64), ("kernels_per_iteration", ctypes.c_int32),
+    ]
+
+
+_lib_handle = None
+_P = ctypes.c_void_p
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles libcfr_gb300.so in-tree (nvcc, sm_103a)."""
+    return _build_library(force=force, verbose=verbose)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """The loaded shared library; raises if it has not been built."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_2408_14778_gb300.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(_LIB_PATH)
+        L.cfr_config_init.argtypes = [ctypes.POINTER(_Config)]
+        L.cfr_config_init.restype = None
+        L.cfr_validate.argtypes = [ctypes.POINTER(_GameDesc), ctypes.c_char_p, ctypes.c_size_t]
+        L.cfr_load_tree.argtypes = [ctypes.POINTER(_GameDesc), ctypes.POINTER(_Config), ctypes.POINTER(_P)]
+        L.cfr_iterate.argtypes = [_P, ctypes.c_int32]
+        L.cfr_synchronize.argtypes = [_P]
+        L.cfr_average_strategy.argtypes = [_P, _P, ctypes.c_int64]
+        L.cfr_current_strategy.argtypes = [_P, _P, ctypes.c_int64]
+        L.cfr_exploitability.argtypes = [_P, _P, _P]
+        L.cfr_get_state.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]
+        L.cfr_set_state.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int64]
+        L.cfr_get_nodes.argtypes = [_P, _P, _P, _P, ctypes.c_int64]
+        L.cfr_get_info.argtypes = [_P, ctypes.POINTER(_Info)]
+        L.cfr_root_value.argtypes = [_P, _P]
+        L.cfr_last_error.argtypes = [_P]
+        L.cfr_last_error.restype = ctypes.c_char_p
+        L.cfr_free.argtypes = [_P]
+        L.cfr_free.restype = None
+        for name in ("cfr_validate", "cfr_load_tree", "cfr_iterate", "cfr_synchronize", "cfr_average_strategy",
+                     "cfr_current_strategy", "cfr_exploitability", "cfr_get_state", "cfr_set_state", "cfr_get_nodes",
+                     "cfr_get_info", "cfr_root_value"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib_handle = L
+    return _lib_handle
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/cfr_gb300.h declares (used to check the exports)."""
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "cfr_gb300.h")
+    text = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(cfr_[a-z_]+)\s*\(", text)) - {"cfr_alloc_fn", "cfr_free_fn"})
+
+
+def _check(st: int, solver_handle=None):
+    if st != CFR_OK:
+        msg = lib().cfr_last_error(solver_handle)
+        raise CfrError(st, msg.decode(errors="replace") if msg else "")
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class _Desc:
+    """Keeps the marshalled arrays alive for the duration of a call."""
+
+    def __init__(self, game):
+        self.arrays = [_arr(game.parent, np.int32), _arr(game.action, np.int32), _arr(game.infoset, np.int32),
+                       _arr(game.infoset_player, np.int8), _arr(game.infoset_num_actions, np.int32),
+                       _arr(game.chance_prob, np.float64), _arr(game.utility, np.float64)]
+        p, a, i, pl, na, cp, u = self.arrays
+        if u.ndim != 2 or u.shape != (p.shape[0], 2):
+            raise ValueError("utility must have shape (num_nodes, 2)")
+        self.c = _GameDesc(p.shape[0], p.ctypes.data, a.ctypes.data, i.ctypes.data, pl.shape[0], pl.ctypes.data,
+                           na.ctypes.data, cp.ctypes.data if cp.size else None, cp.shape[0], u.ctypes.data)
+
+
+def cfr_validate(game) -> tuple[int, str]:
+    """(status, message) without touching the GPU."""
+    d = _Desc(game)
+    buf = ctypes.create_string_buffer(512)
+    st = lib().cfr_validate(ctypes.byref(d.c), buf, len(buf))
+    return st, buf.value.decode(errors="replace")
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+
+        self.torch = torch
+        self.device, self.stream = device, stream
+        self.alloc = _ALLOC_FN(self._alloc)
+        self.free = _FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            return int(self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+        except Exception:  # noqa: BLE001 - reported to the library as NULL (CFR_ERR_OOM)
+            return None
+
+    def _free(self, ptr, ctx):
+        try:
+            self.torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def cfr_load_tree(game, variant=CFR_VANILLA, precision=CFR_FP32, update_mode=CFR_SIMULTANEOUS,
+                  avg_weight=CFR_AVG_DEFAULT, device=None, stream=None, allocator: str = "torch"):
+    """Loads a game and returns a Solver.  stream: None = PyTorch's current stream on the device."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise CfrError(CFR_ERR_CUDA, "no CUDA device is available")
+    dev = torch.cuda.current_device() if device is None else int(device)
+    st_handle = torch.cuda.current_stream(dev).cuda_stream if stream is None else int(stream)
+    cfg = _Config()
+    lib().cfr_config_init(ctypes.byref(cfg))
+    cfg.variant, cfg.precision, cfg.update_mode, cfg.avg_weight = variant, precision, update_mode, avg_weight
+    cfg.device = dev
+    cfg.cuda_stream = st_handle
+    alloc = None
+    if allocator == "torch":
+        alloc = _TorchAllocator(dev, st_handle)
+        cfg.dev_alloc, cfg.dev_free = alloc.alloc, alloc.free
+    elif allocator != "cuda":
+        raise ValueError("allocator must be 'torch' or 'cuda'")
+    d = _Desc(game)
+    h = _P()
+    _check(lib().cfr_load_tree(ctypes.byref(d.c), ctypes.byref(cfg), ctypes.byref(h)))
+    return Solver(h, alloc)
+
+
+def cfr_iterate(s: "Solver", n: int = 1):
+    _check(lib().cfr_iterate(s.handle, int(n)), s.handle)
+
+
+def cfr_synchronize(s: "Solver"):
+    _check(lib().cfr_synchronize(s.handle), s.handle)
+
+
+def cfr_average_strategy(s: "Solver") -> np.ndarray:
+    out = np.empty(max(s.num_q, 1))
+    _check(lib().cfr_average_strategy(s.handle, out.ctypes.data, out.shape[0]), s.handle)
+    return out[: s.num_q]
+
+
+def cfr_current_strategy(s: "Solver") -> np.ndarray:
+    out = np.empty(max(s.num_q, 1))
+    _check(lib().cfr_current_strategy(s.handle, out.ctypes.data, out.shape[0]), s.handle)
+    return out[: s.num_q]
+
+
+def cfr_exploitability(s: "Solver") -> tuple[float, float]:
+    nc, ex = ctypes.c_double(), ctypes.c_double()
+    _check(lib().cfr_exploitability(s.handle, ctypes.byref(nc), ctypes.byref(ex)), s.handle)
+    return nc.value, ex.value
+
+
+def cfr_get_state(s: "Solver") -> dict:
+    q, h = max(s.num_q, 1), max(s.num_infosets, 1)
+    R, S, inst, own = np.empty(q), np.empty(q), np.empty(q), np.empty(h)
+    it = ctypes.c_int64()
+    _check(lib().cfr_get_state(s.handle, R.ctypes.data, S.ctypes.data, inst.ctypes.data, q, own.ctypes.data, h,
+                               ctypes.byref(it)), s.handle)
+    return dict(cum_regret=R[: s.num_q], strat_sum=S[: s.num_q], inst_regret=inst[: s.num_q],
+                own_reach=own[: s.num_infosets], iteration=it.value)
+
+
+def cfr_set_state(s: "Solver", cum_regret, strat_sum, iteration: int):
+    R, S = _arr(cum_regret, np.float64), _arr(strat_sum, np.float64)
+    _check(lib().cfr_set_state(s.handle, R.ctypes.data, S.ctypes.data, R.shape[0], int(iteration)), s.handle)
+
+
+def cfr_get_nodes(s: "Solver") -> dict:
+    n = s.num_nodes
+    u, r1, r2 = np.empty(n), np.empty(n), np.empty(n)
+    _check(lib().cfr_get_nodes(s.handle, u.ctypes.data, r1.ctypes.data, r2.ctypes.data, n), s.handle)
+    return dict(u1=u, cf_reach1=r1, cf_reach2=r2)
+
+
+def cfr_root_value(s: "Solver") -> float:
+    """u-check(sigma^T, v_0, 1) of the last iteration (synchronises the solver's stream)."""
+    v = ctypes.c_double()
+    _check(lib().cfr_root_value(s.handle, ctypes.byref(v)), s.handle)
+    return v.value
+
+
+def cfr_get_info(s: "Solver") -> dict:
+    info = _Info()
+    _check(lib().cfr_get_info(s.handle, ctypes.byref(info)), s.handle)
+    return {name: getattr(info, name) for name, _ in _Info._fields_}
+
+
+def cfr_free(s: "Solver"):
+    s.close()
+
+
+class Solver:
+    """A loaded game on the GPU (owns the C handle)."""
+
+    def __init__(self, handle, allocator=None):
+        self.handle = handle
+        self._allocator = allocator          # keeps the ctypes callbacks alive
+        info = cfr_get_info(self)
+        self.num_nodes = info["num_nodes"]
+        self.num_q = info["num_q"]
+        self.num_infosets = info["num_infosets"]
+
+    def close(self):
+        if self.handle:
+            lib().cfr_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    iterate = cfr_iterate
+    synchronize = cfr_synchronize
+    average_strategy = cfr_average_strategy
+    current_strategy = cfr_current_strategy
+    exploitability = cfr_exploitability
+    get_state = cfr_get_state
+    set_state = cfr_set_state
+    get_nodes = cfr_get_nodes
+    root_value = cfr_root_value
+    info = cfr_get_info

@@ -1,0 +1,600 @@
+// C ABI of the solver (include/cfr_gb300.h): device memory, uploads, the per-iteration launch
+// sequence captured once into a CUDA graph, getters and the GPU best response.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "cfr_gb300.h"
+#include "kernels.cuh"
+#include "layout.hpp"
+
+using namespace cfrgb;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+constexpr int kBlock = 256;
+
+inline int32_t nblocks(int64_t n) { return (int32_t)((n + kBlock - 1) / kBlock); }
+
+// Restores the caller's current device when an entry point returns.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+        if (dev >= 0 && dev != prev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct cfr_solver {
+    cfr_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr;   // borrowed
+    cudaStream_t cap = nullptr;      // private, for graph capture
+    // sizes
+    int64_t N = 0, Nd = 0, Nt = 0, Q = 0;
+    int32_t H = 0, L = 0, max_depth = 0, max_actions = 0;
+    bool single_level = true;
+    std::vector<int32_t> dlevel, hlevel, dnode_user, tnode_user, h_int2user;
+    // device arrays
+    int32_t *dfirst = nullptr, *tfirst = nullptr, *dinfo = nullptr, *qbase = nullptr, *pseq = nullptr,
+            *pseq_h = nullptr, *q_int2user = nullptr, *astar = nullptr;
+    int8_t *iplayer = nullptr;
+    uint32_t *kmask = nullptr, *wbits = nullptr;
+    void *util = nullptr, *sigma = nullptr, *inst = nullptr, *reach1 = nullptr, *reach2 = nullptr,
+         *u = nullptr, *own = nullptr;
+    double *util64 = nullptr, *sigma064 = nullptr, *R = nullptr, *S = nullptr, *stage = nullptr;
+    double *br_reach = nullptr, *br_val = nullptr, *br_cfv = nullptr, *avg = nullptr, *br_out = nullptr;
+    int64_t *d_iter = nullptr;
+    int64_t iteration = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<std::pair<void *, size_t>> blocks;
+    int64_t device_bytes = 0;
+    std::string err;
+    bool poisoned = false;
+
+    size_t real_size() const { return cfg.precision == CFR_FP64 ? sizeof(double) : sizeof(float); }
+};
+
+namespace {
+
+cfr_status set_err(cfr_solver *s, cfr_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    else g_thread_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            s->poisoned = true;                                                                         \
+            return set_err(s, e_ == cudaErrorMemoryAllocation ? CFR_ERR_OOM : CFR_ERR_CUDA, "%s: %s (%s:%d)", \
+                           #call, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+        }                                                                                               \
+    } while (0)
+
+#define CK_LAUNCH() CK(cudaGetLastError())
+
+cfr_status dev_alloc(cfr_solver *s, void **p, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void *ptr = nullptr;
+    if (s->cfg.dev_alloc) {
+        ptr = s->cfg.dev_alloc(bytes, s->cfg.alloc_ctx);
+        if (!ptr) return set_err(s, CFR_ERR_OOM, "device allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&ptr, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(s, CFR_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    s->blocks.emplace_back(ptr, bytes);
+    s->device_bytes += (int64_t)bytes;
+    *p = ptr;
+    return CFR_OK;
+}
+
+template <typename T>
+cfr_status alloc_n(cfr_solver *s, T **p, int64_t n) {
+    return dev_alloc(s, reinterpret_cast<void **>(p), sizeof(T) * (size_t)(n > 0 ? n : 1));
+}
+
+template <typename T>
+cfr_status upload(cfr_solver *s, T *dst, const std::vector<T> &src) {
+    if (src.empty()) return CFR_OK;
+    CK(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s->stream));
+    return CFR_OK;
+}
+
+#define TRY(x)                                \
+    do {                                      \
+        cfr_status st_ = (x);                 \
+        if (st_ != CFR_OK) return st_;        \
+    } while (0)
+
+template <typename real>
+DevTree<real> dev_tree(cfr_solver *s) {
+    DevTree<real> t;
+    t.dfirst = s->dfirst; t.tfirst = s->tfirst; t.dinfo = s->dinfo;
+    t.kmask = s->kmask; t.wbits = s->wbits;
+    t.util = static_cast<const real *>(s->util);
+    t.qbase = s->qbase; t.iplayer = s->iplayer; t.pseq = s->pseq; t.pseq_h = s->pseq_h;
+    t.sigma = static_cast<real *>(s->sigma); t.inst = static_cast<real *>(s->inst);
+    t.reach1 = static_cast<real *>(s->reach1); t.reach2 = static_cast<real *>(s->reach2);
+    t.u = static_cast<real *>(s->u); t.own = static_cast<real *>(s->own);
+    t.R = s->R; t.S = s->S; t.iter = s->d_iter;
+    return t;
+}
+
+// One full-tree iteration, queued on `st` (captured into the solver's graph).
+template <typename real>
+cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st) {
+    DevTree<real> t = dev_tree<real>(s);
+    CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
+    for (int32_t l = 0; l < s->L; ++l) {
+        const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
+        const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
+        const int32_t nb = nblocks(j1 - j0), nh = nblocks(h1 - h0);
+        k_topdown<real><<<nb + nh, kBlock, 0, st>>>(t, j0, j1, nb, h0, h1, l == 0);
+        CK_LAUNCH();
+    }
+    for (int32_t l = s->L - 1; l >= 0; --l) {
+        const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
+        k_bottomup<real><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1);
+        CK_LAUNCH();
+    }
+    const int linear = s->cfg.avg_weight == CFR_AVG_LINEAR;
+    k_update<real><<<nblocks(s->H), kBlock, 0, st>>>(t, s->H, s->cfg.variant == CFR_PLUS, linear);
+    CK_LAUNCH();
+    return CFR_OK;
+}
+
+cfr_status build_graph(cfr_solver *s) {
+    if (s->L == 0) return CFR_OK;
+    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    cfr_status st = s->cfg.precision == CFR_FP64 ? enqueue_iteration<double>(s, s->cap)
+                                                 : enqueue_iteration<float>(s, s->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+    if (st != CFR_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) { s->poisoned = true; return set_err(s, CFR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)); }
+    s->graph = g;
+    CK(cudaGraphInstantiate(&s->graph_exec, g, 0));
+    return CFR_OK;
+}
+
+template <typename real>
+void regret_match_all(cfr_solver *s) {
+    k_regret_match_all<real><<<nblocks(s->H), kBlock, 0, s->stream>>>(static_cast<real *>(s->sigma), s->R, s->qbase,
+                                                                        s->iplayer, s->H);
+}
+
+cfr_status check_usable(cfr_solver *s) {
+    if (!s) return set_err(nullptr, CFR_ERR_INVALID, "solver is NULL");
+    if (s->poisoned) return set_err(s, CFR_ERR_STATE, "solver is unusable after an earlier CUDA error: %s", s->err.c_str());
+    return CFR_OK;
+}
+
+cfr_status load(cfr_solver *s, Layout &Lo) {
+    s->N = Lo.N; s->Nd = Lo.Nd; s->Nt = Lo.Nt; s->Q = Lo.Q; s->H = Lo.H; s->L = Lo.L;
+    s->max_depth = Lo.max_depth; s->max_actions = Lo.max_actions; s->single_level = Lo.single_level;
+    s->dlevel = Lo.dlevel; s->hlevel = Lo.hlevel;
+    s->dnode_user.swap(Lo.dnode_user); s->tnode_user.swap(Lo.tnode_user); s->h_int2user.swap(Lo.h_int2user);
+    const bool fp64 = s->cfg.precision == CFR_FP64;
+    const size_t rs = s->real_size();
+
+    TRY(alloc_n(s, &s->dfirst, s->Nd + 1));
+    TRY(alloc_n(s, &s->tfirst, s->Nd + 1));
+    TRY(alloc_n(s, &s->dinfo, s->Nd));
+    TRY(alloc_n(s, &s->kmask, s->Nd));
+    TRY(alloc_n(s, &s->wbits, (int64_t)Lo.wbits.size()));
+    TRY(alloc_n(s, &s->sigma064, s->Q));
+    TRY(alloc_n(s, &s->util64, s->Nt));
+    if (fp64) s->util = s->util64;
+    else TRY(dev_alloc(s, &s->util, rs * (size_t)std::max<int64_t>(s->Nt, 1)));
+    TRY(alloc_n(s, &s->qbase, (int64_t)s->H + 1));
+    TRY(alloc_n(s, &s->iplayer, s->H));
+    TRY(alloc_n(s, &s->pseq, s->H));
+    TRY(alloc_n(s, &s->pseq_h, s->H));
+    TRY(alloc_n(s, &s->q_int2user, s->Q));
+    TRY(dev_alloc(s, &s->sigma, rs * (size_t)std::max<int64_t>(s->Q, 1)));
+    TRY(dev_alloc(s, &s->inst, rs * (size_t)std::max<int64_t>(s->Q, 1)));
+    TRY(dev_alloc(s, &s->reach1, rs * (size_t)std::max<int64_t>(s->Nd, 1)));
+    TRY(dev_alloc(s, &s->reach2, rs * (size_t)std::max<int64_t>(s->Nd, 1)));
+    TRY(dev_alloc(s, &s->u, rs * (size_t)std::max<int64_t>(s->Nd, 1)));
+    TRY(dev_alloc(s, &s->own, rs * (size_t)std::max<int32_t>(s->H, 1)));
+    TRY(alloc_n(s, &s->R, s->Q));
+    TRY(alloc_n(s, &s->S, s->Q));
+    TRY(alloc_n(s, &s->stage, s->Q));
+    TRY(alloc_n(s, &s->d_iter, 1));
+
+    TRY(upload(s, s->dfirst, Lo.dfirst));
+    TRY(upload(s, s->tfirst, Lo.tfirst));
+    TRY(upload(s, s->dinfo, Lo.dinfo));
+    TRY(upload(s, s->kmask, Lo.kmask));
+    TRY(upload(s, s->wbits, Lo.wbits));
+    TRY(upload(s, s->sigma064, Lo.sigma0));
+    TRY(upload(s, s->util64, Lo.util));
+    std::vector<float> tmpf;
+    if (!fp64) {
+        tmpf.assign(Lo.util.begin(), Lo.util.end());
+        CK(cudaMemcpyAsync(s->util, tmpf.data(), sizeof(float) * tmpf.size(), cudaMemcpyHostToDevice, s->stream));
+    }
+    TRY(upload(s, s->qbase, Lo.qbase));
+    TRY(upload(s, s->iplayer, Lo.iplayer));
+    TRY(upload(s, s->pseq, Lo.pseq));
+    TRY(upload(s, s->pseq_h, Lo.pseq_h));
+    TRY(upload(s, s->q_int2user, Lo.q_int2user));
+    // sigma_0 at chance slots, zero elsewhere; then regret matching of R = 0 gives sigma^(1).
+    if (fp64) {
+        TRY(upload(s, static_cast<double *>(s->sigma), Lo.sigma0));
+    } else {
+        std::vector<float> s0(Lo.sigma0.begin(), Lo.sigma0.end());
+        CK(cudaMemcpyAsync(s->sigma, s0.data(), sizeof(float) * s0.size(), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    CK(cudaMemsetAsync(s->inst, 0, rs * (size_t)std::max<int64_t>(s->Q, 1), s->stream));
+    CK(cudaMemsetAsync(s->R, 0, sizeof(double) * (size_t)std::max<int64_t>(s->Q, 1), s->stream));
+    CK(cudaMemsetAsync(s->S, 0, sizeof(double) * (size_t)std::max<int64_t>(s->Q, 1), s->stream));
+    CK(cudaMemsetAsync(s->own, 0, rs * (size_t)std::max<int32_t>(s->H, 1), s->stream));
+    CK(cudaMemsetAsync(s->u, 0, rs * (size_t)std::max<int64_t>(s->Nd, 1), s->stream));
+    CK(cudaMemsetAsync(s->d_iter, 0, sizeof(int64_t), s->stream));
+    // The root's counterfactual reaches are 1 (Eq. 2, v = v_0) and never change.
+    if (s->Nd > 0) {
+        const double one64 = 1.0;
+        const float one32 = 1.0f;
+        const void *one = fp64 ? (const void *)&one64 : (const void *)&one32;
+        CK(cudaMemcpyAsync(s->reach1, one, rs, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->reach2, one, rs, cudaMemcpyHostToDevice, s->stream));
+    }
+    if (s->H > 0) {
+        if (fp64) regret_match_all<double>(s); else regret_match_all<float>(s);
+        CK_LAUNCH();
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    return build_graph(s);
+}
+
+int64_t bytes_model(const cfr_solver *s) {
+    return s->cfg.precision == CFR_FP64 ? 96 * s->Nd + 8 * s->Nt + 56 * s->Q : 56 * s->Nd + 4 * s->Nt + 44 * s->Q;
+}
+
+template <typename T>
+cfr_status gather_q_to_host(cfr_solver *s, const T *src, double *out) {
+    if (s->Q == 0) return CFR_OK;
+    k_gather_q<T><<<nblocks(s->Q), kBlock, 0, s->stream>>>(src, s->q_int2user, s->stage, (int32_t)s->Q);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(out, s->stage, sizeof(double) * (size_t)s->Q, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CFR_OK;
+}
+
+cfr_status best_response(cfr_solver *s, int player, double *value) {
+    DevBR b;
+    b.dfirst = s->dfirst; b.tfirst = s->tfirst; b.dinfo = s->dinfo;
+    b.kmask = s->kmask; b.wbits = s->wbits;
+    b.util = s->util64; b.qbase = s->qbase; b.iplayer = s->iplayer; b.avg = s->avg;
+    b.preach = s->br_reach; b.val = s->br_val; b.cfv = s->br_cfv; b.astar = s->astar;
+    cudaStream_t st = s->stream;
+    const double one = 1.0;
+    CK(cudaMemcpyAsync(s->br_reach, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(s->br_cfv, 0, sizeof(double) * (size_t)std::max<int64_t>(s->Q, 1), st));
+    for (int32_t l = 0; l + 1 < s->L; ++l) {
+        const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
+        k_br_topdown<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
+        CK_LAUNCH();
+    }
+    for (int32_t l = s->L - 1; l >= 0; --l) {
+        const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
+        const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
+        k_br_nodes<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
+        CK_LAUNCH();
+        if (h1 > h0) {
+            k_br_choose<<<nblocks(h1 - h0), kBlock, 0, st>>>(b, h0, h1, player);
+            CK_LAUNCH();
+        }
+        k_br_pick<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
+        CK_LAUNCH();
+    }
+    CK(cudaMemcpyAsync(value, s->br_val, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return CFR_OK;
+}
+
+}  // namespace
+
+// ================================================================================================
+extern "C" {
+
+void cfr_config_init(cfr_config *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->variant = CFR_VANILLA;
+    c->precision = CFR_FP32;
+    c->update_mode = CFR_SIMULTANEOUS;
+    c->avg_weight = CFR_AVG_DEFAULT;
+    c->device = -1;
+}
+
+cfr_status cfr_validate(const cfr_game_desc *g, char *msg, size_t msg_len) {
+    std::string err;
+    cfr_status st = build_layout(g, nullptr, &err);
+    if (st != CFR_OK) g_thread_err = err;
+    if (msg && msg_len > 0) std::snprintf(msg, msg_len, "%s", st == CFR_OK ? "" : err.c_str());
+    return st;
+}
+
+cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver **out) {
+    if (!out) return set_err(nullptr, CFR_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    cfr_config cfg;
+    if (c) cfg = *c; else cfr_config_init(&cfg);
+    if (cfg.variant != CFR_VANILLA && cfg.variant != CFR_PLUS)
+        return set_err(nullptr, CFR_ERR_INVALID, "variant %d unknown", cfg.variant);
+    if (cfg.precision != CFR_FP32 && cfg.precision != CFR_FP64)
+        return set_err(nullptr, CFR_ERR_INVALID, "precision %d unknown", cfg.precision);
+    if (cfg.update_mode != CFR_SIMULTANEOUS && cfg.update_mode != CFR_ALTERNATING)
+        return set_err(nullptr, CFR_ERR_INVALID, "update_mode %d unknown", cfg.update_mode);
+    if (cfg.update_mode == CFR_ALTERNATING)
+        return set_err(nullptr, CFR_ERR_UNSUPPORTED, "alternating updates are not implemented on the GPU");
+    if (cfg.avg_weight == CFR_AVG_DEFAULT) cfg.avg_weight = cfg.variant == CFR_PLUS ? CFR_AVG_LINEAR : CFR_AVG_UNIFORM;
+    if (cfg.avg_weight != CFR_AVG_UNIFORM && cfg.avg_weight != CFR_AVG_LINEAR)
+        return set_err(nullptr, CFR_ERR_INVALID, "avg_weight %d unknown", cfg.avg_weight);
+    if ((cfg.dev_alloc == nullptr) != (cfg.dev_free == nullptr))
+        return set_err(nullptr, CFR_ERR_INVALID, "dev_alloc and dev_free must both be set or both NULL");
+
+    std::unique_ptr<Layout> Lo(new Layout());
+    std::string err;
+    cfr_status st = build_layout(g, Lo.get(), &err);
+    if (st != CFR_OK) return set_err(nullptr, st, "%s", err.c_str());
+
+    DeviceGuard dg(cfg.device);
+    if (!dg.ok) return set_err(nullptr, CFR_ERR_CUDA, "cannot select CUDA device %d", cfg.device);
+    std::unique_ptr<cfr_solver> s(new cfr_solver());
+    s->cfg = cfg;
+    cudaGetDevice(&s->device);
+    s->stream = static_cast<cudaStream_t>(cfg.cuda_stream);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(nullptr, CFR_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    st = load(s.get(), *Lo);
+    if (st != CFR_OK) {
+        std::string msg = s->err;
+        cfr_free(s.release());
+        return set_err(nullptr, st, "%s", msg.c_str());
+    }
+    *out = s.release();
+    return CFR_OK;
+}
+
+cfr_status cfr_iterate(cfr_solver *s, int32_t n) {
+    TRY(check_usable(s));
+    if (n < 0) return set_err(s, CFR_ERR_INVALID, "n must be >= 0");
+    DeviceGuard dg(s->device);
+    for (int32_t i = 0; i < n && s->graph_exec; ++i) CK(cudaGraphLaunch(s->graph_exec, s->stream));
+    s->iteration += n;
+    return CFR_OK;
+}
+
+cfr_status cfr_synchronize(cfr_solver *s) {
+    TRY(check_usable(s));
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    return CFR_OK;
+}
+
+cfr_status cfr_average_strategy(cfr_solver *s, double *out, int64_t len) {
+    TRY(check_usable(s));
+    if (!out || len < s->Q) return set_err(s, CFR_ERR_INVALID, "output needs %lld entries", (long long)s->Q);
+    DeviceGuard dg(s->device);
+    if (!s->avg) TRY(alloc_n(s, &s->avg, s->Q));
+    if (s->H > 0) {
+        k_average<<<nblocks(s->H), kBlock, 0, s->stream>>>(s->S, s->sigma064, s->qbase, s->iplayer, s->avg, s->H);
+        CK_LAUNCH();
+    }
+    return gather_q_to_host(s, s->avg, out);
+}
+
+cfr_status cfr_current_strategy(cfr_solver *s, double *out, int64_t len) {
+    TRY(check_usable(s));
+    if (!out || len < s->Q) return set_err(s, CFR_ERR_INVALID, "output needs %lld entries", (long long)s->Q);
+    DeviceGuard dg(s->device);
+    if (s->cfg.precision == CFR_FP64) return gather_q_to_host(s, static_cast<double *>(s->sigma), out);
+    return gather_q_to_host(s, static_cast<float *>(s->sigma), out);
+}
+
+cfr_status cfr_exploitability(cfr_solver *s, double *nash_conv, double *exploitability) {
+    TRY(check_usable(s));
+    if (!s->single_level)
+        return set_err(s, CFR_ERR_UNSUPPORTED, "the GPU best response needs every infoset at a single depth");
+    DeviceGuard dg(s->device);
+    double nc = 0.0;
+    if (s->Nd > 0) {
+        if (!s->avg) TRY(alloc_n(s, &s->avg, s->Q));
+        if (!s->br_reach) {
+            TRY(alloc_n(s, &s->br_reach, s->Nd));
+            TRY(alloc_n(s, &s->br_val, s->Nd));
+            TRY(alloc_n(s, &s->br_cfv, s->Q));
+            TRY(alloc_n(s, &s->astar, s->H));
+        }
+        k_average<<<nblocks(s->H), kBlock, 0, s->stream>>>(s->S, s->sigma064, s->qbase, s->iplayer, s->avg, s->H);
+        CK_LAUNCH();
+        for (int p = 1; p <= 2; ++p) {
+            double v = 0.0;
+            TRY(best_response(s, p, &v));
+            nc += v;   // zero-sum: u_1(avg) + u_2(avg) = 0
+        }
+    }
+    if (nash_conv) *nash_conv = nc;
+    if (exploitability) *exploitability = nc / 2.0;
+    return CFR_OK;
+}
+
+cfr_status cfr_get_state(cfr_solver *s, double *cum_regret, double *strat_sum, double *inst_regret, int64_t len_q,
+                         double *own_reach, int64_t len_h, int64_t *iteration) {
+    TRY(check_usable(s));
+    if ((cum_regret || strat_sum || inst_regret) && len_q < s->Q)
+        return set_err(s, CFR_ERR_INVALID, "Q buffers need %lld entries", (long long)s->Q);
+    if (own_reach && len_h < s->H) return set_err(s, CFR_ERR_INVALID, "own_reach needs %d entries", s->H);
+    DeviceGuard dg(s->device);
+    if (cum_regret) TRY(gather_q_to_host(s, s->R, cum_regret));
+    if (strat_sum) TRY(gather_q_to_host(s, s->S, strat_sum));
+    if (inst_regret) {
+        if (s->cfg.precision == CFR_FP64) TRY(gather_q_to_host(s, static_cast<double *>(s->inst), inst_regret));
+        else TRY(gather_q_to_host(s, static_cast<float *>(s->inst), inst_regret));
+    }
+    if (own_reach && s->H > 0) {
+        std::vector<double> tmp((size_t)s->H);
+        if (s->cfg.precision == CFR_FP64) {
+            CK(cudaMemcpy(tmp.data(), s->own, sizeof(double) * s->H, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f((size_t)s->H);
+            CK(cudaStreamSynchronize(s->stream));
+            CK(cudaMemcpy(f.data(), s->own, sizeof(float) * s->H, cudaMemcpyDeviceToHost));
+            for (int32_t h = 0; h < s->H; ++h) tmp[h] = f[h];
+        }
+        for (int32_t h = 0; h < s->H; ++h) own_reach[s->h_int2user[h]] = tmp[h];
+    }
+    if (iteration) *iteration = s->iteration;
+    return CFR_OK;
+}
+
+cfr_status cfr_set_state(cfr_solver *s, const double *cum_regret, const double *strat_sum, int64_t len_q,
+                         int64_t iteration) {
+    TRY(check_usable(s));
+    if (!cum_regret || !strat_sum || len_q != s->Q)
+        return set_err(s, CFR_ERR_INVALID, "cum_regret and strat_sum need exactly %lld entries", (long long)s->Q);
+    if (iteration < 0) return set_err(s, CFR_ERR_INVALID, "iteration must be >= 0");
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    if (s->Q > 0) {
+        CK(cudaMemcpy(s->stage, cum_regret, sizeof(double) * s->Q, cudaMemcpyHostToDevice));
+        k_scatter_player_q<<<nblocks(s->H), kBlock, 0, s->stream>>>(s->stage, s->q_int2user, s->qbase, s->iplayer, s->R, s->H);
+        CK_LAUNCH();
+        CK(cudaStreamSynchronize(s->stream));
+        CK(cudaMemcpy(s->stage, strat_sum, sizeof(double) * s->Q, cudaMemcpyHostToDevice));
+        k_scatter_player_q<<<nblocks(s->H), kBlock, 0, s->stream>>>(s->stage, s->q_int2user, s->qbase, s->iplayer, s->S, s->H);
+        CK_LAUNCH();
+        if (s->cfg.precision == CFR_FP64) regret_match_all<double>(s); else regret_match_all<float>(s);
+        CK_LAUNCH();
+    }
+    CK(cudaMemcpyAsync(s->d_iter, &iteration, sizeof(int64_t), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->iteration = iteration;
+    return CFR_OK;
+}
+
+cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *cf_reach2, int64_t len) {
+    TRY(check_usable(s));
+    if ((u1 || cf_reach1 || cf_reach2) && len < s->N)
+        return set_err(s, CFR_ERR_INVALID, "node buffers need %lld entries", (long long)s->N);
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    const bool fp64 = s->cfg.precision == CFR_FP64;
+    auto fetch = [&](const void *src, int64_t n, std::vector<double> &dst) -> cfr_status {
+        dst.assign((size_t)n, 0.0);
+        if (n == 0) return CFR_OK;
+        if (fp64) {
+            CK(cudaMemcpy(dst.data(), src, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f((size_t)n);
+            CK(cudaMemcpy(f.data(), src, sizeof(float) * n, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < n; ++i) dst[i] = f[i];
+        }
+        return CFR_OK;
+    };
+    std::vector<double> tmp;
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    if (u1) {
+        TRY(fetch(s->u, s->Nd, tmp));
+        for (int64_t j = 0; j < s->Nd; ++j) u1[s->dnode_user[j]] = tmp[j];
+        tmp.assign((size_t)s->Nt, 0.0);
+        if (s->Nt > 0) CK(cudaMemcpy(tmp.data(), s->util64, sizeof(double) * s->Nt, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < s->Nt; ++k) u1[s->tnode_user[k]] = tmp[k];
+    }
+    double *outs[2] = {cf_reach1, cf_reach2};
+    void *srcs[2] = {s->reach1, s->reach2};
+    for (int i = 0; i < 2; ++i) {
+        if (!outs[i]) continue;
+        TRY(fetch(srcs[i], s->Nd, tmp));
+        for (int64_t j = 0; j < s->Nd; ++j) outs[i][s->dnode_user[j]] = tmp[j];
+        for (int64_t k = 0; k < s->Nt; ++k) outs[i][s->tnode_user[k]] = nan;
+    }
+    return CFR_OK;
+}
+
+cfr_status cfr_root_value(cfr_solver *s, double *u1) {
+    TRY(check_usable(s));
+    if (!u1) return set_err(s, CFR_ERR_INVALID, "u1 is NULL");
+    DeviceGuard dg(s->device);
+    if (s->Nd == 0) {
+        CK(cudaMemcpy(u1, s->util64, sizeof(double), cudaMemcpyDeviceToHost));
+        return CFR_OK;
+    }
+    if (s->cfg.precision == CFR_FP64) {
+        CK(cudaMemcpyAsync(u1, s->u, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    } else {
+        float f = 0.0f;
+        CK(cudaMemcpyAsync(&f, s->u, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        *u1 = f;
+    }
+    return CFR_OK;
+}
+
+cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info) {
+    if (!s || !info) return set_err(nullptr, CFR_ERR_INVALID, "solver or info is NULL");
+    std::memset(info, 0, sizeof *info);
+    info->num_nodes = s->N; info->num_decision = s->Nd; info->num_terminal = s->Nt; info->num_q = s->Q;
+    info->num_infosets = s->H; info->num_levels = s->L; info->max_depth = s->max_depth;
+    info->max_actions = s->max_actions; info->single_level_infosets = s->single_level;
+    info->variant = s->cfg.variant; info->precision = s->cfg.precision; info->update_mode = s->cfg.update_mode;
+    info->avg_weight = s->cfg.avg_weight; info->iteration = s->iteration; info->device_bytes = s->device_bytes;
+    info->bytes_per_iteration = bytes_model(s);
+    info->kernels_per_iteration = s->L > 0 ? 2 * s->L + 1 : 0;
+    return CFR_OK;
+}
+
+const char *cfr_last_error(const cfr_solver *s) { return s ? s->err.c_str() : g_thread_err.c_str(); }
+
+void cfr_free(cfr_solver *s) {
+    if (!s) return;
+    DeviceGuard dg(s->device);
+    if (s->stream || s->cap) cudaStreamSynchronize(s->stream);
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    for (auto &b : s->blocks) {
+        if (s->cfg.dev_free) s->cfg.dev_free(b.first, s->cfg.alloc_ctx);
+        else cudaFree(b.first);
+    }
+    if (s->cap) cudaStreamDestroy(s->cap);
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Tolerances (normwise: max_i |x_i - y_i| / max_i |y_i|, per array):
+  FP64 mode 1e-12, FP32 mode 1e-5, exploitability 1e-6 absolute.
+"""
+import numpy as np
+import pytest
+
+import gamegen
+import oracle
+import paper_2408_14778_gb300 as cfr
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32, TOL_EXPL = 1e-12, 1e-5, 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    cfr.build()
+
+
+def normwise(x, y):
+    x, y = np.asarray(x, float), np.asarray(y, float)
+    if y.size == 0:
+        return 0.0
+    return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-30))
+
+
+def player_mask(g):
+    qb = np.concatenate([[0], np.cumsum(g.infoset_num_actions)])
+    m = np.zeros(qb[-1], bool)
+    for h in range(g.num_infosets):
+        if g.infoset_player[h] != 0:
+            m[qb[h]:qb[h + 1]] = True
+    return m
+
+
+def compare_state(s, o, tol, g, what=("cum_regret", "strat_sum", "inst_regret")):
+    gs, os_ = cfr.cfr_get_state(s), o.state()
+    for k in what:
+        e = normwise(gs[k], os_[k])
+        assert e <= tol, f"{k}: normwise error {e:.3e} > {tol:.0e}"
+    e = normwise(cfr.cfr_current_strategy(s), os_["sigma"])
+    assert e <= tol, f"sigma: normwise error {e:.3e}"
+    assert gs["iteration"] == os_["iteration"]
+
+
+def compare_nodes(s, o, tol, g):
+    gn, on = cfr.cfr_get_nodes(s), o.nodes()
+    dec = g.infoset >= 0
+    assert normwise(gn["u1"], on["u1"]) <= tol
+    cf1 = on["r_c"] * on["r_2"]
+    cf2 = on["r_c"] * on["r_1"]
+    assert normwise(gn["cf_reach1"][dec], cf1[dec]) <= tol
+    assert normwise(gn["cf_reach2"][dec], cf2[dec]) <= tol
+    assert np.all(np.isnan(gn["cf_reach1"][~dec]))
+
+
+def small_games():
+    games = [gamegen.config("bucket3_depth6", seed=1),
+             gamegen.public_private(seed=11, num_buckets=3, depth=6, amin=1, amax=4, p_cont=0.7, p_chance=0.3),
+             gamegen.public_private(seed=12, num_buckets=4, depth=7, amin=2, amax=3, p_cont=0.6, p_chance=0.2,
+                                    payoff_kind=gamegen.PAY_FOLD_SHOWDOWN, first_actor=2),
+             gamegen.matrix_game([[0, -1, 1], [1, 0, -1], [-1, 1, 0]]),
+             gamegen.matrix_game(np.arange(12.0).reshape(3, 4) - 5)]
+    games.append(gamegen.permute_nodes(games[1], seed=99))
+    return games
+
+
+@pytest.mark.parametrize("variant", [cfr.CFR_VANILLA, cfr.CFR_PLUS])
+def test_step_by_step_fp64(variant):
+    for g in small_games():
+        o = oracle.Oracle(g, record=True)
+        s = cfr.cfr_load_tree(g, variant=variant, precision=cfr.CFR_FP64)
+        for _ in range(5):
+            o.iterate(1, variant=variant, avg=variant)
+            cfr.cfr_iterate(s, 1)
+            compare_state(s, o, TOL64, g)
+            compare_nodes(s, o, TOL64, g)
+            np.testing.assert_allclose(cfr.cfr_get_state(s)["own_reach"][g.infoset_player > 0],
+                                       o.state()["own_reach"][g.infoset_player > 0], atol=1e-15)
+        s.close()
+
+
+def test_trajectory_fp64_vanilla_1000_iterations():
+    # bucket3_depth6: 6-way deal of 3 buckets, depth 6, |A| in {2,3}; vanilla CFR in FP64.
+    g = gamegen.config("bucket3_depth6", seed=1)
+    o = oracle.Oracle(g)
+    s = cfr.cfr_load_tree(g, variant=cfr.CFR_VANILLA, precision=cfr.CFR_FP64)
+    done = 0
+    for T in (1, 10, 100, 1000):
+        o.iterate(T - done)
+        cfr.cfr_iterate(s, T - done)
+        done = T
+        compare_state(s, o, TOL64, g)
+        assert normwise(cfr.cfr_average_strategy(s), o.average_strategy()) <= TOL64
+        nc_g, ex_g = cfr.cfr_exploitability(s)
+        nc_o, ex_o = o.exploitability()
+        assert abs(nc_g - nc_o) <= TOL_EXPL and abs(ex_g - ex_o) <= TOL_EXPL
+
+
+def test_trajectory_fp64_cfr_plus():
+    for g in small_games()[:3]:
+        o = oracle.Oracle(g)
+        s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP64)
+        o.iterate(300, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+        cfr.cfr_iterate(s, 300)
+        compare_state(s, o, TOL64, g)
+        assert normwise(cfr.cfr_average_strategy(s), o.average_strategy()) <= TOL64
+        assert abs(cfr.cfr_exploitability(s)[0] - o.exploitability()[0]) <= TOL_EXPL
+
+
+@pytest.mark.parametrize("variant", [cfr.CFR_VANILLA, cfr.CFR_PLUS])
+def test_one_iteration_fp32(variant):
+    for g in small_games():
+        o = oracle.Oracle(g, record=True)
+        s = cfr.cfr_load_tree(g, variant=variant, precision=cfr.CFR_FP32)
+        o.iterate(1, variant=variant, avg=variant)
+        cfr.cfr_iterate(s, 1)
+        compare_state(s, o, TOL32, g)
+        compare_nodes(s, o, TOL32, g)
+
+
+def _step_parity(g, variant, Ts, precision, tol, nodes=False):
+    o = oracle.Oracle(g, record=nodes)
+    s = cfr.cfr_load_tree(g, variant=variant, precision=precision)
+    done = 0
+    for T in Ts:
+        o.iterate(T - 1 - done, variant=variant, avg=variant)
+        done = T - 1
+        st = o.state()
+        cfr.cfr_set_state(s, st["cum_regret"], st["strat_sum"], st["iteration"])
+        assert normwise(cfr.cfr_current_strategy(s), st["sigma"]) <= (TOL64 if precision == cfr.CFR_FP64 else 1e-7)
+        o.iterate(1, variant=variant, avg=variant)
+        done += 1
+        cfr.cfr_iterate(s, 1)
+        compare_state(s, o, tol, g)
+        if nodes:
+            compare_nodes(s, o, tol, g)
+    return s, o
+
+
+def test_step_parity_fp32_rank13_depth10():
+    # ~2e6 nodes, 156-way deal, fold/showdown payoffs, CFR+ (the per-iteration tolerance 1e-5 is
+    # checked from the oracle's FP64 state at T = 1, 2, 10, 100 - step parity).
+    g = gamegen.config("rank13_depth10", seed=1)
+    s, o = _step_parity(g, cfr.CFR_PLUS, (1, 2, 10, 100), cfr.CFR_FP32, TOL32)
+    assert abs(cfr.cfr_exploitability(s)[0] - o.exploitability()[0]) <= TOL_EXPL
+
+
+def test_step_parity_fp64_rank13_depth10():
+    g = gamegen.config("rank13_depth10", seed=2)
+    s, o = _step_parity(g, cfr.CFR_VANILLA, (1, 5), cfr.CFR_FP64, TOL64, nodes=True)
+    assert abs(cfr.cfr_exploitability(s)[0] - o.exploitability()[0]) <= TOL_EXPL
+
+
+def test_fp32_trajectory_stays_close_rank13():
+    g = gamegen.config("rank13_depth10", seed=3)
+    o = oracle.Oracle(g)
+    s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32)
+    o.iterate(20, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+    cfr.cfr_iterate(s, 20)
+    assert normwise(cfr.cfr_average_strategy(s), o.average_strategy()) <= 1e-4
+    assert abs(cfr.cfr_exploitability(s)[0] - o.exploitability()[0]) <= 1e-4
+
+
+# ---- edge cases ---------------------------------------------------------------------------------
+
+def test_terminal_root():
+    g = gamegen.GameDesc(np.array([-1], np.int32), np.array([-1], np.int32), np.array([-1], np.int32),
+                         np.zeros(0, np.int8), np.zeros(0, np.int32), np.zeros(0), np.array([[2.0, -2.0]]))
+    s = cfr.cfr_load_tree(g, precision=cfr.CFR_FP64)
+    cfr.cfr_iterate(s, 3)
+    assert cfr.cfr_exploitability(s) == (0.0, 0.0)
+    assert cfr.cfr_get_nodes(s)["u1"][0] == 2.0
+    assert cfr.cfr_get_info(s)["iteration"] == 3
+
+
+def test_chance_only_tree():
+    parent = np.array([-1, 0, 0, 0, 1, 1], np.int32)
+    action = np.array([-1, 0, 1, 2, 0, 1], np.int32)
+    infoset = np.array([0, 1, -1, -1, -1, -1], np.int32)
+    util = np.zeros((6, 2))
+    util[:, 0] = [0, 0, 1.0, -3.0, 2.0, 5.0]
+    util[:, 1] = -util[:, 0]
+    g = gamegen.GameDesc(parent, action, infoset, np.array([0, 0], np.int8), np.array([3, 2], np.int32),
+                         np.array([0.5, 0.25, 0.25, 0.1, 0.9]), util)
+    s = cfr.cfr_load_tree(g, precision=cfr.CFR_FP64)
+    o = oracle.Oracle(g, record=True)
+    o.iterate(2)
+    cfr.cfr_iterate(s, 2)
+    compare_nodes(s, o, TOL64, g)
+    assert cfr.cfr_exploitability(s)[0] == pytest.approx(0.0, abs=1e-15)
+
+
+@pytest.mark.parametrize("m,n", [(1, 3), (33, 2), (64, 3), (5, 64), (200, 3), (3, 1326)])
+def test_wide_and_single_action_infosets(m, n):
+    rng = np.random.default_rng(m * 100 + n)
+    g = gamegen.matrix_game(rng.normal(size=(m, n)))
+    for precision, tol in ((cfr.CFR_FP64, TOL64), (cfr.CFR_FP32, TOL32)):
+        o = oracle.Oracle(g, record=True)
+        s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=precision)
+        o.iterate(7, variant=1, avg=1)
+        cfr.cfr_iterate(s, 7)
+        compare_state(s, o, tol, g)
+        compare_nodes(s, o, tol, g)
+
+
+def test_zero_probability_branch():
+    g = gamegen.public_private(seed=21, num_buckets=3, depth=5, amin=2, amax=3, p_cont=0.8, p_chance=0.4)
+    cp = g.chance_prob.copy()
+    cp[:6] = [0.5, 0.5, 0.0, 0.0, 0.0, 0.0]                  # four of six deals never happen
+    g = gamegen.GameDesc(g.parent, g.action, g.infoset, g.infoset_player, g.infoset_num_actions, cp, g.utility)
+    o = oracle.Oracle(g, record=True)
+    s = cfr.cfr_load_tree(g, precision=cfr.CFR_FP64)
+    o.iterate(10)
+    cfr.cfr_iterate(s, 10)
+    compare_state(s, o, TOL64, g)
+    compare_nodes(s, o, TOL64, g)
+    assert abs(cfr.cfr_exploitability(s)[0] - o.exploitability()[0]) <= TOL_EXPL
+
+
+def test_multilevel_infoset_iterates_but_br_is_unsupported():
+    from test_oracle_pins import multilevel_game
+
+    g = multilevel_game()
+    o = oracle.Oracle(g, record=True)
+    s = cfr.cfr_load_tree(g, precision=cfr.CFR_FP64)
+    assert cfr.cfr_get_info(s)["single_level_infosets"] == 0
+    for _ in range(4):
+        o.iterate(1)
+        cfr.cfr_iterate(s, 1)
+        compare_state(s, o, TOL64, g)
+        compare_nodes(s, o, TOL64, g)
+    with pytest.raises(cfr.CfrError) as e:
+        cfr.cfr_exploitability(s)
+    assert e.value.status == cfr.CFR_ERR_UNSUPPORTED
+
+
+def test_state_roundtrip_and_cuda_allocator():
+    g = gamegen.config("bucket3_depth6", seed=4)
+    a = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP64)
+    cfr.cfr_iterate(a, 17)
+    st = cfr.cfr_get_state(a)
+    b = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP64, allocator="cuda")
+    cfr.cfr_set_state(b, st["cum_regret"], st["strat_sum"], st["iteration"])
+    np.testing.assert_array_equal(cfr.cfr_current_strategy(a), cfr.cfr_current_strategy(b))
+    cfr.cfr_iterate(a, 5)
+    cfr.cfr_iterate(b, 5)
+    assert normwise(cfr.cfr_get_state(b)["cum_regret"], cfr.cfr_get_state(a)["cum_regret"]) <= TOL64
+    assert cfr.cfr_get_info(b)["iteration"] == 22
+    mask = player_mask(g)
+    assert np.all(cfr.cfr_get_state(b)["cum_regret"][~mask] == 0)
+
+
+def test_bad_arguments_raise():
+    g = gamegen.config("bucket3_depth6", seed=4)
+    s = cfr.cfr_load_tree(g)
+    with pytest.raises(cfr.CfrError):
+        cfr.cfr_set_state(s, np.zeros(3), np.zeros(3), 0)
+    with pytest.raises(cfr.CfrError):
+        cfr.cfr_iterate(s, -1)
+    L = cfr.lib()
+    buf = np.zeros(2)
+    assert L.cfr_average_strategy(s.handle, buf.ctypes.data, 2) == cfr.CFR_ERR_INVALID
+    cfr.cfr_iterate(s, 2)                                     # still usable after argument errors
+    cfr.cfr_synchronize(s)
