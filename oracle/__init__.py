@@ -58,6 +58,7 @@ def _lib():
         lib.orc_set_state.argtypes = [_P, _P, _P, ctypes.c_int64]
         lib.orc_get_nodes.restype = ctypes.c_int32
         lib.orc_get_nodes.argtypes = [_P, _P]
+        lib.orc_get_cf_reach_sum.argtypes = [_P, _P]
         lib.orc_recall_violations.restype = ctypes.c_int64
         lib.orc_recall_violations.argtypes = [_P]
         lib.orc_average_strategy.argtypes = [_P, _P]
@@ -120,9 +121,11 @@ class Oracle:
         T = ctypes.c_int64()
         _lib().orc_get_state(self._h, R.ctypes.data, S.ctypes.data, inst.ctypes.data, sig.ctypes.data,
                              own.ctypes.data, ctypes.byref(T))
+        cfs = np.zeros(H)
+        _lib().orc_get_cf_reach_sum(self._h, cfs.ctypes.data)
         q, h = self.num_q, self.num_infosets
         return dict(cum_regret=R[:q], strat_sum=S[:q], inst_regret=inst[:q], sigma=sig[:q], own_reach=own[:h],
-                    iteration=int(T.value))
+                    cf_reach_sum=cfs[:h], iteration=int(T.value))
 
     def set_state(self, cum_regret, strat_sum, iteration: int):
         R = _c(cum_regret, np.float64)
@@ -131,11 +134,12 @@ class Oracle:
         _lib().orc_set_state(self._h, R.ctypes.data, S.ctypes.data, int(iteration))
 
     def nodes(self) -> dict:
-        """Per node of the last pass (needs record=True): u1, u2, r_c, r_1, r_2."""
-        out = np.zeros((self.num_nodes, 5))
+        """Per node of the last pass (needs record=True): node payoffs u1, u2 (Eq. 1), counterfactual
+        reaches cf1, cf2 (Eq. 2) and own reaches own1, own2 (Eq. 4)."""
+        out = np.zeros((self.num_nodes, 6))
         if _lib().orc_get_nodes(self._h, out.ctypes.data) != 0:
             raise RuntimeError("oracle was created without record=True")
-        return dict(u1=out[:, 0], u2=out[:, 1], r_c=out[:, 2], r_1=out[:, 3], r_2=out[:, 4])
+        return dict(u1=out[:, 0], u2=out[:, 1], cf1=out[:, 2], cf2=out[:, 3], own1=out[:, 4], own2=out[:, 5])
 
     def recall_violations(self) -> int:
         return int(_lib().orc_recall_violations(self._h))

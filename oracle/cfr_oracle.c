@@ -9,15 +9,16 @@
  * shares no source, header, table or helper with the CUDA path.
  *
  * What it computes, per iteration T with strategy sigma^T (Section 2.3):
- *   walk(v, r_c, r_1, r_2) returns the node payoffs (u_1(v), u_2(v)) of Eq. 1:
+ *   walk(v, ...) returns the node payoffs (u_1(v), u_2(v)) of Eq. 1:
  *     terminal:  u(v, .)
- *     otherwise: sum_a sigma(h, a) * walk(child_a, ...), where the reach factor of
- *                the acting player (chance, 1 or 2) is multiplied by sigma(h, a).
- *   At a node d of player p in infoset h, with counterfactual reach
- *   pi_-p = r_c * r_opp (Eq. 2) the instantaneous regret of Eq. 7 collects
- *     inst(h, a) += pi_-p * (u_p(child_a) - u_p(d))
+ *     otherwise: sum_a sigma(h, a) * walk(child_a, ...), summed in action order.
+ *   It carries the counterfactual reaches pi-check(v, 1), pi-check(v, 2) by the recursion of
+ *   Eq. 2 and the own reaches pi-hat(v, 1), pi-hat(v, 2) by the recursion of Eq. 4 (read as the
+ *   product of the player's own factors; the printed Eq. 4 recurses on pi-check, a garble).
+ *   At a node d of player p in infoset h the instantaneous regret of Eq. 7 collects
+ *     inst(h, a) += pi-check(d, p) * (u_p(child_a) - u_p(d))
  *   which, summed over the nodes of h, is pi~(h) * (u~(sigma|h->a, h) - u~(sigma, h))
- *   by Eq. 3 and Eq. 6.  The own reach r_p (Eq. 4) of the infoset is recorded.
+ *   by Eq. 3 and Eq. 6.  The own reach of the infoset is recorded.
  * End of the iteration:
  *   regrets   R += inst (vanilla; R = T * rbar of Eq. 8)     or R = max(R + inst, 0) (CFR+)
  *   averages  S += w_T * pi_p(h) * sigma^T  (numerator of Eq. 10; w_T = 1, or T for linear averaging)
@@ -55,10 +56,10 @@ typedef struct {
     int32_t *hnode;
     double *util;      /* n x 2 */
     double *sigma0;    /* Q, chance slots only */
-    double *sigma, *R, *S, *inst, *own;
+    double *sigma, *R, *S, *inst, *own, *cfsum;   /* cfsum: pi~(h) of Eq. 3 in the last pass */
     int64_t T;
     int record;
-    double *rec;       /* n x 5: u1, u2, r_c, r_1, r_2 of the last pass */
+    double *rec;       /* n x 6: u1, u2, pi-check 1, pi-check 2, pi-hat 1, pi-hat 2 of the last pass */
     int64_t recall_violations;
     uint8_t *own_seen;
     /* best-response scratch */
@@ -72,7 +73,7 @@ static void orc_free_all(orc *o) {
     if (!o) return;
     free(o->cstart); free(o->child); free(o->infoset); free(o->player); free(o->nact); free(o->qbase);
     free(o->hstart); free(o->hnode); free(o->util); free(o->sigma0); free(o->sigma); free(o->R); free(o->S);
-    free(o->inst); free(o->own); free(o->rec); free(o->own_seen); free(o->preach); free(o->V); free(o->astar);
+    free(o->inst); free(o->own); free(o->cfsum); free(o->rec); free(o->own_seen); free(o->preach); free(o->V); free(o->astar);
     free(o);
 }
 
@@ -141,8 +142,8 @@ orc *orc_create(int64_t n, const int32_t *parent, const int32_t *action, const i
     int64_t Q = o->Q > 0 ? o->Q : 1;
     o->sigma0 = calloc(Q, sizeof(double)); o->sigma = calloc(Q, sizeof(double));
     o->R = calloc(Q, sizeof(double)); o->S = calloc(Q, sizeof(double)); o->inst = calloc(Q, sizeof(double));
-    o->own = calloc(H + 1, sizeof(double)); o->own_seen = calloc(H + 1, 1);
-    if (!o->sigma0 || !o->sigma || !o->R || !o->S || !o->inst || !o->own || !o->own_seen) goto bad;
+    o->own = calloc(H + 1, sizeof(double)); o->own_seen = calloc(H + 1, 1); o->cfsum = calloc(H + 1, sizeof(double));
+    if (!o->sigma0 || !o->sigma || !o->R || !o->S || !o->inst || !o->own || !o->own_seen || !o->cfsum) goto bad;
     int64_t c = 0;
     for (int32_t h = 0; h < H; ++h) {
         if (player[h] == 0)
@@ -163,14 +164,18 @@ int32_t orc_root(const orc *o) { return o->root; }
 
 void orc_set_record(orc *o, int32_t on) {
     o->record = on;
-    if (on && !o->rec) o->rec = calloc((size_t)o->n * 5, sizeof(double));
+    if (on && !o->rec) o->rec = calloc((size_t)o->n * 6, sizeof(double));
 }
 
-/* One recursive pass; players whose bit is set in `mask` collect regrets and own reach. */
-static void walk(orc *o, int32_t v, double rc, double r1, double r2, int mask, double out[2]) {
+/* One recursive pass; players whose bit is set in `mask` collect regrets and own reach.
+ * cf1, cf2: counterfactual reaches pi-check(v, 1), pi-check(v, 2) of Eq. 2, formed by its
+ * recursion (the parent's value times sigma of the edge unless that player acted there);
+ * own1, own2: own reaches pi-hat(v, 1), pi-hat(v, 2) of Eq. 4 (the parent's value times sigma of
+ * the edge when that player acted there). */
+static void walk(orc *o, int32_t v, double cf1, double cf2, double own1, double own2, int mask, double out[2]) {
     if (o->record) {
-        double *r = o->rec + (size_t)v * 5;
-        r[2] = rc; r[3] = r1; r[4] = r2;
+        double *r = o->rec + (size_t)v * 6;
+        r[2] = cf1; r[3] = cf2; r[4] = own1; r[5] = own2;
     }
     int32_t h = o->infoset[v];
     if (h < 0) {
@@ -184,16 +189,17 @@ static void walk(orc *o, int32_t v, double rc, double r1, double r2, int mask, d
         for (int32_t a = 0; a < na; ++a) {
             double s = o->sigma[qb + a];
             int32_t c = o->child[o->cstart[v] + a];
-            if (p == 0) walk(o, c, rc * s, r1, r2, mask, ua + 2 * a);
-            else if (p == 1) walk(o, c, rc, r1 * s, r2, mask, ua + 2 * a);
-            else walk(o, c, rc, r1, r2 * s, mask, ua + 2 * a);
+            if (p == 0) walk(o, c, cf1 * s, cf2 * s, own1, own2, mask, ua + 2 * a);
+            else if (p == 1) walk(o, c, cf1, cf2 * s, own1 * s, own2, mask, ua + 2 * a);
+            else walk(o, c, cf1 * s, cf2, own1, own2 * s, mask, ua + 2 * a);
             u[0] += s * ua[2 * a];
             u[1] += s * ua[2 * a + 1];
         }
         if (p > 0 && (mask & (1 << p))) {
-            double cf = p == 1 ? rc * r2 : rc * r1;
+            double cf = p == 1 ? cf1 : cf2;
             for (int32_t a = 0; a < na; ++a) o->inst[qb + a] += cf * (ua[2 * a + p - 1] - u[p - 1]);
-            double mine = p == 1 ? r1 : r2;
+            o->cfsum[h] += cf;
+            double mine = p == 1 ? own1 : own2;
             if (o->own_seen[h] && fabs(o->own[h] - mine) > 1e-12 * (fabs(mine) + 1e-300)) o->recall_violations++;
             o->own[h] = mine;
             o->own_seen[h] = 1;
@@ -201,7 +207,7 @@ static void walk(orc *o, int32_t v, double rc, double r1, double r2, int mask, d
         out[0] = u[0]; out[1] = u[1];
     }
     if (o->record) {
-        double *r = o->rec + (size_t)v * 5;
+        double *r = o->rec + (size_t)v * 6;
         r[0] = out[0]; r[1] = out[1];
     }
 }
@@ -211,10 +217,11 @@ static void pass(orc *o, int mask, double root_value[2]) {
         if (o->player[h] > 0 && (mask & (1 << o->player[h]))) {
             for (int32_t a = 0; a < o->nact[h]; ++a) o->inst[o->qbase[h] + a] = 0.0;
             o->own[h] = 0.0;
+            o->cfsum[h] = 0.0;
             o->own_seen[h] = 0;
         }
     }
-    walk(o, o->root, 1.0, 1.0, 1.0, mask, root_value);
+    walk(o, o->root, 1.0, 1.0, 1.0, 1.0, mask, root_value);
 }
 
 static void update(orc *o, int mask, int variant, int avg, int64_t T) {
@@ -251,6 +258,9 @@ void orc_iterate(orc *o, int32_t iters, int32_t variant, int32_t avg, int32_t al
     if (root_value) { root_value[0] = rv[0]; root_value[1] = rv[1]; }
 }
 
+/* pi~(h) of Eq. 3 (sum of the counterfactual reaches of h's nodes) from the last pass. */
+void orc_get_cf_reach_sum(const orc *o, double *out) { memcpy(out, o->cfsum, sizeof(double) * o->H); }
+
 void orc_get_state(const orc *o, double *R, double *S, double *inst, double *sigma, double *own, int64_t *T) {
     if (R) memcpy(R, o->R, sizeof(double) * o->Q);
     if (S) memcpy(S, o->S, sizeof(double) * o->Q);
@@ -268,10 +278,11 @@ void orc_set_state(orc *o, const double *R, const double *S, int64_t T) {
     for (int32_t h = 0; h < o->H; ++h) if (o->player[h] > 0) regret_match(o, h);
 }
 
-/* Per node of the last pass: u1, u2, r_c, r_1, r_2 (needs orc_set_record(o, 1) before the pass). */
+/* Per node of the last pass: u1, u2, pi-check 1, pi-check 2, pi-hat 1, pi-hat 2
+ * (needs orc_set_record(o, 1) before the pass). */
 int32_t orc_get_nodes(const orc *o, double *out) {
     if (!o->rec) return -1;
-    memcpy(out, o->rec, sizeof(double) * 5 * (size_t)o->n);
+    memcpy(out, o->rec, sizeof(double) * 6 * (size_t)o->n);
     return 0;
 }
 

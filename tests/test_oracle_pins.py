@@ -85,10 +85,12 @@ def test_hand_worked_two_iterations_vanilla():
         for v, val in exp["u1_nodes"].items():
             assert nodes["u1"][int(v)] == pytest.approx(val, abs=1e-15)
             assert nodes["u2"][int(v)] == pytest.approx(-val, abs=1e-15)
-        if "reach_rc_r1_r2" in exp:
-            for v, r in exp["reach_rc_r1_r2"].items():
-                got = [nodes["r_c"][int(v)], nodes["r_1"][int(v)], nodes["r_2"][int(v)]]
+        if "reach_cf1_cf2_own1_own2" in exp:
+            for v, r in exp["reach_cf1_cf2_own1_own2"].items():
+                got = [nodes[k][int(v)] for k in ("cf1", "cf2", "own1", "own2")]
                 np.testing.assert_allclose(got, r, atol=1e-15)
+        if "cf_reach_sum" in exp:
+            np.testing.assert_allclose(st["cf_reach_sum"], exp["cf_reach_sum"], atol=1e-15)
         if "own_reach" in exp:
             np.testing.assert_allclose(st["own_reach"], exp["own_reach"], atol=1e-15)
         if "average_strategy" in exp:
@@ -207,7 +209,10 @@ def test_node_values_and_reaches_match_path_products():
         for v in range(tr.n):
             assert nd["u1"][v] == pytest.approx(tr.node_value(prof, v, 1), abs=1e-12)
             assert nd["u2"][v] == pytest.approx(tr.node_value(prof, v, 2), abs=1e-12)
-            np.testing.assert_allclose([nd["r_c"][v], nd["r_1"][v], nd["r_2"][v]], tr.reach_split(prof, v), atol=1e-14)
+            want = [tr.cf_reach(prof, v, 1), tr.cf_reach(prof, v, 2), tr.own_reach(prof, v, 1), tr.own_reach(prof, v, 2)]
+            np.testing.assert_allclose([nd["cf1"][v], nd["cf2"][v], nd["own1"][v], nd["own2"][v]], want, atol=1e-14)
+            rc, r1, r2 = tr.reach_split(prof, v)
+            assert nd["cf1"][v] == pytest.approx(rc * r2, abs=1e-14) and nd["own1"][v] == pytest.approx(r1, abs=1e-14)
         # the root payoff is the expected payoff sum_t pi(t) u(t)  (Section 2.2 / Eq. 1 agree)
         assert rv[0] == pytest.approx(tr.expected_payoff(prof, 1), abs=1e-12)
 
@@ -384,7 +389,7 @@ def test_invariants_every_iteration(variant, avg):
                     # sum_a sigma(h,a) r~(h,a) = 0 exactly: sum_a sigma_a (u_a - u) = 0
                     assert np.dot(prev[sl], st["inst_regret"][sl]) == pytest.approx(0.0, abs=1e-12)
             np.testing.assert_allclose(nd["u1"] + nd["u2"], 0.0, atol=1e-13)
-            pi = nd["r_c"] * nd["r_1"] * nd["r_2"]
+            pi = nd["cf1"] * nd["own1"]                 # non-player-1 factors x player-1 factors
             for lvl in range(depth.max() + 1):
                 tot = pi[depth == lvl].sum() + pi[(depth < lvl) & term].sum()
                 assert tot == pytest.approx(1.0, abs=1e-12)

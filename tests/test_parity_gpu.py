@@ -54,8 +54,7 @@ def compare_nodes(s, o, tol, g):
     gn, on = cfr.cfr_get_nodes(s), o.nodes()
     dec = g.infoset >= 0
     assert normwise(gn["u1"], on["u1"]) <= tol
-    cf1 = on["r_c"] * on["r_2"]
-    cf2 = on["r_c"] * on["r_1"]
+    cf1, cf2 = on["cf1"], on["cf2"]
     assert normwise(gn["cf_reach1"][dec], cf1[dec]) <= tol
     assert normwise(gn["cf_reach2"][dec], cf2[dec]) <= tol
     assert np.all(np.isnan(gn["cf_reach1"][~dec]))
