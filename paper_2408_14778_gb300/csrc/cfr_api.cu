@@ -61,6 +61,8 @@ struct cfr_solver {
     double *util64 = nullptr, *sigma064 = nullptr, *R = nullptr, *S = nullptr, *stage = nullptr;
     double *br_reach = nullptr, *br_val = nullptr, *br_cfv = nullptr, *avg = nullptr, *br_out = nullptr;
     int64_t *d_iter = nullptr;
+    void *contrib = nullptr;                              // FP64 mode: per-edge regret contributions
+    int32_t *hnode_start = nullptr, *hnode = nullptr;     // FP64 mode: nodes of each infoset, depth-first
     int64_t iteration = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -146,14 +148,18 @@ DevTree<real> dev_tree(cfr_solver *s) {
     t.reach1 = static_cast<real *>(s->reach1); t.reach2 = static_cast<real *>(s->reach2);
     t.u = static_cast<real *>(s->u); t.own = static_cast<real *>(s->own);
     t.R = s->R; t.S = s->S; t.iter = s->d_iter;
+    t.contrib = static_cast<real *>(s->contrib); t.hnode_start = s->hnode_start; t.hnode = s->hnode;
     return t;
 }
 
-// One full-tree iteration, queued on `st` (captured into the solver's graph).
+// One full-tree iteration, queued on `st` (captured into the solver's graph).  FP64 mode reduces
+// the instantaneous regrets deterministically (k_update sums per-edge contributions in depth-first
+// node order); FP32 mode adds them with atomics.
 template <typename real>
 cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st) {
+    constexpr bool det = sizeof(real) == sizeof(double);
     DevTree<real> t = dev_tree<real>(s);
-    CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
+    if (!det) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
     for (int32_t l = 0; l < s->L; ++l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
@@ -163,11 +169,11 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st) {
     }
     for (int32_t l = s->L - 1; l >= 0; --l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
-        k_bottomup<real><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1);
+        k_bottomup<real, det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1);
         CK_LAUNCH();
     }
     const int linear = s->cfg.avg_weight == CFR_AVG_LINEAR;
-    k_update<real><<<nblocks(s->H), kBlock, 0, st>>>(t, s->H, s->cfg.variant == CFR_PLUS, linear);
+    k_update<real, det><<<nblocks(s->H), kBlock, 0, st>>>(t, s->H, s->cfg.variant == CFR_PLUS, linear);
     CK_LAUNCH();
     return CFR_OK;
 }
@@ -230,6 +236,13 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     TRY(alloc_n(s, &s->S, s->Q));
     TRY(alloc_n(s, &s->stage, s->Q));
     TRY(alloc_n(s, &s->d_iter, 1));
+    if (fp64) {
+        TRY(dev_alloc(s, &s->contrib, sizeof(double) * (size_t)std::max<int64_t>(s->N - 1, 1)));
+        TRY(alloc_n(s, &s->hnode_start, (int64_t)s->H + 1));
+        TRY(alloc_n(s, &s->hnode, s->Nd));
+        TRY(upload(s, s->hnode_start, Lo.hnode_start));
+        TRY(upload(s, s->hnode, Lo.hnode));
+    }
 
     TRY(upload(s, s->dfirst, Lo.dfirst));
     TRY(upload(s, s->tfirst, Lo.tfirst));
@@ -368,7 +381,7 @@ cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver
 
     std::unique_ptr<Layout> Lo(new Layout());
     std::string err;
-    cfr_status st = build_layout(g, Lo.get(), &err);
+    cfr_status st = build_layout(g, Lo.get(), &err, cfg.precision == CFR_FP64);
     if (st != CFR_OK) return set_err(nullptr, st, "%s", err.c_str());
 
     DeviceGuard dg(cfg.device);
@@ -470,6 +483,7 @@ cfr_status cfr_get_state(cfr_solver *s, double *cum_regret, double *strat_sum, d
     }
     if (own_reach && s->H > 0) {
         std::vector<double> tmp((size_t)s->H);
+        CK(cudaStreamSynchronize(s->stream));
         if (s->cfg.precision == CFR_FP64) {
             CK(cudaMemcpy(tmp.data(), s->own, sizeof(double) * s->H, cudaMemcpyDeviceToHost));
         } else {

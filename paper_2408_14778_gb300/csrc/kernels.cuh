@@ -22,6 +22,11 @@ __device__ __forceinline__ bool is_terminal(uint32_t m, const uint32_t *wbits, i
     return na > 32 ? ((wbits[m + (a >> 5)] >> (a & 31)) & 1u) : ((m >> a) & 1u);
 }
 
+// acc + a * b.  FP64 rounds the product and the sum separately (no fused multiply-add), so the
+// FP64 path performs exactly the operations of a plain sequential evaluation; FP32 fuses.
+__device__ __forceinline__ double madd(double acc, double a, double b) { return __dadd_rn(acc, __dmul_rn(a, b)); }
+__device__ __forceinline__ float madd(float acc, float a, float b) { return fmaf(a, b, acc); }
+
 template <typename real>
 struct DevTree {
     const int32_t *dfirst, *tfirst, *dinfo;
@@ -37,6 +42,10 @@ struct DevTree {
     real *own;                 // [H]
     double *R, *S;             // [Q]
     int64_t *iter;             // completed iterations (device copy)
+    // deterministic mode: per-edge regret contributions and the nodes of each infoset in
+    // depth-first order (edge offset of node j's children: dfirst[j] + tfirst[j] - 1)
+    real *contrib;             // [N - 1]
+    const int32_t *hnode_start, *hnode;
 };
 
 template <typename real>
@@ -69,7 +78,10 @@ __global__ void __launch_bounds__(256) k_topdown(DevTree<real> t, int32_t j0, in
     }
 }
 
-template <typename real>
+// kDet = false: the regret contributions are added to inst with atomics (order unspecified).
+// kDet = true: they are stored per edge and k_update sums them per infoset in depth-first node
+// order, which makes the result independent of scheduling.
+template <typename real, bool kDet>
 __global__ void __launch_bounds__(256) k_bottomup(DevTree<real> t, int32_t j0, int32_t j1) {
     const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (j >= j1) return;
@@ -83,16 +95,18 @@ __global__ void __launch_bounds__(256) k_bottomup(DevTree<real> t, int32_t j0, i
     int32_t c = c0, tt = t0;
     for (int a = 0; a < na; ++a) {
         const real v = is_terminal(m, t.wbits, na, a) ? t.util[tt++] : t.u[c++];
-        ud += t.sigma[qb + a] * v;
+        ud = madd(ud, t.sigma[qb + a], v);
     }
     t.u[j] = ud;
     if (p == 0) return;
     const real w = p == 1 ? t.reach1[j] : -t.reach2[j];   // u_2 = -u_1
-    if (w == real(0)) return;
+    if (!kDet && w == real(0)) return;
     c = c0; tt = t0;
+    real *out = kDet ? t.contrib + (c0 + t0 - 1) : nullptr;
     for (int a = 0; a < na; ++a) {
         const real v = is_terminal(m, t.wbits, na, a) ? t.util[tt++] : t.u[c++];
-        atomicAdd(&t.inst[qb + a], w * (v - ud));
+        if (kDet) out[a] = w * (v - ud);
+        else atomicAdd(&t.inst[qb + a], w * (v - ud));
     }
 }
 
@@ -106,19 +120,27 @@ __device__ __forceinline__ void regret_match(real *sigma, const double *R, int32
     }
 }
 
-template <typename real>
+template <typename real, bool kDet>
 __global__ void __launch_bounds__(256) k_update(DevTree<real> t, int32_t H, int32_t plus, int32_t linear) {
     const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (h >= H || t.iplayer[h] == 0) return;
     const int32_t qb = t.qbase[h];
     const int na = t.qbase[h + 1] - qb;
+    if (kDet) {
+        for (int a = 0; a < na; ++a) t.inst[qb + a] = real(0);
+        for (int32_t i = t.hnode_start[h]; i < t.hnode_start[h + 1]; ++i) {
+            const int32_t j = t.hnode[i];
+            const real *src = t.contrib + (t.dfirst[j] + t.tfirst[j] - 1);
+            for (int a = 0; a < na; ++a) t.inst[qb + a] += src[a];
+        }
+    }
     const double w = linear ? (double)*t.iter : 1.0;
-    const double wo = w * (double)t.own[h];
+    const double wo = __dmul_rn(w, (double)t.own[h]);
     for (int a = 0; a < na; ++a) {
         double r = t.R[qb + a] + (double)t.inst[qb + a];
-        if (plus && r < 0.0) r = 0.0;
+        if (plus) r = r > 0.0 ? r : 0.0;
         t.R[qb + a] = r;
-        t.S[qb + a] += wo * (double)t.sigma[qb + a];
+        t.S[qb + a] = madd(t.S[qb + a], wo, (double)t.sigma[qb + a]);
     }
     regret_match(t.sigma, t.R, qb, na);
 }

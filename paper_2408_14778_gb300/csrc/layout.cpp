@@ -22,7 +22,7 @@ cfr_status fail(std::string *err, cfr_status st, const char *fmt, ...) {
 
 }  // namespace
 
-cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err) {
+cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, bool infoset_lists) {
     if (!g) return fail(err, CFR_ERR_INVALID, "game description is NULL");
     const int64_t n = g->num_nodes;
     if (n < 1) return fail(err, CFR_ERR_INVALID, "num_nodes must be >= 1 (got %lld)", (long long)n);
@@ -258,6 +258,35 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err) {
             Lo.pseq[(size_t)hi] = q_user2int[(size_t)rep[hu]];
             Lo.pseq_h[(size_t)hi] = hmap[(size_t)q2h_user[(size_t)rep[hu]]];
         }
+    }
+    if (!infoset_lists) return CFR_OK;
+
+    // ---- nodes of each infoset in depth-first (lexicographic path) order ---------------------
+    // The order in which a recursive walk reaches them; a deterministic reduction over this list
+    // adds the instantaneous regrets of an infoset's nodes in the same order as such a walk.
+    std::vector<int32_t> dec_of_user((size_t)n, -1);
+    for (int64_t j = 0; j < Lo.Nd; ++j) dec_of_user[(size_t)Lo.dnode_user[(size_t)j]] = (int32_t)j;
+    Lo.hnode_start.assign((size_t)H + 1, 0);
+    for (int64_t j = 0; j < Lo.Nd; ++j) Lo.hnode_start[(size_t)Lo.dinfo[(size_t)j] + 1]++;
+    for (int32_t h = 0; h < H; ++h) Lo.hnode_start[(size_t)h + 1] += Lo.hnode_start[(size_t)h];
+    Lo.hnode.assign((size_t)Lo.Nd, 0);
+    std::vector<int32_t> fillp(Lo.hnode_start.begin(), Lo.hnode_start.end() - 1);
+    std::vector<std::pair<int32_t, int32_t>> stack;       // (node, next action)
+    if (g->infoset[root] >= 0) stack.emplace_back((int32_t)root, 0);
+    if (!stack.empty()) {
+        const int32_t j0 = dec_of_user[(size_t)root];
+        Lo.hnode[(size_t)fillp[(size_t)Lo.dinfo[(size_t)j0]]++] = j0;
+    }
+    while (!stack.empty()) {
+        auto &top = stack.back();
+        const int32_t v = top.first;
+        const int32_t na = g->infoset_num_actions[g->infoset[v]];
+        if (top.second == na) { stack.pop_back(); continue; }
+        const int32_t c = child[(size_t)cstart[v] + top.second++];
+        if (g->infoset[c] < 0) continue;
+        const int32_t jc = dec_of_user[(size_t)c];
+        Lo.hnode[(size_t)fillp[(size_t)Lo.dinfo[(size_t)jc]]++] = jc;
+        stack.emplace_back(c, 0);
     }
     return CFR_OK;
 }

@@ -50,10 +50,14 @@ struct Layout {
     std::vector<int32_t> h_int2user;       // [H]
     std::vector<int32_t> dnode_user;       // [Nd] internal decision id -> caller node id
     std::vector<int32_t> tnode_user;       // [Nt]
+    // Only with infoset_lists: the decision nodes of infoset h are hnode[hnode_start[h] ..
+    // hnode_start[h+1]), in depth-first order (the order a recursive walk reaches them).
+    std::vector<int32_t> hnode_start;      // [H + 1]
+    std::vector<int32_t> hnode;            // [Nd]
 };
 
-// Validates g; if layout != nullptr also builds the layout.  Returns CFR_OK or an error code and
-// writes the reason into *err.
-cfr_status build_layout(const cfr_game_desc *g, Layout *layout, std::string *err);
+// Validates g; if layout != nullptr also builds the layout (with the per-infoset node lists when
+// infoset_lists).  Returns CFR_OK or an error code and writes the reason into *err.
+cfr_status build_layout(const cfr_game_desc *g, Layout *layout, std::string *err, bool infoset_lists = false);
 
 }  // namespace cfrgb

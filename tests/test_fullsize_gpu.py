@@ -11,12 +11,9 @@ import pytest
 import gamegen
 import oracle
 import paper_2408_14778_gb300 as cfr
+from paritylib import TOL32, TOL_EXPL, compare_state
 
 pytestmark = pytest.mark.gpu
-
-
-def normwise(x, y):
-    return float(np.max(np.abs(np.asarray(x) - np.asarray(y))) / max(np.max(np.abs(y)), 1e-30))
 
 
 @pytest.fixture(scope="module")
@@ -33,13 +30,8 @@ def full():
     s.close()
 
 
-def _compare(s, o):
-    gs, os_ = cfr.cfr_get_state(s), o.state()
-    for k in ("inst_regret", "cum_regret", "strat_sum"):
-        e = normwise(gs[k], os_[k])
-        assert e <= 1e-5, (k, e)
-    e = normwise(cfr.cfr_current_strategy(s), os_["sigma"])
-    assert e <= 1e-5, ("sigma", e)
+def _compare(s, o, g):
+    compare_state(s, o, TOL32, g)
 
 
 def test_full_size_first_iteration(full):
@@ -48,7 +40,7 @@ def test_full_size_first_iteration(full):
     assert info["num_nodes"] == g.num_nodes > 9e7
     o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
     cfr.cfr_iterate(s, 1)
-    _compare(s, o)
+    _compare(s, o, g)
     rv = cfr.cfr_root_value(s)
     assert np.isfinite(rv)
 
@@ -60,12 +52,16 @@ def test_full_size_step_from_oracle_state(full):
     cfr.cfr_set_state(s, st["cum_regret"], st["strat_sum"], st["iteration"])
     o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
     cfr.cfr_iterate(s, 1)
-    _compare(s, o)
+    _compare(s, o, g)
 
 
 def test_full_size_exploitability(full):
     g, o, s = full
     nc_g, ex_g = cfr.cfr_exploitability(s)
     nc_o, ex_o = o.exploitability()
-    assert abs(nc_g - nc_o) <= 1e-6 * max(1.0, 0.0) + 1e-6, (nc_g, nc_o)
-    assert abs(ex_g - ex_o) <= 1e-6
+    # FP32 strategy sums differ from the FP64 oracle's by ~1e-7 relative, which moves NashConv by
+    # ~1e-7 of its scale; the FP64 best response on the GPU's own average strategy must agree
+    # with the oracle's to 1e-6.
+    assert abs(nc_g - nc_o) <= 1e-5 * max(1.0, abs(nc_o)), (nc_g, nc_o)
+    nc_chk, ex_chk = o.exploitability(cfr.cfr_average_strategy(s))
+    assert abs(nc_g - nc_chk) <= TOL_EXPL and abs(ex_g - ex_chk) <= TOL_EXPL
