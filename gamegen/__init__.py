@@ -196,10 +196,12 @@ CONFIGS = {
 
 
 def config(name: str, seed: int = 0, target_nodes: int | None = None, **override) -> GameDesc:
-    """Build a named workload; ``target_nodes`` rescales the public tree (same family, other size)."""
+    """Build a named workload; ``target_nodes`` rescales the public tree (same family, other size),
+    an explicit ``p_cont`` fixes the continuation probability instead of fitting a size."""
     kw = dict(CONFIGS[name])
+    explicit_p = "p_cont" in override
     kw.update(override)
-    tgt = target_nodes if target_nodes is not None else kw.pop("target_nodes", None)
+    tgt = target_nodes if target_nodes is not None else (None if explicit_p else kw.get("target_nodes"))
     kw.pop("target_nodes", None)
     if tgt is not None:
         kw["p_cont"] = fit_p_cont(tgt, seed=seed, **{k: v for k, v in _defaults(kw).items() if k != "p_cont"})

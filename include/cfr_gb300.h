@@ -142,6 +142,23 @@ cfr_status cfr_current_strategy(cfr_solver *s, double *out, int64_t len);
  * NashConv / 2.  Either pointer may be NULL.  CFR_ERR_UNSUPPORTED if some infoset spans two depths. */
 cfr_status cfr_exploitability(cfr_solver *s, double *nash_conv, double *exploitability);
 
+/* Size of the fixed working region used by cfr_exploitability_static, per GPU. */
+#define CFR_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* cfr_exploitability without any device allocation.  The paper has no counterpart; this entry
+ * point exists for callers that may not allocate GPU memory while they run (a host application
+ * that gives the library a fixed memory budget at set-up, or a real-time loop where cudaMalloc and
+ * cudaFree, and the synchronisation they bring, are not allowed).  It runs the same best-response
+ * kernels, but keeps all of their working memory in one region compiled into this library,
+ * CFR_STATIC_SCRATCH_BYTES per GPU, which every GPU that loads the library holds until the process
+ * exits.  A game needing more - 16 (num_decision + num_q) + 4 num_infosets bytes, rounded up -
+ * returns CFR_ERR_UNSUPPORTED and leaves cfr_exploitability as the way to evaluate it.
+ * The first call on a device looks up the region's device address (set-up, once per device); make
+ * that first call before any stream capture.  All calls share the region and leave their contents
+ * in it (each call resets what must start at zero), so calls that overlap on the GPU - from two
+ * streams or two threads - race and give wrong results.  Results equal cfr_exploitability's. */
+cfr_status cfr_exploitability_static(cfr_solver *s, double *nash_conv, double *exploitability);
+
 /* Copies the FP64 cumulative regrets R (R = T * r-bar of Eq. 8), strategy sums S (numerator of
  * Eq. 10 with one node's own reach per infoset), the last iteration's instantaneous regrets (Eq. 7)
  * into [len_q] buffers, the last iteration's own reach per infoset (Eq. 4) into own_reach[len_h],

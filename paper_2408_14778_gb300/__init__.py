@@ -113,6 +113,8 @@ def lib():
         L.cfr_get_nodes.argtypes = [_P, _P, _P, _P, ctypes.c_int64]
         L.cfr_get_info.argtypes = [_P, ctypes.POINTER(_Info)]
         L.cfr_root_value.argtypes = [_P, _P]
+        L.cfr_exploitability_static.argtypes = [_P, _P, _P]
+        L.cfr_exploitability_static.restype = ctypes.c_int
         L.cfr_last_error.argtypes = [_P]
         L.cfr_last_error.restype = ctypes.c_char_p
         L.cfr_free.argtypes = [_P]
@@ -238,6 +240,22 @@ def cfr_exploitability(s: "Solver") -> tuple[float, float]:
     nc, ex = ctypes.c_double(), ctypes.c_double()
     _check(lib().cfr_exploitability(s.handle, ctypes.byref(nc), ctypes.byref(ex)), s.handle)
     return nc.value, ex.value
+
+
+def cfr_exploitability_static(s: "Solver") -> tuple[float, float]:
+    """cfr_exploitability with its working memory in the library's fixed per-GPU region.
+
+    For callers that may not allocate device memory while running (fixed memory budget, real-time
+    loops).  Games needing more than CFR_STATIC_SCRATCH_BYTES raise CFR_ERR_UNSUPPORTED.  The first
+    call on a device performs a one-time set-up and should come before any stream capture; calls
+    that overlap on the GPU share the region and race.  This wrapper allocates no device memory.
+    """
+    nc, ex = ctypes.c_double(), ctypes.c_double()
+    _check(lib().cfr_exploitability_static(s.handle, ctypes.byref(nc), ctypes.byref(ex)), s.handle)
+    return nc.value, ex.value
+
+
+CFR_STATIC_SCRATCH_BYTES = 32 << 20
 
 
 def cfr_get_state(s: "Solver") -> dict:

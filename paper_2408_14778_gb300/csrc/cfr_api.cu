@@ -8,6 +8,7 @@
 #include <cstring>
 #include <limits>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -612,3 +613,104 @@ void cfr_free(cfr_solver *s) {
 }
 
 }  // extern "C"
+
+// ================================================================================================
+// Exploitability without device allocation (cfr_exploitability_static).
+//
+// Some callers may not allocate GPU memory once they are running: a host application that hands
+// the library a fixed memory budget up front, or a real-time loop in which an allocation (and the
+// synchronisation cudaMalloc/cudaFree imply) is not allowed.  For them this variant runs the same
+// best-response kernels as cfr_exploitability with all of its working memory - the average
+// strategy, the opponent reaches, the node values, the per-action sums and the chosen actions - in
+// one fixed region compiled into this library, kStaticScratchBytes per GPU, which every GPU that
+// loads the library holds until the process exits.  Calls share the region and leave their
+// contents in it; calls that overlap on the GPU (two streams, or two threads) race on it.
+namespace {
+
+constexpr size_t kStaticScratchBytes = CFR_STATIC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxStaticDevices] = {};
+
+// The region's device address on the current device; looked up once per device.  Host code must
+// not use the symbol itself: on the host it names a host-side stand-in, not device memory.
+cudaError_t static_scratch(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= kMaxStaticDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_static_ptr[dev]);
+    return cudaSuccess;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" cfr_status cfr_exploitability_static(cfr_solver *s, double *nash_conv, double *exploitability) {
+    TRY(check_usable(s));
+    if (!s->single_level)
+        return set_err(s, CFR_ERR_UNSUPPORTED, "the GPU best response needs every infoset at a single depth");
+    const size_t need = align256(sizeof(double) * (size_t)s->Q) * 2 + align256(sizeof(double) * (size_t)s->Nd) * 2 +
+                        align256(sizeof(int32_t) * (size_t)s->H) + 256;
+    if (need > kStaticScratchBytes)
+        return set_err(s, CFR_ERR_UNSUPPORTED,
+                       "cfr_exploitability_static needs %zu bytes of working memory for this game; its fixed region "
+                       "holds %zu (use cfr_exploitability)", need, kStaticScratchBytes);
+    DeviceGuard dg(s->device);
+    unsigned char *base = nullptr;
+    CK(static_scratch(s->device, &base));
+    double nc = 0.0;
+    if (s->Nd > 0) {
+        unsigned char *p = base;
+        double *avg = reinterpret_cast<double *>(p);        p += align256(sizeof(double) * (size_t)s->Q);
+        double *cfv = reinterpret_cast<double *>(p);        p += align256(sizeof(double) * (size_t)s->Q);
+        double *preach = reinterpret_cast<double *>(p);     p += align256(sizeof(double) * (size_t)s->Nd);
+        double *val = reinterpret_cast<double *>(p);        p += align256(sizeof(double) * (size_t)s->Nd);
+        int32_t *astar = reinterpret_cast<int32_t *>(p);
+        cudaStream_t st = s->stream;
+        k_average<<<nblocks(s->H), kBlock, 0, st>>>(s->S, s->sigma064, s->qbase, s->iplayer, avg, s->H);
+        CK_LAUNCH();
+        DevBR b;
+        b.dfirst = s->dfirst; b.tfirst = s->tfirst; b.dinfo = s->dinfo;
+        b.kmask = s->kmask; b.wbits = s->wbits;
+        b.util = s->util64; b.qbase = s->qbase; b.iplayer = s->iplayer; b.avg = avg;
+        b.preach = preach; b.val = val; b.cfv = cfv; b.astar = astar;
+        const double one = 1.0;
+        for (int player = 1; player <= 2; ++player) {
+            // the region keeps the previous call's contents: the root reach and the sums restart here
+            CK(cudaMemcpyAsync(preach, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+            CK(cudaMemsetAsync(cfv, 0, sizeof(double) * (size_t)std::max<int64_t>(s->Q, 1), st));
+            for (int32_t l = 0; l + 1 < s->L; ++l) {
+                const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
+                k_br_topdown<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
+                CK_LAUNCH();
+            }
+            for (int32_t l = s->L - 1; l >= 0; --l) {
+                const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
+                const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
+                k_br_nodes<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
+                CK_LAUNCH();
+                if (h1 > h0) {
+                    k_br_choose<<<nblocks(h1 - h0), kBlock, 0, st>>>(b, h0, h1, player);
+                    CK_LAUNCH();
+                }
+                k_br_pick<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
+                CK_LAUNCH();
+            }
+            double v = 0.0;
+            CK(cudaMemcpyAsync(&v, val, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            nc += v;   // zero-sum: u_1(avg) + u_2(avg) = 0
+        }
+    }
+    if (nash_conv) *nash_conv = nc;
+    if (exploitability) *exploitability = nc / 2.0;
+    return CFR_OK;
+}
