@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="holdem169_depth12")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--nodes", type=int, default=None,
+                    help="same workload family rescaled to about this many nodes (profiling captures)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--variant", choices=["plus", "vanilla"], default="plus")
     ap.add_argument("--no-e2e", action="store_true")
@@ -211,7 +213,7 @@ def run_reference(args, world, rank):
     import oracle
 
     variant = 1 if args.variant == "plus" else 0
-    g = gamegen.config(args.workload, seed=args.seed)
+    g = gamegen.config(args.workload, seed=args.seed, target_nodes=args.nodes)
     budget = max(0.05, 90.0 / max(args.steps + args.warmup, 1))
     sub = oracle_sample(g, budget)
     o = oracle.Oracle(sub)
@@ -243,12 +245,13 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     variant = cfr.CFR_PLUS if args.variant == "plus" else cfr.CFR_VANILLA
     precision = cfr.CFR_FP32 if args.precision == "fp32" else cfr.CFR_FP64
-    g = gamegen.config(args.workload, seed=args.seed)
+    g = gamegen.config(args.workload, seed=args.seed, target_nodes=args.nodes)
     s = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local)
     info = cfr.cfr_get_info(s)
     stream = torch.cuda.current_stream(local)
     cfr.cfr_iterate(s, args.warmup)
     cfr.cfr_synchronize(s)
+    launches0 = cfr.cfr_get_info(s)["kernel_launches"]
 
     sampler = ClockSampler(local)
     barrier(world)
@@ -267,12 +270,25 @@ def run_ours(args, world, rank, local):
     N = info["num_nodes"]
     value = world * N * args.steps / t_max
     iter_s = t / args.steps
-    achieved = info["bytes_per_iteration"] / iter_s / 1e9
+    # Per-phase times: iterations launched kernel by kernel with CUDA events between the phases on the
+    # solver's stream (each is a real iteration), averaged; the dominant phase gives the roofline.
+    launches = cfr.cfr_get_info(s)["kernel_launches"]
+    ph = [cfr.cfr_phase_times(s) for _ in range(5)]
+    names = [f"top-down depth {l}" for l in range(len(ph[0]["topdown_us"]))] + \
+            [f"bottom-up depth {l}" for l in reversed(range(len(ph[0]["bottomup_us"])))] + ["update"]
+    us = np.mean([np.concatenate([p["topdown_us"], p["bottomup_us"], [p["update_us"]]]) for p in ph], axis=0)
+    by = np.concatenate([ph[0]["topdown_bytes"], ph[0]["bottomup_bytes"], [ph[0]["update_bytes"]]])
+    k = int(np.argmax(us))
     peak, peak_src = measured_hbm_peak()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+    dom = by[k] / (us[k] * 1e-6) / 1e9
+    achieved = info["bytes_per_iteration"] / iter_s / 1e9
+    roofline = {"bound": "hbm", "achieved": dom, "peak": peak, "unit": "GB/s", "frac": dom / peak,
                 "traffic": recorded_traffic(args.workload, args.precision),
-                "kernel": "one full CFR iteration (graph of per-depth kernels)",
-                "algorithmic_bytes_per_launch": info["bytes_per_iteration"], "peak_source": peak_src}
+                "kernel": f"{names[k]} ({'k_update_tiled' if names[k] == 'update' else 'k_bottomup' if 'bottom' in names[k] else 'k_topdown'})",
+                "algorithmic_bytes_per_launch": float(by[k]), "launch_us": float(us[k]), "peak_source": peak_src,
+                "iteration": {"achieved": achieved, "frac": achieved / peak,
+                              "algorithmic_bytes": info["bytes_per_iteration"]}}
+    phase_us = {n: round(float(u), 2) for n, u in zip(names, us)}
 
     e2e = None
     if not args.no_e2e:
@@ -312,8 +328,9 @@ def run_ours(args, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
                 "data": "synthetic", "config": workload_config(args, g, info),
                 "iterations_per_s": args.steps / t_max, "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
-                "gpu_launches": info["kernels_per_iteration"] * args.steps, "clocks": clocks,
+                "gpu_launches": launches - launches0, "clocks": clocks,
                 "parallelism": "replicas" if world > 1 else "single GPU"}
+        line["phase_us"] = phase_us
         print(json.dumps(line), flush=True)
     del np
 

@@ -99,6 +99,7 @@ typedef struct {
     int64_t bytes_per_iteration;  /* algorithmic bytes of one iteration: 56 Nd + 4 Nt + 44 Q (FP32 mode) or
                                      96 Nd + 8 Nt + 56 Q (FP64 mode) */
     int32_t kernels_per_iteration;/* kernel launches of one iteration */
+    int64_t kernel_launches;      /* kernel launches made by cfr_iterate so far */
 } cfr_info;
 
 /* Fills *c with defaults: vanilla, FP32, simultaneous, default averaging, current device,
@@ -180,6 +181,15 @@ cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *c
  * of Eq. 1 at the root, which equals u-hat(sigma^(T), 1) of Section 2.2.  One scalar; synchronises
  * the stream (a per-iteration progress read).  0 before the first iteration. */
 cfr_status cfr_root_value(cfr_solver *s, double *u1);
+
+/* Runs ONE iteration (it counts: T advances by 1) as individually launched kernels with CUDA events
+ * between its phases, and returns per phase the elapsed time in microseconds (us) and the phase's
+ * algorithmic bytes (bytes): top-down from depth 0, 1, ..., num_levels-1, then bottom-up at depth
+ * num_levels-1, ..., 0, then the per-infoset update - 2 num_levels + 1 phases (0 for a game without
+ * decision nodes).  The bytes add up to cfr_info.bytes_per_iteration.  *nphases receives the count;
+ * with us and bytes both NULL only the count is returned (no iteration runs), otherwise len must be
+ * at least the count.  Tracing hook. */
+cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t len, int32_t *nphases);
 
 cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info);
 

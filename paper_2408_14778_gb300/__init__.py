@@ -75,6 +75,7 @@ class _Info(ctypes.Structure):
         ("variant", ctypes.c_int32), ("precision", ctypes.c_int32), ("update_mode", ctypes.c_int32),
         ("avg_weight", ctypes.c_int32), ("iteration", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
         ("bytes_per_iteration", ctypes.c_int64), ("kernels_per_iteration", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
 
@@ -113,6 +114,8 @@ def lib():
         L.cfr_get_nodes.argtypes = [_P, _P, _P, _P, ctypes.c_int64]
         L.cfr_get_info.argtypes = [_P, ctypes.POINTER(_Info)]
         L.cfr_root_value.argtypes = [_P, _P]
+        L.cfr_phase_times.argtypes = [_P, _P, _P, ctypes.c_int32, _P]
+        L.cfr_phase_times.restype = ctypes.c_int
         L.cfr_exploitability_static.argtypes = [_P, _P, _P]
         L.cfr_exploitability_static.restype = ctypes.c_int
         L.cfr_last_error.argtypes = [_P]
@@ -287,6 +290,21 @@ def cfr_root_value(s: "Solver") -> float:
     return v.value
 
 
+def cfr_phase_times(s: "Solver") -> dict:
+    """Runs one iteration as individually timed kernels (it counts as an iteration) and returns per
+    phase its time (us) and algorithmic bytes: top-down by depth, bottom-up by depth (deepest
+    first), update."""
+    n = ctypes.c_int32()
+    _check(lib().cfr_phase_times(s.handle, None, None, 0, ctypes.byref(n)), s.handle)
+    if n.value == 0:
+        return {}
+    us, by = np.zeros(n.value), np.zeros(n.value)
+    _check(lib().cfr_phase_times(s.handle, us.ctypes.data, by.ctypes.data, n.value, ctypes.byref(n)), s.handle)
+    L = (n.value - 1) // 2
+    return dict(topdown_us=us[:L], bottomup_us=us[L:2 * L], update_us=float(us[2 * L]),
+                topdown_bytes=by[:L], bottomup_bytes=by[L:2 * L], update_bytes=float(by[2 * L]))
+
+
 def cfr_get_info(s: "Solver") -> dict:
     info = _Info()
     _check(lib().cfr_get_info(s.handle, ctypes.byref(info)), s.handle)
@@ -328,4 +346,5 @@ class Solver:
     set_state = cfr_set_state
     get_nodes = cfr_get_nodes
     root_value = cfr_root_value
+    phase_times = cfr_phase_times
     info = cfr_get_info

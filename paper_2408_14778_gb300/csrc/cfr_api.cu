@@ -56,7 +56,7 @@ struct cfr_solver {
     int32_t *dfirst = nullptr, *tfirst = nullptr, *dinfo = nullptr, *qbase = nullptr, *pseq = nullptr,
             *pseq_h = nullptr, *q_int2user = nullptr, *astar = nullptr;
     int8_t *iplayer = nullptr;
-    uint32_t *kmask = nullptr, *wbits = nullptr;
+    uint32_t *kmask = nullptr, *wbits = nullptr, *qp = nullptr;
     void *util = nullptr, *sigma = nullptr, *inst = nullptr, *reach1 = nullptr, *reach2 = nullptr,
          *u = nullptr, *own = nullptr;
     double *util64 = nullptr, *sigma064 = nullptr, *R = nullptr, *S = nullptr, *stage = nullptr;
@@ -64,6 +64,14 @@ struct cfr_solver {
     int64_t *d_iter = nullptr;
     void *contrib = nullptr;                              // FP64 mode: per-edge regret contributions
     int32_t *hnode_start = nullptr, *hnode = nullptr;     // FP64 mode: nodes of each infoset, depth-first
+    int32_t *wide = nullptr;                              // nodes with more than 32 actions, by depth
+    std::vector<int32_t> wlevel;
+    std::vector<char> ddepth_children;                    // depth l has a node with a decision child
+    std::vector<int64_t> level_children;                  // children of the decision nodes of depth l
+    int32_t *tiles = nullptr;                             // FP32 mode: infoset tiles of k_update_tiled
+    int32_t ntiles = 0;
+    int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
+    int64_t kernel_launches = 0;
     int64_t iteration = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -142,7 +150,7 @@ template <typename real>
 DevTree<real> dev_tree(cfr_solver *s) {
     DevTree<real> t;
     t.dfirst = s->dfirst; t.tfirst = s->tfirst; t.dinfo = s->dinfo;
-    t.kmask = s->kmask; t.wbits = s->wbits;
+    t.kmask = s->kmask; t.wbits = s->wbits; t.qp = s->qp;
     t.util = static_cast<const real *>(s->util);
     t.qbase = s->qbase; t.iplayer = s->iplayer; t.pseq = s->pseq; t.pseq_h = s->pseq_h;
     t.sigma = static_cast<real *>(s->sigma); t.inst = static_cast<real *>(s->inst);
@@ -155,28 +163,94 @@ DevTree<real> dev_tree(cfr_solver *s) {
 
 // One full-tree iteration, queued on `st` (captured into the solver's graph).  FP64 mode reduces
 // the instantaneous regrets deterministically (k_update sums per-edge contributions in depth-first
-// node order); FP32 mode adds them with atomics.
+// node order); FP32 mode adds them with atomics.  With `ev` (2 L + 2 events), an event is recorded
+// before the first phase and after each phase: top-down from depth 0 .. L-1, bottom-up at depth
+// L-1 .. 0, update.
 template <typename real>
-cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st) {
+cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = nullptr) {
     constexpr bool det = sizeof(real) == sizeof(double);
     DevTree<real> t = dev_tree<real>(s);
+    int ne = 0;
+    auto mark = [&]() -> cfr_status {
+        if (ev) CK(cudaEventRecord(ev[ne++], st));
+        return CFR_OK;
+    };
     if (!det) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
+    TRY(mark());
     for (int32_t l = 0; l < s->L; ++l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
-        const int32_t nb = nblocks(j1 - j0), nh = nblocks(h1 - h0);
-        k_topdown<real><<<nb + nh, kBlock, 0, st>>>(t, j0, j1, nb, h0, h1, l == 0);
-        CK_LAUNCH();
+        // a depth whose nodes have no decision children (the last one) only needs its own reaches
+        // (depth 0 always launches: its first thread counts the iteration)
+        const int32_t nb = s->ddepth_children[l] || l == 0 ? nblocks(j1 - j0) : 0, nh = nblocks(h1 - h0);
+        if (nb + nh > 0) {
+            k_topdown<real, !det><<<nb + nh, kBlock, 0, st>>>(t, j0, j1, nb, h0, h1, l == 0);
+            CK_LAUNCH();
+        }
+        const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
+        if (!det && nw > 0) {
+            k_topdown_wide<real><<<nw, kBlock, 0, st>>>(t, s->wide, s->wlevel[l]);
+            CK_LAUNCH();
+        }
+        TRY(mark());
     }
     for (int32_t l = s->L - 1; l >= 0; --l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         k_bottomup<real, det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1);
         CK_LAUNCH();
+        const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
+        if (!det && nw > 0) {
+            k_bottomup_wide<real><<<nw, kBlock, 0, st>>>(t, s->wide, s->wlevel[l]);
+            CK_LAUNCH();
+        }
+        TRY(mark());
     }
     const int linear = s->cfg.avg_weight == CFR_AVG_LINEAR;
-    k_update<real, det><<<nblocks(s->H), kBlock, 0, st>>>(t, s->H, s->cfg.variant == CFR_PLUS, linear);
-    CK_LAUNCH();
+    if constexpr (det) {
+        if (s->Hp > 0) {
+            k_update<real, det><<<nblocks(s->Hp), kBlock, 0, st>>>(t, s->Hp, s->cfg.variant == CFR_PLUS, linear);
+            CK_LAUNCH();
+        }
+    } else {
+        if (s->ntiles > 0) {
+            k_update_tiled<<<s->ntiles, kBlock, 0, st>>>(t, s->tiles, s->cfg.variant == CFR_PLUS, linear);
+            CK_LAUNCH();
+        }
+    }
+    TRY(mark());
     return CFR_OK;
+}
+
+// Algorithmic bytes of each phase, in the order of enqueue_iteration's events (FP32 mode; FP64 mode
+// doubles the value bytes: 32 Nd(l) + 16 Nd(l+1), 40 Nd(l) + 8 C(l), 56 Q):
+//   top-down from depth l:  20 Nd(l) + 8 Nd(l+1)   (node fields and reaches read, child reaches written)
+//   bottom-up at depth l:   24 Nd(l) + 4 C(l)      (node fields, reach, value write; one value per child)
+//   update:                 44 Q                   (r~ read and zeroed, R and S read+written, sigma written)
+// They add up to the iteration's model, 56 Nd + 4 Nt + 44 Q (96 Nd + 8 Nt + 56 Q in FP64 mode), since
+// every node but the root is a child once.
+std::vector<double> phase_bytes(const cfr_solver *s) {
+    const bool f64 = s->cfg.precision == CFR_FP64;
+    std::vector<double> b;
+    auto nd = [&](int32_t l) -> double { return l < s->L ? (double)(s->dlevel[l + 1] - s->dlevel[l]) : 0.0; };
+    for (int32_t l = 0; l < s->L; ++l) b.push_back(f64 ? 32 * nd(l) + 16 * nd(l + 1) : 20 * nd(l) + 8 * nd(l + 1));
+    for (int32_t l = s->L - 1; l >= 0; --l) {
+        const double children = (double)s->level_children[l];
+        b.push_back(f64 ? 40 * nd(l) + 8 * children : 24 * nd(l) + 4 * children);
+    }
+    b.push_back((f64 ? 56.0 : 44.0) * (double)s->Q);
+    return b;
+}
+
+// Kernel launches of one iteration (for cfr_info and the benchmark's launch count).
+int32_t launches_per_iteration(const cfr_solver *s) {
+    if (s->L == 0) return 0;
+    const bool det = s->cfg.precision == CFR_FP64;
+    int32_t n = s->L + 1;                                   // bottom-up depths + update
+    for (int32_t l = 0; l < s->L; ++l) {
+        n += s->ddepth_children[l] || l == 0 || s->hlevel[l + 1] > s->hlevel[l];   // top-down
+        if (!det) n += 2 * (s->wlevel[l + 1] > s->wlevel[l]);
+    }
+    return n;
 }
 
 cfr_status build_graph(cfr_solver *s) {
@@ -205,10 +279,23 @@ cfr_status check_usable(cfr_solver *s) {
     return CFR_OK;
 }
 
+// Waits for the solver's stream.
+cfr_status sync_and_check(cfr_solver *s) {
+    CK(cudaStreamSynchronize(s->stream));
+    return CFR_OK;
+}
+
 cfr_status load(cfr_solver *s, Layout &Lo) {
     s->N = Lo.N; s->Nd = Lo.Nd; s->Nt = Lo.Nt; s->Q = Lo.Q; s->H = Lo.H; s->L = Lo.L;
     s->max_depth = Lo.max_depth; s->max_actions = Lo.max_actions; s->single_level = Lo.single_level;
-    s->dlevel = Lo.dlevel; s->hlevel = Lo.hlevel;
+    s->dlevel = Lo.dlevel; s->hlevel = Lo.hlevel; s->wlevel = Lo.wlevel; s->Hp = Lo.Hp;
+    s->ddepth_children.assign((size_t)s->L, 0);
+    s->level_children.assign((size_t)s->L, 0);
+    for (int32_t l = 0; l < s->L; ++l) {
+        const size_t a = (size_t)s->dlevel[l], b = (size_t)s->dlevel[l + 1];
+        s->ddepth_children[l] = Lo.dfirst[b] > Lo.dfirst[a];
+        s->level_children[l] = (int64_t)(Lo.dfirst[b] - Lo.dfirst[a]) + (Lo.tfirst[b] - Lo.tfirst[a]);
+    }
     s->dnode_user.swap(Lo.dnode_user); s->tnode_user.swap(Lo.tnode_user); s->h_int2user.swap(Lo.h_int2user);
     const bool fp64 = s->cfg.precision == CFR_FP64;
     const size_t rs = s->real_size();
@@ -217,6 +304,7 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     TRY(alloc_n(s, &s->tfirst, s->Nd + 1));
     TRY(alloc_n(s, &s->dinfo, s->Nd));
     TRY(alloc_n(s, &s->kmask, s->Nd));
+    TRY(alloc_n(s, &s->qp, s->Nd));
     TRY(alloc_n(s, &s->wbits, (int64_t)Lo.wbits.size()));
     TRY(alloc_n(s, &s->sigma064, s->Q));
     TRY(alloc_n(s, &s->util64, s->Nt));
@@ -244,11 +332,31 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
         TRY(upload(s, s->hnode_start, Lo.hnode_start));
         TRY(upload(s, s->hnode, Lo.hnode));
     }
+    TRY(alloc_n(s, &s->wide, (int64_t)Lo.wide.size()));
+    TRY(upload(s, s->wide, Lo.wide));
+    if (!fp64) {
+        // tiles of player infosets for k_update_tiled: at most kBlock infosets and kTileQ slots each
+        // (an infoset wider than kTileQ gets a tile of its own)
+        std::vector<int32_t> tiles;
+        int32_t h0 = 0;
+        while (h0 < s->Hp) {
+            int32_t h1 = h0 + 1;
+            while (h1 < s->Hp && h1 - h0 < kBlock && Lo.qbase[(size_t)h1 + 1] - Lo.qbase[(size_t)h0] <= kTileQ) ++h1;
+            tiles.push_back(h0);
+            h0 = h1;
+        }
+        tiles.push_back(s->Hp);
+        s->ntiles = (int32_t)tiles.size() - 1;
+        TRY(alloc_n(s, &s->tiles, (int64_t)tiles.size()));
+        TRY(upload(s, s->tiles, tiles));
+        CK(cudaStreamSynchronize(s->stream));
+    }
 
     TRY(upload(s, s->dfirst, Lo.dfirst));
     TRY(upload(s, s->tfirst, Lo.tfirst));
     TRY(upload(s, s->dinfo, Lo.dinfo));
     TRY(upload(s, s->kmask, Lo.kmask));
+    TRY(upload(s, s->qp, Lo.qp));
     TRY(upload(s, s->wbits, Lo.wbits));
     TRY(upload(s, s->sigma064, Lo.sigma0));
     TRY(upload(s, s->util64, Lo.util));
@@ -302,8 +410,7 @@ cfr_status gather_q_to_host(cfr_solver *s, const T *src, double *out) {
     k_gather_q<T><<<nblocks(s->Q), kBlock, 0, s->stream>>>(src, s->q_int2user, s->stage, (int32_t)s->Q);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(out, s->stage, sizeof(double) * (size_t)s->Q, cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
-    return CFR_OK;
+    return sync_and_check(s);
 }
 
 cfr_status best_response(cfr_solver *s, int player, double *value) {
@@ -334,8 +441,7 @@ cfr_status best_response(cfr_solver *s, int player, double *value) {
         CK_LAUNCH();
     }
     CK(cudaMemcpyAsync(value, s->br_val, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return CFR_OK;
+    return sync_and_check(s);
 }
 
 }  // namespace
@@ -410,7 +516,10 @@ cfr_status cfr_iterate(cfr_solver *s, int32_t n) {
     TRY(check_usable(s));
     if (n < 0) return set_err(s, CFR_ERR_INVALID, "n must be >= 0");
     DeviceGuard dg(s->device);
-    for (int32_t i = 0; i < n && s->graph_exec; ++i) CK(cudaGraphLaunch(s->graph_exec, s->stream));
+    for (int32_t i = 0; i < n && s->graph_exec; ++i) {
+        CK(cudaGraphLaunch(s->graph_exec, s->stream));
+        s->kernel_launches += launches_per_iteration(s);
+    }
     s->iteration += n;
     return CFR_OK;
 }
@@ -418,8 +527,7 @@ cfr_status cfr_iterate(cfr_solver *s, int32_t n) {
 cfr_status cfr_synchronize(cfr_solver *s) {
     TRY(check_usable(s));
     DeviceGuard dg(s->device);
-    CK(cudaStreamSynchronize(s->stream));
-    return CFR_OK;
+    return sync_and_check(s);
 }
 
 cfr_status cfr_average_strategy(cfr_solver *s, double *out, int64_t len) {
@@ -583,6 +691,37 @@ cfr_status cfr_root_value(cfr_solver *s, double *u1) {
     return CFR_OK;
 }
 
+cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t len, int32_t *nphases) {
+    TRY(check_usable(s));
+    const int32_t n = s->L > 0 ? 2 * s->L + 1 : 0;
+    if (nphases) *nphases = n;
+    if (!us && !bytes) return CFR_OK;
+    if (len < n) return set_err(s, CFR_ERR_INVALID, "phase buffers need %d entries", n);
+    if (n == 0) return CFR_OK;
+    DeviceGuard dg(s->device);
+    std::vector<cudaEvent_t> ev((size_t)n + 1, nullptr);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    cfr_status st = s->cfg.precision == CFR_FP64 ? enqueue_iteration<double>(s, s->stream, ev.data())
+                                                 : enqueue_iteration<float>(s, s->stream, ev.data());
+    if (st == CFR_OK) {
+        s->iteration += 1;
+        s->kernel_launches += launches_per_iteration(s);
+        cudaError_t e = cudaEventSynchronize(ev[(size_t)n]);
+        for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[(size_t)k], ev[(size_t)k + 1]);
+            if (us) us[k] = 1e3 * (double)ms;
+        }
+        if (e != cudaSuccess) { s->poisoned = true; st = set_err(s, CFR_ERR_CUDA, "phase timing: %s", cudaGetErrorString(e)); }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st == CFR_OK && bytes) {
+        const std::vector<double> b = phase_bytes(s);
+        for (int32_t k = 0; k < n; ++k) bytes[k] = b[(size_t)k];
+    }
+    return st;
+}
+
 cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info) {
     if (!s || !info) return set_err(nullptr, CFR_ERR_INVALID, "solver or info is NULL");
     std::memset(info, 0, sizeof *info);
@@ -592,7 +731,8 @@ cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info) {
     info->variant = s->cfg.variant; info->precision = s->cfg.precision; info->update_mode = s->cfg.update_mode;
     info->avg_weight = s->cfg.avg_weight; info->iteration = s->iteration; info->device_bytes = s->device_bytes;
     info->bytes_per_iteration = bytes_model(s);
-    info->kernels_per_iteration = s->L > 0 ? 2 * s->L + 1 : 0;
+    info->kernels_per_iteration = launches_per_iteration(s);
+    info->kernel_launches = s->kernel_launches;
     return CFR_OK;
 }
 

@@ -1,16 +1,19 @@
 // Device kernels of one full-tree CFR iteration over the level-ordered layout (layout.hpp).
 //
-//   k_topdown   depth l -> l+1: counterfactual reaches of the decision children (Eq. 2 / Eq. 13,
+//   top-down    depth l -> l+1: counterfactual reaches of the decision children (Eq. 2 / Eq. 13,
 //               the top-down recurrence for Pi-check) and, for the infosets whose shallowest depth
 //               is l, the own reach pi_i(h) (Eq. 4 restricted to the acting player).
-//   k_bottomup  depth l: node values u(d) = sum_a sigma(h,a) u(child_a) (Eq. 1 / Eq. 11) and the
+//   bottom-up   depth l: node values u(d) = sum_a sigma(h,a) u(child_a) (Eq. 1 / Eq. 11) and the
 //               instantaneous regret scatter r~(h,a) += pi-check(d) (u_p(child_a) - u_p(d)) (Eq. 7,
 //               summed over the nodes of h as in Eq. 3 and Eq. 6; the vector form of Section 3.2.3).
-//   k_update    per infoset: R += r~ (Eq. 8 / Eq. 15 as a cumulative sum; CFR+ clips at 0),
+//   update      per infoset: R += r~ (Eq. 8 / Eq. 15 as a cumulative sum; CFR+ clips at 0),
 //               S += w_T pi_i(h) sigma (Eq. 10 / Eq. 14 numerator), sigma' = regret matching (Eq. 9).
 //
-// Per decision node the tree layout costs dfirst/tfirst/dinfo/kmask (4 B each);
-// the infoset tables (qbase, iplayer) and the strategy sigma are small and stay L2-resident.
+// One kernel per depth and step; one iteration's launches are captured into a CUDA graph.  The step
+// bodies are __device__ functions; their template flag C selects L1-bypassing loads for callers that
+// read data written earlier in the same launch (the kernels here read with ordinary cached loads).
+// Per decision node the layout costs dfirst/tfirst/kmask/qp (4 B each); the infoset tables and the
+// strategy sigma are small and mostly L2-resident.
 #pragma once
 
 #include <cstdint>
@@ -27,11 +30,57 @@ __device__ __forceinline__ bool is_terminal(uint32_t m, const uint32_t *wbits, i
 __device__ __forceinline__ double madd(double acc, double a, double b) { return __dadd_rn(acc, __dmul_rn(a, b)); }
 __device__ __forceinline__ float madd(float acc, float a, float b) { return fmaf(a, b, acc); }
 
+// Load of data written during the current launch (C = true: through L2, bypassing a possibly
+// stale L1 line of this SM).
+template <bool C, typename T>
+__device__ __forceinline__ T ldm(const T *p) {
+    if constexpr (C) return __ldcg(p);
+    else return *p;
+}
+
+// Per-node word qp (layout.hpp): the infoset's first slot, a wide flag and the acting player.
+__device__ __forceinline__ int32_t qp_base(uint32_t w) { return (int32_t)(w & 0x1fffffffu); }
+__device__ __forceinline__ bool qp_wide(uint32_t w) { return (w >> 29) & 1u; }
+__device__ __forceinline__ int qp_player(uint32_t w) { return (int)(w >> 30); }
+
+// Number of terminal children among actions 0..a-1 of a node whose mask words are wb.
+__device__ __forceinline__ int terminals_before(const uint32_t *wb, int a) {
+    int n = __popc(wb[a >> 5] & ((1u << (a & 31)) - 1u));
+    for (int w = 0; w < (a >> 5); ++w) n += __popc(wb[w]);
+    return n;
+}
+
+// Exact float -> double by bit manipulation (integer pipe); zero keeps its sign, and subnormal,
+// infinite or NaN inputs take the hardware conversion.  GB300's FP64 pipe is narrow, so the update
+// keeps it for the two FP64 additions.
+__device__ __forceinline__ double widen(float x) {
+    const uint32_t b = __float_as_uint(x);
+    if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)x;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// Sum over the block (every thread gets it); scratch32 holds one value per warp.
+template <typename real>
+__device__ __forceinline__ real block_sum(real v, real *scratch32) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) scratch32[threadIdx.x >> 5] = v;
+    __syncthreads();
+    real s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += scratch32[w];
+    __syncthreads();
+    return s;
+}
+
 template <typename real>
 struct DevTree {
     const int32_t *dfirst, *tfirst, *dinfo;
     const uint32_t *kmask;     // terminal-child mask, or offset into wbits when |A| > 32
     const uint32_t *wbits;
+    const uint32_t *qp;        // per node: infoset's first slot | wide << 29 | player << 30
     const real *util;          // u(t, 1) per terminal
     const int32_t *qbase;      // [H + 1]
     const int8_t *iplayer;     // [H]
@@ -48,66 +97,312 @@ struct DevTree {
     const int32_t *hnode_start, *hnode;
 };
 
-template <typename real>
-__global__ void __launch_bounds__(256) k_topdown(DevTree<real> t, int32_t j0, int32_t j1, int32_t nblk_nodes,
-                                                 int32_t h0, int32_t h1, int32_t bump) {
-    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
-    if ((int32_t)blockIdx.x < nblk_nodes) {
-        const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-        if (j >= j1) return;
-        int32_t c = t.dfirst[j];
-        if (c == t.dfirst[j + 1]) return;                 // no decision children
-        const int32_t h = t.dinfo[j];
-        const int p = t.iplayer[h];
-        const int32_t qb = t.qbase[h];
-        const int na = t.qbase[h + 1] - qb;
-        const uint32_t m = t.kmask[j];
-        const real r1 = t.reach1[j], r2 = t.reach2[j];
-        for (int a = 0; a < na; ++a) {
-            if (is_terminal(m, t.wbits, na, a)) continue;
-            const real s = t.sigma[qb + a];
-            t.reach1[c] = p == 1 ? r1 : r1 * s;
-            t.reach2[c] = p == 2 ? r2 : r2 * s;
-            ++c;
+// Nodes with up to kUnroll actions take a fully unrolled path in which every child-value and strategy
+// load is issued before any is used.  The operations and their order are those of the general loop.
+constexpr int kUnroll = 8;
+
+// ---- step bodies ---------------------------------------------------------------------------------
+
+// Own reach of infoset h (Eq. 4 for its acting player): the parent sequence's own reach times sigma.
+template <typename real, bool C>
+__device__ __forceinline__ void own_infoset(const DevTree<real> &t, int32_t h) {
+    if (t.iplayer[h] == 0) return;
+    const int32_t ps = t.pseq[h];
+    t.own[h] = ps < 0 ? real(1) : ldm<C>(t.own + t.pseq_h[h]) * ldm<C>(t.sigma + ps);
+}
+
+// Top-down step of decision node j: reaches of its decision children.
+// kSkipWide: nodes with more than 32 actions are left to td_wide.
+template <typename real, bool kSkipWide, bool C>
+__device__ __forceinline__ void td_node(const DevTree<real> &t, int32_t j) {
+    int32_t c = t.dfirst[j];
+    const int32_t nd = t.dfirst[j + 1] - c;
+    if (nd == 0) return;                                  // no decision children
+    const uint32_t w = t.qp[j];
+    if (kSkipWide && qp_wide(w)) return;
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
+    const uint32_t m = t.kmask[j];
+    const real r1 = ldm<C>(t.reach1 + j), r2 = ldm<C>(t.reach2 + j);
+    if (!qp_wide(w)) {
+        const int na = nd + __popc(m);
+        if (na <= kUnroll) {
+            real s[kUnroll];
+#pragma unroll
+            for (int a = 0; a < kUnroll; ++a) s[a] = a < na ? ldm<C>(t.sigma + qb + a) : real(0);
+#pragma unroll
+            for (int a = 0; a < kUnroll; ++a) {
+                if (a < na && !((m >> a) & 1u)) {
+                    t.reach1[c] = p == 1 ? r1 : r1 * s[a];
+                    t.reach2[c] = p == 2 ? r2 : r2 * s[a];
+                    ++c;
+                }
+            }
+            return;
         }
-    } else {
-        const int32_t h = h0 + (int32_t)((blockIdx.x - nblk_nodes) * blockDim.x + threadIdx.x);
-        if (h >= h1 || t.iplayer[h] == 0) return;
-        const int32_t ps = t.pseq[h];
-        t.own[h] = ps < 0 ? real(1) : t.own[t.pseq_h[h]] * t.sigma[ps];
+    }
+    const int na = nd + (t.tfirst[j + 1] - t.tfirst[j]);
+    for (int a = 0; a < na; ++a) {
+        if (is_terminal(m, t.wbits, na, a)) continue;
+        const real s = ldm<C>(t.sigma + qb + a);
+        t.reach1[c] = p == 1 ? r1 : r1 * s;
+        t.reach2[c] = p == 2 ? r2 : r2 * s;
+        ++c;
     }
 }
 
-// kDet = false: the regret contributions are added to inst with atomics (order unspecified).
+// Bottom-up step of decision node j.
+// kDet = false: the regret contributions are added to inst with atomics (order unspecified), and
+// nodes with more than 32 actions are left to bu_wide.
 // kDet = true: they are stored per edge and k_update sums them per infoset in depth-first node
-// order, which makes the result independent of scheduling.
-template <typename real, bool kDet>
-__global__ void __launch_bounds__(256) k_bottomup(DevTree<real> t, int32_t j0, int32_t j1) {
-    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (j >= j1) return;
-    const int32_t h = t.dinfo[j];
-    const int p = t.iplayer[h];
-    const int32_t qb = t.qbase[h];
-    const int na = t.qbase[h + 1] - qb;
+// order, which makes the result independent of scheduling; every node is summed sequentially.
+template <typename real, bool kDet, bool C>
+__device__ __forceinline__ void bu_node(const DevTree<real> &t, int32_t j) {
+    const uint32_t w = t.qp[j];
+    if (!kDet && qp_wide(w)) return;
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
     const uint32_t m = t.kmask[j];
     const int32_t c0 = t.dfirst[j], t0 = t.tfirst[j];
+    const int32_t nd = t.dfirst[j + 1] - c0;
+    const int na = qp_wide(w) ? nd + (t.tfirst[j + 1] - t0) : nd + __popc(m);
+    real *out = kDet ? t.contrib + (c0 + t0 - 1) : nullptr;
+    if (na <= kUnroll) {
+        real v[kUnroll], s[kUnroll];
+        int kt = 0, kd = 0;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a) {
+            if (a < na) {
+                const bool term = (m >> a) & 1u;
+                v[a] = term ? t.util[t0 + kt] : ldm<C>(t.u + c0 + kd);
+                kt += term;
+                kd += !term;
+                s[a] = ldm<C>(t.sigma + qb + a);
+            }
+        }
+        real ud = 0;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a)
+            if (a < na) ud = madd(ud, s[a], v[a]);
+        t.u[j] = ud;
+        if (p == 0) return;
+        const real wr = p == 1 ? ldm<C>(t.reach1 + j) : -ldm<C>(t.reach2 + j);   // u_2 = -u_1
+        if (!kDet && wr == real(0)) return;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a) {
+            if (a < na) {
+                if (kDet) out[a] = wr * (v[a] - ud);
+                else atomicAdd(&t.inst[qb + a], wr * (v[a] - ud));
+            }
+        }
+        return;
+    }
     real ud = 0;
     int32_t c = c0, tt = t0;
     for (int a = 0; a < na; ++a) {
-        const real v = is_terminal(m, t.wbits, na, a) ? t.util[tt++] : t.u[c++];
-        ud = madd(ud, t.sigma[qb + a], v);
+        const real v = is_terminal(m, t.wbits, na, a) ? t.util[tt++] : ldm<C>(t.u + c++);
+        ud = madd(ud, ldm<C>(t.sigma + qb + a), v);
     }
     t.u[j] = ud;
     if (p == 0) return;
-    const real w = p == 1 ? t.reach1[j] : -t.reach2[j];   // u_2 = -u_1
-    if (!kDet && w == real(0)) return;
+    const real wr = p == 1 ? ldm<C>(t.reach1 + j) : -ldm<C>(t.reach2 + j);
+    if (!kDet && wr == real(0)) return;
     c = c0; tt = t0;
-    real *out = kDet ? t.contrib + (c0 + t0 - 1) : nullptr;
     for (int a = 0; a < na; ++a) {
-        const real v = is_terminal(m, t.wbits, na, a) ? t.util[tt++] : t.u[c++];
-        if (kDet) out[a] = w * (v - ud);
-        else atomicAdd(&t.inst[qb + a], w * (v - ud));
+        const real v = is_terminal(m, t.wbits, na, a) ? t.util[tt++] : ldm<C>(t.u + c++);
+        if (kDet) out[a] = wr * (v - ud);
+        else atomicAdd(&t.inst[qb + a], wr * (v - ud));
     }
+}
+
+// Top-down step of a node with more than 32 actions, shared by the threads of a block.
+template <typename real, bool C>
+__device__ __forceinline__ void td_wide(const DevTree<real> &t, int32_t j) {
+    const uint32_t w = t.qp[j];
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
+    const uint32_t *wb = t.wbits + t.kmask[j];
+    const int32_t d0 = t.dfirst[j];
+    const int na = (t.dfirst[j + 1] - d0) + (t.tfirst[j + 1] - t.tfirst[j]);
+    const real r1 = ldm<C>(t.reach1 + j), r2 = ldm<C>(t.reach2 + j);
+    for (int a = threadIdx.x; a < na; a += blockDim.x) {
+        if ((wb[a >> 5] >> (a & 31)) & 1u) continue;
+        const int32_t c = d0 + (a - terminals_before(wb, a));
+        const real s = ldm<C>(t.sigma + qb + a);
+        t.reach1[c] = p == 1 ? r1 : r1 * s;
+        t.reach2[c] = p == 2 ? r2 : r2 * s;
+    }
+}
+
+template <typename real, bool C>
+__device__ __forceinline__ real wide_child_value(const DevTree<real> &t, const uint32_t *wb, int32_t d0, int32_t t0,
+                                                 int a) {
+    const int tb = terminals_before(wb, a);
+    return ((wb[a >> 5] >> (a & 31)) & 1u) ? t.util[t0 + tb] : ldm<C>(t.u + d0 + (a - tb));
+}
+
+// Bottom-up step of a node with more than 32 actions, shared by the threads of a block (all of which
+// must call it).
+template <typename real, bool C>
+__device__ __forceinline__ void bu_wide(const DevTree<real> &t, int32_t j, real *scratch32) {
+    const uint32_t w = t.qp[j];
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
+    const uint32_t *wb = t.wbits + t.kmask[j];
+    const int32_t d0 = t.dfirst[j], t0 = t.tfirst[j];
+    const int na = (t.dfirst[j + 1] - d0) + (t.tfirst[j + 1] - t0);
+    real part = 0;
+    for (int a = threadIdx.x; a < na; a += blockDim.x)
+        part = madd(part, ldm<C>(t.sigma + qb + a), wide_child_value<real, C>(t, wb, d0, t0, a));
+    const real ud = block_sum(part, scratch32);
+    if (threadIdx.x == 0) t.u[j] = ud;
+    if (p == 0) return;
+    const real wr = p == 1 ? ldm<C>(t.reach1 + j) : -ldm<C>(t.reach2 + j);
+    if (wr == real(0)) return;
+    for (int a = threadIdx.x; a < na; a += blockDim.x)
+        atomicAdd(&t.inst[qb + a], wr * (wide_child_value<real, C>(t, wb, d0, t0, a) - ud));
+}
+
+// ---- per-infoset update, FP32 mode: a tile of infosets staged through shared memory --------------
+// A tile is a run of player infosets whose slots qbase[h0] .. qbase[h1] fit kTileQ (or a single wider
+// infoset).  Slots are read and written with consecutive threads on consecutive slots; only the
+// positive-regret sums run per infoset, from shared memory.  The two FP64 accumulations stay FP64
+// (R += r~, S += w pi_i sigma); regret matching itself runs in FP32, the strategy's precision.
+// All threads of the block must call it.
+
+constexpr int kTileQ = 2048;
+
+template <bool C>
+__device__ __forceinline__ void update_tile(const DevTree<float> &t, int32_t h0, int32_t h1, bool plus, float w,
+                                            float *s_own, float *s_pos, float *s_red) {
+    const int32_t qs = t.qbase[h0];
+    const int32_t nq = t.qbase[h1] - qs;
+    if (nq > kTileQ) {                // a single infoset wider than a tile: the block shares its actions
+        const float wo = w * ldm<C>(t.own + h0);
+        float part = 0.f;
+        for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) {
+            const int32_t q = qs + i;
+            double r = ldm<C>(t.R + q) + widen(ldm<C>(t.inst + q));
+            if (plus) r = r > 0.0 ? r : 0.0;
+            t.R[q] = r;
+            t.S[q] = ldm<C>(t.S + q) + widen(wo * ldm<C>(t.sigma + q));
+            part += r > 0.0 ? (float)r : 0.f;
+        }
+        const float sum = block_sum(part, s_red);   // (its barriers also order the R writes above)
+        if (sum >= 1e-30f || sum == 0.f) {
+            for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) {
+                const double r = ldm<C>(t.R + qs + i);
+                t.sigma[qs + i] = sum > 0.f ? (r > 0.0 ? (float)r : 0.f) * (1.f / sum) : 1.f / (float)nq;
+            }
+        } else {                          // sums below FP32 range: normalise in FP64
+            double pos = 0.0;
+            for (int32_t i = 0; i < nq; ++i) pos += fmax(ldm<C>(t.R + qs + i), 0.0);
+            for (int32_t i = threadIdx.x; i < nq; i += blockDim.x)
+                t.sigma[qs + i] = (float)(fmax(ldm<C>(t.R + qs + i), 0.0) / pos);
+        }
+        __syncthreads();
+        return;
+    }
+    for (int32_t h = h0 + (int32_t)threadIdx.x; h < h1; h += blockDim.x) {
+        const float o = ldm<C>(t.own + h);
+        for (int32_t q = t.qbase[h]; q < t.qbase[h + 1]; ++q) s_own[q - qs] = o;
+    }
+    __syncthreads();
+    for (int32_t i0 = threadIdx.x; i0 < nq; i0 += 4 * 256) {   // four slots per thread, loads first
+        double rr[4];
+        float in[4], sg[4], inc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int32_t i = i0 + k * 256;
+            if (i < nq) { rr[k] = ldm<C>(t.R + qs + i); in[k] = ldm<C>(t.inst + qs + i); sg[k] = ldm<C>(t.sigma + qs + i); }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int32_t i = i0 + k * 256;
+            if (i >= nq) continue;
+            const double r0 = rr[k] + widen(in[k]);
+            const bool positive = __double_as_longlong(r0) > 0;  // r0 > 0 without an FP64 compare
+            const double r = plus && !positive ? 0.0 : r0;
+            t.R[qs + i] = r;
+            s_pos[i] = positive ? __double2float_rn(r) : 0.f;
+            inc[k] = w * s_own[i] * sg[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {                            // nothing accrues where own reach or sigma is 0
+            const int32_t i = i0 + k * 256;
+            if (i < nq && inc[k] != 0.f) rr[k] = ldm<C>(t.S + qs + i);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int32_t i = i0 + k * 256;
+            if (i < nq && inc[k] != 0.f) t.S[qs + i] = rr[k] + widen(inc[k]);
+        }
+    }
+    __syncthreads();
+    for (int32_t h = h0 + (int32_t)threadIdx.x; h < h1; h += blockDim.x) {
+        const int32_t a0 = t.qbase[h] - qs, na = t.qbase[h + 1] - t.qbase[h];
+        float sum = 0.f;
+        for (int k = 0; k < na; ++k) sum += s_pos[a0 + k];
+        float f;
+        if (sum >= 1e-30f) {
+            f = 1.f / sum;
+        } else if (sum > 0.f) {           // sums below FP32 range: normalise in FP64 (R is visible here)
+            double pos = 0.0;
+            for (int k = 0; k < na; ++k) pos += fmax(ldm<C>(t.R + qs + a0 + k), 0.0);
+            for (int k = 0; k < na; ++k) s_pos[a0 + k] = (float)(fmax(ldm<C>(t.R + qs + a0 + k), 0.0) / pos);
+            f = 1.f;
+        } else {
+            f = -1.f / (float)na;         // no positive regret: uniform (Eq. 9)
+        }
+        for (int k = 0; k < na; ++k) s_own[a0 + k] = f;
+    }
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) {
+        const float f = s_own[i];
+        t.sigma[qs + i] = f >= 0.f ? s_pos[i] * f : -f;
+    }
+    __syncthreads();
+}
+
+// ---- one kernel per depth and step ----------------------------------------------------------------
+
+// Top-down from depth l (blocks [0, nblk_nodes): one thread per decision node of depth l) and, in the
+// remaining blocks, the own reach of the infosets whose shallowest depth is l.
+template <typename real, bool kSkipWide>
+__global__ void __launch_bounds__(256) k_topdown(DevTree<real> t, int32_t j0, int32_t j1, int32_t nblk_nodes,
+                                                 int32_t h0, int32_t h1, int32_t bump) {
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
+    if ((int32_t)blockIdx.x >= nblk_nodes) {
+        const int32_t h = h0 + (int32_t)((blockIdx.x - nblk_nodes) * blockDim.x + threadIdx.x);
+        if (h < h1) own_infoset<real, false>(t, h);
+        return;
+    }
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j < j1) td_node<real, kSkipWide, false>(t, j);
+}
+
+template <typename real, bool kDet>
+__global__ void __launch_bounds__(256) k_bottomup(DevTree<real> t, int32_t j0, int32_t j1) {
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j < j1) bu_node<real, kDet, false>(t, j);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) k_topdown_wide(DevTree<real> t, const int32_t *wide, int32_t w0) {
+    td_wide<real, false>(t, wide[w0 + blockIdx.x]);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) k_bottomup_wide(DevTree<real> t, const int32_t *wide, int32_t w0) {
+    __shared__ real s_red[32];
+    bu_wide<real, false>(t, wide[w0 + blockIdx.x], s_red);
+}
+
+__global__ void __launch_bounds__(256) k_update_tiled(DevTree<float> t, const int32_t *tiles, int32_t plus,
+                                                      int32_t linear) {
+    __shared__ float s_own[kTileQ], s_pos[kTileQ], s_red[32];
+    update_tile<false>(t, tiles[blockIdx.x], tiles[blockIdx.x + 1], plus != 0, linear ? (float)*t.iter : 1.f, s_own,
+                       s_pos, s_red);
 }
 
 template <typename real>
@@ -120,6 +415,7 @@ __device__ __forceinline__ void regret_match(real *sigma, const double *R, int32
     }
 }
 
+// Per-infoset update, one thread per infoset, FP64 operations in the oracle's order (FP64 mode).
 template <typename real, bool kDet>
 __global__ void __launch_bounds__(256) k_update(DevTree<real> t, int32_t H, int32_t plus, int32_t linear) {
     const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -144,6 +440,8 @@ __global__ void __launch_bounds__(256) k_update(DevTree<real> t, int32_t H, int3
     }
     regret_match(t.sigma, t.R, qb, na);
 }
+
+// ---- state access -----------------------------------------------------------------------------------
 
 // sigma := regret matching of R for every player infoset (uniform when R = 0: sigma^(1)).
 template <typename real>

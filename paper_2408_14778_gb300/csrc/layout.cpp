@@ -139,7 +139,9 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
     order[0] = (int32_t)root;
     int64_t head = 0, tail = 1;
     int64_t nd_proc = 0, dq = 0, tq = 0;     // decision nodes processed; decision/terminal nodes enqueued
-    int32_t nh = 0, depth = 0;
+    int32_t Hp = 0;                          // player infosets take internal ids [0, Hp), chance ones [Hp, H)
+    for (int32_t h = 0; h < H; ++h) Hp += g->infoset_player[h] > 0;
+    int32_t nh = 0, nhc = 0, depth = 0;
     if (g->infoset[root] >= 0) {
         dq = 1;
         if (build) Lo.dnode_user.push_back((int32_t)root);
@@ -157,7 +159,11 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
             if (hu < 0) continue;
             if (!level_has_decision) {
                 level_has_decision = true;
-                if (build) { Lo.dlevel.push_back((int32_t)nd_proc); Lo.hlevel.push_back(nh); }
+                if (build) {
+                    Lo.dlevel.push_back((int32_t)nd_proc);
+                    Lo.hlevel.push_back(nh);
+                    Lo.wlevel.push_back((int32_t)Lo.wide.size());
+                }
             }
             const int p = g->infoset_player[hu];
             if (p > 0) {
@@ -168,9 +174,10 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
                                 "imperfect recall: infoset %d holds nodes with different own histories of player %d "
                                 "(e.g. node %d)", hu, p, v);
             }
-            if (hmap[hu] < 0) { hmap[hu] = nh++; hlvl[hu] = depth; }
+            if (hmap[hu] < 0) { hmap[hu] = p > 0 ? nh++ : Hp + nhc++; hlvl[hu] = depth; }
             else if (hlvl[hu] != depth) single_level = false;
             const int32_t na = g->infoset_num_actions[hu];
+            if (build && na > 32) Lo.wide.push_back((int32_t)nd_proc);
             uint32_t mask = 0;
             size_t woff = 0;
             if (build && na > 32) {
@@ -221,10 +228,13 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
     Lo.single_level = single_level;
     Lo.dlevel.push_back((int32_t)Lo.Nd);
     Lo.hlevel.push_back(nh);
+    Lo.wlevel.push_back((int32_t)Lo.wide.size());
     Lo.dfirst.push_back((int32_t)Lo.Nd);
     Lo.tfirst.push_back((int32_t)Lo.Nt);
-    // infosets without nodes go last
-    for (int32_t h = 0; h < H; ++h) if (hmap[h] < 0) hmap[h] = nh++;
+    Lo.Hp = Hp;
+    // infosets without nodes follow the others of their kind
+    for (int32_t h = 0; h < H; ++h)
+        if (hmap[h] < 0) hmap[h] = g->infoset_player[h] > 0 ? nh++ : Hp + nhc++;
     Lo.h_int2user.assign((size_t)H, 0);
     for (int32_t h = 0; h < H; ++h) Lo.h_int2user[(size_t)hmap[h]] = h;
     Lo.qbase.assign((size_t)H + 1, 0);
@@ -258,6 +268,16 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
             Lo.pseq[(size_t)hi] = q_user2int[(size_t)rep[hu]];
             Lo.pseq_h[(size_t)hi] = hmap[(size_t)q2h_user[(size_t)rep[hu]]];
         }
+    }
+    // Per decision node, its infoset's first slot, a wide flag and the acting player in one word, so
+    // the iteration kernels need no dependent lookup through the infoset tables.
+    if (Q >= ((int64_t)1 << 29))
+        return fail(err, CFR_ERR_UNSUPPORTED, "too many infoset-action pairs (%lld; at most 2^29)", (long long)Q);
+    Lo.qp.resize((size_t)Lo.Nd);
+    for (int64_t j = 0; j < Lo.Nd; ++j) {
+        const int32_t hi = Lo.dinfo[(size_t)j];
+        const uint32_t wide = Lo.qbase[(size_t)hi + 1] - Lo.qbase[(size_t)hi] > 32 ? 1u : 0u;
+        Lo.qp[(size_t)j] = (uint32_t)Lo.qbase[(size_t)hi] | (wide << 29) | ((uint32_t)Lo.iplayer[(size_t)hi] << 30);
     }
     if (!infoset_lists) return CFR_OK;
 

@@ -11,8 +11,9 @@
 //     action order).  A node with more than 32 actions instead stores in kmask[j] the offset of
 //     its ceil(|A|/32) mask words in the side table wbits.  dlevel[l] .. dlevel[l+1] are the
 //     decision nodes of depth l.
-//   * Infosets get internal ids in order of first appearance in that order, so they are sorted by
-//     their shallowest depth; qbase[h] .. qbase[h+1] are infoset h's (infoset, action) slots
+//   * Player infosets get internal ids [0, Hp) in order of first appearance in that order, so they
+//     are sorted by their shallowest depth; chance infosets follow.  qbase[h] .. qbase[h+1] are
+//     infoset h's (infoset, action) slots
 //     (the mask M^(H+,Q+)), and the slot of child a of j is qbase[dinfo[j]] + a (M^(Q+,V)).
 //   * pseq[h] is the slot of the acting player's last own (infoset, action) above h (-1 if none);
 //     under perfect recall it is the same for every node of h and gives the own reach recursion
@@ -38,8 +39,12 @@ struct Layout {
     std::vector<int32_t> dinfo;            // [Nd] internal infoset
     std::vector<uint32_t> kmask;           // [Nd] terminal-child mask, or offset into wbits
     std::vector<uint32_t> wbits;           // mask words of nodes with > 32 actions
+    std::vector<uint32_t> qp;              // [Nd] qbase[dinfo[j]] | (|A| > 32) << 29 | player << 30
     std::vector<int32_t> dlevel;           // [L + 1]
-    std::vector<int32_t> hlevel;           // [L + 1]: infosets whose shallowest depth is l
+    std::vector<int32_t> hlevel;           // [L + 1]: player infosets whose shallowest depth is l
+    int32_t Hp = 0;                        // player infosets: internal ids [0, Hp); chance ones [Hp, H)
+    std::vector<int32_t> wide;             // decision nodes with more than 32 actions, by depth
+    std::vector<int32_t> wlevel;           // [L + 1]: wide[wlevel[l] .. wlevel[l+1]) are at depth l
     std::vector<double> util;              // [Nt] u(t, 1)
     std::vector<int32_t> qbase;            // [H + 1] internal
     std::vector<int8_t> iplayer;           // [H]

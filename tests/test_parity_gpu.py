@@ -270,3 +270,24 @@ def test_bad_arguments_raise():
     assert L.cfr_average_strategy(s.handle, buf.ctypes.data, 2) == cfr.CFR_ERR_INVALID
     cfr.cfr_iterate(s, 2)                                     # still usable after argument errors
     cfr.cfr_synchronize(s)
+
+
+@pytest.mark.parametrize("precision", [cfr.CFR_FP64, cfr.CFR_FP32])
+def test_phase_times_run_a_real_iteration(precision):
+    g = gamegen.config("rank13_depth10", seed=6, target_nodes=None, p_cont=0.6)
+    o = oracle.Oracle(g)
+    s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=precision)
+    o.iterate(2, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+    st = o.state()                                            # (FP32 is compared one step from FP64 state)
+    cfr.cfr_set_state(s, st["cum_regret"], st["strat_sum"], st["iteration"])
+    ph = cfr.cfr_phase_times(s)                               # the third iteration, kernel by kernel
+    o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+    compare_state(s, o, TOL64 if precision == cfr.CFR_FP64 else TOL32, g)
+    info = cfr.cfr_get_info(s)
+    assert info["iteration"] == 3
+    total = ph["topdown_bytes"].sum() + ph["bottomup_bytes"].sum() + ph["update_bytes"]
+    # every node but the root is some depth's child: the phases add up to the iteration's model less
+    # the root's share as a child (12 bytes in FP32 mode, 24 in FP64 mode)
+    assert 0 <= info["bytes_per_iteration"] - total <= 24
+    assert np.all(ph["bottomup_us"] > 0) and ph["update_us"] > 0
+    assert len(ph["topdown_us"]) == len(ph["bottomup_us"]) == info["num_levels"]
