@@ -33,7 +33,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="holdem169_depth12")
@@ -152,16 +152,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, precision: str):
-    """DRAM bytes per iteration from the committed ncu summary, if taken on the current kernels."""
+def recorded_traffic(workload: str, precision: str, phase: str):
+    """ncu DRAM bytes per launch of the given phase's kernel, from the committed summary, if it was taken on the
+    current kernel sources."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None
     want = kernel_source_hash()
     for line in open(p):
+        if line.startswith("#"):
+            continue
         kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
-        if kv.get("kernels_sha") == want and kv.get("workload") == workload and kv.get("precision") == precision:
-            return float(kv["dram_bytes_per_iteration"])
+        if (kv.get("kernels_sha") == want and kv.get("workload") == workload and kv.get("precision") == precision
+                and kv.get("phase") == phase.replace(" ", "_")):
+            return float(kv["dram_bytes_per_launch"])
     return None
 
 
@@ -283,7 +287,7 @@ def run_ours(args, world, rank, local):
     dom = by[k] / (us[k] * 1e-6) / 1e9
     achieved = info["bytes_per_iteration"] / iter_s / 1e9
     roofline = {"bound": "hbm", "achieved": dom, "peak": peak, "unit": "GB/s", "frac": dom / peak,
-                "traffic": recorded_traffic(args.workload, args.precision),
+                "traffic": recorded_traffic(args.workload, args.precision, names[k]),
                 "kernel": f"{names[k]} ({'k_update_tiled' if names[k] == 'update' else 'k_bottomup' if 'bottom' in names[k] else 'k_topdown'})",
                 "algorithmic_bytes_per_launch": float(by[k]), "launch_us": float(us[k]), "peak_source": peak_src,
                 "iteration": {"achieved": achieved, "frac": achieved / peak,
