@@ -42,6 +42,8 @@ def parse():
                     help="same workload family rescaled to about this many nodes (profiling captures)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--variant", choices=["plus", "vanilla"], default="plus")
+    ap.add_argument("--fuse-levels", type=int, default=-1,
+                    help="FP32 mode: deepest depths run by the fused kernel (-1 automatic, 0 none)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -206,7 +208,9 @@ def workload_config(args, g, info=None):
          "update": "simultaneous", "l2": "resident state larger than L2 (no flush needed)"}
     if info:
         c.update(decision_nodes=info["num_decision"], terminals=info["num_terminal"], infosets=info["num_infosets"],
-                 infoset_actions=info["num_q"], levels=info["num_levels"], device_bytes=info["device_bytes"])
+                 infoset_actions=info["num_q"], levels=info["num_levels"], device_bytes=info["device_bytes"],
+                 fused_from_depth=info["fused_from_depth"], fused_tiles=info["fused_tiles"],
+                 kernels_per_iteration=info["kernels_per_iteration"])
     return c
 
 
@@ -250,7 +254,7 @@ def run_ours(args, world, rank, local):
     variant = cfr.CFR_PLUS if args.variant == "plus" else cfr.CFR_VANILLA
     precision = cfr.CFR_FP32 if args.precision == "fp32" else cfr.CFR_FP64
     g = gamegen.config(args.workload, seed=args.seed, target_nodes=args.nodes)
-    s = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local)
+    s = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local, fuse_levels=args.fuse_levels)
     info = cfr.cfr_get_info(s)
     stream = torch.cuda.current_stream(local)
     cfr.cfr_iterate(s, args.warmup)
@@ -278,17 +282,19 @@ def run_ours(args, world, rank, local):
     # solver's stream (each is a real iteration), averaged; the dominant phase gives the roofline.
     launches = cfr.cfr_get_info(s)["kernel_launches"]
     ph = [cfr.cfr_phase_times(s) for _ in range(5)]
-    names = [f"top-down depth {l}" for l in range(len(ph[0]["topdown_us"]))] + \
-            [f"bottom-up depth {l}" for l in reversed(range(len(ph[0]["bottomup_us"])))] + ["update"]
-    us = np.mean([np.concatenate([p["topdown_us"], p["bottomup_us"], [p["update_us"]]]) for p in ph], axis=0)
-    by = np.concatenate([ph[0]["topdown_bytes"], ph[0]["bottomup_bytes"], [ph[0]["update_bytes"]]])
+    names = [p["name"] for p in ph[0]]
+    us = np.mean([[p["us"] for p in run] for run in ph], axis=0)
+    by = np.array([p["bytes"] for p in ph[0]])
+    kernel_of = {cfr.CFR_PHASE_TOPDOWN: "k_topdown", cfr.CFR_PHASE_BOTTOMUP: "k_bottomup", cfr.CFR_PHASE_FUSED: "k_fused",
+                 cfr.CFR_PHASE_OWN: "k_own",
+                 cfr.CFR_PHASE_UPDATE: "k_update_tiled" if args.precision == "fp32" else "k_update"}
     k = int(np.argmax(us))
     peak, peak_src = measured_hbm_peak()
     dom = by[k] / (us[k] * 1e-6) / 1e9
     achieved = info["bytes_per_iteration"] / iter_s / 1e9
     roofline = {"bound": "hbm", "achieved": dom, "peak": peak, "unit": "GB/s", "frac": dom / peak,
                 "traffic": recorded_traffic(args.workload, args.precision, names[k]),
-                "kernel": f"{names[k]} ({'k_update_tiled' if names[k] == 'update' else 'k_bottomup' if 'bottom' in names[k] else 'k_topdown'})",
+                "kernel": f"{names[k]} ({kernel_of[ph[0][k]['kind']]})",
                 "algorithmic_bytes_per_launch": float(by[k]), "launch_us": float(us[k]), "peak_source": peak_src,
                 "iteration": {"achieved": achieved, "frac": achieved / peak,
                               "algorithmic_bytes": info["bytes_per_iteration"]}}
@@ -302,7 +308,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
-        s2 = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local)
+        s2 = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local, fuse_levels=args.fuse_levels)
         for _ in range(args.steps):
             cfr.cfr_iterate(s2, 1)
             cfr.cfr_root_value(s2)

@@ -52,6 +52,8 @@ enum { CFR_SIMULTANEOUS = 0, CFR_ALTERNATING = 1 };
 /* Weight of iteration T in the average strategy: 1 (Eq. 10) or T.  DEFAULT = UNIFORM for vanilla
  * and LINEAR for CFR+. */
 enum { CFR_AVG_DEFAULT = -1, CFR_AVG_UNIFORM = 0, CFR_AVG_LINEAR = 1 };
+/* Phases of one iteration reported by cfr_phase_times. */
+enum { CFR_PHASE_TOPDOWN = 0, CFR_PHASE_BOTTOMUP = 1, CFR_PHASE_FUSED = 2, CFR_PHASE_UPDATE = 3, CFR_PHASE_OWN = 4 };
 
 typedef struct cfr_solver cfr_solver;   /* opaque; owned by the library */
 
@@ -82,6 +84,14 @@ typedef struct {
     cfr_alloc_fn dev_alloc; /* optional device allocator (both or neither) */
     cfr_free_fn dev_free;
     void *alloc_ctx;
+    int32_t fuse_levels;    /* FP32 mode: the deepest depths run as one kernel, tile by tile in shared
+                               memory, with their reaches and values kept on chip.  -1 = automatic
+                               (default), 0 or 1 = none (one kernel per depth and pass), k >= 2 = at
+                               most k depths (fewer where a subtree exceeds a tile or a node has more
+                               than 32 actions).  Ignored in FP64 mode. */
+    int32_t record_nodes;   /* 1: fused depths also write every node's value and reaches to device
+                               memory, so that cfr_get_nodes can return them; 0 (default): they do
+                               not, and cfr_get_nodes returns CFR_ERR_STATE when depths are fused. */
 } cfr_config;
 
 /* Sizes and accounting of a loaded solver. */
@@ -96,10 +106,14 @@ typedef struct {
     int32_t variant, precision, update_mode, avg_weight;
     int64_t iteration;            /* completed iterations T */
     int64_t device_bytes;         /* device memory held by the solver */
-    int64_t bytes_per_iteration;  /* algorithmic bytes of one iteration: 56 Nd + 4 Nt + 44 Q (FP32 mode) or
-                                     96 Nd + 8 Nt + 56 Q (FP64 mode) */
+    int64_t bytes_per_iteration;  /* algorithmic bytes of one iteration, the sum over cfr_phase_times'
+                                     phases; with nothing fused 56 Nd + 4 Nt + 44 Q + 13 Hp - 12 (FP32
+                                     mode) or 96 Nd + 8 Nt + 56 Q + 17 Hp - 24 (FP64 mode), Hp the
+                                     player infosets */
     int32_t kernels_per_iteration;/* kernel launches of one iteration */
     int64_t kernel_launches;      /* kernel launches made by cfr_iterate so far */
+    int32_t fused_from_depth;     /* first depth run by the fused kernel (num_levels: none) */
+    int32_t fused_tiles;          /* thread blocks of the fused kernel that process nodes */
 } cfr_info;
 
 /* Fills *c with defaults: vanilla, FP32, simultaneous, default averaging, current device,
@@ -174,7 +188,8 @@ cfr_status cfr_set_state(cfr_solver *s, const double *cum_regret, const double *
 
 /* Per node of the last iteration, in caller node order ([len] each, len == num_nodes; any pointer
  * may be NULL): u1 = u-check(v, 1) (Eq. 1; the utility at terminals), cf_reach1 = pi-check(v, 1)
- * and cf_reach2 = pi-check(v, 2) (Eq. 2) at decision nodes, NaN at terminals.  Test hook. */
+ * and cf_reach2 = pi-check(v, 2) (Eq. 2) at decision nodes, NaN at terminals.  CFR_ERR_STATE when
+ * depths are fused and the solver was loaded without cfr_config.record_nodes.  Test hook. */
 cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *cf_reach2, int64_t len);
 
 /* Expected payoff of player 1 under the last iteration's profile sigma^(T): u-check(sigma^(T), v_0, 1)
@@ -182,14 +197,18 @@ cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *c
  * the stream (a per-iteration progress read).  0 before the first iteration. */
 cfr_status cfr_root_value(cfr_solver *s, double *u1);
 
-/* Runs ONE iteration (it counts: T advances by 1) as individually launched kernels with CUDA events
- * between its phases, and returns per phase the elapsed time in microseconds (us) and the phase's
- * algorithmic bytes (bytes): top-down from depth 0, 1, ..., num_levels-1, then bottom-up at depth
- * num_levels-1, ..., 0, then the per-infoset update - 2 num_levels + 1 phases (0 for a game without
- * decision nodes).  The bytes add up to cfr_info.bytes_per_iteration.  *nphases receives the count;
- * with us and bytes both NULL only the count is returned (no iteration runs), otherwise len must be
- * at least the count.  Tracing hook. */
-cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t len, int32_t *nphases);
+/* Runs ONE iteration (it counts: T advances by 1) as individually launched kernels on the solver's
+ * stream with CUDA events between its phases, and returns per phase the elapsed time in
+ * microseconds (us), the phase's algorithmic bytes (bytes), its kind (CFR_PHASE_*) and depth (depth;
+ * the first fused depth for CFR_PHASE_FUSED, -1 for the own reaches and the update).  Phases in order:
+ * the own reaches of all infosets (Eq. 4; if there are player infosets - cfr_iterate runs them beside
+ * the node passes), top-down from depth 0, 1, ..., f-1, the fused depths f .. num_levels-1 (if any;
+ * f = cfr_info.fused_from_depth), bottom-up at depth f-1, ..., 0, then the per-infoset update (no phase
+ * at all for a game without decision nodes).  The bytes add up to cfr_info.bytes_per_iteration.
+ * *nphases receives the count; with us, bytes, kind and depth all NULL only the count is returned (no
+ * iteration runs), otherwise len must be at least the count (NULL arrays are skipped).  Tracing hook. */
+cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t *kind, int32_t *depth, int32_t len,
+                           int32_t *nphases);
 
 cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info);
 

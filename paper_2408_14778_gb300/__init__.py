@@ -23,6 +23,7 @@ CFR_VANILLA, CFR_PLUS = 0, 1
 CFR_FP32, CFR_FP64 = 0, 1
 CFR_SIMULTANEOUS, CFR_ALTERNATING = 0, 1
 CFR_AVG_DEFAULT, CFR_AVG_UNIFORM, CFR_AVG_LINEAR = -1, 0, 1
+CFR_PHASE_TOPDOWN, CFR_PHASE_BOTTOMUP, CFR_PHASE_FUSED, CFR_PHASE_UPDATE, CFR_PHASE_OWN = 0, 1, 2, 3, 4
 
 _STATUS_NAMES = {0: "CFR_OK", 1: "CFR_ERR_INVALID", 2: "CFR_ERR_CUDA", 3: "CFR_ERR_OOM", 4: "CFR_ERR_TIMEOUT",
                  5: "CFR_ERR_STATE", 6: "CFR_ERR_UNSUPPORTED"}
@@ -64,6 +65,8 @@ class _Config(ctypes.Structure):
         ("dev_alloc", _ALLOC_FN),
         ("dev_free", _FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
+        ("fuse_levels", ctypes.c_int32),
+        ("record_nodes", ctypes.c_int32),
     ]
 
 
@@ -75,7 +78,7 @@ class _Info(ctypes.Structure):
         ("variant", ctypes.c_int32), ("precision", ctypes.c_int32), ("update_mode", ctypes.c_int32),
         ("avg_weight", ctypes.c_int32), ("iteration", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
         ("bytes_per_iteration", ctypes.c_int64), ("kernels_per_iteration", ctypes.c_int32),
-        ("kernel_launches", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64), ("fused_from_depth", ctypes.c_int32), ("fused_tiles", ctypes.c_int32),
     ]
 
 
@@ -114,7 +117,7 @@ def lib():
         L.cfr_get_nodes.argtypes = [_P, _P, _P, _P, ctypes.c_int64]
         L.cfr_get_info.argtypes = [_P, ctypes.POINTER(_Info)]
         L.cfr_root_value.argtypes = [_P, _P]
-        L.cfr_phase_times.argtypes = [_P, _P, _P, ctypes.c_int32, _P]
+        L.cfr_phase_times.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int32, _P]
         L.cfr_phase_times.restype = ctypes.c_int
         L.cfr_exploitability_static.argtypes = [_P, _P, _P]
         L.cfr_exploitability_static.restype = ctypes.c_int
@@ -194,8 +197,10 @@ class _TorchAllocator:
 
 
 def cfr_load_tree(game, variant=CFR_VANILLA, precision=CFR_FP32, update_mode=CFR_SIMULTANEOUS,
-                  avg_weight=CFR_AVG_DEFAULT, device=None, stream=None, allocator: str = "torch"):
-    """Loads a game and returns a Solver.  stream: None = PyTorch's current stream on the device."""
+                  avg_weight=CFR_AVG_DEFAULT, device=None, stream=None, allocator: str = "torch",
+                  fuse_levels: int = -1, record_nodes: bool = False):
+    """Loads a game and returns a Solver.  stream: None = PyTorch's current stream on the device.
+    fuse_levels / record_nodes: cfr_config's fields of the same names."""
     import torch
 
     if not torch.cuda.is_available():
@@ -207,6 +212,8 @@ def cfr_load_tree(game, variant=CFR_VANILLA, precision=CFR_FP32, update_mode=CFR
     cfg.variant, cfg.precision, cfg.update_mode, cfg.avg_weight = variant, precision, update_mode, avg_weight
     cfg.device = dev
     cfg.cuda_stream = st_handle
+    cfg.fuse_levels = int(fuse_levels)
+    cfg.record_nodes = 1 if record_nodes else 0
     alloc = None
     if allocator == "torch":
         alloc = _TorchAllocator(dev, st_handle)
@@ -290,19 +297,21 @@ def cfr_root_value(s: "Solver") -> float:
     return v.value
 
 
-def cfr_phase_times(s: "Solver") -> dict:
-    """Runs one iteration as individually timed kernels (it counts as an iteration) and returns per
-    phase its time (us) and algorithmic bytes: top-down by depth, bottom-up by depth (deepest
-    first), update."""
+def cfr_phase_times(s: "Solver") -> list:
+    """Runs one iteration as individually timed kernels (it counts as an iteration) and returns its
+    phases in launch order, each a dict: name, kind (CFR_PHASE_*), depth, us and algorithmic bytes."""
     n = ctypes.c_int32()
-    _check(lib().cfr_phase_times(s.handle, None, None, 0, ctypes.byref(n)), s.handle)
+    _check(lib().cfr_phase_times(s.handle, None, None, None, None, 0, ctypes.byref(n)), s.handle)
     if n.value == 0:
-        return {}
+        return []
     us, by = np.zeros(n.value), np.zeros(n.value)
-    _check(lib().cfr_phase_times(s.handle, us.ctypes.data, by.ctypes.data, n.value, ctypes.byref(n)), s.handle)
-    L = (n.value - 1) // 2
-    return dict(topdown_us=us[:L], bottomup_us=us[L:2 * L], update_us=float(us[2 * L]),
-                topdown_bytes=by[:L], bottomup_bytes=by[L:2 * L], update_bytes=float(by[2 * L]))
+    kind, depth = np.zeros(n.value, np.int32), np.zeros(n.value, np.int32)
+    _check(lib().cfr_phase_times(s.handle, us.ctypes.data, by.ctypes.data, kind.ctypes.data, depth.ctypes.data,
+                                 n.value, ctypes.byref(n)), s.handle)
+    names = {CFR_PHASE_TOPDOWN: "top-down depth {}", CFR_PHASE_BOTTOMUP: "bottom-up depth {}",
+             CFR_PHASE_FUSED: "fused depths {}+", CFR_PHASE_UPDATE: "update", CFR_PHASE_OWN: "own reaches"}
+    return [dict(name=names[int(k)].format(int(d)), kind=int(k), depth=int(d), us=float(u), bytes=float(b))
+            for k, d, u, b in zip(kind, depth, us, by)]
 
 
 def cfr_get_info(s: "Solver") -> dict:

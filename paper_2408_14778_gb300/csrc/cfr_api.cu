@@ -15,6 +15,7 @@
 #include "cfr_gb300.h"
 #include "kernels.cuh"
 #include "layout.hpp"
+#include "stream.cuh"
 
 using namespace cfrgb;
 
@@ -23,6 +24,8 @@ namespace {
 thread_local std::string g_thread_err;
 
 constexpr int kBlock = 256;
+constexpr int32_t kFuseAuto = 0;   // fused depths when cfr_config.fuse_levels < 0
+constexpr int32_t kStreamMinNodes = 32768;   // FP32 bottom-up depths this large use k_bottomup_stream
 
 inline int32_t nblocks(int64_t n) { return (int32_t)((n + kBlock - 1) / kBlock); }
 
@@ -47,6 +50,8 @@ struct cfr_solver {
     int device = 0;
     cudaStream_t stream = nullptr;   // borrowed
     cudaStream_t cap = nullptr;      // private, for graph capture
+    cudaStream_t side = nullptr;     // private: the own-reach branch of the captured iteration
+    cudaEvent_t fork = nullptr, join = nullptr;
     // sizes
     int64_t N = 0, Nd = 0, Nt = 0, Q = 0;
     int32_t H = 0, L = 0, max_depth = 0, max_actions = 0;
@@ -62,14 +67,22 @@ struct cfr_solver {
     double *util64 = nullptr, *sigma064 = nullptr, *R = nullptr, *S = nullptr, *stage = nullptr;
     double *br_reach = nullptr, *br_val = nullptr, *br_cfv = nullptr, *avg = nullptr, *br_out = nullptr;
     int64_t *d_iter = nullptr;
+    int *d_err = nullptr;                                 // set by a device-side wait that expired
+    int32_t sb_grid = 0, td_grid = 0;                     // k_bottomup_stream / k_topdown_stream: resident blocks
     void *contrib = nullptr;                              // FP64 mode: per-edge regret contributions
     int32_t *hnode_start = nullptr, *hnode = nullptr;     // FP64 mode: nodes of each infoset, depth-first
     int32_t *wide = nullptr;                              // nodes with more than 32 actions, by depth
     std::vector<int32_t> wlevel;
     std::vector<char> ddepth_children;                    // depth l has a node with a decision child
     std::vector<int64_t> level_children;                  // children of the decision nodes of depth l
+    std::vector<int64_t> level_terminals;                 // terminal children of the decision nodes of depth l
     int32_t *tiles = nullptr;                             // FP32 mode: infoset tiles of k_update_tiled
     int32_t ntiles = 0;
+    // FP32 mode: depths fuse_r .. L-1 run in k_fused (fuse_r == L: none), in fuse_ntiles tiles whose
+    // node ranges per fused depth are fuse_bounds[k][0 .. fuse_ntiles]
+    int32_t fuse_r = 0, fuse_ntiles = 0;
+    int32_t *fuse_bounds = nullptr;
+    bool fuse_tail = false;                               // the last two depths by k_tail (no tiles)
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
     int64_t kernel_launches = 0;
     int64_t iteration = 0;
@@ -163,13 +176,18 @@ DevTree<real> dev_tree(cfr_solver *s) {
 
 // One full-tree iteration, queued on `st` (captured into the solver's graph).  FP64 mode reduces
 // the instantaneous regrets deterministically (k_update sums per-edge contributions in depth-first
-// node order); FP32 mode adds them with atomics.  With `ev` (2 L + 2 events), an event is recorded
-// before the first phase and after each phase: top-down from depth 0 .. L-1, bottom-up at depth
-// L-1 .. 0, update.
+// node order); FP32 mode adds them with atomics, streams large depths through shared memory, and
+// runs the depths fuse_r .. L-1 in one kernel when fusion is on.  The own reaches (k_own, one launch
+// per depth) depend only on sigma and on shallower own reaches: in the graph they run on a branch
+// forked from `st` that joins before the update.  With `ev` (one more than the phases), everything
+// runs on `st` and an event is recorded before the first phase and after each phase: own reaches,
+// top-down from depth 0 .. fuse_r - 1, the fused depths (if any), bottom-up at depth fuse_r - 1 .. 0,
+// update.
 template <typename real>
 cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = nullptr) {
     constexpr bool det = sizeof(real) == sizeof(double);
     DevTree<real> t = dev_tree<real>(s);
+    const int32_t r = det ? s->L : s->fuse_r;
     int ne = 0;
     auto mark = [&]() -> cfr_status {
         if (ev) CK(cudaEventRecord(ev[ne++], st));
@@ -177,14 +195,38 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
     };
     if (!det) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
     TRY(mark());
+    // own reaches, depth by depth
+    const bool branch = ev == nullptr && s->Hp > 0;
+    cudaStream_t os = st;
+    if (branch) {
+        os = s->side;
+        CK(cudaEventRecord(s->fork, st));
+        CK(cudaStreamWaitEvent(os, s->fork, 0));
+    }
     for (int32_t l = 0; l < s->L; ++l) {
-        const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
-        // a depth whose nodes have no decision children (the last one) only needs its own reaches
+        if (h1 > h0) {
+            k_own<real><<<nblocks(h1 - h0), kBlock, 0, os>>>(t, h0, h1);
+            CK_LAUNCH();
+        }
+    }
+    if (branch) CK(cudaEventRecord(s->join, os));
+    if (s->Hp > 0) TRY(mark());
+    for (int32_t l = 0; l < r; ++l) {
+        const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
+        // a depth whose nodes have no decision children (the last one) has no top-down step
         // (depth 0 always launches: its first thread counts the iteration)
-        const int32_t nb = s->ddepth_children[l] || l == 0 ? nblocks(j1 - j0) : 0, nh = nblocks(h1 - h0);
-        if (nb + nh > 0) {
-            k_topdown<real, !det><<<nb + nh, kBlock, 0, st>>>(t, j0, j1, nb, h0, h1, l == 0);
+        if (s->ddepth_children[l] || l == 0) {
+            bool streamed = false;
+            if constexpr (!det) {
+                if (j1 - j0 >= kStreamMinNodes && s->td_grid > 0) {
+                    const int32_t grid = std::min<int32_t>(s->td_grid, (j1 - j0 + kSBN - 1) / kSBN);
+                    k_topdown_stream<<<grid, kSBThreads, sizeof(TDStage) * TopDownTiles::kStages, st>>>(
+                        t, j0, j1, l == 0, s->d_err);
+                    streamed = true;
+                }
+            }
+            if (!streamed) k_topdown<real, !det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1, l == 0);
             CK_LAUNCH();
         }
         const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
@@ -194,9 +236,35 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         }
         TRY(mark());
     }
-    for (int32_t l = s->L - 1; l >= 0; --l) {
+    if constexpr (!det) {
+        if (r < s->L && s->fuse_tail) {
+            const int32_t j0 = s->dlevel[r], j1 = s->dlevel[r + 1];
+            k_tail<<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1, s->cfg.record_nodes != 0, r == 0);
+            CK_LAUNCH();
+            TRY(mark());
+        } else if (r < s->L) {
+            FuseArgs fa;
+            fa.bounds = s->fuse_bounds;
+            fa.ntiles = s->fuse_ntiles;
+            fa.levels = s->L - r;
+            fa.record = s->cfg.record_nodes != 0;
+            fa.bump = r == 0;
+            k_fused<<<s->fuse_ntiles, kBlock, 0, st>>>(t, fa);
+            CK_LAUNCH();
+            TRY(mark());
+        }
+    }
+    for (int32_t l = r - 1; l >= 0; --l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
-        k_bottomup<real, det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1);
+        bool streamed = false;
+        if constexpr (!det) {
+            if (j1 - j0 >= kStreamMinNodes && s->sb_grid > 0) {
+                const int32_t grid = std::min<int32_t>(s->sb_grid, (j1 - j0 + kSBN - 1) / kSBN);
+                k_bottomup_stream<<<grid, kSBThreads, sizeof(SBStage) * kSBStages, st>>>(t, j0, j1, s->d_err);
+                streamed = true;
+            }
+        }
+        if (!streamed) k_bottomup<real, det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1);
         CK_LAUNCH();
         const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
         if (!det && nw > 0) {
@@ -205,6 +273,7 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         }
         TRY(mark());
     }
+    if (branch) CK(cudaStreamWaitEvent(st, s->join, 0));
     const int linear = s->cfg.avg_weight == CFR_AVG_LINEAR;
     if constexpr (det) {
         if (s->Hp > 0) {
@@ -221,23 +290,61 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
     return CFR_OK;
 }
 
-// Algorithmic bytes of each phase, in the order of enqueue_iteration's events (FP32 mode; FP64 mode
-// doubles the value bytes: 32 Nd(l) + 16 Nd(l+1), 40 Nd(l) + 8 C(l), 56 Q):
-//   top-down from depth l:  20 Nd(l) + 8 Nd(l+1)   (node fields and reaches read, child reaches written)
-//   bottom-up at depth l:   24 Nd(l) + 4 C(l)      (node fields, reach, value write; one value per child)
-//   update:                 44 Q                   (r~ read and zeroed, R and S read+written, sigma written)
-// They add up to the iteration's model, 56 Nd + 4 Nt + 44 Q (96 Nd + 8 Nt + 56 Q in FP64 mode), since
-// every node but the root is a child once.
+// First fused depth (L when nothing is fused).
+int32_t fused_from(const cfr_solver *s) { return s->cfg.precision == CFR_FP64 ? s->L : s->fuse_r; }
+
+// Phases of one iteration, in the order of enqueue_iteration's events: kind (CFR_PHASE_*) and depth.
+std::vector<std::pair<int32_t, int32_t>> phases(const cfr_solver *s) {
+    std::vector<std::pair<int32_t, int32_t>> p;
+    if (s->L == 0) return p;
+    const int32_t r = fused_from(s);
+    if (s->Hp > 0) p.push_back({CFR_PHASE_OWN, -1});
+    for (int32_t l = 0; l < r; ++l) p.push_back({CFR_PHASE_TOPDOWN, l});
+    if (r < s->L) p.push_back({CFR_PHASE_FUSED, r});
+    for (int32_t l = r - 1; l >= 0; --l) p.push_back({CFR_PHASE_BOTTOMUP, l});
+    p.push_back({CFR_PHASE_UPDATE, -1});
+    return p;
+}
+
+// Algorithmic bytes of each phase, in the order of phases() (FP32 mode; FP64 mode doubles the value
+// bytes: 17 Hp, 32 Nd(l) + 16 Nd(l+1), 40 Nd(l) + 8 C(l), 56 Q):
+//   own reaches:            13 Hp                  pseq, pseq_h, player read, own written
+//   top-down from depth l:  20 Nd(l) + 8 Nd(l+1)   node fields and reaches read, child reaches written
+//   bottom-up at depth l:   24 Nd(l) + 4 C(l)      node fields, reach, value write; one value per child
+//   last two depths (k_tail, r = L-2):
+//                           28 Nd(r) + 12 Nd(r+1)  node fields and reaches of depth r, value written;
+//                                                  node fields of depth r+1
+//                         + 4 T(r) + 4 T(r+1)      one utility per terminal child
+//   fused depths r..L-1 (k_fused tiles):
+//                           16 Nd(>=r) + 4 T(>=r)  node fields; one utility per terminal child
+//                         + 12 Nd(r)               the tile roots' reaches read and values written
+//   update:                 44 Q                   r~ read and zeroed, R and S read+written, sigma written
+// With nothing fused they add up to 56 Nd + 4 Nt + 44 Q + 13 Hp - 12 (96 Nd + 8 Nt + 56 Q + 17 Hp - 24
+// in FP64 mode), since every node but the root is a child once.  Hp counts the player infosets, C(l)
+// all children of depth l's nodes, T(l) their terminal children.
 std::vector<double> phase_bytes(const cfr_solver *s) {
     const bool f64 = s->cfg.precision == CFR_FP64;
     std::vector<double> b;
     auto nd = [&](int32_t l) -> double { return l < s->L ? (double)(s->dlevel[l + 1] - s->dlevel[l]) : 0.0; };
-    for (int32_t l = 0; l < s->L; ++l) b.push_back(f64 ? 32 * nd(l) + 16 * nd(l + 1) : 20 * nd(l) + 8 * nd(l + 1));
-    for (int32_t l = s->L - 1; l >= 0; --l) {
-        const double children = (double)s->level_children[l];
-        b.push_back(f64 ? 40 * nd(l) + 8 * children : 24 * nd(l) + 4 * children);
+    for (const auto &ph : phases(s)) {
+        const int32_t l = ph.second;
+        if (ph.first == CFR_PHASE_OWN) {
+            b.push_back((f64 ? 17.0 : 13.0) * (double)s->Hp);
+        } else if (ph.first == CFR_PHASE_TOPDOWN) {
+            b.push_back(f64 ? 32 * nd(l) + 16 * nd(l + 1) : 20 * nd(l) + 8 * nd(l + 1));
+        } else if (ph.first == CFR_PHASE_BOTTOMUP) {
+            const double children = (double)s->level_children[l];
+            b.push_back(f64 ? 40 * nd(l) + 8 * children : 24 * nd(l) + 4 * children);
+        } else if (ph.first == CFR_PHASE_FUSED && s->fuse_tail) {
+            b.push_back(28 * nd(l) + 12 * nd(l + 1) + 4 * (double)(s->level_terminals[l] + s->level_terminals[l + 1]));
+        } else if (ph.first == CFR_PHASE_FUSED) {
+            double x = 12 * nd(l);
+            for (int32_t k = l; k < s->L; ++k) x += 16 * nd(k) + 4 * (double)s->level_terminals[k];
+            b.push_back(x);
+        } else {
+            b.push_back((f64 ? 56.0 : 44.0) * (double)s->Q);
+        }
     }
-    b.push_back((f64 ? 56.0 : 44.0) * (double)s->Q);
     return b;
 }
 
@@ -245,9 +352,11 @@ std::vector<double> phase_bytes(const cfr_solver *s) {
 int32_t launches_per_iteration(const cfr_solver *s) {
     if (s->L == 0) return 0;
     const bool det = s->cfg.precision == CFR_FP64;
-    int32_t n = s->L + 1;                                   // bottom-up depths + update
-    for (int32_t l = 0; l < s->L; ++l) {
-        n += s->ddepth_children[l] || l == 0 || s->hlevel[l + 1] > s->hlevel[l];   // top-down
+    const int32_t r = fused_from(s);
+    int32_t n = r + 1 + (r < s->L);                           // bottom-up depths, fused, update
+    for (int32_t l = 0; l < s->L; ++l) n += s->hlevel[l + 1] > s->hlevel[l];   // own reaches
+    for (int32_t l = 0; l < r; ++l) {
+        n += s->ddepth_children[l] || l == 0;                 // top-down
         if (!det) n += 2 * (s->wlevel[l + 1] > s->wlevel[l]);
     }
     return n;
@@ -279,9 +388,77 @@ cfr_status check_usable(cfr_solver *s) {
     return CFR_OK;
 }
 
-// Waits for the solver's stream.
+// Waits for the solver's stream; a device-side wait that expired poisons the solver.
 cfr_status sync_and_check(cfr_solver *s) {
     CK(cudaStreamSynchronize(s->stream));
+    if (s->d_err) {
+        int e = 0;
+        CK(cudaMemcpy(&e, s->d_err, sizeof e, cudaMemcpyDeviceToHost));
+        if (e) {
+            s->poisoned = true;
+            return set_err(s, CFR_ERR_TIMEOUT, "a bounded device-side wait expired (TMA copy not completed)");
+        }
+    }
+    return CFR_OK;
+}
+
+// FP32 mode: picks the fused depths r .. L-1 and cuts them into tiles for k_fused.  At most
+// cfg.fuse_levels depths (kFuseAuto when negative; none below 2) are fused, fewer where a depth-r
+// node's decision subtree exceeds kFuseCap or a depth >= r holds a node with more than 32 actions.
+// Tiles take consecutive depth-r nodes while their subtrees fit kFuseCap together.
+cfr_status plan_fusion(cfr_solver *s, const Layout &Lo) {
+    s->fuse_r = s->L;
+    s->fuse_ntiles = 0;
+    int32_t want = s->cfg.fuse_levels < 0 ? kFuseAuto : s->cfg.fuse_levels;
+    want = std::min(std::min(want, (int32_t)kFuseMaxLevels), s->L);
+    if (want < 2) return CFR_OK;
+    int32_t wdeep = -1;                                        // deepest depth holding a wide node
+    for (int32_t l = 0; l < s->L; ++l)
+        if (s->wlevel[l + 1] > s->wlevel[l]) wdeep = l;
+    const int32_t rmin = std::max(s->L - want, wdeep + 1);
+    if (s->L - rmin < 2) return CFR_OK;
+    if (want == 2) {                                           // thread per node of depth L-2
+        s->fuse_r = s->L - 2;
+        s->fuse_tail = true;
+        return CFR_OK;
+    }
+    // decision nodes in the subtree of each node of depth >= rmin (children have larger ids)
+    const int32_t jmin = s->dlevel[rmin];
+    std::vector<int32_t> cnt((size_t)(s->Nd - jmin), 0);
+    for (int64_t j = s->Nd - 1; j >= jmin; --j) {
+        int64_t c = 1;
+        for (int32_t d = Lo.dfirst[j]; d < Lo.dfirst[j + 1]; ++d) c += cnt[(size_t)(d - jmin)];
+        cnt[(size_t)(j - jmin)] = (int32_t)std::min<int64_t>(c, INT32_MAX);
+    }
+    int32_t r = rmin;
+    for (; s->L - r >= 2; ++r) {
+        bool fits = true;
+        for (int32_t j = s->dlevel[r]; j < s->dlevel[r + 1] && fits; ++j) fits = cnt[(size_t)(j - jmin)] <= kFuseCap;
+        if (fits) break;
+    }
+    if (s->L - r < 2) return CFR_OK;
+    std::vector<int32_t> roots;
+    int64_t acc = 0;
+    for (int32_t j = s->dlevel[r]; j < s->dlevel[r + 1]; ++j) {
+        const int32_t c = cnt[(size_t)(j - jmin)];
+        if (roots.empty() || acc + c > kFuseCap) { roots.push_back(j); acc = 0; }
+        acc += c;
+    }
+    roots.push_back(s->dlevel[r + 1]);
+    const int32_t K = s->L - r, nt = (int32_t)roots.size() - 1;
+    std::vector<int32_t> bounds((size_t)K * (nt + 1));
+    for (int32_t i = 0; i <= nt; ++i) {
+        int32_t j = roots[(size_t)i];
+        for (int32_t k = 0; k < K; ++k) {
+            bounds[(size_t)k * (nt + 1) + i] = j;
+            j = Lo.dfirst[(size_t)j];
+        }
+    }
+    TRY(alloc_n(s, &s->fuse_bounds, (int64_t)bounds.size()));
+    TRY(upload(s, s->fuse_bounds, bounds));
+    CK(cudaStreamSynchronize(s->stream));
+    s->fuse_r = r;
+    s->fuse_ntiles = nt;
     return CFR_OK;
 }
 
@@ -291,10 +468,12 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     s->dlevel = Lo.dlevel; s->hlevel = Lo.hlevel; s->wlevel = Lo.wlevel; s->Hp = Lo.Hp;
     s->ddepth_children.assign((size_t)s->L, 0);
     s->level_children.assign((size_t)s->L, 0);
+    s->level_terminals.assign((size_t)s->L, 0);
     for (int32_t l = 0; l < s->L; ++l) {
         const size_t a = (size_t)s->dlevel[l], b = (size_t)s->dlevel[l + 1];
         s->ddepth_children[l] = Lo.dfirst[b] > Lo.dfirst[a];
         s->level_children[l] = (int64_t)(Lo.dfirst[b] - Lo.dfirst[a]) + (Lo.tfirst[b] - Lo.tfirst[a]);
+        s->level_terminals[l] = (int64_t)(Lo.tfirst[b] - Lo.tfirst[a]);
     }
     s->dnode_user.swap(Lo.dnode_user); s->tnode_user.swap(Lo.tnode_user); s->h_int2user.swap(Lo.h_int2user);
     const bool fp64 = s->cfg.precision == CFR_FP64;
@@ -325,6 +504,7 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     TRY(alloc_n(s, &s->S, s->Q));
     TRY(alloc_n(s, &s->stage, s->Q));
     TRY(alloc_n(s, &s->d_iter, 1));
+    TRY(alloc_n(s, &s->d_err, 1));
     if (fp64) {
         TRY(dev_alloc(s, &s->contrib, sizeof(double) * (size_t)std::max<int64_t>(s->N - 1, 1)));
         TRY(alloc_n(s, &s->hnode_start, (int64_t)s->H + 1));
@@ -350,6 +530,7 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
         TRY(alloc_n(s, &s->tiles, (int64_t)tiles.size()));
         TRY(upload(s, s->tiles, tiles));
         CK(cudaStreamSynchronize(s->stream));
+        TRY(plan_fusion(s, Lo));
     }
 
     TRY(upload(s, s->dfirst, Lo.dfirst));
@@ -384,6 +565,20 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     CK(cudaMemsetAsync(s->own, 0, rs * (size_t)std::max<int32_t>(s->H, 1), s->stream));
     CK(cudaMemsetAsync(s->u, 0, rs * (size_t)std::max<int64_t>(s->Nd, 1), s->stream));
     CK(cudaMemsetAsync(s->d_iter, 0, sizeof(int64_t), s->stream));
+    CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+    if (!fp64) {
+        // resident blocks of k_bottomup_stream (its stages exceed the default 48 KB of shared memory)
+        const int smem = (int)(sizeof(SBStage) * kSBStages);
+        CK(cudaFuncSetAttribute(k_bottomup_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int per_sm = 0, sms = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bottomup_stream, kSBThreads, smem));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+        s->sb_grid = per_sm * sms;
+        const int tsmem = (int)(sizeof(TDStage) * TopDownTiles::kStages);
+        CK(cudaFuncSetAttribute(k_topdown_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_topdown_stream, kSBThreads, tsmem));
+        s->td_grid = per_sm * sms;
+    }
     // The root's counterfactual reaches are 1 (Eq. 2, v = v_0) and never change.
     if (s->Nd > 0) {
         const double one64 = 1.0;
@@ -401,7 +596,9 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
 }
 
 int64_t bytes_model(const cfr_solver *s) {
-    return s->cfg.precision == CFR_FP64 ? 96 * s->Nd + 8 * s->Nt + 56 * s->Q : 56 * s->Nd + 4 * s->Nt + 44 * s->Q;
+    double b = 0;
+    for (double x : phase_bytes(s)) b += x;
+    return (int64_t)b;
 }
 
 template <typename T>
@@ -498,9 +695,14 @@ cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver
     cudaGetDevice(&s->device);
     s->stream = static_cast<cudaStream_t>(cfg.cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return set_err(nullptr, CFR_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        std::string msg = cudaGetErrorString(e);
+        cfr_free(s.release());
+        return set_err(nullptr, CFR_ERR_CUDA, "stream/event creation: %s", msg.c_str());
     }
     st = load(s.get(), *Lo);
     if (st != CFR_OK) {
@@ -636,6 +838,8 @@ cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *c
     TRY(check_usable(s));
     if ((u1 || cf_reach1 || cf_reach2) && len < s->N)
         return set_err(s, CFR_ERR_INVALID, "node buffers need %lld entries", (long long)s->N);
+    if (fused_from(s) < s->L && !s->cfg.record_nodes)
+        return set_err(s, CFR_ERR_STATE, "node values of fused depths are not kept: load with record_nodes = 1");
     DeviceGuard dg(s->device);
     CK(cudaStreamSynchronize(s->stream));
     const bool fp64 = s->cfg.precision == CFR_FP64;
@@ -691,11 +895,13 @@ cfr_status cfr_root_value(cfr_solver *s, double *u1) {
     return CFR_OK;
 }
 
-cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t len, int32_t *nphases) {
+cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t *kind, int32_t *depth, int32_t len,
+                           int32_t *nphases) {
     TRY(check_usable(s));
-    const int32_t n = s->L > 0 ? 2 * s->L + 1 : 0;
+    const auto ph = phases(s);
+    const int32_t n = (int32_t)ph.size();
     if (nphases) *nphases = n;
-    if (!us && !bytes) return CFR_OK;
+    if (!us && !bytes && !kind && !depth) return CFR_OK;
     if (len < n) return set_err(s, CFR_ERR_INVALID, "phase buffers need %d entries", n);
     if (n == 0) return CFR_OK;
     DeviceGuard dg(s->device);
@@ -715,9 +921,13 @@ cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t len
         if (e != cudaSuccess) { s->poisoned = true; st = set_err(s, CFR_ERR_CUDA, "phase timing: %s", cudaGetErrorString(e)); }
     }
     for (auto &e : ev) cudaEventDestroy(e);
-    if (st == CFR_OK && bytes) {
+    if (st == CFR_OK) {
         const std::vector<double> b = phase_bytes(s);
-        for (int32_t k = 0; k < n; ++k) bytes[k] = b[(size_t)k];
+        for (int32_t k = 0; k < n; ++k) {
+            if (bytes) bytes[k] = b[(size_t)k];
+            if (kind) kind[k] = ph[(size_t)k].first;
+            if (depth) depth[k] = ph[(size_t)k].second;
+        }
     }
     return st;
 }
@@ -733,6 +943,9 @@ cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info) {
     info->bytes_per_iteration = bytes_model(s);
     info->kernels_per_iteration = launches_per_iteration(s);
     info->kernel_launches = s->kernel_launches;
+    info->fused_from_depth = fused_from(s);
+    info->fused_tiles = fused_from(s) == s->L ? 0
+                        : s->fuse_tail ? nblocks(s->dlevel[s->fuse_r + 1] - s->dlevel[s->fuse_r]) : s->fuse_ntiles;
     return CFR_OK;
 }
 
@@ -748,7 +961,11 @@ void cfr_free(cfr_solver *s) {
         if (s->cfg.dev_free) s->cfg.dev_free(b.first, s->cfg.alloc_ctx);
         else cudaFree(b.first);
     }
+    if (s->side) cudaStreamSynchronize(s->side);
     if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->join) cudaEventDestroy(s->join);
     delete s;
 }
 

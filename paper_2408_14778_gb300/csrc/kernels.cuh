@@ -1,8 +1,10 @@
 // Device kernels of one full-tree CFR iteration over the level-ordered layout (layout.hpp).
 //
+//   own reach   per depth l, for the infosets whose shallowest depth is l: pi_i(h) (Eq. 4 restricted
+//               to the acting player), from the parent sequence's own reach; independent of the node
+//               passes, so it runs on a parallel branch of the iteration's graph.
 //   top-down    depth l -> l+1: counterfactual reaches of the decision children (Eq. 2 / Eq. 13,
-//               the top-down recurrence for Pi-check) and, for the infosets whose shallowest depth
-//               is l, the own reach pi_i(h) (Eq. 4 restricted to the acting player).
+//               the top-down recurrence for Pi-check).
 //   bottom-up   depth l: node values u(d) = sum_a sigma(h,a) u(child_a) (Eq. 1 / Eq. 11) and the
 //               instantaneous regret scatter r~(h,a) += pi-check(d) (u_p(child_a) - u_p(d)) (Eq. 7,
 //               summed over the nodes of h as in Eq. 3 and Eq. 6; the vector form of Section 3.2.3).
@@ -366,17 +368,17 @@ __device__ __forceinline__ void update_tile(const DevTree<float> &t, int32_t h0,
 
 // ---- one kernel per depth and step ----------------------------------------------------------------
 
-// Top-down from depth l (blocks [0, nblk_nodes): one thread per decision node of depth l) and, in the
-// remaining blocks, the own reach of the infosets whose shallowest depth is l.
+// Own reaches of the player infosets [h0, h1) (those whose shallowest depth is one given depth).
+template <typename real>
+__global__ void __launch_bounds__(256) k_own(DevTree<real> t, int32_t h0, int32_t h1) {
+    const int32_t h = h0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (h < h1) own_infoset<real, false>(t, h);
+}
+
+// Top-down from depth l: one thread per decision node of depth l.  bump: count the iteration.
 template <typename real, bool kSkipWide>
-__global__ void __launch_bounds__(256) k_topdown(DevTree<real> t, int32_t j0, int32_t j1, int32_t nblk_nodes,
-                                                 int32_t h0, int32_t h1, int32_t bump) {
+__global__ void __launch_bounds__(256) k_topdown(DevTree<real> t, int32_t j0, int32_t j1, int32_t bump) {
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
-    if ((int32_t)blockIdx.x >= nblk_nodes) {
-        const int32_t h = h0 + (int32_t)((blockIdx.x - nblk_nodes) * blockDim.x + threadIdx.x);
-        if (h < h1) own_infoset<real, false>(t, h);
-        return;
-    }
     const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (j < j1) td_node<real, kSkipWide, false>(t, j);
 }
@@ -403,6 +405,328 @@ __global__ void __launch_bounds__(256) k_update_tiled(DevTree<float> t, const in
     __shared__ float s_own[kTileQ], s_pos[kTileQ], s_red[32];
     update_tile<false>(t, tiles[blockIdx.x], tiles[blockIdx.x + 1], plus != 0, linear ? (float)*t.iter : 1.f, s_own,
                        s_pos, s_red);
+}
+
+// ---- fused deepest depths, FP32 mode ----------------------------------------------------------------
+// The depths r .. L-1, which hold most of the nodes, in one launch.  Block b takes a tile of
+// consecutive depth-r nodes with all their decision descendants - consecutive at every depth, since
+// the children of consecutive nodes are consecutive - and stages the tile's node fields in shared
+// memory.  It then runs the top-down step depth by depth with the reaches kept in shared memory, and
+// the bottom-up step from the deepest depth up with the values kept in shared memory.  Global memory
+// sees the node fields once, the tile roots' reaches (read) and values (written), the terminal
+// utilities, the strategy gathers and the regret scatter; the reaches and values of the deeper
+// nodes never leave the SM unless the solver records them for cfr_get_nodes.  The arithmetic per
+// node, and its order, is that of td_node and bu_node.  Nodes with more than 32 actions are not
+// fused (the host keeps such depths out of the fused range).
+constexpr int kFuseCap = 1024;       // decision nodes of one tile, all fused depths together
+constexpr int kFuseMaxLevels = 8;
+constexpr int kFuseBatch = 4;        // staging loads in flight per thread
+
+struct FuseArgs {
+    const int32_t *bounds;   // [levels][ntiles + 1]: tile i holds nodes bounds[k][i] .. bounds[k][i+1] - 1
+                             // at fused depth r + k
+    int32_t ntiles, levels;
+    int32_t record;          // also write the values and reaches of every fused node
+    int32_t bump;            // the fused depths start at the root: count the iteration
+};
+
+struct FuseShared {
+    uint32_t qp[kFuseCap], km[kFuseCap];
+    int32_t df[kFuseCap + kFuseMaxLevels], tf[kFuseCap + kFuseMaxLevels];   // n_k + 1 entries per depth
+    float r1[kFuseCap], r2[kFuseCap], u[kFuseCap];
+    int32_t lo[kFuseMaxLevels + 1], off[kFuseMaxLevels + 1];
+};
+
+// Top-down step of node i of fused depth k (as td_node, reaches from and to shared memory).
+__device__ __forceinline__ void fused_td(const DevTree<float> &t, FuseShared &sh, int k, int32_t i, bool record) {
+    const int32_t x = sh.off[k] + i, e = x + k;
+    int32_t c = sh.df[e];
+    const int32_t nd = sh.df[e + 1] - c;
+    if (nd == 0) return;
+    const uint32_t w = sh.qp[x];
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
+    const uint32_t m = sh.km[x];
+    const float r1 = sh.r1[x], r2 = sh.r2[x];
+    int32_t y = sh.off[k + 1] + (c - sh.lo[k + 1]);
+    const int na = nd + __popc(m);
+    if (na <= kUnroll) {
+        float s[kUnroll];
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a) s[a] = a < na ? __ldg(t.sigma + qb + a) : 0.f;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a) {
+            if (a < na && !((m >> a) & 1u)) {
+                const float c1 = p == 1 ? r1 : r1 * s[a], c2 = p == 2 ? r2 : r2 * s[a];
+                sh.r1[y] = c1;
+                sh.r2[y] = c2;
+                if (record) { t.reach1[c] = c1; t.reach2[c] = c2; }
+                ++y;
+                ++c;
+            }
+        }
+        return;
+    }
+    for (int a = 0; a < na; ++a) {
+        if ((m >> a) & 1u) continue;
+        const float s = __ldg(t.sigma + qb + a);
+        const float c1 = p == 1 ? r1 : r1 * s, c2 = p == 2 ? r2 : r2 * s;
+        sh.r1[y] = c1;
+        sh.r2[y] = c2;
+        if (record) { t.reach1[c] = c1; t.reach2[c] = c2; }
+        ++y;
+        ++c;
+    }
+}
+
+// Bottom-up step of node i of fused depth k (as bu_node with atomics; child values of decision
+// children from shared memory).
+__device__ __forceinline__ void fused_bu(const DevTree<float> &t, FuseShared &sh, int k, int32_t i, bool record) {
+    const int32_t x = sh.off[k] + i, e = x + k;
+    const uint32_t w = sh.qp[x];
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
+    const uint32_t m = sh.km[x];
+    const int32_t c0 = sh.df[e], t0 = sh.tf[e];
+    const int32_t nd = sh.df[e + 1] - c0;
+    const int na = nd + __popc(m);
+    const float *dv = sh.u + (sh.off[k + 1] + (c0 - sh.lo[k + 1]));   // read only when nd > 0 (k + 1 fused)
+    const float *tv = t.util + t0;
+    float ud = 0.f;
+    if (na <= kUnroll) {
+        float v[kUnroll], s[kUnroll];
+        int kt = 0, kd = 0;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a) {
+            if (a < na) {
+                const bool term = (m >> a) & 1u;
+                v[a] = term ? __ldg(tv + kt) : dv[kd];
+                kt += term;
+                kd += !term;
+                s[a] = __ldg(t.sigma + qb + a);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a)
+            if (a < na) ud = madd(ud, s[a], v[a]);
+        sh.u[x] = ud;
+        if (k == 0 || record) t.u[sh.lo[k] + i] = ud;
+        if (p == 0) return;
+        const float wr = p == 1 ? sh.r1[x] : -sh.r2[x];
+        if (wr == 0.f) return;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a)
+            if (a < na) atomicAdd(&t.inst[qb + a], wr * (v[a] - ud));
+        return;
+    }
+    int kt = 0, kd = 0;
+    for (int a = 0; a < na; ++a) {
+        const float v = ((m >> a) & 1u) ? __ldg(tv + kt++) : dv[kd++];
+        ud = madd(ud, __ldg(t.sigma + qb + a), v);
+    }
+    sh.u[x] = ud;
+    if (k == 0 || record) t.u[sh.lo[k] + i] = ud;
+    if (p == 0) return;
+    const float wr = p == 1 ? sh.r1[x] : -sh.r2[x];
+    if (wr == 0.f) return;
+    kt = kd = 0;
+    for (int a = 0; a < na; ++a) {
+        const float v = ((m >> a) & 1u) ? __ldg(tv + kt++) : dv[kd++];
+        atomicAdd(&t.inst[qb + a], wr * (v - ud));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fused(DevTree<float> t, FuseArgs a) {
+    __shared__ FuseShared sh;
+    if (a.bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
+    const int K = a.levels;
+    if (threadIdx.x == 0) {
+        int32_t off = 0;
+        for (int k = 0; k < K; ++k) {
+            const int32_t *b = a.bounds + (size_t)k * (a.ntiles + 1) + blockIdx.x;
+            sh.lo[k] = b[0];
+            sh.off[k] = off;
+            off += b[1] - b[0];
+        }
+        sh.off[K] = off;
+        sh.lo[K] = 0;
+    }
+    __syncthreads();
+    // Stage the node fields: entry f of depth k's run [off_k + k, off_{k+1} + k + 1) is node lo_k + f - (off_k + k)
+    // (dfirst and tfirst take one entry more per depth, for the last node's end).
+    const int32_t nent = sh.off[K] + K;
+    for (int32_t f0 = threadIdx.x; f0 < nent; f0 += kFuseBatch * blockDim.x) {
+        int32_t vd[kFuseBatch], vt[kFuseBatch];
+        uint32_t vq[kFuseBatch], vk[kFuseBatch];
+        float v1[kFuseBatch], v2[kFuseBatch];
+        int kk[kFuseBatch];
+        int32_t ii[kFuseBatch];
+#pragma unroll
+        for (int b = 0; b < kFuseBatch; ++b) {
+            const int32_t f = f0 + b * (int32_t)blockDim.x;
+            kk[b] = -1;
+            if (f < nent) {
+                int k = 0;
+                while (k + 1 < K && f >= sh.off[k + 1] + k + 1) ++k;
+                const int32_t i = f - (sh.off[k] + k);
+                const int32_t j = sh.lo[k] + i;
+                kk[b] = k;
+                ii[b] = i;
+                vd[b] = __ldg(t.dfirst + j);
+                vt[b] = __ldg(t.tfirst + j);
+                if (i < sh.off[k + 1] - sh.off[k]) {
+                    vq[b] = __ldg(t.qp + j);
+                    vk[b] = __ldg(t.kmask + j);
+                    if (k == 0) { v1[b] = __ldg(t.reach1 + j); v2[b] = __ldg(t.reach2 + j); }
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kFuseBatch; ++b) {
+            const int k = kk[b];
+            if (k < 0) continue;
+            const int32_t f = f0 + b * (int32_t)blockDim.x, i = ii[b];
+            sh.df[f] = vd[b];
+            sh.tf[f] = vt[b];
+            if (i < sh.off[k + 1] - sh.off[k]) {
+                sh.qp[sh.off[k] + i] = vq[b];
+                sh.km[sh.off[k] + i] = vk[b];
+                if (k == 0) { sh.r1[i] = v1[b]; sh.r2[i] = v2[b]; }
+            }
+        }
+    }
+    __syncthreads();
+    const bool record = a.record != 0;
+    for (int k = 0; k + 1 < K; ++k) {
+        const int32_t n = sh.off[k + 1] - sh.off[k];
+        for (int32_t i = threadIdx.x; i < n; i += blockDim.x) fused_td(t, sh, k, i, record);
+        __syncthreads();
+    }
+    for (int k = K - 1; k >= 0; --k) {
+        const int32_t n = sh.off[k + 1] - sh.off[k];
+        for (int32_t i = threadIdx.x; i < n; i += blockDim.x) fused_bu(t, sh, k, i, record);
+        __syncthreads();
+    }
+}
+
+// ---- the last two depths in one pass, FP32 mode -----------------------------------------------------
+// One thread per node j of depth L-2 runs the top-down step of j (its children's reaches stay in
+// registers), the bottom-up step of each decision child c (depth L-1, terminal children only) and then
+// the bottom-up step of j.  The reaches and values of depth L-1 never go through memory unless the
+// solver records them.  Per node the arithmetic and its order are those of td_node and bu_node.
+// Nodes with more than 32 actions are not handled here (the host keeps such trees on the per-depth
+// kernels).
+
+// Bottom-up step of a node of the last depth (terminal children only) with the given reaches; returns
+// its value.
+__device__ __forceinline__ float tail_leaf(const DevTree<float> &t, int32_t c, float q1, float q2, bool record) {
+    const uint32_t w = __ldg(t.qp + c);
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
+    const int na = __popc(__ldg(t.kmask + c));
+    const float *tv = t.util + __ldg(t.tfirst + c);
+    float ud = 0.f;
+    float v[kUnroll], s[kUnroll];
+    if (na <= kUnroll) {
+#pragma unroll
+        for (int b = 0; b < kUnroll; ++b) {
+            if (b < na) {
+                v[b] = __ldg(tv + b);
+                s[b] = __ldg(t.sigma + qb + b);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kUnroll; ++b)
+            if (b < na) ud = madd(ud, s[b], v[b]);
+    } else {
+        for (int b = 0; b < na; ++b) ud = madd(ud, __ldg(t.sigma + qb + b), __ldg(tv + b));
+    }
+    if (record) {
+        t.u[c] = ud;
+        t.reach1[c] = q1;
+        t.reach2[c] = q2;
+    }
+    if (p == 0) return ud;
+    const float wr = p == 1 ? q1 : -q2;
+    if (wr == 0.f) return ud;
+    if (na <= kUnroll) {
+#pragma unroll
+        for (int b = 0; b < kUnroll; ++b)
+            if (b < na) atomicAdd(&t.inst[qb + b], wr * (v[b] - ud));
+    } else {
+        for (int b = 0; b < na; ++b) atomicAdd(&t.inst[qb + b], wr * (__ldg(tv + b) - ud));
+    }
+    return ud;
+}
+
+// bump: depth L-2 is the root's, so no top-down launch precedes this one; count the iteration.
+__global__ void __launch_bounds__(256) k_tail(DevTree<float> t, int32_t j0, int32_t j1, int32_t record,
+                                              int32_t bump) {
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j >= j1) return;
+    const bool rec = record != 0;
+    const uint32_t w = __ldg(t.qp + j);
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
+    const uint32_t m = __ldg(t.kmask + j);
+    const int32_t c0 = __ldg(t.dfirst + j);
+    const int32_t nd = __ldg(t.dfirst + j + 1) - c0;
+    const int32_t t0 = __ldg(t.tfirst + j);
+    const float r1 = __ldg(t.reach1 + j), r2 = __ldg(t.reach2 + j);
+    const int na = nd + __popc(m);
+    float ud = 0.f;
+    if (na <= kUnroll) {
+        float s[kUnroll], v[kUnroll];
+        int kt = 0;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a) {
+            if (a < na) {
+                s[a] = __ldg(t.sigma + qb + a);
+                if ((m >> a) & 1u) v[a] = __ldg(t.util + t0 + kt++);
+            }
+        }
+        int kd = 0;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a) {
+            if (a < na && !((m >> a) & 1u)) {
+                const float q1 = p == 1 ? r1 : r1 * s[a], q2 = p == 2 ? r2 : r2 * s[a];
+                v[a] = tail_leaf(t, c0 + kd++, q1, q2, rec);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a)
+            if (a < na) ud = madd(ud, s[a], v[a]);
+        t.u[j] = ud;
+        if (p == 0) return;
+        const float wr = p == 1 ? r1 : -r2;
+        if (wr == 0.f) return;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a)
+            if (a < na) atomicAdd(&t.inst[qb + a], wr * (v[a] - ud));
+        return;
+    }
+    // more than kUnroll actions (at most 32): child values are recomputed from memory in the second
+    // loop only for terminals; decision children's values are kept in a per-thread array
+    float vd[32];
+    int kt = 0, kd = 0;
+    for (int a = 0; a < na; ++a) {
+        const float s = __ldg(t.sigma + qb + a);
+        float v;
+        if ((m >> a) & 1u) {
+            v = __ldg(t.util + t0 + kt++);
+        } else {
+            const float q1 = p == 1 ? r1 : r1 * s, q2 = p == 2 ? r2 : r2 * s;
+            v = tail_leaf(t, c0 + kd++, q1, q2, rec);
+        }
+        vd[a] = v;
+        ud = madd(ud, s, v);
+    }
+    t.u[j] = ud;
+    if (p == 0) return;
+    const float wr = p == 1 ? r1 : -r2;
+    if (wr == 0.f) return;
+    for (int a = 0; a < na; ++a) atomicAdd(&t.inst[qb + a], wr * (vd[a] - ud));
 }
 
 template <typename real>

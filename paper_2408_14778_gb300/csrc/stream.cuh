@@ -1,0 +1,445 @@
+// Bottom-up step of a large depth (FP32 mode) with its inputs streamed into shared memory by TMA.
+//
+// The per-depth kernel k_bottomup gives each thread a chain of dependent global loads (node fields,
+// then child values and strategy entries), so the bytes in flight per SM - and with them the HBM
+// bandwidth - are capped by occupancy.  Here one producer warp per block moves tiles of kSBN
+// consecutive nodes into a ring of shared-memory stages with bulk copies (cp.async.bulk, completion
+// counted in bytes on a "full" mbarrier per stage): the node fields (qp, kmask, dfirst, tfirst), both
+// counterfactual reaches, and the contiguous ranges of the tile's child values - the terminal
+// utilities and the decision children's values.  Eight consumer warps wait for a stage, handle two
+// nodes per thread exactly as bu_node does (strategy entries are gathered from global memory, mostly
+// L2 hits), and release the stage on its "empty" mbarrier.  A tile whose child ranges exceed the stage
+// reads its child values from global memory instead.  Nodes with more than 32 actions are left to
+// k_bottomup_wide.
+//
+// Every wait is bounded by kWaitNs of %globaltimer (and a poll count).  A wait that expires sets *err,
+// raises the block's abort flag (which ends the other waits), and the producer waits - bounded again -
+// for the copies it issued before the block exits; the host turns *err into CFR_ERR_TIMEOUT.
+#pragma once
+
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace cfrgb {
+
+constexpr int kSBN = 512;                  // nodes per tile
+constexpr int kSBT = 3072;                 // staged terminal-child values per tile
+constexpr int kSBD = 2048;                 // staged decision-child values per tile
+constexpr int kSBStages = 2;
+constexpr int kSBConsumerWarps = 8;        // 256 consumer threads, two nodes each
+constexpr int kSBThreads = 32 * (kSBConsumerWarps + 1);
+constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
+constexpr uint32_t kWaitPolls = 1u << 26;
+
+struct SBStage {                           // element 0 of each array is the 16-byte-aligned copy start
+    uint32_t qp[kSBN + 4], km[kSBN + 4];
+    int32_t df[kSBN + 8], tf[kSBN + 8];
+    float r1[kSBN + 4], r2[kSBN + 4];
+    float tval[kSBT + 4], dval[kSBD + 4];
+};
+
+struct SBTile {
+    int32_t j0, n, o;                      // first node, node count, offset of node j0 in the field arrays
+    int32_t tal, dal;                      // global index of tval[0] / dval[0]
+    int32_t staged;                        // child values in tval/dval (else global memory)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits until the phase with the given parity has completed.  False when the wait expired or the
+// block is aborting (abort != nullptr and *abort set).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0; i < kWaitPolls; ++i) {
+        if (mbar_test(bar, parity)) return true;
+        if (abort && *abort) return false;
+        if ((i & 255u) == 255u && globaltimer_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+
+// 1-D bulk copy global -> shared: addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Elements [a, b) of a 4-byte array widened to 16-byte boundaries: first index, and the bytes.  The
+// solver's arrays are allocated in multiples of 256 bytes, so the widened end stays inside them.
+__device__ __forceinline__ int32_t widen16(int32_t a, int32_t b, uint32_t *bytes) {
+    const int32_t a0 = a & ~3, b0 = (b + 3) & ~3;
+    *bytes = (uint32_t)(b0 - a0) * 4u;
+    return a0;
+}
+
+// Producer: the copies of nodes [j0, j0 + n) into stage st.
+__device__ __forceinline__ void sb_issue(const DevTree<float> &t, int32_t j0, int32_t n, SBStage *st, SBTile *ti,
+                                         uint64_t *full) {
+    uint32_t bf, bd, btv = 0, bdv = 0;
+    const int32_t jal = widen16(j0, j0 + n, &bf);
+    widen16(j0, j0 + n + 1, &bd);
+    const int32_t ts = t.tfirst[j0], te = t.tfirst[j0 + n];
+    const int32_t ds = t.dfirst[j0], de = t.dfirst[j0 + n];
+    const int32_t tal = widen16(ts, te, &btv);
+    const int32_t dal = widen16(ds, de, &bdv);
+    const bool staged = btv <= 4u * (kSBT + 4) && bdv <= 4u * (kSBD + 4);
+    ti->j0 = j0; ti->n = n; ti->o = j0 - jal;
+    ti->tal = tal; ti->dal = dal; ti->staged = staged;
+    uint32_t total = 4 * bf + 2 * bd;
+    if (staged) total += btv + bdv;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(full, total);
+    bulk_g2s(st->qp, t.qp + jal, bf, full);
+    bulk_g2s(st->km, t.kmask + jal, bf, full);
+    bulk_g2s(st->df, t.dfirst + jal, bd, full);
+    bulk_g2s(st->tf, t.tfirst + jal, bd, full);
+    bulk_g2s(st->r1, t.reach1 + jal, bf, full);
+    bulk_g2s(st->r2, t.reach2 + jal, bf, full);
+    if (staged) {
+        if (btv) bulk_g2s(st->tval, t.util + tal, btv, full);
+        if (bdv) bulk_g2s(st->dval, t.u + dal, bdv, full);
+    }
+}
+
+// Consumer: bottom-up step of nodes i and i2 (i2 may be past the tile) of a staged tile, with the loads
+// of both nodes issued before either is used.  Per node the operations and their order are bu_node's.
+__device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage &st, const SBTile &ti, int32_t i,
+                                         int32_t i2) {
+    const int32_t ii[2] = {i, i2};
+    float v[2][kUnroll], s[2][kUnroll];
+    int na[2], pl[2];
+    int32_t qb[2];
+    uint32_t m[2];
+    bool go[2];
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        go[x] = false;
+        na[x] = 0;
+        if (ii[x] >= ti.n) continue;
+        const int32_t k = ti.o + ii[x];
+        const uint32_t w = st.qp[k];
+        if (qp_wide(w)) continue;
+        go[x] = true;
+        qb[x] = qp_base(w);
+        pl[x] = qp_player(w);
+        m[x] = st.km[k];
+        na[x] = (st.df[k + 1] - st.df[k]) + __popc(m[x]);
+    }
+    // general path (more than kUnroll actions): one node at a time, as bu_node's loop
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        if (!go[x] || na[x] <= kUnroll) continue;
+        const int32_t k = ti.o + ii[x], c0 = st.df[k], t0 = st.tf[k];
+        const float *tv = ti.staged ? st.tval + (t0 - ti.tal) : t.util + t0;
+        const float *dv = ti.staged ? st.dval + (c0 - ti.dal) : t.u + c0;
+        float ud = 0.f;
+        int kt = 0, kd = 0;
+        for (int a = 0; a < na[x]; ++a) {
+            const float val = ((m[x] >> a) & 1u) ? tv[kt++] : dv[kd++];
+            ud = madd(ud, __ldg(t.sigma + qb[x] + a), val);
+        }
+        t.u[ti.j0 + ii[x]] = ud;
+        go[x] = false;
+        if (pl[x] == 0) continue;
+        const float wr = pl[x] == 1 ? st.r1[k] : -st.r2[k];
+        if (wr == 0.f) continue;
+        kt = kd = 0;
+        for (int a = 0; a < na[x]; ++a) {
+            const float val = ((m[x] >> a) & 1u) ? tv[kt++] : dv[kd++];
+            atomicAdd(&t.inst[qb[x] + a], wr * (val - ud));
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        if (!go[x]) continue;
+        const int32_t k = ti.o + ii[x], c0 = st.df[k], t0 = st.tf[k];
+        const float *tv = ti.staged ? st.tval + (t0 - ti.tal) : t.util + t0;
+        const float *dv = ti.staged ? st.dval + (c0 - ti.dal) : t.u + c0;
+        int kt = 0, kd = 0;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a) {
+            if (a < na[x]) {
+                const bool term = (m[x] >> a) & 1u;
+                v[x][a] = term ? tv[kt] : dv[kd];
+                kt += term;
+                kd += !term;
+                s[x][a] = __ldg(t.sigma + qb[x] + a);
+            }
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        if (!go[x]) continue;
+        const int32_t k = ti.o + ii[x];
+        float ud = 0.f;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a)
+            if (a < na[x]) ud = madd(ud, s[x][a], v[x][a]);
+        t.u[ti.j0 + ii[x]] = ud;
+        if (pl[x] == 0) continue;
+        const float wr = pl[x] == 1 ? st.r1[k] : -st.r2[k];
+        if (wr == 0.f) continue;
+#pragma unroll
+        for (int a = 0; a < kUnroll; ++a)
+            if (a < na[x]) atomicAdd(&t.inst[qb[x] + a], wr * (v[x][a] - ud));
+    }
+}
+
+// Named barrier 1 over the consumer threads (the producer warp does not take part).
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kSBConsumerWarps * 32) : "memory");
+}
+
+// Named barrier 1 over the consumer threads that also returns, to every one of them, whether any
+// passed true.
+__device__ __forceinline__ bool consumers_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kSBConsumerWarps * 32)
+        : "memory");
+    return r != 0;
+}
+
+// ---- the producer/consumer pipeline --------------------------------------------------------------
+// P supplies the tile work: P::Stage and P::Tile (shared-memory stage and its description),
+// P::kStages, ntiles(), issue(tile, stage, tile info, full barrier) run by one producer thread, and
+// consume(stage, tile info, consumer thread index) run by each of the kSBConsumerWarps * 32 consumer
+// threads.  P::kConsumerSync: consume() synchronises the consumer threads, so they agree (one
+// barrier with an OR) on whether to take each tile or stop.  Block b takes tiles b, b + gridDim.x, ...  Returns true in consumer threads once their
+// tiles are done (false in the producer warp), so a kernel may continue with other consumer work.
+template <class P>
+__device__ __forceinline__ bool run_pipeline(const P &p, int *err) {
+    using Stage = typename P::Stage;
+    constexpr int S = P::kStages;
+    extern __shared__ __align__(128) unsigned char pipe_smem[];
+    Stage *stage = reinterpret_cast<Stage *>(pipe_smem);
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ typename P::Tile tinfo[S];
+    __shared__ int abort_flag;
+    const int32_t ntiles = p.ntiles();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kSBConsumerWarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    volatile int *abort = &abort_flag;
+    if (warp == kSBConsumerWarps) {                                   // producer warp
+        if (lane != 0) return false;
+        int32_t issued = 0;
+        for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++issued) {
+            const int s = issued % S;
+            if (issued >= S && !mbar_wait(&empty[s], (uint32_t)((issued / S - 1) & 1), abort)) {
+                if (!*abort) { atomicExch(err, 1); *abort = 1; }
+                break;
+            }
+            p.issue(tile, &stage[s], &tinfo[s], &full[s]);
+        }
+        // the block must not exit with copies in flight: wait for the last use of each stage
+        for (int s = 0; s < S && s < issued; ++s) {
+            const int32_t last = s + ((issued - 1 - s) / S) * S;
+            if (!mbar_wait(&full[s], (uint32_t)((last / S) & 1), nullptr)) atomicExch(err, 1);
+        }
+        return false;
+    }
+    int32_t k = 0;
+    for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int s = k % S;
+        const bool ok = mbar_wait(&full[s], (uint32_t)((k / S) & 1), abort);
+        if (!ok && !*abort) { atomicExch(err, 1); *abort = 1; }
+        if constexpr (P::kConsumerSync) {
+            // consume() synchronises the consumer threads: they must all take the tile or all stop
+            if (consumers_any(!ok || *abort)) break;
+        } else if (!ok) {
+            break;
+        }
+        p.consume(stage[s], tinfo[s], (int)threadIdx.x);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    return true;
+}
+
+// Bottom-up at depth [jb, je): the stages of SBStage described above.
+struct BottomUpTiles {
+    using Stage = SBStage;
+    using Tile = SBTile;
+    static constexpr int kStages = kSBStages;
+    static constexpr bool kConsumerSync = false;
+    DevTree<float> t;
+    int32_t jb, je;
+    __device__ int32_t ntiles() const { return (je - jb + kSBN - 1) / kSBN; }
+    __device__ void issue(int32_t tile, Stage *st, Tile *ti, uint64_t *full) const {
+        const int32_t j0 = jb + tile * kSBN;
+        sb_issue(t, j0, min(kSBN, je - j0), st, ti, full);
+    }
+    __device__ void consume(const Stage &st, const Tile &ti, int c) const {
+        const Tile tl = ti;
+        sb_nodes(t, st, tl, c, c + kSBConsumerWarps * 32);
+    }
+};
+
+__global__ void __launch_bounds__(kSBThreads) k_bottomup_stream(DevTree<float> t, int32_t jb, int32_t je, int *err) {
+    run_pipeline(BottomUpTiles{t, jb, je}, err);
+}
+
+// Top-down from depth [jb, je): tiles of kSBN nodes stage qp, kmask, dfirst and both reaches.  The
+// consumers compute the decision children's reaches as td_node does into a shared-memory buffer, then
+// store the tile's contiguous child range [dfirst[j0], dfirst[j0 + n]) with coalesced writes (a tile
+// with more than kTDOut children writes them directly instead).  Nodes with more than 32 actions are
+// left to k_topdown_wide.
+constexpr int kTDOut = 4096;
+
+struct TDStage {
+    uint32_t qp[kSBN + 4], km[kSBN + 4];
+    int32_t df[kSBN + 8];
+    float r1[kSBN + 4], r2[kSBN + 4];
+};
+
+struct TDTile {
+    int32_t j0, n, o;
+};
+
+struct TopDownTiles {
+    using Stage = TDStage;
+    using Tile = TDTile;
+    static constexpr int kStages = 3;
+    static constexpr bool kConsumerSync = true;
+    DevTree<float> t;
+    int32_t jb, je;
+    float *o1, *o2;                                  // shared-memory output buffers, kTDOut each
+    __device__ int32_t ntiles() const { return (je - jb + kSBN - 1) / kSBN; }
+    __device__ void issue(int32_t tile, Stage *st, Tile *ti, uint64_t *full) const {
+        const int32_t j0 = jb + tile * kSBN, n = min(kSBN, je - j0);
+        uint32_t bf, bd;
+        const int32_t jal = widen16(j0, j0 + n, &bf);
+        widen16(j0, j0 + n + 1, &bd);
+        ti->j0 = j0; ti->n = n; ti->o = j0 - jal;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(full, 4 * bf + bd);
+        bulk_g2s(st->qp, t.qp + jal, bf, full);
+        bulk_g2s(st->km, t.kmask + jal, bf, full);
+        bulk_g2s(st->df, t.dfirst + jal, bd, full);
+        bulk_g2s(st->r1, t.reach1 + jal, bf, full);
+        bulk_g2s(st->r2, t.reach2 + jal, bf, full);
+    }
+    // Nodes c and c + 256 of the tile: strategy loads of both issued before the stores.
+    __device__ void consume(const Stage &st, const Tile &ti, int c) const {
+        const int32_t ds = st.df[ti.o], nc = st.df[ti.o + ti.n] - ds;
+        const bool buffered = nc <= kTDOut;            // uniform over the block
+        float *w1 = buffered ? o1 - ds : t.reach1;     // child reach destinations, by global child index
+        float *w2 = buffered ? o2 - ds : t.reach2;
+        const int32_t ii[2] = {c, c + kSBConsumerWarps * 32};
+        float s[2][kUnroll];
+        int na[2], pl[2];
+        int32_t c0[2];
+        uint32_t m[2];
+        float r1[2], r2[2];
+        bool go[2];
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+            go[x] = false;
+            na[x] = 0;
+            if (ii[x] >= ti.n) continue;
+            const int32_t k = ti.o + ii[x];
+            const uint32_t w = st.qp[k];
+            c0[x] = st.df[k];
+            const int32_t nd = st.df[k + 1] - c0[x];
+            if (nd == 0 || qp_wide(w)) continue;
+            go[x] = true;
+            m[x] = st.km[k];
+            na[x] = nd + __popc(m[x]);
+            pl[x] = qp_player(w);
+            r1[x] = st.r1[k];
+            r2[x] = st.r2[k];
+            const int32_t qb = qp_base(w);
+            if (na[x] <= kUnroll) {
+#pragma unroll
+                for (int a = 0; a < kUnroll; ++a) s[x][a] = a < na[x] ? __ldg(t.sigma + qb + a) : 0.f;
+            } else {                                       // more than kUnroll actions: td_node's loop
+                int32_t cc = c0[x];
+                for (int a = 0; a < na[x]; ++a) {
+                    if ((m[x] >> a) & 1u) continue;
+                    const float sv = __ldg(t.sigma + qb + a);
+                    w1[cc] = pl[x] == 1 ? r1[x] : r1[x] * sv;
+                    w2[cc] = pl[x] == 2 ? r2[x] : r2[x] * sv;
+                    ++cc;
+                }
+                go[x] = false;
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+            if (!go[x]) continue;
+            int32_t cc = c0[x];
+#pragma unroll
+            for (int a = 0; a < kUnroll; ++a) {
+                if (a < na[x] && !((m[x] >> a) & 1u)) {
+                    w1[cc] = pl[x] == 1 ? r1[x] : r1[x] * s[x][a];
+                    w2[cc] = pl[x] == 2 ? r2[x] : r2[x] * s[x][a];
+                    ++cc;
+                }
+            }
+        }
+        if (!buffered) return;
+        consumers_sync();                              // the tile's child reaches are in o1/o2
+        for (int32_t i = c; i < nc; i += kSBConsumerWarps * 32) {
+            t.reach1[ds + i] = o1[i];
+            t.reach2[ds + i] = o2[i];
+        }
+        consumers_sync();                              // o1/o2 free for the next tile
+    }
+};
+
+__global__ void __launch_bounds__(kSBThreads) k_topdown_stream(DevTree<float> t, int32_t jb, int32_t je, int32_t bump,
+                                                               int *err) {
+    __shared__ float out1[kTDOut], out2[kTDOut];
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
+    run_pipeline(TopDownTiles{t, jb, je, out1, out2}, err);
+}
+
+}  // namespace cfrgb

@@ -92,20 +92,40 @@ def test_fp64_is_bit_identical_to_the_oracle():
     np.testing.assert_array_equal(cfr.cfr_current_strategy(s), os_["sigma"])
 
 
+@pytest.mark.parametrize("fuse", [0, 2, 4])
 @pytest.mark.parametrize("variant", [cfr.CFR_VANILLA, cfr.CFR_PLUS])
-def test_one_iteration_fp32(variant):
+def test_one_iteration_fp32(variant, fuse):
+    # fuse: the deepest depths in one kernel (none; the last two by k_tail; four in tiles)
     for g in small_games():
         o = oracle.Oracle(g, record=True)
-        s = cfr.cfr_load_tree(g, variant=variant, precision=cfr.CFR_FP32)
+        s = cfr.cfr_load_tree(g, variant=variant, precision=cfr.CFR_FP32, fuse_levels=fuse, record_nodes=True)
         o.iterate(1, variant=variant, avg=variant)
         cfr.cfr_iterate(s, 1)
         compare_state(s, o, TOL32, g)
         compare_nodes(s, o, TOL32, g)
 
 
-def _step_parity(g, variant, Ts, precision, tol, nodes=False):
+def test_fp32_nine_to_twelve_actions():
+    # 9..12 actions per node at every depth: the streamed kernels' general (more than 8 actions) path on
+    # depths of >= 32768 nodes, and the unrolled per-depth kernels' general path on the small ones.
+    g = gamegen.public_private(seed=31, num_buckets=13, depth=6, amin=9, amax=12, p_cont=0.45)
+    for variant in (cfr.CFR_VANILLA, cfr.CFR_PLUS):
+        o = oracle.Oracle(g, record=True)
+        s = cfr.cfr_load_tree(g, variant=variant, precision=cfr.CFR_FP32, record_nodes=True)
+        o.iterate(1, variant=variant, avg=variant)
+        cfr.cfr_iterate(s, 1)
+        compare_state(s, o, TOL32, g)
+        compare_nodes(s, o, TOL32, g)
+        st = o.state()
+        cfr.cfr_set_state(s, st["cum_regret"], st["strat_sum"], st["iteration"])
+        o.iterate(1, variant=variant, avg=variant)
+        cfr.cfr_iterate(s, 1)
+        compare_state(s, o, TOL32, g)
+
+
+def _step_parity(g, variant, Ts, precision, tol, nodes=False, fuse=-1):
     o = oracle.Oracle(g, record=nodes)
-    s = cfr.cfr_load_tree(g, variant=variant, precision=precision)
+    s = cfr.cfr_load_tree(g, variant=variant, precision=precision, fuse_levels=fuse, record_nodes=nodes)
     done = 0
     for T in Ts:
         o.iterate(T - 1 - done, variant=variant, avg=variant)
@@ -122,11 +142,14 @@ def _step_parity(g, variant, Ts, precision, tol, nodes=False):
     return s, o
 
 
-def test_step_parity_fp32_rank13_depth10():
+@pytest.mark.parametrize("fuse", [2, 0])
+def test_step_parity_fp32_rank13_depth10(fuse):
     # ~2e6 nodes, 156-way deal, fold/showdown payoffs, CFR+: one FP32 step from the oracle's FP64
-    # state at T = 1, 2, 10, 100 (step parity).
+    # state at T = 1, 2, 10, 100 (step parity), with the last two depths fused and not.
     g = gamegen.config("rank13_depth10", seed=1)
-    s, o = _step_parity(g, cfr.CFR_PLUS, (1, 2, 10, 100), cfr.CFR_FP32, TOL32)
+    s, o = _step_parity(g, cfr.CFR_PLUS, (1, 2, 10, 100), cfr.CFR_FP32, TOL32, nodes=fuse == 2, fuse=fuse)
+    info = cfr.cfr_get_info(s)
+    assert (info["fused_from_depth"] < info["num_levels"]) == (fuse == 2)
     nc_g, _ = cfr.cfr_exploitability(s)
     nc_o, _ = o.exploitability()
     assert abs(nc_g - nc_o) <= 1e-5 * max(1.0, abs(nc_o))
@@ -184,13 +207,13 @@ def test_chance_only_tree():
     assert cfr.cfr_exploitability(s)[0] == pytest.approx(0.0, abs=1e-15)
 
 
-@pytest.mark.parametrize("m,n", [(1, 3), (33, 2), (64, 3), (5, 64), (200, 3), (3, 1326)])
+@pytest.mark.parametrize("m,n", [(1, 3), (12, 20), (9, 32), (33, 2), (64, 3), (5, 64), (200, 3), (3, 1326)])
 def test_wide_and_single_action_infosets(m, n):
     rng = np.random.default_rng(m * 100 + n)
     g = gamegen.matrix_game(rng.normal(size=(m, n)))
     for precision, tol in ((cfr.CFR_FP64, TOL64), (cfr.CFR_FP32, TOL32)):
         o = oracle.Oracle(g, record=True)
-        s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=precision)
+        s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=precision, record_nodes=True)
         o.iterate(1, variant=1, avg=1)
         cfr.cfr_iterate(s, 1)
         compare_state(s, o, tol, g)
@@ -230,6 +253,49 @@ def test_multilevel_infoset_iterates_but_br_is_unsupported():
     with pytest.raises(cfr.CfrError) as e:
         cfr.cfr_exploitability(s)
     assert e.value.status == cfr.CFR_ERR_UNSUPPORTED
+
+
+def _edge_games():
+    from test_oracle_pins import multilevel_game
+
+    g = gamegen.public_private(seed=21, num_buckets=3, depth=5, amin=2, amax=3, p_cont=0.8, p_chance=0.4)
+    cp = g.chance_prob.copy()
+    cp[:6] = [0.5, 0.5, 0.0, 0.0, 0.0, 0.0]
+    zero = gamegen.GameDesc(g.parent, g.action, g.infoset, g.infoset_player, g.infoset_num_actions, cp, g.utility)
+    deep = gamegen.public_private(seed=22, num_buckets=3, depth=9, amin=2, amax=3, p_cont=0.7, p_chance=0.2)
+    return {"zero_probability_branch": zero, "multilevel_infoset": multilevel_game(), "public_chance_depth9": deep}
+
+
+@pytest.mark.parametrize("fuse", [2, 8])
+@pytest.mark.parametrize("name", ["zero_probability_branch", "multilevel_infoset", "public_chance_depth9"])
+def test_fp32_fused_depths_on_edge_games(name, fuse):
+    # The fused kernel on chance nodes inside the fused depths, unreachable subtrees, an infoset spanning
+    # depths (own reach through the own-sequence chain) and up to 8 fused depths from the root.
+    g = _edge_games()[name]
+    o = oracle.Oracle(g, record=True)
+    s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, fuse_levels=fuse, record_nodes=True)
+    info = cfr.cfr_get_info(s)
+    assert info["fused_from_depth"] < info["num_levels"]
+    for T in (1, 2, 3):
+        o.iterate(1, variant=1, avg=1)
+        cfr.cfr_iterate(s, 1)
+        compare_state(s, o, TOL32, g)
+        compare_nodes(s, o, TOL32, g)
+        st = o.state()                                  # next step from the oracle's state (step parity)
+        cfr.cfr_set_state(s, st["cum_regret"], st["strat_sum"], st["iteration"])
+
+
+def test_get_nodes_needs_record_when_fused():
+    g = gamegen.config("bucket3_depth6", seed=1)
+    s = cfr.cfr_load_tree(g, precision=cfr.CFR_FP32, fuse_levels=2)
+    info = cfr.cfr_get_info(s)
+    assert info["fused_from_depth"] < info["num_levels"] and info["fused_tiles"] > 0
+    cfr.cfr_iterate(s, 1)
+    with pytest.raises(cfr.CfrError) as e:
+        cfr.cfr_get_nodes(s)
+    assert e.value.status == cfr.CFR_ERR_STATE
+    cfr.cfr_iterate(s, 1)                                 # still usable
+    cfr.cfr_synchronize(s)
 
 
 def test_state_roundtrip_and_cuda_allocator():
@@ -272,11 +338,11 @@ def test_bad_arguments_raise():
     cfr.cfr_synchronize(s)
 
 
-@pytest.mark.parametrize("precision", [cfr.CFR_FP64, cfr.CFR_FP32])
-def test_phase_times_run_a_real_iteration(precision):
+@pytest.mark.parametrize("precision,fuse", [(cfr.CFR_FP64, -1), (cfr.CFR_FP32, 0), (cfr.CFR_FP32, -1)])
+def test_phase_times_run_a_real_iteration(precision, fuse):
     g = gamegen.config("rank13_depth10", seed=6, target_nodes=None, p_cont=0.6)
     o = oracle.Oracle(g)
-    s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=precision)
+    s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=precision, fuse_levels=fuse)
     o.iterate(2, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
     st = o.state()                                            # (FP32 is compared one step from FP64 state)
     cfr.cfr_set_state(s, st["cum_regret"], st["strat_sum"], st["iteration"])
@@ -285,9 +351,18 @@ def test_phase_times_run_a_real_iteration(precision):
     compare_state(s, o, TOL64 if precision == cfr.CFR_FP64 else TOL32, g)
     info = cfr.cfr_get_info(s)
     assert info["iteration"] == 3
-    total = ph["topdown_bytes"].sum() + ph["bottomup_bytes"].sum() + ph["update_bytes"]
-    # every node but the root is some depth's child: the phases add up to the iteration's model less
-    # the root's share as a child (12 bytes in FP32 mode, 24 in FP64 mode)
-    assert 0 <= info["bytes_per_iteration"] - total <= 24
-    assert np.all(ph["bottomup_us"] > 0) and ph["update_us"] > 0
-    assert len(ph["topdown_us"]) == len(ph["bottomup_us"]) == info["num_levels"]
+    assert all(p["us"] > 0 for p in ph)
+    assert abs(sum(p["bytes"] for p in ph) - info["bytes_per_iteration"]) <= 1
+    L, f = info["num_levels"], info["fused_from_depth"]
+    kinds = [p["kind"] for p in ph]
+    assert kinds == [cfr.CFR_PHASE_OWN] + [cfr.CFR_PHASE_TOPDOWN] * f + [cfr.CFR_PHASE_FUSED] * (f < L) + \
+        [cfr.CFR_PHASE_BOTTOMUP] * f + [cfr.CFR_PHASE_UPDATE]
+    if f == L:
+        # every node but the root is some depth's child: the byte model in closed form
+        Nd, Nt, Q = info["num_decision"], info["num_terminal"], info["num_q"]
+        Hp = int((g.infoset_player > 0).sum())
+        want = (96 * Nd + 8 * Nt + 56 * Q + 17 * Hp - 24 if precision == cfr.CFR_FP64
+                else 56 * Nd + 4 * Nt + 44 * Q + 13 * Hp - 12)
+        assert info["bytes_per_iteration"] == want
+    else:
+        assert precision == cfr.CFR_FP32 and info["fused_tiles"] > 0
