@@ -287,7 +287,7 @@ def run_ours(args, world, rank, local):
     by = np.array([p["bytes"] for p in ph[0]])
     kernel_of = {cfr.CFR_PHASE_TOPDOWN: "k_topdown", cfr.CFR_PHASE_BOTTOMUP: "k_bottomup", cfr.CFR_PHASE_FUSED: "k_fused",
                  cfr.CFR_PHASE_OWN: "k_own",
-                 cfr.CFR_PHASE_UPDATE: "k_update_tiled" if args.precision == "fp32" else "k_update"}
+                 cfr.CFR_PHASE_UPDATE: "k_update_rows" if args.precision == "fp32" else "k_update"}
     k = int(np.argmax(us))
     peak, peak_src = measured_hbm_peak()
     dom = by[k] / (us[k] * 1e-6) / 1e9

@@ -24,6 +24,7 @@ namespace {
 thread_local std::string g_thread_err;
 
 constexpr int kBlock = 256;
+constexpr int kWideBlock = 1024;   // nodes and infosets with more than 32 actions: one block each
 constexpr int32_t kFuseAuto = 0;   // fused depths when cfr_config.fuse_levels < 0
 constexpr int32_t kStreamMinNodes = 32768;   // FP32 bottom-up depths this large use k_bottomup_stream
 
@@ -68,7 +69,12 @@ struct cfr_solver {
     double *br_reach = nullptr, *br_val = nullptr, *br_cfv = nullptr, *avg = nullptr, *br_out = nullptr;
     int64_t *d_iter = nullptr;
     int *d_err = nullptr;                                 // set by a device-side wait that expired
-    int32_t sb_grid = 0, td_grid = 0;                     // k_bottomup_stream / k_topdown_stream: resident blocks
+    int32_t sb_grid[3] = {0, 0, 0}, td_grid[3] = {0, 0, 0};   // streamed kernels: resident blocks, per
+                                                                // unrolled action count (kStreamNA)
+    std::vector<int32_t> level_na;                        // per depth: index into kStreamNA
+    int32_t hp_na = 0;                                    // FP32 update: largest action count of at most 32
+    int32_t nwide_h = 0;                                  // player infosets with more than 32 actions
+    int32_t *wide_h = nullptr;
     void *contrib = nullptr;                              // FP64 mode: per-edge regret contributions
     int32_t *hnode_start = nullptr, *hnode = nullptr;     // FP64 mode: nodes of each infoset, depth-first
     int32_t *wide = nullptr;                              // nodes with more than 32 actions, by depth
@@ -76,8 +82,6 @@ struct cfr_solver {
     std::vector<char> ddepth_children;                    // depth l has a node with a decision child
     std::vector<int64_t> level_children;                  // children of the decision nodes of depth l
     std::vector<int64_t> level_terminals;                 // terminal children of the decision nodes of depth l
-    int32_t *tiles = nullptr;                             // FP32 mode: infoset tiles of k_update_tiled
-    int32_t ntiles = 0;
     // FP32 mode: depths fuse_r .. L-1 run in k_fused (fuse_r == L: none), in fuse_ntiles tiles whose
     // node ranges per fused depth are fuse_bounds[k][0 .. fuse_ntiles]
     int32_t fuse_r = 0, fuse_ntiles = 0;
@@ -174,6 +178,46 @@ DevTree<real> dev_tree(cfr_solver *s) {
     return t;
 }
 
+// Streamed top-down (bottom_up false) or bottom-up step of depth l = [j0, j1) in the instantiation
+// for the depth's largest action count.  False when the kernels could not be set up (then the caller
+// launches the per-depth kernel).
+template <int NA>
+void launch_stream_na(const cfr_solver *s, const DevTree<float> &t, cudaStream_t st, bool bottom_up, int32_t l,
+                      int32_t j0, int32_t j1, int gi) {
+    const int32_t tiles = (j1 - j0 + kSBN - 1) / kSBN;
+    if (bottom_up)
+        k_bottomup_stream<NA><<<std::min(s->sb_grid[gi], tiles), kSBThreads, sizeof(SBStage) * kSBStages, st>>>(
+            t, j0, j1, s->d_err);
+    else
+        k_topdown_stream<NA><<<std::min(s->td_grid[gi], tiles), kSBThreads,
+                               sizeof(TDStage) * TopDownTiles<NA>::kStages, st>>>(t, j0, j1, l == 0, s->d_err);
+}
+
+bool launch_stream(const cfr_solver *s, const DevTree<float> &t, cudaStream_t st, bool bottom_up, int32_t l,
+                   int32_t j0, int32_t j1) {
+    const int gi = s->level_na[(size_t)l];
+    if ((bottom_up ? s->sb_grid[gi] : s->td_grid[gi]) <= 0) return false;
+    if (gi == 0) launch_stream_na<kStreamNA[0]>(s, t, st, bottom_up, l, j0, j1, gi);
+    else if (gi == 1) launch_stream_na<kStreamNA[1]>(s, t, st, bottom_up, l, j0, j1, gi);
+    else launch_stream_na<kStreamNA[2]>(s, t, st, bottom_up, l, j0, j1, gi);
+    return true;
+}
+
+// Shared-memory limits and resident blocks of the streamed kernels built for NA actions.
+template <int NA>
+cfr_status setup_stream_na(cfr_solver *s, int gi, int sms) {
+    int per_sm = 0;
+    const int bsmem = (int)(sizeof(SBStage) * kSBStages);
+    CK(cudaFuncSetAttribute(k_bottomup_stream<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bsmem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bottomup_stream<NA>, kSBThreads, bsmem));
+    s->sb_grid[gi] = per_sm * sms;
+    const int tsmem = (int)(sizeof(TDStage) * TopDownTiles<NA>::kStages);
+    CK(cudaFuncSetAttribute(k_topdown_stream<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_topdown_stream<NA>, kSBThreads, tsmem));
+    s->td_grid[gi] = per_sm * sms;
+    return CFR_OK;
+}
+
 // One full-tree iteration, queued on `st` (captured into the solver's graph).  FP64 mode reduces
 // the instantaneous regrets deterministically (k_update sums per-edge contributions in depth-first
 // node order); FP32 mode adds them with atomics, streams large depths through shared memory, and
@@ -219,19 +263,14 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         if (s->ddepth_children[l] || l == 0) {
             bool streamed = false;
             if constexpr (!det) {
-                if (j1 - j0 >= kStreamMinNodes && s->td_grid > 0) {
-                    const int32_t grid = std::min<int32_t>(s->td_grid, (j1 - j0 + kSBN - 1) / kSBN);
-                    k_topdown_stream<<<grid, kSBThreads, sizeof(TDStage) * TopDownTiles::kStages, st>>>(
-                        t, j0, j1, l == 0, s->d_err);
-                    streamed = true;
-                }
+                if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(s, t, st, false, l, j0, j1);
             }
             if (!streamed) k_topdown<real, !det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1, l == 0);
             CK_LAUNCH();
         }
         const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
         if (!det && nw > 0) {
-            k_topdown_wide<real><<<nw, kBlock, 0, st>>>(t, s->wide, s->wlevel[l]);
+            k_topdown_wide<real><<<nw, kWideBlock, 0, st>>>(t, s->wide, s->wlevel[l]);
             CK_LAUNCH();
         }
         TRY(mark());
@@ -258,17 +297,13 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         bool streamed = false;
         if constexpr (!det) {
-            if (j1 - j0 >= kStreamMinNodes && s->sb_grid > 0) {
-                const int32_t grid = std::min<int32_t>(s->sb_grid, (j1 - j0 + kSBN - 1) / kSBN);
-                k_bottomup_stream<<<grid, kSBThreads, sizeof(SBStage) * kSBStages, st>>>(t, j0, j1, s->d_err);
-                streamed = true;
-            }
+            if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(s, t, st, true, l, j0, j1);
         }
         if (!streamed) k_bottomup<real, det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1);
         CK_LAUNCH();
         const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
         if (!det && nw > 0) {
-            k_bottomup_wide<real><<<nw, kBlock, 0, st>>>(t, s->wide, s->wlevel[l]);
+            k_bottomup_wide<real><<<nw, kWideBlock, 0, st>>>(t, s->wide, s->wlevel[l]);
             CK_LAUNCH();
         }
         TRY(mark());
@@ -281,9 +316,18 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
             CK_LAUNCH();
         }
     } else {
-        if (s->ntiles > 0) {
-            k_update_tiled<<<s->ntiles, kBlock, 0, st>>>(t, s->tiles, s->cfg.variant == CFR_PLUS, linear);
-            CK_LAUNCH();
+        {
+            if (s->Hp > 0) {
+                const int plus = s->cfg.variant == CFR_PLUS;
+                if (s->hp_na <= 3) k_update_rows<3><<<nblocks(s->Hp), kBlock, 0, st>>>(t, s->Hp, plus, linear);
+                else if (s->hp_na <= 5) k_update_rows<5><<<nblocks(s->Hp), kBlock, 0, st>>>(t, s->Hp, plus, linear);
+                else k_update_rows<8><<<nblocks(s->Hp), kBlock, 0, st>>>(t, s->Hp, plus, linear);
+                CK_LAUNCH();
+            }
+            if (s->nwide_h > 0) {
+                k_update_list<<<s->nwide_h, kWideBlock, 0, st>>>(t, s->wide_h, s->cfg.variant == CFR_PLUS, linear);
+                CK_LAUNCH();
+            }
         }
     }
     TRY(mark());
@@ -515,22 +559,18 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     TRY(alloc_n(s, &s->wide, (int64_t)Lo.wide.size()));
     TRY(upload(s, s->wide, Lo.wide));
     if (!fp64) {
-        // tiles of player infosets for k_update_tiled: at most kBlock infosets and kTileQ slots each
-        // (an infoset wider than kTileQ gets a tile of its own)
-        std::vector<int32_t> tiles;
-        int32_t h0 = 0;
-        while (h0 < s->Hp) {
-            int32_t h1 = h0 + 1;
-            while (h1 < s->Hp && h1 - h0 < kBlock && Lo.qbase[(size_t)h1 + 1] - Lo.qbase[(size_t)h0] <= kTileQ) ++h1;
-            tiles.push_back(h0);
-            h0 = h1;
-        }
-        tiles.push_back(s->Hp);
-        s->ntiles = (int32_t)tiles.size() - 1;
-        TRY(alloc_n(s, &s->tiles, (int64_t)tiles.size()));
-        TRY(upload(s, s->tiles, tiles));
-        CK(cudaStreamSynchronize(s->stream));
         TRY(plan_fusion(s, Lo));
+        {
+            std::vector<int32_t> wh;
+            for (int32_t h = 0; h < s->Hp; ++h) {
+                const int32_t na = Lo.qbase[(size_t)h + 1] - Lo.qbase[h];
+                if (na > 32) wh.push_back(h); else s->hp_na = std::max(s->hp_na, na);
+            }
+            s->nwide_h = (int32_t)wh.size();
+            TRY(alloc_n(s, &s->wide_h, (int64_t)wh.size()));
+            TRY(upload(s, s->wide_h, wh));
+            CK(cudaStreamSynchronize(s->stream));
+        }
     }
 
     TRY(upload(s, s->dfirst, Lo.dfirst));
@@ -567,17 +607,21 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     CK(cudaMemsetAsync(s->d_iter, 0, sizeof(int64_t), s->stream));
     CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
     if (!fp64) {
-        // resident blocks of k_bottomup_stream (its stages exceed the default 48 KB of shared memory)
-        const int smem = (int)(sizeof(SBStage) * kSBStages);
-        CK(cudaFuncSetAttribute(k_bottomup_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        int per_sm = 0, sms = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bottomup_stream, kSBThreads, smem));
+        int sms = 0;
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-        s->sb_grid = per_sm * sms;
-        const int tsmem = (int)(sizeof(TDStage) * TopDownTiles::kStages);
-        CK(cudaFuncSetAttribute(k_topdown_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_topdown_stream, kSBThreads, tsmem));
-        s->td_grid = per_sm * sms;
+        TRY(setup_stream_na<kStreamNA[0]>(s, 0, sms));
+        TRY(setup_stream_na<kStreamNA[1]>(s, 1, sms));
+        TRY(setup_stream_na<kStreamNA[2]>(s, 2, sms));
+        // per depth, the smallest unrolled action count covering its largest node of at most 32 actions
+        s->level_na.assign((size_t)s->L, 2);
+        for (int32_t l = 0; l < s->L; ++l) {
+            int32_t maxa = 0;
+            for (int32_t j = s->dlevel[l]; j < s->dlevel[l + 1]; ++j) {
+                if ((Lo.qp[(size_t)j] >> 29) & 1u) continue;
+                maxa = std::max<int32_t>(maxa, (Lo.dfirst[(size_t)j + 1] - Lo.dfirst[j]) + __builtin_popcount(Lo.kmask[j]));
+            }
+            s->level_na[(size_t)l] = maxa <= kStreamNA[0] ? 0 : maxa <= kStreamNA[1] ? 1 : 2;
+        }
     }
     // The root's counterfactual reaches are 1 (Eq. 2, v = v_0) and never change.
     if (s->Nd > 0) {

@@ -265,105 +265,127 @@ __device__ __forceinline__ void bu_wide(const DevTree<real> &t, int32_t j, real 
         atomicAdd(&t.inst[qb + a], wr * (wide_child_value<real, C>(t, wb, d0, t0, a) - ud));
 }
 
-// ---- per-infoset update, FP32 mode: a tile of infosets staged through shared memory --------------
-// A tile is a run of player infosets whose slots qbase[h0] .. qbase[h1] fit kTileQ (or a single wider
-// infoset).  Slots are read and written with consecutive threads on consecutive slots; only the
-// positive-regret sums run per infoset, from shared memory.  The two FP64 accumulations stay FP64
-// (R += r~, S += w pi_i sigma); regret matching itself runs in FP32, the strategy's precision.
-// All threads of the block must call it.
-
-constexpr int kTileQ = 2048;
-
-template <bool C>
-__device__ __forceinline__ void update_tile(const DevTree<float> &t, int32_t h0, int32_t h1, bool plus, float w,
-                                            float *s_own, float *s_pos, float *s_red) {
-    const int32_t qs = t.qbase[h0];
-    const int32_t nq = t.qbase[h1] - qs;
-    if (nq > kTileQ) {                // a single infoset wider than a tile: the block shares its actions
-        const float wo = w * ldm<C>(t.own + h0);
-        float part = 0.f;
+// ---- per-infoset update of a wide infoset (more than 32 actions), FP32 mode ----------------------
+// The block shares the infoset's actions; the two FP64 accumulations stay FP64 (R += r~,
+// S += w pi_i sigma) and regret matching runs in FP32, the strategy's precision, with the positive
+// regrets summed over the block.  All threads of the block must call it.
+__device__ __forceinline__ void update_wide(const DevTree<float> &t, int32_t h, bool plus, float w, float *s_red) {
+    const int32_t qs = t.qbase[h];
+    const int32_t nq = t.qbase[h + 1] - qs;
+    const float wo = w * t.own[h];
+    float part = 0.f;
+    for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) {
+        const int32_t q = qs + i;
+        double r = t.R[q] + widen(t.inst[q]);
+        if (plus) r = r > 0.0 ? r : 0.0;
+        t.R[q] = r;
+        t.S[q] = t.S[q] + widen(wo * t.sigma[q]);
+        part += r > 0.0 ? (float)r : 0.f;
+    }
+    const float sum = block_sum(part, s_red);   // (its barriers also order the R writes above)
+    if (sum >= 1e-30f || sum == 0.f) {
         for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) {
-            const int32_t q = qs + i;
-            double r = ldm<C>(t.R + q) + widen(ldm<C>(t.inst + q));
-            if (plus) r = r > 0.0 ? r : 0.0;
-            t.R[q] = r;
-            t.S[q] = ldm<C>(t.S + q) + widen(wo * ldm<C>(t.sigma + q));
-            part += r > 0.0 ? (float)r : 0.f;
+            const double r = t.R[qs + i];
+            t.sigma[qs + i] = sum > 0.f ? (r > 0.0 ? (float)r : 0.f) * (1.f / sum) : 1.f / (float)nq;
         }
-        const float sum = block_sum(part, s_red);   // (its barriers also order the R writes above)
-        if (sum >= 1e-30f || sum == 0.f) {
-            for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) {
-                const double r = ldm<C>(t.R + qs + i);
-                t.sigma[qs + i] = sum > 0.f ? (r > 0.0 ? (float)r : 0.f) * (1.f / sum) : 1.f / (float)nq;
+    } else {                          // sums below FP32 range: normalise in FP64
+        double pos = 0.0;
+        for (int32_t i = 0; i < nq; ++i) pos += fmax(t.R[qs + i], 0.0);
+        for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) t.sigma[qs + i] = (float)(fmax(t.R[qs + i], 0.0) / pos);
+    }
+}
+
+// ---- per-infoset update, FP32 mode: one thread per infoset ---------------------------------------
+// The arithmetic of update_wide, per infoset, with no block-wide barriers: a thread loads all of its
+// infoset's R, r~ and sigma entries at once, then S where something accrues.  Infosets with more than
+// 32 actions are skipped (k_update_list takes them, one block each).
+
+// R += r~ (CFR+: clipped at 0) for one slot; returns the slot's positive regret as a float.
+__device__ __forceinline__ float update_regret(double *R, double rr, float in, bool plus) {
+    const double r0 = rr + widen(in);
+    const bool positive = __double_as_longlong(r0) > 0;      // r0 > 0 without an FP64 compare
+    const double r = plus && !positive ? 0.0 : r0;
+    *R = r;
+    return positive ? __double2float_rn(r) : 0.f;
+}
+
+// sigma' of an infoset whose positive regrets sum to `sum` below FP32's normal range: FP64 division.
+__device__ __forceinline__ void regret_match_tiny(const DevTree<float> &t, int32_t qs, int na) {
+    double p = 0.0;
+    for (int a = 0; a < na; ++a) p += fmax(t.R[qs + a], 0.0);
+    for (int a = 0; a < na; ++a) t.sigma[qs + a] = (float)(fmax(t.R[qs + a], 0.0) / p);
+}
+
+template <int NA>
+__global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t Hp, int32_t plus, int32_t linear) {
+    const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (h >= Hp) return;
+    const int32_t qs = t.qbase[h];
+    const int na = t.qbase[h + 1] - qs;
+    if (na > 32) return;
+    const float w = linear ? (float)*t.iter : 1.f;
+    const float wo = w * t.own[h];
+    if (na <= NA) {
+        double rr[NA];
+        float in[NA], sg[NA], pos[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+            if (a < na) { rr[a] = t.R[qs + a]; in[a] = t.inst[qs + a]; sg[a] = t.sigma[qs + a]; }
+        float sum = 0.f;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            if (a < na) {
+                pos[a] = update_regret(t.R + qs + a, rr[a], in[a], plus != 0);
+                sg[a] = wo * sg[a];                            // the strategy-sum increment
             }
-        } else {                          // sums below FP32 range: normalise in FP64
-            double pos = 0.0;
-            for (int32_t i = 0; i < nq; ++i) pos += fmax(ldm<C>(t.R + qs + i), 0.0);
-            for (int32_t i = threadIdx.x; i < nq; i += blockDim.x)
-                t.sigma[qs + i] = (float)(fmax(ldm<C>(t.R + qs + i), 0.0) / pos);
         }
-        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < NA; ++a)                            // nothing accrues where own reach or sigma is 0
+            if (a < na && sg[a] != 0.f) rr[a] = t.S[qs + a];
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+            if (a < na && sg[a] != 0.f) t.S[qs + a] = rr[a] + widen(sg[a]);
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+            if (a < na) sum += pos[a];
+        if (sum >= 1e-30f) {
+            const float f = 1.f / sum;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                if (a < na) t.sigma[qs + a] = pos[a] * f;
+        } else if (sum > 0.f) {
+            regret_match_tiny(t, qs, na);
+        } else {
+            const float u = 1.f / (float)na;                   // no positive regret: uniform (Eq. 9)
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                if (a < na) t.sigma[qs + a] = u;
+        }
         return;
     }
-    for (int32_t h = h0 + (int32_t)threadIdx.x; h < h1; h += blockDim.x) {
-        const float o = ldm<C>(t.own + h);
-        for (int32_t q = t.qbase[h]; q < t.qbase[h + 1]; ++q) s_own[q - qs] = o;
+    float pos[32];
+    float sum = 0.f;
+    for (int a = 0; a < na; ++a) {
+        pos[a] = update_regret(t.R + qs + a, t.R[qs + a], t.inst[qs + a], plus != 0);
+        const float inc = wo * t.sigma[qs + a];
+        if (inc != 0.f) t.S[qs + a] = t.S[qs + a] + widen(inc);
     }
-    __syncthreads();
-    for (int32_t i0 = threadIdx.x; i0 < nq; i0 += 4 * 256) {   // four slots per thread, loads first
-        double rr[4];
-        float in[4], sg[4], inc[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int32_t i = i0 + k * 256;
-            if (i < nq) { rr[k] = ldm<C>(t.R + qs + i); in[k] = ldm<C>(t.inst + qs + i); sg[k] = ldm<C>(t.sigma + qs + i); }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int32_t i = i0 + k * 256;
-            if (i >= nq) continue;
-            const double r0 = rr[k] + widen(in[k]);
-            const bool positive = __double_as_longlong(r0) > 0;  // r0 > 0 without an FP64 compare
-            const double r = plus && !positive ? 0.0 : r0;
-            t.R[qs + i] = r;
-            s_pos[i] = positive ? __double2float_rn(r) : 0.f;
-            inc[k] = w * s_own[i] * sg[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {                            // nothing accrues where own reach or sigma is 0
-            const int32_t i = i0 + k * 256;
-            if (i < nq && inc[k] != 0.f) rr[k] = ldm<C>(t.S + qs + i);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int32_t i = i0 + k * 256;
-            if (i < nq && inc[k] != 0.f) t.S[qs + i] = rr[k] + widen(inc[k]);
-        }
+    for (int a = 0; a < na; ++a) sum += pos[a];
+    if (sum >= 1e-30f) {
+        const float f = 1.f / sum;
+        for (int a = 0; a < na; ++a) t.sigma[qs + a] = pos[a] * f;
+    } else if (sum > 0.f) {
+        regret_match_tiny(t, qs, na);
+    } else {
+        for (int a = 0; a < na; ++a) t.sigma[qs + a] = 1.f / (float)na;
     }
-    __syncthreads();
-    for (int32_t h = h0 + (int32_t)threadIdx.x; h < h1; h += blockDim.x) {
-        const int32_t a0 = t.qbase[h] - qs, na = t.qbase[h + 1] - t.qbase[h];
-        float sum = 0.f;
-        for (int k = 0; k < na; ++k) sum += s_pos[a0 + k];
-        float f;
-        if (sum >= 1e-30f) {
-            f = 1.f / sum;
-        } else if (sum > 0.f) {           // sums below FP32 range: normalise in FP64 (R is visible here)
-            double pos = 0.0;
-            for (int k = 0; k < na; ++k) pos += fmax(ldm<C>(t.R + qs + a0 + k), 0.0);
-            for (int k = 0; k < na; ++k) s_pos[a0 + k] = (float)(fmax(ldm<C>(t.R + qs + a0 + k), 0.0) / pos);
-            f = 1.f;
-        } else {
-            f = -1.f / (float)na;         // no positive regret: uniform (Eq. 9)
-        }
-        for (int k = 0; k < na; ++k) s_own[a0 + k] = f;
-    }
-    __syncthreads();
-    for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) {
-        const float f = s_own[i];
-        t.sigma[qs + i] = f >= 0.f ? s_pos[i] * f : -f;
-    }
-    __syncthreads();
+}
+
+// The infosets hs[0 .. gridDim.x) (more than 32 actions), one block each (up to 1024 threads).
+__global__ void __launch_bounds__(1024) k_update_list(DevTree<float> t, const int32_t *hs, int32_t plus,
+                                                      int32_t linear) {
+    __shared__ float s_red[32];
+    update_wide(t, hs[blockIdx.x], plus != 0, linear ? (float)*t.iter : 1.f, s_red);
 }
 
 // ---- one kernel per depth and step ----------------------------------------------------------------
@@ -390,21 +412,14 @@ __global__ void __launch_bounds__(256) k_bottomup(DevTree<real> t, int32_t j0, i
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256) k_topdown_wide(DevTree<real> t, const int32_t *wide, int32_t w0) {
+__global__ void __launch_bounds__(1024) k_topdown_wide(DevTree<real> t, const int32_t *wide, int32_t w0) {
     td_wide<real, false>(t, wide[w0 + blockIdx.x]);
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256) k_bottomup_wide(DevTree<real> t, const int32_t *wide, int32_t w0) {
+__global__ void __launch_bounds__(1024) k_bottomup_wide(DevTree<real> t, const int32_t *wide, int32_t w0) {
     __shared__ real s_red[32];
     bu_wide<real, false>(t, wide[w0 + blockIdx.x], s_red);
-}
-
-__global__ void __launch_bounds__(256) k_update_tiled(DevTree<float> t, const int32_t *tiles, int32_t plus,
-                                                      int32_t linear) {
-    __shared__ float s_own[kTileQ], s_pos[kTileQ], s_red[32];
-    update_tile<false>(t, tiles[blockIdx.x], tiles[blockIdx.x + 1], plus != 0, linear ? (float)*t.iter : 1.f, s_own,
-                       s_pos, s_red);
 }
 
 // ---- fused deepest depths, FP32 mode ----------------------------------------------------------------

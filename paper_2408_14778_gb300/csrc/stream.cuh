@@ -138,14 +138,17 @@ __device__ __forceinline__ void sb_issue(const DevTree<float> &t, int32_t j0, in
 
 // Consumer: bottom-up step of nodes i and i2 (i2 may be past the tile) of a staged tile, with the loads
 // of both nodes issued before either is used.  Per node the operations and their order are bu_node's.
+// NA: the unrolled action count (at least the depth's largest action count for full unrolling; nodes
+// with more actions take bu_node's loop).
+template <int NA>
 __device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage &st, const SBTile &ti, int32_t i,
                                          int32_t i2) {
     const int32_t ii[2] = {i, i2};
-    float v[2][kUnroll], s[2][kUnroll];
+    float v[2][NA], s[2][NA];
     int na[2], pl[2];
-    int32_t qb[2];
+    int32_t qb[2], c0[2], t0[2];
     uint32_t m[2];
-    bool go[2];
+    bool go[2], allterm[2];
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
         go[x] = false;
@@ -158,15 +161,19 @@ __device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage 
         qb[x] = qp_base(w);
         pl[x] = qp_player(w);
         m[x] = st.km[k];
-        na[x] = (st.df[k + 1] - st.df[k]) + __popc(m[x]);
+        c0[x] = st.df[k];
+        t0[x] = st.tf[k];
+        const int32_t nd = st.df[k + 1] - c0[x];
+        allterm[x] = nd == 0;
+        na[x] = nd + __popc(m[x]);
     }
-    // general path (more than kUnroll actions): one node at a time, as bu_node's loop
+    // general path (more than NA actions): one node at a time, as bu_node's loop
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
-        if (!go[x] || na[x] <= kUnroll) continue;
-        const int32_t k = ti.o + ii[x], c0 = st.df[k], t0 = st.tf[k];
-        const float *tv = ti.staged ? st.tval + (t0 - ti.tal) : t.util + t0;
-        const float *dv = ti.staged ? st.dval + (c0 - ti.dal) : t.u + c0;
+        if (!go[x] || na[x] <= NA) continue;
+        const int32_t k = ti.o + ii[x];
+        const float *tv = ti.staged ? st.tval + (t0[x] - ti.tal) : t.util + t0[x];
+        const float *dv = ti.staged ? st.dval + (c0[x] - ti.dal) : t.u + c0[x];
         float ud = 0.f;
         int kt = 0, kd = 0;
         for (int a = 0; a < na[x]; ++a) {
@@ -187,18 +194,27 @@ __device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage 
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
         if (!go[x]) continue;
-        const int32_t k = ti.o + ii[x], c0 = st.df[k], t0 = st.tf[k];
-        const float *tv = ti.staged ? st.tval + (t0 - ti.tal) : t.util + t0;
-        const float *dv = ti.staged ? st.dval + (c0 - ti.dal) : t.u + c0;
-        int kt = 0, kd = 0;
+        const float *tv = ti.staged ? st.tval + (t0[x] - ti.tal) : t.util + t0[x];
+        if (allterm[x]) {                              // terminal children only (the deepest depth)
 #pragma unroll
-        for (int a = 0; a < kUnroll; ++a) {
-            if (a < na[x]) {
-                const bool term = (m[x] >> a) & 1u;
-                v[x][a] = term ? tv[kt] : dv[kd];
-                kt += term;
-                kd += !term;
-                s[x][a] = __ldg(t.sigma + qb[x] + a);
+            for (int a = 0; a < NA; ++a) {
+                if (a < na[x]) {
+                    v[x][a] = tv[a];
+                    s[x][a] = __ldg(t.sigma + qb[x] + a);
+                }
+            }
+        } else {
+            const float *dv = ti.staged ? st.dval + (c0[x] - ti.dal) : t.u + c0[x];
+            int kt = 0, kd = 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                if (a < na[x]) {
+                    const bool term = (m[x] >> a) & 1u;
+                    v[x][a] = term ? tv[kt] : dv[kd];
+                    kt += term;
+                    kd += !term;
+                    s[x][a] = __ldg(t.sigma + qb[x] + a);
+                }
             }
         }
     }
@@ -208,14 +224,14 @@ __device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage 
         const int32_t k = ti.o + ii[x];
         float ud = 0.f;
 #pragma unroll
-        for (int a = 0; a < kUnroll; ++a)
+        for (int a = 0; a < NA; ++a)
             if (a < na[x]) ud = madd(ud, s[x][a], v[x][a]);
         t.u[ti.j0 + ii[x]] = ud;
         if (pl[x] == 0) continue;
         const float wr = pl[x] == 1 ? st.r1[k] : -st.r2[k];
         if (wr == 0.f) continue;
 #pragma unroll
-        for (int a = 0; a < kUnroll; ++a)
+        for (int a = 0; a < NA; ++a)
             if (a < na[x]) atomicAdd(&t.inst[qb[x] + a], wr * (v[x][a] - ud));
     }
 }
@@ -305,6 +321,7 @@ __device__ __forceinline__ bool run_pipeline(const P &p, int *err) {
 }
 
 // Bottom-up at depth [jb, je): the stages of SBStage described above.
+template <int NA>
 struct BottomUpTiles {
     using Stage = SBStage;
     using Tile = SBTile;
@@ -319,12 +336,13 @@ struct BottomUpTiles {
     }
     __device__ void consume(const Stage &st, const Tile &ti, int c) const {
         const Tile tl = ti;
-        sb_nodes(t, st, tl, c, c + kSBConsumerWarps * 32);
+        sb_nodes<NA>(t, st, tl, c, c + kSBConsumerWarps * 32);
     }
 };
 
+template <int NA>
 __global__ void __launch_bounds__(kSBThreads) k_bottomup_stream(DevTree<float> t, int32_t jb, int32_t je, int *err) {
-    run_pipeline(BottomUpTiles{t, jb, je}, err);
+    run_pipeline(BottomUpTiles<NA>{t, jb, je}, err);
 }
 
 // Top-down from depth [jb, je): tiles of kSBN nodes stage qp, kmask, dfirst and both reaches.  The
@@ -344,6 +362,7 @@ struct TDTile {
     int32_t j0, n, o;
 };
 
+template <int NA>
 struct TopDownTiles {
     using Stage = TDStage;
     using Tile = TDTile;
@@ -374,7 +393,7 @@ struct TopDownTiles {
         float *w1 = buffered ? o1 - ds : t.reach1;     // child reach destinations, by global child index
         float *w2 = buffered ? o2 - ds : t.reach2;
         const int32_t ii[2] = {c, c + kSBConsumerWarps * 32};
-        float s[2][kUnroll];
+        float s[2][NA];
         int na[2], pl[2];
         int32_t c0[2];
         uint32_t m[2];
@@ -397,10 +416,10 @@ struct TopDownTiles {
             r1[x] = st.r1[k];
             r2[x] = st.r2[k];
             const int32_t qb = qp_base(w);
-            if (na[x] <= kUnroll) {
+            if (na[x] <= NA) {
 #pragma unroll
-                for (int a = 0; a < kUnroll; ++a) s[x][a] = a < na[x] ? __ldg(t.sigma + qb + a) : 0.f;
-            } else {                                       // more than kUnroll actions: td_node's loop
+                for (int a = 0; a < NA; ++a) s[x][a] = a < na[x] ? __ldg(t.sigma + qb + a) : 0.f;
+            } else {                                       // more than NA actions: td_node's loop
                 int32_t cc = c0[x];
                 for (int a = 0; a < na[x]; ++a) {
                     if ((m[x] >> a) & 1u) continue;
@@ -417,7 +436,7 @@ struct TopDownTiles {
             if (!go[x]) continue;
             int32_t cc = c0[x];
 #pragma unroll
-            for (int a = 0; a < kUnroll; ++a) {
+            for (int a = 0; a < NA; ++a) {
                 if (a < na[x] && !((m[x] >> a) & 1u)) {
                     w1[cc] = pl[x] == 1 ? r1[x] : r1[x] * s[x][a];
                     w2[cc] = pl[x] == 2 ? r2[x] : r2[x] * s[x][a];
@@ -435,11 +454,16 @@ struct TopDownTiles {
     }
 };
 
+template <int NA>
 __global__ void __launch_bounds__(kSBThreads) k_topdown_stream(DevTree<float> t, int32_t jb, int32_t je, int32_t bump,
                                                                int *err) {
     __shared__ float out1[kTDOut], out2[kTDOut];
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
-    run_pipeline(TopDownTiles{t, jb, je, out1, out2}, err);
+    run_pipeline(TopDownTiles<NA>{t, jb, je, out1, out2}, err);
 }
+
+// Unrolled action counts the streamed kernels are built for; a depth takes the smallest one that
+// covers its largest (non-wide) node.
+constexpr int kStreamNA[3] = {3, 5, 8};
 
 }  // namespace cfrgb
