@@ -46,6 +46,7 @@ def parse():
                     help="FP32 mode: deepest depths run by the fused kernel (-1 automatic, 0 none)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-exploitability-1e-3 measurement")
     return ap.parse_args()
 
 
@@ -179,6 +180,52 @@ def oracle_sample(g, budget_s: float):
     rate = 1.0e7                               # oracle node-updates/s, order of magnitude, sizing only
     k = max(1, min(int(g.meta["deals"]), int(budget_s * rate / per_deal)))
     return gamegen.first_deals(g, k)
+
+
+TTT_TARGET = 1e-3          # exploitability (NashConv / 2), absolute, payoff units
+TTT_CHECK = 25             # iterations between exploitability evaluations
+TTT_MAX_ITERS = 100000
+TTT_ORACLE_SECONDS = 60.0
+
+
+def _ttt_run(step, expl, max_iters: int, max_seconds: float) -> dict:
+    """Iterates in chunks of TTT_CHECK until the exploitability of the average strategy is at most
+    TTT_TARGET; the time includes the evaluations."""
+    t0, it, ex = time.perf_counter(), 0, float("inf")
+    while it < max_iters and time.perf_counter() - t0 < max_seconds:
+        step(TTT_CHECK)
+        it += TTT_CHECK
+        ex = expl()
+        if ex <= TTT_TARGET:
+            break
+    return {"reached": ex <= TTT_TARGET, "seconds": time.perf_counter() - t0, "iterations": it, "exploitability": ex}
+
+
+def time_to_exploitability(args, local: int) -> dict:
+    """CFR+ (linear averaging, simultaneous updates) on the 13-rank fold/showdown game (payoffs up to 8):
+    time until the average strategy's exploitability reaches 1e-3, on the GPU (FP32 mode) for the full
+    2e6-node game and a 2e5-node cut, and for the oracle (one core) on the same cut."""
+    import gamegen
+    import oracle
+    import paper_2408_14778_gb300 as cfr
+
+    out = {"target": TTT_TARGET, "check_every": TTT_CHECK, "variant": "cfr+ linear averaging, simultaneous",
+           "time_includes": "iterations and the exploitability evaluations"}
+    for name, nodes in (("rank13_depth10", None), ("rank13_depth10_2e5", 200_000)):
+        g = gamegen.config("rank13_depth10", seed=args.seed, target_nodes=nodes)
+        s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, device=local)
+        cfr.cfr_synchronize(s)
+        r = _ttt_run(lambda n: cfr.cfr_iterate(s, n), lambda: cfr.cfr_exploitability(s)[1], TTT_MAX_ITERS, 30.0)
+        r["nodes"] = g.num_nodes
+        out[f"gpu_{name}"] = r
+        s.close()
+        if nodes is not None:
+            o = oracle.Oracle(g)
+            r = _ttt_run(lambda n: o.iterate(n, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR),
+                         lambda: o.exploitability()[1], TTT_MAX_ITERS, TTT_ORACLE_SECONDS)
+            r.update(nodes=g.num_nodes, cores=1, capped_at_seconds=TTT_ORACLE_SECONDS)
+            out[f"oracle_{name}"] = r
+    return out
 
 
 def cpu_baseline(g, variant: int, seconds: float = 12.0) -> dict:
@@ -331,6 +378,9 @@ def run_ours(args, world, rank, local):
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(g, 1 if args.variant == "plus" else 0)
+    ttt = None
+    if rank == 0 and world == 1 and not args.no_ttt:
+        ttt = time_to_exploitability(args, local)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -340,6 +390,7 @@ def run_ours(args, world, rank, local):
                 "iterations_per_s": args.steps / t_max, "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches - launches0, "clocks": clocks,
                 "parallelism": "replicas" if world > 1 else "single GPU"}
+        line["time_to_exploitability"] = ttt
         line["phase_us"] = phase_us
         print(json.dumps(line), flush=True)
     del np

@@ -107,9 +107,9 @@ typedef struct {
     int64_t iteration;            /* completed iterations T */
     int64_t device_bytes;         /* device memory held by the solver */
     int64_t bytes_per_iteration;  /* algorithmic bytes of one iteration, the sum over cfr_phase_times'
-                                     phases; with nothing fused 56 Nd + 4 Nt + 44 Q + 13 Hp - 12 (FP32
-                                     mode) or 96 Nd + 8 Nt + 56 Q + 17 Hp - 24 (FP64 mode), Hp the
-                                     player infosets */
+                                     phases; with nothing fused 56 Nd + 4 Nt + 44 Q + 13 Hp - 12 - 20 Ndl
+                                     (FP32 mode) or 96 Nd + 8 Nt + 56 Q + 17 Hp - 24 - 32 Ndl (FP64 mode),
+                                     Hp the player infosets, Ndl the decision nodes of the last depth */
     int32_t kernels_per_iteration;/* kernel launches of one iteration */
     int64_t kernel_launches;      /* kernel launches made by cfr_iterate so far */
     int32_t fused_from_depth;     /* first depth run by the fused kernel (num_levels: none) */

@@ -178,6 +178,14 @@ DevTree<real> dev_tree(cfr_solver *s) {
     return t;
 }
 
+// Whether the top-down step from depth l launches anything: a depth whose nodes have no decision
+// children (the last one) has none, except depth 0, whose first thread counts the iteration, and
+// FP32 mode's wide nodes, whose kernel runs regardless.
+bool topdown_launches(const cfr_solver *s, int32_t l) {
+    return s->ddepth_children[l] || l == 0 ||
+           (s->cfg.precision == CFR_FP32 && s->wlevel[l + 1] > s->wlevel[l]);
+}
+
 // Streamed top-down (bottom_up false) or bottom-up step of depth l = [j0, j1) in the instantiation
 // for the depth's largest action count.  False when the kernels could not be set up (then the caller
 // launches the per-depth kernel).
@@ -257,9 +265,8 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
     if (branch) CK(cudaEventRecord(s->join, os));
     if (s->Hp > 0) TRY(mark());
     for (int32_t l = 0; l < r; ++l) {
+        if (!topdown_launches(s, l)) continue;
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
-        // a depth whose nodes have no decision children (the last one) has no top-down step
-        // (depth 0 always launches: its first thread counts the iteration)
         if (s->ddepth_children[l] || l == 0) {
             bool streamed = false;
             if constexpr (!det) {
@@ -343,7 +350,8 @@ std::vector<std::pair<int32_t, int32_t>> phases(const cfr_solver *s) {
     if (s->L == 0) return p;
     const int32_t r = fused_from(s);
     if (s->Hp > 0) p.push_back({CFR_PHASE_OWN, -1});
-    for (int32_t l = 0; l < r; ++l) p.push_back({CFR_PHASE_TOPDOWN, l});
+    for (int32_t l = 0; l < r; ++l)
+        if (topdown_launches(s, l)) p.push_back({CFR_PHASE_TOPDOWN, l});
     if (r < s->L) p.push_back({CFR_PHASE_FUSED, r});
     for (int32_t l = r - 1; l >= 0; --l) p.push_back({CFR_PHASE_BOTTOMUP, l});
     p.push_back({CFR_PHASE_UPDATE, -1});
@@ -363,9 +371,10 @@ std::vector<std::pair<int32_t, int32_t>> phases(const cfr_solver *s) {
 //                           16 Nd(>=r) + 4 T(>=r)  node fields; one utility per terminal child
 //                         + 12 Nd(r)               the tile roots' reaches read and values written
 //   update:                 44 Q                   r~ read and zeroed, R and S read+written, sigma written
-// With nothing fused they add up to 56 Nd + 4 Nt + 44 Q + 13 Hp - 12 (96 Nd + 8 Nt + 56 Q + 17 Hp - 24
-// in FP64 mode), since every node but the root is a child once.  Hp counts the player infosets, C(l)
-// all children of depth l's nodes, T(l) their terminal children.
+// With nothing fused they add up to 56 Nd + 4 Nt + 44 Q + 13 Hp - 12 - 20 Nd(L-1) (96 Nd + 8 Nt + 56 Q
+// + 17 Hp - 24 - 32 Nd(L-1) in FP64 mode): every node but the root is a child once, and the last depth
+// has no top-down step (topdown_launches).  Hp counts the player infosets, C(l) all children of depth
+// l's nodes, T(l) their terminal children.
 std::vector<double> phase_bytes(const cfr_solver *s) {
     const bool f64 = s->cfg.precision == CFR_FP64;
     std::vector<double> b;

@@ -338,6 +338,18 @@ def test_bad_arguments_raise():
     cfr.cfr_synchronize(s)
 
 
+def _node_depths(g):
+    """Depth of every node (root 0), by following parents."""
+    d = np.full(g.num_nodes, -1, np.int64)
+    d[g.parent < 0] = 0
+    while (d < 0).any():
+        todo = d < 0
+        known = d[g.parent[todo]] >= 0
+        idx = np.nonzero(todo)[0][known]
+        d[idx] = d[g.parent[idx]] + 1
+    return d
+
+
 @pytest.mark.parametrize("precision,fuse", [(cfr.CFR_FP64, -1), (cfr.CFR_FP32, 0), (cfr.CFR_FP32, -1)])
 def test_phase_times_run_a_real_iteration(precision, fuse):
     g = gamegen.config("rank13_depth10", seed=6, target_nodes=None, p_cont=0.6)
@@ -355,14 +367,18 @@ def test_phase_times_run_a_real_iteration(precision, fuse):
     assert abs(sum(p["bytes"] for p in ph) - info["bytes_per_iteration"]) <= 1
     L, f = info["num_levels"], info["fused_from_depth"]
     kinds = [p["kind"] for p in ph]
-    assert kinds == [cfr.CFR_PHASE_OWN] + [cfr.CFR_PHASE_TOPDOWN] * f + [cfr.CFR_PHASE_FUSED] * (f < L) + \
+    n_td = f if f < L else max(L - 1, 1)                     # the last depth has no top-down step
+    assert kinds == [cfr.CFR_PHASE_OWN] + [cfr.CFR_PHASE_TOPDOWN] * n_td + [cfr.CFR_PHASE_FUSED] * (f < L) + \
         [cfr.CFR_PHASE_BOTTOMUP] * f + [cfr.CFR_PHASE_UPDATE]
     if f == L:
-        # every node but the root is some depth's child: the byte model in closed form
+        # every node but the root is some depth's child, and the last depth (no decision children) has no
+        # top-down step: the byte model in closed form
         Nd, Nt, Q = info["num_decision"], info["num_terminal"], info["num_q"]
         Hp = int((g.infoset_player > 0).sum())
-        want = (96 * Nd + 8 * Nt + 56 * Q + 17 * Hp - 24 if precision == cfr.CFR_FP64
-                else 56 * Nd + 4 * Nt + 44 * Q + 13 * Hp - 12)
+        dd = _node_depths(g)[g.infoset >= 0]
+        last = int((dd == dd.max()).sum()) if L >= 2 else 0
+        want = (96 * Nd + 8 * Nt + 56 * Q + 17 * Hp - 24 - 32 * last if precision == cfr.CFR_FP64
+                else 56 * Nd + 4 * Nt + 44 * Q + 13 * Hp - 12 - 20 * last)
         assert info["bytes_per_iteration"] == want
     else:
         assert precision == cfr.CFR_FP32 and info["fused_tiles"] > 0
