@@ -25,7 +25,7 @@ thread_local std::string g_thread_err;
 
 constexpr int kBlock = 256;
 constexpr int kWideBlock = 1024;   // nodes and infosets with more than 32 actions: one block each
-constexpr int32_t kFuseAuto = 0;   // fused depths when cfr_config.fuse_levels < 0
+constexpr int32_t kFuseAuto = 2;   // fused depths when cfr_config.fuse_levels < 0
 constexpr int32_t kStreamMinNodes = 32768;   // FP32 bottom-up depths this large use k_bottomup_stream
 
 inline int32_t nblocks(int64_t n) { return (int32_t)((n + kBlock - 1) / kBlock); }
@@ -86,7 +86,9 @@ struct cfr_solver {
     // node ranges per fused depth are fuse_bounds[k][0 .. fuse_ntiles]
     int32_t fuse_r = 0, fuse_ntiles = 0;
     int32_t *fuse_bounds = nullptr;
-    bool fuse_tail = false;                               // the last two depths by k_tail (no tiles)
+    bool fuse_tail = false;                               // the last two depths by k_tail / k_tail_stream
+    int32_t *tail_tiles = nullptr;                        // k_tail_stream: tile boundaries at depth L-2
+    int32_t ntail_tiles = 0, tl_grid[3] = {0, 0, 0};
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
     int64_t kernel_launches = 0;
     int64_t iteration = 0;
@@ -178,6 +180,41 @@ DevTree<real> dev_tree(cfr_solver *s) {
     return t;
 }
 
+// Kernel launches of one queued iteration.  In the captured graph (pdl) a kernel that directly follows
+// another kernel on its stream is a programmatic dependent launch: its blocks may be scheduled while
+// the previous kernel drains, and it waits for that kernel in grid_dependency_wait.  Any other
+// operation on the stream (a memset, an event) ends the chain (`cut`).
+struct Launcher {
+    bool pdl = false;
+    cudaStream_t chained[2] = {nullptr, nullptr};   // streams whose last operation was a kernel
+    int nchained = 0;
+    bool follows_kernel(cudaStream_t st) const {
+        for (int i = 0; i < nchained; ++i)
+            if (chained[i] == st) return true;
+        return false;
+    }
+    void cut(cudaStream_t st) {
+        for (int i = 0; i < nchained; ++i)
+            if (chained[i] == st) chained[i] = chained[--nchained];
+    }
+    template <typename... P, typename... A>
+    cudaError_t operator()(void (*k)(P...), int grid, int block, size_t smem, cudaStream_t st, A... args) {
+        cudaLaunchConfig_t c = {};
+        c.gridDim = dim3((unsigned)grid);
+        c.blockDim = dim3((unsigned)block);
+        c.dynamicSmemBytes = smem;
+        c.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        c.attrs = at;
+        c.numAttrs = pdl && follows_kernel(st) ? 1 : 0;
+        const cudaError_t e = cudaLaunchKernelEx(&c, k, args...);
+        if (!follows_kernel(st) && nchained < 2) chained[nchained++] = st;
+        return e;
+    }
+};
+
 // Whether the top-down step from depth l launches anything: a depth whose nodes have no decision
 // children (the last one) has none, except depth 0, whose first thread counts the iteration, and
 // FP32 mode's wide nodes, whose kernel runs regardless.
@@ -190,24 +227,23 @@ bool topdown_launches(const cfr_solver *s, int32_t l) {
 // for the depth's largest action count.  False when the kernels could not be set up (then the caller
 // launches the per-depth kernel).
 template <int NA>
-void launch_stream_na(const cfr_solver *s, const DevTree<float> &t, cudaStream_t st, bool bottom_up, int32_t l,
-                      int32_t j0, int32_t j1, int gi) {
+cudaError_t launch_stream_na(Launcher &go, const cfr_solver *s, const DevTree<float> &t, cudaStream_t st,
+                             bool bottom_up, int32_t l, int32_t j0, int32_t j1, int gi) {
     const int32_t tiles = (j1 - j0 + kSBN - 1) / kSBN;
     if (bottom_up)
-        k_bottomup_stream<NA><<<std::min(s->sb_grid[gi], tiles), kSBThreads, sizeof(SBStage) * kSBStages, st>>>(
-            t, j0, j1, s->d_err);
-    else
-        k_topdown_stream<NA><<<std::min(s->td_grid[gi], tiles), kSBThreads,
-                               sizeof(TDStage) * TopDownTiles<NA>::kStages, st>>>(t, j0, j1, l == 0, s->d_err);
+        return go(k_bottomup_stream<NA>, std::min(s->sb_grid[gi], tiles), kSBThreads, sizeof(SBStage) * kSBStages, st,
+                  t, j0, j1, s->d_err);
+    return go(k_topdown_stream<NA>, std::min(s->td_grid[gi], tiles), kSBThreads,
+              sizeof(TDStage) * TopDownTiles<NA>::kStages, st, t, j0, j1, (int32_t)(l == 0), s->d_err);
 }
 
-bool launch_stream(const cfr_solver *s, const DevTree<float> &t, cudaStream_t st, bool bottom_up, int32_t l,
-                   int32_t j0, int32_t j1) {
+bool launch_stream(Launcher &go, const cfr_solver *s, const DevTree<float> &t, cudaStream_t st, bool bottom_up,
+                   int32_t l, int32_t j0, int32_t j1) {
     const int gi = s->level_na[(size_t)l];
     if ((bottom_up ? s->sb_grid[gi] : s->td_grid[gi]) <= 0) return false;
-    if (gi == 0) launch_stream_na<kStreamNA[0]>(s, t, st, bottom_up, l, j0, j1, gi);
-    else if (gi == 1) launch_stream_na<kStreamNA[1]>(s, t, st, bottom_up, l, j0, j1, gi);
-    else launch_stream_na<kStreamNA[2]>(s, t, st, bottom_up, l, j0, j1, gi);
+    if (gi == 0) launch_stream_na<kStreamNA[0]>(go, s, t, st, bottom_up, l, j0, j1, gi);
+    else if (gi == 1) launch_stream_na<kStreamNA[1]>(go, s, t, st, bottom_up, l, j0, j1, gi);
+    else launch_stream_na<kStreamNA[2]>(go, s, t, st, bottom_up, l, j0, j1, gi);
     return true;
 }
 
@@ -223,6 +259,10 @@ cfr_status setup_stream_na(cfr_solver *s, int gi, int sms) {
     CK(cudaFuncSetAttribute(k_topdown_stream<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_topdown_stream<NA>, kSBThreads, tsmem));
     s->td_grid[gi] = per_sm * sms;
+    const int lsmem = (int)(sizeof(TLStage) * TailTiles<NA>::kStages);
+    CK(cudaFuncSetAttribute(k_tail_stream<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail_stream<NA>, kSBThreads, lsmem));
+    s->tl_grid[gi] = per_sm * sms;
     return CFR_OK;
 }
 
@@ -240,9 +280,14 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
     constexpr bool det = sizeof(real) == sizeof(double);
     DevTree<real> t = dev_tree<real>(s);
     const int32_t r = det ? s->L : s->fuse_r;
+    Launcher go;
+    go.pdl = ev == nullptr;
     int ne = 0;
     auto mark = [&]() -> cfr_status {
-        if (ev) CK(cudaEventRecord(ev[ne++], st));
+        if (ev) {
+            CK(cudaEventRecord(ev[ne++], st));
+            go.cut(st);
+        }
         return CFR_OK;
     };
     if (!det) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
@@ -257,12 +302,12 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
     }
     for (int32_t l = 0; l < s->L; ++l) {
         const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
-        if (h1 > h0) {
-            k_own<real><<<nblocks(h1 - h0), kBlock, 0, os>>>(t, h0, h1);
-            CK_LAUNCH();
-        }
+        if (h1 > h0) CK(go(k_own<real>, nblocks(h1 - h0), kBlock, 0, os, t, h0, h1));
     }
-    if (branch) CK(cudaEventRecord(s->join, os));
+    if (branch) {
+        CK(cudaEventRecord(s->join, os));
+        go.cut(os);
+    }
     if (s->Hp > 0) TRY(mark());
     for (int32_t l = 0; l < r; ++l) {
         if (!topdown_launches(s, l)) continue;
@@ -270,23 +315,30 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         if (s->ddepth_children[l] || l == 0) {
             bool streamed = false;
             if constexpr (!det) {
-                if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(s, t, st, false, l, j0, j1);
+                if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(go, s, t, st, false, l, j0, j1);
             }
-            if (!streamed) k_topdown<real, !det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1, l == 0);
+            if (!streamed) CK(go(k_topdown<real, !det>, nblocks(j1 - j0), kBlock, 0, st, t, j0, j1, (int32_t)(l == 0)));
             CK_LAUNCH();
         }
         const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
-        if (!det && nw > 0) {
-            k_topdown_wide<real><<<nw, kWideBlock, 0, st>>>(t, s->wide, s->wlevel[l]);
-            CK_LAUNCH();
-        }
+        if (!det && nw > 0) CK(go(k_topdown_wide<real>, nw, kWideBlock, 0, st, t, (const int32_t *)s->wide, s->wlevel[l]));
         TRY(mark());
     }
     if constexpr (!det) {
         if (r < s->L && s->fuse_tail) {
             const int32_t j0 = s->dlevel[r], j1 = s->dlevel[r + 1];
-            k_tail<<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1, s->cfg.record_nodes != 0, r == 0);
-            CK_LAUNCH();
+            const int32_t rec = s->cfg.record_nodes != 0, bump = r == 0;
+            const int gi = std::max(s->level_na[(size_t)r], s->level_na[(size_t)r + 1]);
+            if (s->ntail_tiles > 0 && s->tl_grid[gi] > 0) {
+                const int grid = std::min(s->tl_grid[gi], s->ntail_tiles);
+                const size_t smem = sizeof(TLStage) * TailTiles<3>::kStages;
+                const int32_t *tb = s->tail_tiles;
+                if (gi == 0) CK(go(k_tail_stream<kStreamNA[0]>, grid, kSBThreads, smem, st, t, tb, s->ntail_tiles, rec, bump, s->d_err));
+                else if (gi == 1) CK(go(k_tail_stream<kStreamNA[1]>, grid, kSBThreads, smem, st, t, tb, s->ntail_tiles, rec, bump, s->d_err));
+                else CK(go(k_tail_stream<kStreamNA[2]>, grid, kSBThreads, smem, st, t, tb, s->ntail_tiles, rec, bump, s->d_err));
+            } else {
+                CK(go(k_tail, nblocks(j1 - j0), kBlock, 0, st, t, j0, j1, rec, bump));
+            }
             TRY(mark());
         } else if (r < s->L) {
             FuseArgs fa;
@@ -295,8 +347,7 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
             fa.levels = s->L - r;
             fa.record = s->cfg.record_nodes != 0;
             fa.bump = r == 0;
-            k_fused<<<s->fuse_ntiles, kBlock, 0, st>>>(t, fa);
-            CK_LAUNCH();
+            CK(go(k_fused, s->fuse_ntiles, kBlock, 0, st, t, fa));
             TRY(mark());
         }
     }
@@ -304,38 +355,29 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         bool streamed = false;
         if constexpr (!det) {
-            if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(s, t, st, true, l, j0, j1);
+            if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(go, s, t, st, true, l, j0, j1);
         }
-        if (!streamed) k_bottomup<real, det><<<nblocks(j1 - j0), kBlock, 0, st>>>(t, j0, j1);
+        if (!streamed) CK(go(k_bottomup<real, det>, nblocks(j1 - j0), kBlock, 0, st, t, j0, j1));
         CK_LAUNCH();
         const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
-        if (!det && nw > 0) {
-            k_bottomup_wide<real><<<nw, kWideBlock, 0, st>>>(t, s->wide, s->wlevel[l]);
-            CK_LAUNCH();
-        }
+        if (!det && nw > 0) CK(go(k_bottomup_wide<real>, nw, kWideBlock, 0, st, t, (const int32_t *)s->wide, s->wlevel[l]));
         TRY(mark());
     }
-    if (branch) CK(cudaStreamWaitEvent(st, s->join, 0));
-    const int linear = s->cfg.avg_weight == CFR_AVG_LINEAR;
+    if (branch) {
+        CK(cudaStreamWaitEvent(st, s->join, 0));
+        go.cut(st);
+    }
+    const int32_t linear = s->cfg.avg_weight == CFR_AVG_LINEAR, plus = s->cfg.variant == CFR_PLUS;
     if constexpr (det) {
-        if (s->Hp > 0) {
-            k_update<real, det><<<nblocks(s->Hp), kBlock, 0, st>>>(t, s->Hp, s->cfg.variant == CFR_PLUS, linear);
-            CK_LAUNCH();
-        }
+        if (s->Hp > 0) CK(go(k_update<real, det>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, plus, linear));
     } else {
-        {
-            if (s->Hp > 0) {
-                const int plus = s->cfg.variant == CFR_PLUS;
-                if (s->hp_na <= 3) k_update_rows<3><<<nblocks(s->Hp), kBlock, 0, st>>>(t, s->Hp, plus, linear);
-                else if (s->hp_na <= 5) k_update_rows<5><<<nblocks(s->Hp), kBlock, 0, st>>>(t, s->Hp, plus, linear);
-                else k_update_rows<8><<<nblocks(s->Hp), kBlock, 0, st>>>(t, s->Hp, plus, linear);
-                CK_LAUNCH();
-            }
-            if (s->nwide_h > 0) {
-                k_update_list<<<s->nwide_h, kWideBlock, 0, st>>>(t, s->wide_h, s->cfg.variant == CFR_PLUS, linear);
-                CK_LAUNCH();
-            }
+        if (s->Hp > 0) {
+            if (s->hp_na <= 3) CK(go(k_update_rows<3>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, plus, linear));
+            else if (s->hp_na <= 5) CK(go(k_update_rows<5>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, plus, linear));
+            else CK(go(k_update_rows<8>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, plus, linear));
         }
+        if (s->nwide_h > 0)
+            CK(go(k_update_list, s->nwide_h, kWideBlock, 0, st, t, (const int32_t *)s->wide_h, plus, linear));
     }
     TRY(mark());
     return CFR_OK;
@@ -470,9 +512,31 @@ cfr_status plan_fusion(cfr_solver *s, const Layout &Lo) {
         if (s->wlevel[l + 1] > s->wlevel[l]) wdeep = l;
     const int32_t rmin = std::max(s->L - want, wdeep + 1);
     if (s->L - rmin < 2) return CFR_OK;
-    if (want == 2) {                                           // thread per node of depth L-2
-        s->fuse_r = s->L - 2;
+    if (want == 2) {                                           // the last two depths in one pass
+        const int32_t r = s->L - 2;
+        s->fuse_r = r;
         s->fuse_tail = true;
+        if (s->dlevel[r + 1] - s->dlevel[r] >= kStreamMinNodes) {
+            // tiles for k_tail_stream: consecutive parents while every staged range fits its array
+            // (4 elements of each kept free for the 16-byte widening of the copies)
+            std::vector<int32_t> tb{s->dlevel[r]};
+            int32_t n = 0, nc = 0, npt = 0, nct = 0;
+            for (int32_t j = s->dlevel[r]; j < s->dlevel[r + 1]; ++j) {
+                const int32_t d0 = Lo.dfirst[(size_t)j], d1 = Lo.dfirst[(size_t)j + 1];
+                const int32_t ndj = d1 - d0, ptj = Lo.tfirst[(size_t)j + 1] - Lo.tfirst[(size_t)j];
+                const int32_t ctj = Lo.tfirst[(size_t)d1] - Lo.tfirst[(size_t)d0];
+                if (n + 1 > kTP || nc + ndj > kTC - 4 || npt + ptj > kTPT - 4 || nct + ctj > kTCT - 4) {
+                    tb.push_back(j);
+                    n = nc = npt = nct = 0;
+                }
+                ++n; nc += ndj; npt += ptj; nct += ctj;
+            }
+            tb.push_back(s->dlevel[r + 1]);
+            s->ntail_tiles = (int32_t)tb.size() - 1;
+            TRY(alloc_n(s, &s->tail_tiles, (int64_t)tb.size()));
+            TRY(upload(s, s->tail_tiles, tb));
+            CK(cudaStreamSynchronize(s->stream));
+        }
         return CFR_OK;
     }
     // decision nodes in the subtree of each node of depth >= rmin (children have larger ids)
@@ -998,7 +1062,8 @@ cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info) {
     info->kernel_launches = s->kernel_launches;
     info->fused_from_depth = fused_from(s);
     info->fused_tiles = fused_from(s) == s->L ? 0
-                        : s->fuse_tail ? nblocks(s->dlevel[s->fuse_r + 1] - s->dlevel[s->fuse_r]) : s->fuse_ntiles;
+                        : !s->fuse_tail ? s->fuse_ntiles
+                        : s->ntail_tiles > 0 ? s->ntail_tiles : nblocks(s->dlevel[s->fuse_r + 1] - s->dlevel[s->fuse_r]);
     return CFR_OK;
 }
 

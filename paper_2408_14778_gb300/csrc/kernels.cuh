@@ -40,6 +40,12 @@ __device__ __forceinline__ T ldm(const T *p) {
     else return *p;
 }
 
+// Waits until the kernels this launch depends on have completed and their writes are visible.  The
+// iteration's kernels are launched as programmatic dependent launches (their blocks may be scheduled
+// while the previous kernel drains), so each calls this before touching memory; for an ordinary
+// launch it returns at once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Per-node word qp (layout.hpp): the infoset's first slot, a wide flag and the acting player.
 __device__ __forceinline__ int32_t qp_base(uint32_t w) { return (int32_t)(w & 0x1fffffffu); }
 __device__ __forceinline__ bool qp_wide(uint32_t w) { return (w >> 29) & 1u; }
@@ -115,17 +121,20 @@ __device__ __forceinline__ void own_infoset(const DevTree<real> &t, int32_t h) {
 
 // Top-down step of decision node j: reaches of its decision children.
 // kSkipWide: nodes with more than 32 actions are left to td_wide.
+// The node's fields are all loaded before any is used (one memory round trip; the kernels that call
+// this on small depths are latency-bound).
 template <typename real, bool kSkipWide, bool C>
 __device__ __forceinline__ void td_node(const DevTree<real> &t, int32_t j) {
     int32_t c = t.dfirst[j];
-    const int32_t nd = t.dfirst[j + 1] - c;
-    if (nd == 0) return;                                  // no decision children
+    const int32_t c1 = t.dfirst[j + 1];
     const uint32_t w = t.qp[j];
+    const uint32_t m = t.kmask[j];
+    const real r1 = ldm<C>(t.reach1 + j), r2 = ldm<C>(t.reach2 + j);
+    const int32_t nd = c1 - c;
+    if (nd == 0) return;                                  // no decision children
     if (kSkipWide && qp_wide(w)) return;
     const int32_t qb = qp_base(w);
     const int p = qp_player(w);
-    const uint32_t m = t.kmask[j];
-    const real r1 = ldm<C>(t.reach1 + j), r2 = ldm<C>(t.reach2 + j);
     if (!qp_wide(w)) {
         const int na = nd + __popc(m);
         if (na <= kUnroll) {
@@ -158,16 +167,19 @@ __device__ __forceinline__ void td_node(const DevTree<real> &t, int32_t j) {
 // nodes with more than 32 actions are left to bu_wide.
 // kDet = true: they are stored per edge and k_update sums them per infoset in depth-first node
 // order, which makes the result independent of scheduling; every node is summed sequentially.
+// The node's fields, both reaches included, are loaded before any is used (one memory round trip
+// before the child values; the kernels that call this on small depths are latency-bound).
 template <typename real, bool kDet, bool C>
 __device__ __forceinline__ void bu_node(const DevTree<real> &t, int32_t j) {
     const uint32_t w = t.qp[j];
+    const uint32_t m = t.kmask[j];
+    const int32_t c0 = t.dfirst[j], c1 = t.dfirst[j + 1], t0 = t.tfirst[j], t1 = t.tfirst[j + 1];
+    const real rr1 = ldm<C>(t.reach1 + j), rr2 = ldm<C>(t.reach2 + j);
     if (!kDet && qp_wide(w)) return;
     const int32_t qb = qp_base(w);
     const int p = qp_player(w);
-    const uint32_t m = t.kmask[j];
-    const int32_t c0 = t.dfirst[j], t0 = t.tfirst[j];
-    const int32_t nd = t.dfirst[j + 1] - c0;
-    const int na = qp_wide(w) ? nd + (t.tfirst[j + 1] - t0) : nd + __popc(m);
+    const int32_t nd = c1 - c0;
+    const int na = qp_wide(w) ? nd + (t1 - t0) : nd + __popc(m);
     real *out = kDet ? t.contrib + (c0 + t0 - 1) : nullptr;
     if (na <= kUnroll) {
         real v[kUnroll], s[kUnroll];
@@ -188,7 +200,7 @@ __device__ __forceinline__ void bu_node(const DevTree<real> &t, int32_t j) {
             if (a < na) ud = madd(ud, s[a], v[a]);
         t.u[j] = ud;
         if (p == 0) return;
-        const real wr = p == 1 ? ldm<C>(t.reach1 + j) : -ldm<C>(t.reach2 + j);   // u_2 = -u_1
+        const real wr = p == 1 ? rr1 : -rr2;   // u_2 = -u_1
         if (!kDet && wr == real(0)) return;
 #pragma unroll
         for (int a = 0; a < kUnroll; ++a) {
@@ -207,7 +219,7 @@ __device__ __forceinline__ void bu_node(const DevTree<real> &t, int32_t j) {
     }
     t.u[j] = ud;
     if (p == 0) return;
-    const real wr = p == 1 ? ldm<C>(t.reach1 + j) : -ldm<C>(t.reach2 + j);
+    const real wr = p == 1 ? rr1 : -rr2;
     if (!kDet && wr == real(0)) return;
     c = c0; tt = t0;
     for (int a = 0; a < na; ++a) {
@@ -318,6 +330,7 @@ __device__ __forceinline__ void regret_match_tiny(const DevTree<float> &t, int32
 
 template <int NA>
 __global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t Hp, int32_t plus, int32_t linear) {
+    grid_dependency_wait();
     const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (h >= Hp) return;
     const int32_t qs = t.qbase[h];
@@ -384,6 +397,7 @@ __global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t H
 // The infosets hs[0 .. gridDim.x) (more than 32 actions), one block each (up to 1024 threads).
 __global__ void __launch_bounds__(1024) k_update_list(DevTree<float> t, const int32_t *hs, int32_t plus,
                                                       int32_t linear) {
+    grid_dependency_wait();
     __shared__ float s_red[32];
     update_wide(t, hs[blockIdx.x], plus != 0, linear ? (float)*t.iter : 1.f, s_red);
 }
@@ -393,6 +407,7 @@ __global__ void __launch_bounds__(1024) k_update_list(DevTree<float> t, const in
 // Own reaches of the player infosets [h0, h1) (those whose shallowest depth is one given depth).
 template <typename real>
 __global__ void __launch_bounds__(256) k_own(DevTree<real> t, int32_t h0, int32_t h1) {
+    grid_dependency_wait();
     const int32_t h = h0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (h < h1) own_infoset<real, false>(t, h);
 }
@@ -400,6 +415,7 @@ __global__ void __launch_bounds__(256) k_own(DevTree<real> t, int32_t h0, int32_
 // Top-down from depth l: one thread per decision node of depth l.  bump: count the iteration.
 template <typename real, bool kSkipWide>
 __global__ void __launch_bounds__(256) k_topdown(DevTree<real> t, int32_t j0, int32_t j1, int32_t bump) {
+    grid_dependency_wait();
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
     const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (j < j1) td_node<real, kSkipWide, false>(t, j);
@@ -407,17 +423,20 @@ __global__ void __launch_bounds__(256) k_topdown(DevTree<real> t, int32_t j0, in
 
 template <typename real, bool kDet>
 __global__ void __launch_bounds__(256) k_bottomup(DevTree<real> t, int32_t j0, int32_t j1) {
+    grid_dependency_wait();
     const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (j < j1) bu_node<real, kDet, false>(t, j);
 }
 
 template <typename real>
 __global__ void __launch_bounds__(1024) k_topdown_wide(DevTree<real> t, const int32_t *wide, int32_t w0) {
+    grid_dependency_wait();
     td_wide<real, false>(t, wide[w0 + blockIdx.x]);
 }
 
 template <typename real>
 __global__ void __launch_bounds__(1024) k_bottomup_wide(DevTree<real> t, const int32_t *wide, int32_t w0) {
+    grid_dependency_wait();
     __shared__ real s_red[32];
     bu_wide<real, false>(t, wide[w0 + blockIdx.x], s_red);
 }
@@ -552,6 +571,7 @@ __device__ __forceinline__ void fused_bu(const DevTree<float> &t, FuseShared &sh
 }
 
 __global__ void __launch_bounds__(256) k_fused(DevTree<float> t, FuseArgs a) {
+    grid_dependency_wait();
     __shared__ FuseShared sh;
     if (a.bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
     const int K = a.levels;
@@ -677,6 +697,7 @@ __device__ __forceinline__ float tail_leaf(const DevTree<float> &t, int32_t c, f
 // bump: depth L-2 is the root's, so no top-down launch precedes this one; count the iteration.
 __global__ void __launch_bounds__(256) k_tail(DevTree<float> t, int32_t j0, int32_t j1, int32_t record,
                                               int32_t bump) {
+    grid_dependency_wait();
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
     const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (j >= j1) return;
@@ -757,6 +778,7 @@ __device__ __forceinline__ void regret_match(real *sigma, const double *R, int32
 // Per-infoset update, one thread per infoset, FP64 operations in the oracle's order (FP64 mode).
 template <typename real, bool kDet>
 __global__ void __launch_bounds__(256) k_update(DevTree<real> t, int32_t H, int32_t plus, int32_t linear) {
+    grid_dependency_wait();
     const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (h >= H || t.iplayer[h] == 0) return;
     const int32_t qb = t.qbase[h];

@@ -342,6 +342,7 @@ struct BottomUpTiles {
 
 template <int NA>
 __global__ void __launch_bounds__(kSBThreads) k_bottomup_stream(DevTree<float> t, int32_t jb, int32_t je, int *err) {
+    grid_dependency_wait();
     run_pipeline(BottomUpTiles<NA>{t, jb, je}, err);
 }
 
@@ -457,9 +458,249 @@ struct TopDownTiles {
 template <int NA>
 __global__ void __launch_bounds__(kSBThreads) k_topdown_stream(DevTree<float> t, int32_t jb, int32_t je, int32_t bump,
                                                                int *err) {
+    grid_dependency_wait();
     __shared__ float out1[kTDOut], out2[kTDOut];
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
     run_pipeline(TopDownTiles<NA>{t, jb, je, out1, out2}, err);
+}
+
+// ---- the last two depths, streamed (FP32 mode) -------------------------------------------------------
+// One pass over the depths L-2 and L-1 (the nodes of L-1 have terminal children only) in tiles of
+// consecutive depth-(L-2) nodes ("parents"), cut on the host so that every range below fits its stage
+// array (tail_tiles in the host code).  The producer stages the parents' fields and reaches, their
+// decision children's fields (qp, kmask, tfirst) and the two contiguous utility ranges: the parents'
+// terminal children and the children's terminal children.  The consumers then run
+//   phase 0, one thread per parent: the top-down step (td_node's arithmetic) with the children's
+//            reaches written to shared memory, the parent's strategy entries kept in registers;
+//   phase 1, one thread per child: its bottom-up step (bu_node's arithmetic), value to shared memory;
+//   phase 2, one thread per parent: its bottom-up step.
+// Global memory sees the staged inputs once, the parents' values (written), the strategy gathers and
+// the regret scatter; the children's reaches and values stay on chip unless record is set.  Nodes with
+// more than 32 actions are not handled (the host keeps such trees off this kernel).
+constexpr int kTP = 256;                   // parents per tile (one per consumer thread)
+constexpr int kTC = 768;                   // children per tile, at most
+constexpr int kTPT = 768;                  // parents' terminal children per tile, at most
+constexpr int kTCT = 3072;                 // children's terminal children per tile, at most
+
+struct TLStage {                           // + 4 / + 8: room for widening the copies to 16 bytes
+    uint32_t qp[kTP + 4], km[kTP + 4];
+    float r1[kTP + 4], r2[kTP + 4];
+    int32_t df[kTP + 8], tf[kTP + 8];
+    uint32_t cqp[kTC + 4], ckm[kTC + 4];
+    int32_t ctf[kTC + 8];
+    float pu[kTPT + 4], cu[kTCT + 4];
+};
+
+struct TLTile {
+    int32_t j0, n, o;                      // parents [j0, j0 + n); node j0 at index o of the parent arrays
+    int32_t cs, nc, co;                    // children [cs, cs + nc); child cs at index co of the child arrays
+    int32_t pal, cal;                      // global terminal index of pu[0] / cu[0]
+};
+
+template <int NA>
+struct TailTiles {
+    using Stage = TLStage;
+    using Tile = TLTile;
+    static constexpr int kStages = 2;
+    static constexpr bool kConsumerSync = true;
+    DevTree<float> t;
+    const int32_t *tb;                     // tile i: parents tb[i] .. tb[i + 1] - 1
+    int32_t nt, record;
+    float *q1, *q2, *cu;                   // shared memory, kTC each: children's reaches and values
+    __device__ int32_t ntiles() const { return nt; }
+    __device__ void issue(int32_t tile, Stage *st, Tile *ti, uint64_t *full) const {
+        const int32_t j0 = tb[tile], n = tb[tile + 1] - j0;
+        uint32_t bf, bd, bc, bct, bpu, bcu;
+        const int32_t jal = widen16(j0, j0 + n, &bf);
+        widen16(j0, j0 + n + 1, &bd);
+        const int32_t cs = t.dfirst[j0], ce = t.dfirst[j0 + n];
+        const int32_t pts = t.tfirst[j0], pte = t.tfirst[j0 + n];
+        const int32_t cts = t.tfirst[cs], cte = t.tfirst[ce];
+        const int32_t cal_n = widen16(cs, ce, &bc);
+        widen16(cs, ce + 1, &bct);
+        const int32_t pal = widen16(pts, pte, &bpu);
+        const int32_t cal = widen16(cts, cte, &bcu);
+        ti->j0 = j0; ti->n = n; ti->o = j0 - jal;
+        ti->cs = cs; ti->nc = ce - cs; ti->co = cs - cal_n;
+        ti->pal = pal; ti->cal = cal;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(full, 4 * bf + 2 * bd + 2 * bc + bct + bpu + bcu);
+        bulk_g2s(st->qp, t.qp + jal, bf, full);
+        bulk_g2s(st->km, t.kmask + jal, bf, full);
+        bulk_g2s(st->r1, t.reach1 + jal, bf, full);
+        bulk_g2s(st->r2, t.reach2 + jal, bf, full);
+        bulk_g2s(st->df, t.dfirst + jal, bd, full);
+        bulk_g2s(st->tf, t.tfirst + jal, bd, full);
+        if (bc) {
+            bulk_g2s(st->cqp, t.qp + cal_n, bc, full);
+            bulk_g2s(st->ckm, t.kmask + cal_n, bc, full);
+        }
+        bulk_g2s(st->ctf, t.tfirst + cal_n, bct, full);
+        if (bpu) bulk_g2s(st->pu, t.util + pal, bpu, full);
+        if (bcu) bulk_g2s(st->cu, t.util + cal, bcu, full);
+    }
+    // Thread c takes parent c and children c, c + 256, c + 512 (kTCPer of them); the strategy entries of
+    // all of them are loaded in one round before phase 0.
+    static constexpr int kTCPer = (kTC + kSBConsumerWarps * 32 - 1) / (kSBConsumerWarps * 32);
+    __device__ void consume(const Stage &st, const Tile &ti, int c) const {
+        constexpr int kC = kSBConsumerWarps * 32;
+        const bool act = c < ti.n;
+        const int32_t k = ti.o + c;
+        uint32_t m = 0;
+        int32_t c0 = 0, t0 = 0, qb = 0;
+        int na = 0, p = 0;
+        float r1 = 0.f, r2 = 0.f;
+        float s[NA];
+        if (act) {
+            const uint32_t w = st.qp[k];
+            m = st.km[k];
+            c0 = st.df[k];
+            na = (st.df[k + 1] - c0) + __popc(m);
+            t0 = st.tf[k];
+            r1 = st.r1[k];
+            r2 = st.r2[k];
+            qb = qp_base(w);
+            p = qp_player(w);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) s[a] = a < na ? __ldg(t.sigma + qb + a) : 0.f;
+        }
+        uint32_t cm[kTCPer];
+        int32_t cqb[kTCPer];
+        float sc[kTCPer][NA];
+#pragma unroll
+        for (int r = 0; r < kTCPer; ++r) {
+            const int32_t ci = c + r * kC;
+            cm[r] = 0;
+            cqb[r] = 0;
+            if (ci < ti.nc) {
+                const uint32_t cw = st.cqp[ti.co + ci];
+                cm[r] = st.ckm[ti.co + ci];
+                cqb[r] = (int32_t)cw;                      // qp word; base and player taken below
+                const int cna = __popc(cm[r]);
+#pragma unroll
+                for (int b = 0; b < NA; ++b) sc[r][b] = b < cna ? __ldg(t.sigma + qp_base(cw) + b) : 0.f;
+            }
+        }
+        // phase 0: parent c's top-down step, the children's reaches to shared memory
+        if (act) {
+            int32_t y = c0 - ti.cs;
+            if (na <= NA) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    if (a < na && !((m >> a) & 1u)) {
+                        q1[y] = p == 1 ? r1 : r1 * s[a];
+                        q2[y] = p == 2 ? r2 : r2 * s[a];
+                        ++y;
+                    }
+                }
+            } else {
+                for (int a = 0; a < na; ++a) {
+                    if ((m >> a) & 1u) continue;
+                    const float sv = __ldg(t.sigma + qb + a);
+                    q1[y] = p == 1 ? r1 : r1 * sv;
+                    q2[y] = p == 2 ? r2 : r2 * sv;
+                    ++y;
+                }
+            }
+        }
+        consumers_sync();
+        // phase 1: the children's bottom-up steps (terminal children only)
+#pragma unroll
+        for (int r = 0; r < kTCPer; ++r) {
+            const int32_t ci = c + r * kC;
+            if (ci >= ti.nc) continue;
+            const uint32_t cw = (uint32_t)cqb[r];
+            const int32_t cq = qp_base(cw);
+            const int cp = qp_player(cw);
+            const int cna = __popc(cm[r]);
+            const float *tv = st.cu + (st.ctf[ti.co + ci] - ti.cal);
+            float ud = 0.f;
+            float v[NA];
+            if (cna <= NA) {
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    if (b < cna) {
+                        v[b] = tv[b];
+                        ud = madd(ud, sc[r][b], v[b]);
+                    }
+                }
+            } else {
+                for (int b = 0; b < cna; ++b) ud = madd(ud, __ldg(t.sigma + cq + b), tv[b]);
+            }
+            cu[ci] = ud;
+            const float cq1 = q1[ci], cq2 = q2[ci];
+            if (record) {
+                const int32_t cg = ti.cs + ci;
+                t.u[cg] = ud;
+                t.reach1[cg] = cq1;
+                t.reach2[cg] = cq2;
+            }
+            if (cp == 0) continue;
+            const float wr = cp == 1 ? cq1 : -cq2;
+            if (wr == 0.f) continue;
+            if (cna <= NA) {
+#pragma unroll
+                for (int b = 0; b < NA; ++b)
+                    if (b < cna) atomicAdd(&t.inst[cq + b], wr * (v[b] - ud));
+            } else {
+                for (int b = 0; b < cna; ++b) atomicAdd(&t.inst[cq + b], wr * (tv[b] - ud));
+            }
+        }
+        consumers_sync();
+        // phase 2: parent c's bottom-up step
+        if (!act) return;
+        const float *pv = st.pu + (t0 - ti.pal);
+        const float *dv = cu + (c0 - ti.cs);
+        float ud = 0.f;
+        if (na <= NA) {
+            float v[NA];
+            int kt = 0, kd = 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                if (a < na) {
+                    const bool term = (m >> a) & 1u;
+                    v[a] = term ? pv[kt] : dv[kd];
+                    kt += term;
+                    kd += !term;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                if (a < na) ud = madd(ud, s[a], v[a]);
+            t.u[ti.j0 + c] = ud;
+            if (p == 0) return;
+            const float wr = p == 1 ? r1 : -r2;
+            if (wr == 0.f) return;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                if (a < na) atomicAdd(&t.inst[qb + a], wr * (v[a] - ud));
+            return;
+        }
+        int kt = 0, kd = 0;
+        for (int a = 0; a < na; ++a) {
+            const float val = ((m >> a) & 1u) ? pv[kt++] : dv[kd++];
+            ud = madd(ud, __ldg(t.sigma + qb + a), val);
+        }
+        t.u[ti.j0 + c] = ud;
+        if (p == 0) return;
+        const float wr = p == 1 ? r1 : -r2;
+        if (wr == 0.f) return;
+        kt = kd = 0;
+        for (int a = 0; a < na; ++a) {
+            const float val = ((m >> a) & 1u) ? pv[kt++] : dv[kd++];
+            atomicAdd(&t.inst[qb + a], wr * (val - ud));
+        }
+    }
+};
+
+// bump: depth L-2 is the root's, so no top-down launch precedes this one; count the iteration.
+template <int NA>
+__global__ void __launch_bounds__(kSBThreads) k_tail_stream(DevTree<float> t, const int32_t *tb, int32_t nt,
+                                                            int32_t record, int32_t bump, int *err) {
+    grid_dependency_wait();
+    __shared__ float q1[kTC], q2[kTC], cu[kTC];
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
+    run_pipeline(TailTiles<NA>{t, tb, nt, record, q1, q2, cu}, err);
 }
 
 // Unrolled action counts the streamed kernels are built for; a depth takes the smallest one that
