@@ -87,7 +87,7 @@ struct cfr_solver {
     int32_t fuse_r = 0, fuse_ntiles = 0;
     int32_t *fuse_bounds = nullptr;
     bool fuse_tail = false;                               // the last two depths by k_tail / k_tail_stream
-    int32_t *tail_tiles = nullptr;                        // k_tail_stream: tile boundaries at depth L-2
+    int32_t *tail_tiles = nullptr;                        // k_tail_stream: 8 words per tile (TailTiles::tm)
     int32_t ntail_tiles = 0, tl_grid[3] = {0, 0, 0};
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
     int64_t kernel_launches = 0;
@@ -292,8 +292,9 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
     };
     if (!det) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
     TRY(mark());
-    // own reaches, depth by depth
-    const bool branch = ev == nullptr && s->Hp > 0;
+    // own reaches, depth by depth; in the graph on a branch beside the node passes that joins before the
+    // update
+    const bool branch = ev == nullptr;
     cudaStream_t os = st;
     if (branch) {
         os = s->side;
@@ -332,7 +333,7 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
             if (s->ntail_tiles > 0 && s->tl_grid[gi] > 0) {
                 const int grid = std::min(s->tl_grid[gi], s->ntail_tiles);
                 const size_t smem = sizeof(TLStage) * TailTiles<3>::kStages;
-                const int32_t *tb = s->tail_tiles;
+                const int4 *tb = reinterpret_cast<const int4 *>(s->tail_tiles);
                 if (gi == 0) CK(go(k_tail_stream<kStreamNA[0]>, grid, kSBThreads, smem, st, t, tb, s->ntail_tiles, rec, bump, s->d_err));
                 else if (gi == 1) CK(go(k_tail_stream<kStreamNA[1]>, grid, kSBThreads, smem, st, t, tb, s->ntail_tiles, rec, bump, s->d_err));
                 else CK(go(k_tail_stream<kStreamNA[2]>, grid, kSBThreads, smem, st, t, tb, s->ntail_tiles, rec, bump, s->d_err));
@@ -533,8 +534,18 @@ cfr_status plan_fusion(cfr_solver *s, const Layout &Lo) {
             }
             tb.push_back(s->dlevel[r + 1]);
             s->ntail_tiles = (int32_t)tb.size() - 1;
-            TRY(alloc_n(s, &s->tail_tiles, (int64_t)tb.size()));
-            TRY(upload(s, s->tail_tiles, tb));
+            // per tile: {j0, j1, cs, ce}, {pts, pte, cts, cte} (k_tail_stream's TailTiles::tm)
+            std::vector<int32_t> meta;
+            meta.reserve((size_t)8 * s->ntail_tiles);
+            for (int32_t i = 0; i < s->ntail_tiles; ++i) {
+                const int32_t j0 = tb[(size_t)i], j1 = tb[(size_t)i + 1];
+                const int32_t cs = Lo.dfirst[(size_t)j0], ce = Lo.dfirst[(size_t)j1];
+                const int32_t v[8] = {j0, j1, cs, ce, Lo.tfirst[(size_t)j0], Lo.tfirst[(size_t)j1], Lo.tfirst[(size_t)cs],
+                                      Lo.tfirst[(size_t)ce]};
+                meta.insert(meta.end(), v, v + 8);
+            }
+            TRY(alloc_n(s, &s->tail_tiles, (int64_t)meta.size()));
+            TRY(upload(s, s->tail_tiles, meta));
             CK(cudaStreamSynchronize(s->stream));
         }
         return CFR_OK;

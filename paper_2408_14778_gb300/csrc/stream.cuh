@@ -107,14 +107,14 @@ __device__ __forceinline__ int32_t widen16(int32_t a, int32_t b, uint32_t *bytes
     return a0;
 }
 
-// Producer: the copies of nodes [j0, j0 + n) into stage st.
-__device__ __forceinline__ void sb_issue(const DevTree<float> &t, int32_t j0, int32_t n, SBStage *st, SBTile *ti,
-                                         uint64_t *full) {
+// Producer: the copies of nodes [j0, j0 + n) into stage st; r = {tfirst[j0], tfirst[j0 + n],
+// dfirst[j0], dfirst[j0 + n]} (loaded a tile ahead).
+__device__ __forceinline__ void sb_issue(const DevTree<float> &t, int32_t j0, int32_t n, const int32_t *r, SBStage *st,
+                                         SBTile *ti, uint64_t *full) {
     uint32_t bf, bd, btv = 0, bdv = 0;
     const int32_t jal = widen16(j0, j0 + n, &bf);
     widen16(j0, j0 + n + 1, &bd);
-    const int32_t ts = t.tfirst[j0], te = t.tfirst[j0 + n];
-    const int32_t ds = t.dfirst[j0], de = t.dfirst[j0 + n];
+    const int32_t ts = r[0], te = r[1], ds = r[2], de = r[3];
     const int32_t tal = widen16(ts, te, &btv);
     const int32_t dal = widen16(ds, de, &bdv);
     const bool staged = btv <= 4u * (kSBT + 4) && bdv <= 4u * (kSBD + 4);
@@ -258,7 +258,8 @@ __device__ __forceinline__ bool consumers_any(bool v) {
 
 // ---- the producer/consumer pipeline --------------------------------------------------------------
 // P supplies the tile work: P::Stage and P::Tile (shared-memory stage and its description),
-// P::kStages, ntiles(), issue(tile, stage, tile info, full barrier) run by one producer thread, and
+// P::kStages, ntiles(), prefetch(tile, meta) (loads P::kMetaWords words of P::Meta describing a tile,
+// one tile ahead), issue(tile, meta, stage, tile info, full barrier) run by one producer thread, and
 // consume(stage, tile info, consumer thread index) run by each of the kSBConsumerWarps * 32 consumer
 // threads.  P::kConsumerSync: consume() synchronises the consumer threads, so they agree (one
 // barrier with an OR) on whether to take each tile or stop.  Block b takes tiles b, b + gridDim.x, ...  Returns true in consumer threads once their
@@ -287,13 +288,17 @@ __device__ __forceinline__ bool run_pipeline(const P &p, int *err) {
     if (warp == kSBConsumerWarps) {                                   // producer warp
         if (lane != 0) return false;
         int32_t issued = 0;
+        typename P::Meta meta[2][P::kMetaWords];
+        if ((int32_t)blockIdx.x < ntiles) p.prefetch(blockIdx.x, meta[0]);
         for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++issued) {
             const int s = issued % S;
+            // the next tile's description is loaded while this one waits for its stage
+            if (tile + (int32_t)gridDim.x < ntiles) p.prefetch(tile + gridDim.x, meta[(issued + 1) & 1]);
             if (issued >= S && !mbar_wait(&empty[s], (uint32_t)((issued / S - 1) & 1), abort)) {
                 if (!*abort) { atomicExch(err, 1); *abort = 1; }
                 break;
             }
-            p.issue(tile, &stage[s], &tinfo[s], &full[s]);
+            p.issue(tile, meta[issued & 1], &stage[s], &tinfo[s], &full[s]);
         }
         // the block must not exit with copies in flight: wait for the last use of each stage
         for (int s = 0; s < S && s < issued; ++s) {
@@ -330,9 +335,18 @@ struct BottomUpTiles {
     DevTree<float> t;
     int32_t jb, je;
     __device__ int32_t ntiles() const { return (je - jb + kSBN - 1) / kSBN; }
-    __device__ void issue(int32_t tile, Stage *st, Tile *ti, uint64_t *full) const {
+    using Meta = int32_t;
+    static constexpr int kMetaWords = 4;
+    __device__ void prefetch(int32_t tile, int32_t *r) const {        // the tile's child ranges
+        const int32_t j0 = jb + tile * kSBN, j1 = min(je, j0 + kSBN);
+        r[0] = __ldg(t.tfirst + j0);
+        r[1] = __ldg(t.tfirst + j1);
+        r[2] = __ldg(t.dfirst + j0);
+        r[3] = __ldg(t.dfirst + j1);
+    }
+    __device__ void issue(int32_t tile, const int32_t *r, Stage *st, Tile *ti, uint64_t *full) const {
         const int32_t j0 = jb + tile * kSBN;
-        sb_issue(t, j0, min(kSBN, je - j0), st, ti, full);
+        sb_issue(t, j0, min(kSBN, je - j0), r, st, ti, full);
     }
     __device__ void consume(const Stage &st, const Tile &ti, int c) const {
         const Tile tl = ti;
@@ -373,7 +387,10 @@ struct TopDownTiles {
     int32_t jb, je;
     float *o1, *o2;                                  // shared-memory output buffers, kTDOut each
     __device__ int32_t ntiles() const { return (je - jb + kSBN - 1) / kSBN; }
-    __device__ void issue(int32_t tile, Stage *st, Tile *ti, uint64_t *full) const {
+    using Meta = int32_t;
+    static constexpr int kMetaWords = 1;
+    __device__ void prefetch(int32_t, int32_t *) const {}
+    __device__ void issue(int32_t tile, const int32_t *, Stage *st, Tile *ti, uint64_t *full) const {
         const int32_t j0 = jb + tile * kSBN, n = min(kSBN, je - j0);
         uint32_t bf, bd;
         const int32_t jal = widen16(j0, j0 + n, &bf);
@@ -477,7 +494,7 @@ __global__ void __launch_bounds__(kSBThreads) k_topdown_stream(DevTree<float> t,
 // Global memory sees the staged inputs once, the parents' values (written), the strategy gathers and
 // the regret scatter; the children's reaches and values stay on chip unless record is set.  Nodes with
 // more than 32 actions are not handled (the host keeps such trees off this kernel).
-constexpr int kTP = 256;                   // parents per tile (one per consumer thread)
+constexpr int kTP = 256;                   // parents per tile, at most (one per consumer thread)
 constexpr int kTC = 768;                   // children per tile, at most
 constexpr int kTPT = 768;                  // parents' terminal children per tile, at most
 constexpr int kTCT = 3072;                 // children's terminal children per tile, at most
@@ -504,18 +521,23 @@ struct TailTiles {
     static constexpr int kStages = 2;
     static constexpr bool kConsumerSync = true;
     DevTree<float> t;
-    const int32_t *tb;                     // tile i: parents tb[i] .. tb[i + 1] - 1
+    const int4 *tm;                        // per tile two int4: {j0, j1, cs, ce}, {pts, pte, cts, cte}: its
+                                           // parents, their decision children, and the two terminal ranges
     int32_t nt, record;
     float *q1, *q2, *cu;                   // shared memory, kTC each: children's reaches and values
     __device__ int32_t ntiles() const { return nt; }
-    __device__ void issue(int32_t tile, Stage *st, Tile *ti, uint64_t *full) const {
-        const int32_t j0 = tb[tile], n = tb[tile + 1] - j0;
+    using Meta = int4;
+    static constexpr int kMetaWords = 2;
+    __device__ void prefetch(int32_t tile, int4 *meta) const {
+        meta[0] = __ldg(tm + 2 * tile);
+        meta[1] = __ldg(tm + 2 * tile + 1);
+    }
+    __device__ void issue(int32_t, const int4 *meta, Stage *st, Tile *ti, uint64_t *full) const {
+        const int32_t j0 = meta[0].x, n = meta[0].y - j0, cs = meta[0].z, ce = meta[0].w;
+        const int32_t pts = meta[1].x, pte = meta[1].y, cts = meta[1].z, cte = meta[1].w;
         uint32_t bf, bd, bc, bct, bpu, bcu;
         const int32_t jal = widen16(j0, j0 + n, &bf);
         widen16(j0, j0 + n + 1, &bd);
-        const int32_t cs = t.dfirst[j0], ce = t.dfirst[j0 + n];
-        const int32_t pts = t.tfirst[j0], pte = t.tfirst[j0 + n];
-        const int32_t cts = t.tfirst[cs], cte = t.tfirst[ce];
         const int32_t cal_n = widen16(cs, ce, &bc);
         widen16(cs, ce + 1, &bct);
         const int32_t pal = widen16(pts, pte, &bpu);
@@ -695,12 +717,12 @@ struct TailTiles {
 
 // bump: depth L-2 is the root's, so no top-down launch precedes this one; count the iteration.
 template <int NA>
-__global__ void __launch_bounds__(kSBThreads) k_tail_stream(DevTree<float> t, const int32_t *tb, int32_t nt,
+__global__ void __launch_bounds__(kSBThreads) k_tail_stream(DevTree<float> t, const int4 *tm, int32_t nt,
                                                             int32_t record, int32_t bump, int *err) {
     grid_dependency_wait();
     __shared__ float q1[kTC], q2[kTC], cu[kTC];
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
-    run_pipeline(TailTiles<NA>{t, tb, nt, record, q1, q2, cu}, err);
+    run_pipeline(TailTiles<NA>{t, tm, nt, record, q1, q2, cu}, err);
 }
 
 // Unrolled action counts the streamed kernels are built for; a depth takes the smallest one that
