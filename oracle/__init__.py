@@ -20,7 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 
-VANILLA, CFR_PLUS = 0, 1
+VANILLA, CFR_PLUS, LINEAR, DISCOUNTED = 0, 1, 2, 3
 AVG_UNIFORM, AVG_LINEAR = 0, 1
 
 
@@ -53,7 +53,7 @@ def _lib():
         lib.orc_root.restype = ctypes.c_int32
         lib.orc_root.argtypes = [_P]
         lib.orc_set_record.argtypes = [_P, ctypes.c_int32]
-        lib.orc_iterate.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
+        lib.orc_iterate.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]
         lib.orc_get_state.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         lib.orc_set_state.argtypes = [_P, _P, _P, ctypes.c_int64]
         lib.orc_get_nodes.restype = ctypes.c_int32
@@ -108,10 +108,14 @@ class Oracle:
     def root(self) -> int:
         return int(_lib().orc_root(self._h))
 
-    def iterate(self, n: int = 1, variant: int = VANILLA, avg: int = AVG_UNIFORM, alternating: bool = False):
-        """Runs n CFR iterations; returns the root payoffs (u1, u2) of the last pass."""
+    def iterate(self, n: int = 1, variant: int = VANILLA, avg: int = AVG_UNIFORM, alternating: bool = False,
+                dcfr=(1.5, 0.0, 2.0)):
+        """Runs n CFR iterations; returns the root payoffs (u1, u2) of the last pass.  variant: VANILLA,
+        CFR_PLUS, LINEAR or DISCOUNTED (with dcfr = (alpha, beta, gamma)); avg is ignored by the last two."""
         rv = np.zeros(2)
-        _lib().orc_iterate(self._h, int(n), int(variant), int(avg), int(bool(alternating)), rv.ctypes.data)
+        d = np.asarray(dcfr, dtype=np.float64)
+        _lib().orc_iterate(self._h, int(n), int(variant), int(avg), int(bool(alternating)), d.ctypes.data,
+                           rv.ctypes.data)
         return rv
 
     def state(self) -> dict:

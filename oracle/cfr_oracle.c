@@ -30,6 +30,14 @@
  *   - Eq. 9's "sum of positive regrets = 0" branch is an exact test of the FP64 sum.
  *   - Alternating updates: player 1's pass and update first, then player 2's pass under the new
  *     sigma_1.
+ * Variants beyond the paper (its Section 5 calls such reweightings direct in the matrix form):
+ *   - Linear CFR: iteration T's instantaneous regret and average-strategy contribution are both
+ *     weighted by T:  R += T * inst,  S += T * pi_p(h) * sigma^T.
+ *   - Discounted CFR(alpha, beta, gamma) (Brown and Sandholm, 2019), read as: after iteration T's
+ *     regret is added, the accumulated regret is scaled by T^alpha / (T^alpha + 1) where it is
+ *     positive and by T^beta / (T^beta + 1) elsewhere; iteration T's average-strategy contribution
+ *     is weighted by T^gamma:
+ *       x = R + inst;  R = x * (x > 0 ? T^a/(T^a+1) : T^b/(T^b+1));  S += T^gamma * pi_p(h) * sigma^T.
  * Best response / exploitability (used in Appendix A for sanity testing; Section 2.2 defines
  * Nash and epsilon-Nash): a best response for player i against a fixed profile picks, at each of
  * i's infosets, argmax_a sum_{d in h} pi_-i(d) V(child_a(d)), where V is the value below with i
@@ -224,34 +232,55 @@ static void pass(orc *o, int mask, double root_value[2]) {
     walk(o, o->root, 1.0, 1.0, 1.0, 1.0, mask, root_value);
 }
 
-static void update(orc *o, int mask, int variant, int avg, int64_t T) {
-    double w = avg == 1 ? (double)T : 1.0;
+/* variant: 0 vanilla, 1 CFR+, 2 linear CFR, 3 discounted CFR with dcfr = {alpha, beta, gamma}. */
+static void update(orc *o, int mask, int variant, int avg, const double *dcfr, int64_t T) {
+    const double t = (double)T;
+    double w = avg == 1 ? t : 1.0;
+    double fpos = 1.0, fneg = 1.0;
+    if (variant == 2) w = t;
+    if (variant == 3) {
+        const double ta = pow(t, dcfr[0]), tb = pow(t, dcfr[1]);
+        fpos = ta / (ta + 1.0);
+        fneg = tb / (tb + 1.0);
+        w = pow(t, dcfr[2]);
+    }
     for (int32_t h = 0; h < o->H; ++h) {
         int p = o->player[h];
         if (p == 0 || !(mask & (1 << p))) continue;
         int64_t qb = o->qbase[h];
         for (int32_t a = 0; a < o->nact[h]; ++a) {
-            double r = o->R[qb + a] + o->inst[qb + a];
-            o->R[qb + a] = variant == 1 ? (r > 0.0 ? r : 0.0) : r;
+            const double in = o->inst[qb + a];
+            if (variant == 2) {
+                o->R[qb + a] = o->R[qb + a] + t * in;
+            } else if (variant == 3) {
+                const double x = o->R[qb + a] + in;
+                o->R[qb + a] = x * (x > 0.0 ? fpos : fneg);
+            } else {
+                double r = o->R[qb + a] + in;
+                o->R[qb + a] = variant == 1 ? (r > 0.0 ? r : 0.0) : r;
+            }
             o->S[qb + a] += w * o->own[h] * o->sigma[qb + a];
         }
         regret_match(o, h);
     }
 }
 
-/* variant: 0 vanilla CFR, 1 CFR+;  avg: 0 uniform weights, 1 linear (w_T = T);  alternating: 0/1. */
-void orc_iterate(orc *o, int32_t iters, int32_t variant, int32_t avg, int32_t alternating, double *root_value) {
+/* variant: 0 vanilla CFR, 1 CFR+, 2 linear CFR, 3 discounted CFR (dcfr = {alpha, beta, gamma}, may be
+ * NULL otherwise);  avg: 0 uniform weights, 1 linear (w_T = T), ignored by variants 2 and 3;
+ * alternating: 0/1. */
+void orc_iterate(orc *o, int32_t iters, int32_t variant, int32_t avg, int32_t alternating, const double *dcfr,
+                 double *root_value) {
     double rv[2] = {0.0, 0.0};
     for (int32_t it = 0; it < iters; ++it) {
         int64_t T = o->T + 1;
         if (!alternating) {
             pass(o, 6, rv);
-            update(o, 6, variant, avg, T);
+            update(o, 6, variant, avg, dcfr, T);
         } else {
             pass(o, 2, rv);
-            update(o, 2, variant, avg, T);
+            update(o, 2, variant, avg, dcfr, T);
             pass(o, 4, rv);
-            update(o, 4, variant, avg, T);
+            update(o, 4, variant, avg, dcfr, T);
         }
         o->T = T;
     }

@@ -131,7 +131,9 @@ def test_rock_paper_scissors_is_a_fixed_point():
 
 @pytest.mark.parametrize("a,b,c", [(1.0, 2.0, 3.0), (2.0, 0.5, 1.0)])
 @pytest.mark.parametrize("variant,avg,alt,iters,tol", [(0, 0, False, 20000, 2e-2), (1, 1, False, 5000, 1e-2),
-                                                     (1, 1, True, 5000, 1e-3)])
+                                                     (1, 1, True, 5000, 1e-3), (2, 0, False, 5000, 2e-2),
+                                                     (2, 0, True, 5000, 1e-2), (3, 0, False, 5000, 1e-2),
+                                                     (3, 0, True, 5000, 1e-2)])
 def test_weighted_rps_closed_form(a, b, c, variant, avg, alt, iters, tol):
     # Skew-symmetric payoff [[0,-a,b],[a,0,-c],[-b,c,0]]: the unique equilibrium is (c, b, a) / (a+b+c)
     # for both players, value 0 (each column of x^T A vanishes).
@@ -260,6 +262,55 @@ def test_cfr_plus_first_iteration_equals_vanilla():
         b.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
         np.testing.assert_array_equal(a.current_strategy(), b.current_strategy())
         np.testing.assert_array_equal(a.state()["strat_sum"], b.state()["strat_sum"])
+
+
+def test_linear_and_discounted_first_iteration_against_vanilla():
+    # At T = 1 every weight is 1 (linear CFR, and 1^gamma for discounted CFR) and the discount is
+    # 1^a / (1^a + 1) = 1/2 whatever the sign: linear CFR equals vanilla, discounted CFR halves its regrets.
+    for g, tr in tiny_games(3, seed0=650):
+        v, lin, dis = oracle.Oracle(g), oracle.Oracle(g), oracle.Oracle(g)
+        v.iterate(1)
+        lin.iterate(1, variant=oracle.LINEAR)
+        dis.iterate(1, variant=oracle.DISCOUNTED, dcfr=(1.5, 0.0, 2.0))
+        sv, sl, sd = v.state(), lin.state(), dis.state()
+        np.testing.assert_array_equal(sl["cum_regret"], sv["cum_regret"])
+        np.testing.assert_array_equal(sl["strat_sum"], sv["strat_sum"])
+        np.testing.assert_array_equal(sd["cum_regret"], sv["cum_regret"] * 0.5)
+        np.testing.assert_array_equal(sd["strat_sum"], sv["strat_sum"])
+        np.testing.assert_array_equal(dis.current_strategy(), v.current_strategy())   # RM is scale-free
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+def test_linear_and_discounted_cfr_by_definition(variant):
+    # Regrets from path enumeration (Eq. 3, 6, 7), accumulated with the variant's weights.
+    a_, b_, c_ = 1.5, 0.5, 2.0
+    for g, tr in tiny_games(3, seed0=660 + variant):
+        o = oracle.Oracle(g)
+        R = np.zeros(tr.Q)
+        S = np.zeros(tr.Q)
+        player_q = np.zeros(tr.Q, bool)
+        for h in range(tr.H):
+            if tr.player[h] != 0:
+                player_q[tr.qbase[h]:tr.qbase[h] + tr.nact[h]] = True
+        for T in range(1, 7):
+            prof = o.current_strategy().copy()
+            inst = np.where(player_q, tr.inst_regret(prof), 0.0)
+            if variant == 2:
+                R = R + T * inst
+                w = float(T)
+            else:
+                x = R + inst
+                R = x * np.where(x > 0, T ** a_ / (T ** a_ + 1), T ** b_ / (T ** b_ + 1))
+                w = float(T) ** c_
+            for h in range(tr.H):
+                if tr.player[h] != 0:
+                    own = tr.own_reach(prof, tr.nodes_of[h][0], tr.player[h]) if tr.nodes_of[h] else 0.0
+                    sl = slice(tr.qbase[h], tr.qbase[h] + tr.nact[h])
+                    S[sl] += w * own * prof[sl]
+            o.iterate(1, variant=variant, dcfr=(a_, b_, c_))
+            st = o.state()
+            np.testing.assert_allclose(st["cum_regret"], R, rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(st["strat_sum"], S, rtol=1e-12, atol=1e-12)
 
 
 def test_alternating_updates_by_definition():
