@@ -42,15 +42,22 @@ typedef enum {
 } cfr_status;
 
 /* Variants.  CFR+ is named in Section 1 without formulas; it is read as regret-matching+
- * (cumulative regrets clipped at 0 after every iteration) with linear averaging. */
-enum { CFR_VANILLA = 0, CFR_PLUS = 1 };
+ * (cumulative regrets clipped at 0 after every iteration) with linear averaging.  Linear and
+ * discounted CFR are reweightings of Eq. 8 and Eq. 10 (Section 5 calls such variants direct in the
+ * matrix form): linear CFR weights iteration T's instantaneous regret and average contribution by T;
+ * discounted CFR (Brown and Sandholm, 2019) scales the accumulated regret, after adding iteration T's,
+ * by T^alpha / (T^alpha + 1) where positive and T^beta / (T^beta + 1) elsewhere, and weights the
+ * average contribution by T^gamma (cfr_config.dcfr_*). */
+enum { CFR_VANILLA = 0, CFR_PLUS = 1, CFR_LINEAR = 2, CFR_DISCOUNTED = 3 };
 /* Precision (Section 4.1 runs FP32 and FP64).  CFR_FP32: reach, node values and instantaneous
  * regrets in FP32, cumulative regrets and strategy sums in FP64.  CFR_FP64: everything FP64. */
 enum { CFR_FP32 = 0, CFR_FP64 = 1 };
-/* Both players update from the same iteration (the paper's vector form, Section 3.2). */
+/* Simultaneous: both players update from the same iteration (the paper's vector form, Section 3.2).
+ * Alternating: player 1's pass and update, then player 2's pass under player 1's new strategy (both
+ * weighted as iteration T). */
 enum { CFR_SIMULTANEOUS = 0, CFR_ALTERNATING = 1 };
 /* Weight of iteration T in the average strategy: 1 (Eq. 10) or T.  DEFAULT = UNIFORM for vanilla
- * and LINEAR for CFR+. */
+ * and LINEAR for CFR+.  Linear and discounted CFR fix their own weights (T, T^gamma). */
 enum { CFR_AVG_DEFAULT = -1, CFR_AVG_UNIFORM = 0, CFR_AVG_LINEAR = 1 };
 /* Phases of one iteration reported by cfr_phase_times. */
 enum { CFR_PHASE_TOPDOWN = 0, CFR_PHASE_BOTTOMUP = 1, CFR_PHASE_FUSED = 2, CFR_PHASE_UPDATE = 3, CFR_PHASE_OWN = 4 };
@@ -92,6 +99,9 @@ typedef struct {
     int32_t record_nodes;   /* 1: fused depths also write every node's value and reaches to device
                                memory, so that cfr_get_nodes can return them; 0 (default): they do
                                not, and cfr_get_nodes returns CFR_ERR_STATE when depths are fused. */
+    double dcfr_alpha;      /* CFR_DISCOUNTED: alpha, beta, gamma (defaults 1.5, 0, 2); finite */
+    double dcfr_beta;
+    double dcfr_gamma;
 } cfr_config;
 
 /* Sizes and accounting of a loaded solver. */

@@ -19,7 +19,7 @@ from ._build import LIB as _LIB_PATH
 from ._build import build as _build_library
 
 CFR_OK, CFR_ERR_INVALID, CFR_ERR_CUDA, CFR_ERR_OOM, CFR_ERR_TIMEOUT, CFR_ERR_STATE, CFR_ERR_UNSUPPORTED = range(7)
-CFR_VANILLA, CFR_PLUS = 0, 1
+CFR_VANILLA, CFR_PLUS, CFR_LINEAR, CFR_DISCOUNTED = 0, 1, 2, 3
 CFR_FP32, CFR_FP64 = 0, 1
 CFR_SIMULTANEOUS, CFR_ALTERNATING = 0, 1
 CFR_AVG_DEFAULT, CFR_AVG_UNIFORM, CFR_AVG_LINEAR = -1, 0, 1
@@ -67,6 +67,9 @@ class _Config(ctypes.Structure):
         ("alloc_ctx", ctypes.c_void_p),
         ("fuse_levels", ctypes.c_int32),
         ("record_nodes", ctypes.c_int32),
+        ("dcfr_alpha", ctypes.c_double),
+        ("dcfr_beta", ctypes.c_double),
+        ("dcfr_gamma", ctypes.c_double),
     ]
 
 
@@ -198,9 +201,10 @@ class _TorchAllocator:
 
 def cfr_load_tree(game, variant=CFR_VANILLA, precision=CFR_FP32, update_mode=CFR_SIMULTANEOUS,
                   avg_weight=CFR_AVG_DEFAULT, device=None, stream=None, allocator: str = "torch",
-                  fuse_levels: int = -1, record_nodes: bool = False):
+                  fuse_levels: int = -1, record_nodes: bool = False, dcfr=(1.5, 0.0, 2.0)):
     """Loads a game and returns a Solver.  stream: None = PyTorch's current stream on the device.
-    fuse_levels / record_nodes: cfr_config's fields of the same names."""
+    fuse_levels / record_nodes: cfr_config's fields of the same names; dcfr: (alpha, beta, gamma) of
+    CFR_DISCOUNTED."""
     import torch
 
     if not torch.cuda.is_available():
@@ -214,6 +218,7 @@ def cfr_load_tree(game, variant=CFR_VANILLA, precision=CFR_FP32, update_mode=CFR
     cfg.cuda_stream = st_handle
     cfg.fuse_levels = int(fuse_levels)
     cfg.record_nodes = 1 if record_nodes else 0
+    cfg.dcfr_alpha, cfg.dcfr_beta, cfg.dcfr_gamma = (float(x) for x in dcfr)
     alloc = None
     if allocator == "torch":
         alloc = _TorchAllocator(dev, st_handle)

@@ -52,7 +52,8 @@ struct cfr_solver {
     cudaStream_t stream = nullptr;   // borrowed
     cudaStream_t cap = nullptr;      // private, for graph capture
     cudaStream_t side = nullptr;     // private: the own-reach branch of the captured iteration
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr};   // per pass of an iteration
+    double *wts = nullptr;                                // linear / discounted CFR weights (k_weights)
     // sizes
     int64_t N = 0, Nd = 0, Nt = 0, Q = 0;
     int32_t H = 0, L = 0, max_depth = 0, max_actions = 0;
@@ -177,6 +178,8 @@ DevTree<real> dev_tree(cfr_solver *s) {
     t.u = static_cast<real *>(s->u); t.own = static_cast<real *>(s->own);
     t.R = s->R; t.S = s->S; t.iter = s->d_iter;
     t.contrib = static_cast<real *>(s->contrib); t.hnode_start = s->hnode_start; t.hnode = s->hnode;
+    t.pmask = 6;
+    t.wts = s->wts;
     return t;
 }
 
@@ -228,22 +231,22 @@ bool topdown_launches(const cfr_solver *s, int32_t l) {
 // launches the per-depth kernel).
 template <int NA>
 cudaError_t launch_stream_na(Launcher &go, const cfr_solver *s, const DevTree<float> &t, cudaStream_t st,
-                             bool bottom_up, int32_t l, int32_t j0, int32_t j1, int gi) {
+                             bool bottom_up, int32_t l, int32_t j0, int32_t j1, int gi, bool first) {
     const int32_t tiles = (j1 - j0 + kSBN - 1) / kSBN;
     if (bottom_up)
         return go(k_bottomup_stream<NA>, std::min(s->sb_grid[gi], tiles), kSBThreads, sizeof(SBStage) * kSBStages, st,
                   t, j0, j1, s->d_err);
     return go(k_topdown_stream<NA>, std::min(s->td_grid[gi], tiles), kSBThreads,
-              sizeof(TDStage) * TopDownTiles<NA>::kStages, st, t, j0, j1, (int32_t)(l == 0), s->d_err);
+              sizeof(TDStage) * TopDownTiles<NA>::kStages, st, t, j0, j1, (int32_t)(first && l == 0), s->d_err);
 }
 
 bool launch_stream(Launcher &go, const cfr_solver *s, const DevTree<float> &t, cudaStream_t st, bool bottom_up,
-                   int32_t l, int32_t j0, int32_t j1) {
+                   int32_t l, int32_t j0, int32_t j1, bool first) {
     const int gi = s->level_na[(size_t)l];
     if ((bottom_up ? s->sb_grid[gi] : s->td_grid[gi]) <= 0) return false;
-    if (gi == 0) launch_stream_na<kStreamNA[0]>(go, s, t, st, bottom_up, l, j0, j1, gi);
-    else if (gi == 1) launch_stream_na<kStreamNA[1]>(go, s, t, st, bottom_up, l, j0, j1, gi);
-    else launch_stream_na<kStreamNA[2]>(go, s, t, st, bottom_up, l, j0, j1, gi);
+    if (gi == 0) launch_stream_na<kStreamNA[0]>(go, s, t, st, bottom_up, l, j0, j1, gi, first);
+    else if (gi == 1) launch_stream_na<kStreamNA[1]>(go, s, t, st, bottom_up, l, j0, j1, gi, first);
+    else launch_stream_na<kStreamNA[2]>(go, s, t, st, bottom_up, l, j0, j1, gi, first);
     return true;
 }
 
@@ -266,6 +269,20 @@ cfr_status setup_stream_na(cfr_solver *s, int gi, int sms) {
     return CFR_OK;
 }
 
+// FP32 update of variant V: one thread per infoset (k_update_rows, instantiated for the largest action
+// count) and one block per infoset of more than 32 actions.
+template <int V>
+cfr_status launch_update(Launcher &go, cfr_solver *s, const DevTree<float> &t, cudaStream_t st, int32_t linear) {
+    if (s->Hp > 0) {
+        const int g = nblocks(s->Hp);
+        if (s->hp_na <= 3) CK(go(k_update_rows<3, V>, g, kBlock, 0, st, t, s->Hp, linear));
+        else if (s->hp_na <= 5) CK(go(k_update_rows<5, V>, g, kBlock, 0, st, t, s->Hp, linear));
+        else CK(go(k_update_rows<8, V>, g, kBlock, 0, st, t, s->Hp, linear));
+    }
+    if (s->nwide_h > 0) CK(go(k_update_list<V>, s->nwide_h, kWideBlock, 0, st, t, (const int32_t *)s->wide_h, linear));
+    return CFR_OK;
+}
+
 // One full-tree iteration, queued on `st` (captured into the solver's graph).  FP64 mode reduces
 // the instantaneous regrets deterministically (k_update sums per-edge contributions in depth-first
 // node order); FP32 mode adds them with atomics, streams large depths through shared memory, and
@@ -276,9 +293,12 @@ cfr_status setup_stream_na(cfr_solver *s, int gi, int sms) {
 // top-down from depth 0 .. fuse_r - 1, the fused depths (if any), bottom-up at depth fuse_r - 1 .. 0,
 // update.
 template <typename real>
-cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t pmask, bool first) {
     constexpr bool det = sizeof(real) == sizeof(double);
     DevTree<real> t = dev_tree<real>(s);
+    t.pmask = pmask;
+    const bool alt = pmask != 6;
+    const int pi = pmask == 4;                                   // which fork/join events
     const int32_t r = det ? s->L : s->fuse_r;
     Launcher go;
     go.pdl = ev == nullptr;
@@ -290,7 +310,8 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         }
         return CFR_OK;
     };
-    if (!det) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
+    if (!det && !alt) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
+    if (!det && alt && s->Hp > 0) CK(go(k_zero_inst<real>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp));
     TRY(mark());
     // own reaches, depth by depth; in the graph on a branch beside the node passes that joins before the
     // update
@@ -298,15 +319,15 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
     cudaStream_t os = st;
     if (branch) {
         os = s->side;
-        CK(cudaEventRecord(s->fork, st));
-        CK(cudaStreamWaitEvent(os, s->fork, 0));
+        CK(cudaEventRecord(s->fork[pi], st));
+        CK(cudaStreamWaitEvent(os, s->fork[pi], 0));
     }
     for (int32_t l = 0; l < s->L; ++l) {
         const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
         if (h1 > h0) CK(go(k_own<real>, nblocks(h1 - h0), kBlock, 0, os, t, h0, h1));
     }
     if (branch) {
-        CK(cudaEventRecord(s->join, os));
+        CK(cudaEventRecord(s->join[pi], os));
         go.cut(os);
     }
     if (s->Hp > 0) TRY(mark());
@@ -316,9 +337,10 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         if (s->ddepth_children[l] || l == 0) {
             bool streamed = false;
             if constexpr (!det) {
-                if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(go, s, t, st, false, l, j0, j1);
+                if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(go, s, t, st, false, l, j0, j1, first);
             }
-            if (!streamed) CK(go(k_topdown<real, !det>, nblocks(j1 - j0), kBlock, 0, st, t, j0, j1, (int32_t)(l == 0)));
+            if (!streamed)
+                CK(go(k_topdown<real, !det>, nblocks(j1 - j0), kBlock, 0, st, t, j0, j1, (int32_t)(first && l == 0)));
             CK_LAUNCH();
         }
         const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
@@ -328,7 +350,7 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
     if constexpr (!det) {
         if (r < s->L && s->fuse_tail) {
             const int32_t j0 = s->dlevel[r], j1 = s->dlevel[r + 1];
-            const int32_t rec = s->cfg.record_nodes != 0, bump = r == 0;
+            const int32_t rec = s->cfg.record_nodes != 0, bump = first && r == 0;
             const int gi = std::max(s->level_na[(size_t)r], s->level_na[(size_t)r + 1]);
             if (s->ntail_tiles > 0 && s->tl_grid[gi] > 0) {
                 const int grid = std::min(s->tl_grid[gi], s->ntail_tiles);
@@ -347,7 +369,7 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
             fa.ntiles = s->fuse_ntiles;
             fa.levels = s->L - r;
             fa.record = s->cfg.record_nodes != 0;
-            fa.bump = r == 0;
+            fa.bump = first && r == 0;
             CK(go(k_fused, s->fuse_ntiles, kBlock, 0, st, t, fa));
             TRY(mark());
         }
@@ -356,7 +378,7 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         bool streamed = false;
         if constexpr (!det) {
-            if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(go, s, t, st, true, l, j0, j1);
+            if (j1 - j0 >= kStreamMinNodes) streamed = launch_stream(go, s, t, st, true, l, j0, j1, first);
         }
         if (!streamed) CK(go(k_bottomup<real, det>, nblocks(j1 - j0), kBlock, 0, st, t, j0, j1));
         CK_LAUNCH();
@@ -365,23 +387,33 @@ cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = n
         TRY(mark());
     }
     if (branch) {
-        CK(cudaStreamWaitEvent(st, s->join, 0));
+        CK(cudaStreamWaitEvent(st, s->join[pi], 0));
         go.cut(st);
     }
-    const int32_t linear = s->cfg.avg_weight == CFR_AVG_LINEAR, plus = s->cfg.variant == CFR_PLUS;
+    const int32_t linear = s->cfg.avg_weight == CFR_AVG_LINEAR, variant = s->cfg.variant;
+    if (first && variant == CFR_DISCOUNTED)
+        CK(go(k_weights, 1, 1, 0, st, (const int64_t *)s->d_iter, s->wts, s->cfg.dcfr_alpha, s->cfg.dcfr_beta,
+              s->cfg.dcfr_gamma));
     if constexpr (det) {
-        if (s->Hp > 0) CK(go(k_update<real, det>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, plus, linear));
+        if (s->Hp > 0) CK(go(k_update<real, det>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, variant, linear));
     } else {
-        if (s->Hp > 0) {
-            if (s->hp_na <= 3) CK(go(k_update_rows<3>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, plus, linear));
-            else if (s->hp_na <= 5) CK(go(k_update_rows<5>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, plus, linear));
-            else CK(go(k_update_rows<8>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, plus, linear));
-        }
-        if (s->nwide_h > 0)
-            CK(go(k_update_list, s->nwide_h, kWideBlock, 0, st, t, (const int32_t *)s->wide_h, plus, linear));
+        if (variant == CFR_VANILLA) TRY(launch_update<CFRV_VANILLA>(go, s, t, st, linear));
+        else if (variant == CFR_PLUS) TRY(launch_update<CFRV_PLUS>(go, s, t, st, linear));
+        else if (variant == CFR_LINEAR) TRY(launch_update<CFRV_LINEAR>(go, s, t, st, linear));
+        else TRY(launch_update<CFRV_DISCOUNTED>(go, s, t, st, linear));
     }
     TRY(mark());
     return CFR_OK;
+}
+
+// One full-tree iteration: one pass over both players (simultaneous updates), or a pass for player 1
+// and then one for player 2 under player 1's new strategy (alternating updates); the phase events
+// (ev) are for simultaneous updates only.
+template <typename real>
+cfr_status enqueue_iteration(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+    if (s->cfg.update_mode != CFR_ALTERNATING) return enqueue_pass<real>(s, st, ev, 6, true);
+    TRY(enqueue_pass<real>(s, st, nullptr, 2, true));
+    return enqueue_pass<real>(s, st, nullptr, 4, false);
 }
 
 // First fused depth (L when nothing is fused).
@@ -445,8 +477,15 @@ std::vector<double> phase_bytes(const cfr_solver *s) {
 }
 
 // Kernel launches of one iteration (for cfr_info and the benchmark's launch count).
+int32_t launches_per_pass(const cfr_solver *s);
 int32_t launches_per_iteration(const cfr_solver *s) {
     if (s->L == 0) return 0;
+    const bool alt = s->cfg.update_mode == CFR_ALTERNATING;
+    const int32_t zero = alt && s->cfg.precision == CFR_FP32 && s->Hp > 0;   // k_zero_inst per pass
+    return (alt ? 2 * (launches_per_pass(s) + zero) : launches_per_pass(s)) + (s->cfg.variant == CFR_DISCOUNTED);
+}
+
+int32_t launches_per_pass(const cfr_solver *s) {
     const bool det = s->cfg.precision == CFR_FP64;
     const int32_t r = fused_from(s);
     int32_t n = r + 1 + (r < s->L);                           // bottom-up depths, fused, update
@@ -633,6 +672,7 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     TRY(alloc_n(s, &s->stage, s->Q));
     TRY(alloc_n(s, &s->d_iter, 1));
     TRY(alloc_n(s, &s->d_err, 1));
+    TRY(alloc_n(s, &s->wts, 4));
     if (fp64) {
         TRY(dev_alloc(s, &s->contrib, sizeof(double) * (size_t)std::max<int64_t>(s->N - 1, 1)));
         TRY(alloc_n(s, &s->hnode_start, (int64_t)s->H + 1));
@@ -726,6 +766,7 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
 int64_t bytes_model(const cfr_solver *s) {
     double b = 0;
     for (double x : phase_bytes(s)) b += x;
+    if (s->cfg.update_mode == CFR_ALTERNATING) b *= 2;       // two passes (the zeroing of r~ aside)
     return (int64_t)b;
 }
 
@@ -782,6 +823,10 @@ void cfr_config_init(cfr_config *c) {
     c->update_mode = CFR_SIMULTANEOUS;
     c->avg_weight = CFR_AVG_DEFAULT;
     c->device = -1;
+    c->fuse_levels = -1;
+    c->dcfr_alpha = 1.5;
+    c->dcfr_beta = 0.0;
+    c->dcfr_gamma = 2.0;
 }
 
 cfr_status cfr_validate(const cfr_game_desc *g, char *msg, size_t msg_len) {
@@ -797,15 +842,16 @@ cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver
     *out = nullptr;
     cfr_config cfg;
     if (c) cfg = *c; else cfr_config_init(&cfg);
-    if (cfg.variant != CFR_VANILLA && cfg.variant != CFR_PLUS)
+    if (cfg.variant < CFR_VANILLA || cfg.variant > CFR_DISCOUNTED)
         return set_err(nullptr, CFR_ERR_INVALID, "variant %d unknown", cfg.variant);
+    if (cfg.variant == CFR_DISCOUNTED &&
+        !(std::isfinite(cfg.dcfr_alpha) && std::isfinite(cfg.dcfr_beta) && std::isfinite(cfg.dcfr_gamma)))
+        return set_err(nullptr, CFR_ERR_INVALID, "discounted CFR needs finite alpha, beta, gamma");
     if (cfg.precision != CFR_FP32 && cfg.precision != CFR_FP64)
         return set_err(nullptr, CFR_ERR_INVALID, "precision %d unknown", cfg.precision);
     if (cfg.update_mode != CFR_SIMULTANEOUS && cfg.update_mode != CFR_ALTERNATING)
         return set_err(nullptr, CFR_ERR_INVALID, "update_mode %d unknown", cfg.update_mode);
-    if (cfg.update_mode == CFR_ALTERNATING)
-        return set_err(nullptr, CFR_ERR_UNSUPPORTED, "alternating updates are not implemented on the GPU");
-    if (cfg.avg_weight == CFR_AVG_DEFAULT) cfg.avg_weight = cfg.variant == CFR_PLUS ? CFR_AVG_LINEAR : CFR_AVG_UNIFORM;
+    if (cfg.avg_weight == CFR_AVG_DEFAULT) cfg.avg_weight = cfg.variant == CFR_VANILLA ? CFR_AVG_UNIFORM : CFR_AVG_LINEAR;
     if (cfg.avg_weight != CFR_AVG_UNIFORM && cfg.avg_weight != CFR_AVG_LINEAR)
         return set_err(nullptr, CFR_ERR_INVALID, "avg_weight %d unknown", cfg.avg_weight);
     if ((cfg.dev_alloc == nullptr) != (cfg.dev_free == nullptr))
@@ -824,8 +870,10 @@ cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver
     s->stream = static_cast<cudaStream_t>(cfg.cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&s->fork[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[i], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         std::string msg = cudaGetErrorString(e);
@@ -1026,6 +1074,8 @@ cfr_status cfr_root_value(cfr_solver *s, double *u1) {
 cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t *kind, int32_t *depth, int32_t len,
                            int32_t *nphases) {
     TRY(check_usable(s));
+    if (s->cfg.update_mode == CFR_ALTERNATING)
+        return set_err(s, CFR_ERR_UNSUPPORTED, "phase timing covers simultaneous updates only");
     const auto ph = phases(s);
     const int32_t n = (int32_t)ph.size();
     if (nphases) *nphases = n;
@@ -1093,8 +1143,10 @@ void cfr_free(cfr_solver *s) {
     if (s->side) cudaStreamSynchronize(s->side);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->side) cudaStreamDestroy(s->side);
-    if (s->fork) cudaEventDestroy(s->fork);
-    if (s->join) cudaEventDestroy(s->join);
+    for (int i = 0; i < 2; ++i) {
+        if (s->fork[i]) cudaEventDestroy(s->fork[i]);
+        if (s->join[i]) cudaEventDestroy(s->join[i]);
+    }
     delete s;
 }
 

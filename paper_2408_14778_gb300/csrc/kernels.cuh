@@ -103,7 +103,16 @@ struct DevTree {
     // depth-first order (edge offset of node j's children: dfirst[j] + tfirst[j] - 1)
     real *contrib;             // [N - 1]
     const int32_t *hnode_start, *hnode;
+    int32_t pmask;             // bit p set: player p collects regrets and is updated in this pass (6: both)
+    const double *wts;         // linear / discounted CFR: this iteration's weights (k_weights)
 };
+
+// Variants (the values of cfr_gb300.h's CFR_VANILLA .. CFR_DISCOUNTED).
+constexpr int CFRV_VANILLA = 0, CFRV_PLUS = 1, CFRV_LINEAR = 2, CFRV_DISCOUNTED = 3;
+
+// Whether the acting player p (0 = chance) collects regrets in this pass.
+template <typename real>
+__device__ __forceinline__ bool collects(const DevTree<real> &t, int p) { return (t.pmask >> p) & 1; }
 
 // Nodes with up to kUnroll actions take a fully unrolled path in which every child-value and strategy
 // load is issued before any is used.  The operations and their order are those of the general loop.
@@ -114,7 +123,8 @@ constexpr int kUnroll = 8;
 // Own reach of infoset h (Eq. 4 for its acting player): the parent sequence's own reach times sigma.
 template <typename real, bool C>
 __device__ __forceinline__ void own_infoset(const DevTree<real> &t, int32_t h) {
-    if (t.iplayer[h] == 0) return;
+    const int p = t.iplayer[h];
+    if (p == 0 || !collects(t, p)) return;
     const int32_t ps = t.pseq[h];
     t.own[h] = ps < 0 ? real(1) : ldm<C>(t.own + t.pseq_h[h]) * ldm<C>(t.sigma + ps);
 }
@@ -199,7 +209,7 @@ __device__ __forceinline__ void bu_node(const DevTree<real> &t, int32_t j) {
         for (int a = 0; a < kUnroll; ++a)
             if (a < na) ud = madd(ud, s[a], v[a]);
         t.u[j] = ud;
-        if (p == 0) return;
+        if (!collects(t, p)) return;
         const real wr = p == 1 ? rr1 : -rr2;   // u_2 = -u_1
         if (!kDet && wr == real(0)) return;
 #pragma unroll
@@ -218,7 +228,7 @@ __device__ __forceinline__ void bu_node(const DevTree<real> &t, int32_t j) {
         ud = madd(ud, ldm<C>(t.sigma + qb + a), v);
     }
     t.u[j] = ud;
-    if (p == 0) return;
+    if (!collects(t, p)) return;
     const real wr = p == 1 ? rr1 : -rr2;
     if (!kDet && wr == real(0)) return;
     c = c0; tt = t0;
@@ -270,29 +280,75 @@ __device__ __forceinline__ void bu_wide(const DevTree<real> &t, int32_t j, real 
         part = madd(part, ldm<C>(t.sigma + qb + a), wide_child_value<real, C>(t, wb, d0, t0, a));
     const real ud = block_sum(part, scratch32);
     if (threadIdx.x == 0) t.u[j] = ud;
-    if (p == 0) return;
+    if (!collects(t, p)) return;
     const real wr = p == 1 ? ldm<C>(t.reach1 + j) : -ldm<C>(t.reach2 + j);
     if (wr == real(0)) return;
     for (int a = threadIdx.x; a < na; a += blockDim.x)
         atomicAdd(&t.inst[qb + a], wr * (wide_child_value<real, C>(t, wb, d0, t0, a) - ud));
 }
 
+// ---- per-infoset update, FP32 mode: one thread per infoset ---------------------------------------
+// The arithmetic of update_wide, per infoset, with no block-wide barriers: a thread loads all of its
+// infoset's R, r~ and sigma entries at once, then S where something accrues.  Infosets with more than
+// 32 actions are skipped (k_update_list takes them, one block each).
+
+// Iteration weights of the FP32 update: T, the average weight w, and the discounted-CFR regret factors.
+struct UpdWeights {
+    double T, fpos, fneg;
+    float w;
+};
+
+template <typename real>
+__device__ __forceinline__ UpdWeights update_weights(const DevTree<real> &t, int variant, bool linear) {
+    UpdWeights u;
+    u.T = (double)*t.iter;
+    u.fpos = u.fneg = 1.0;
+    u.w = linear ? (float)u.T : 1.f;
+    if (variant == CFRV_LINEAR) u.w = (float)u.T;
+    if (variant == CFRV_DISCOUNTED) {
+        u.w = (float)t.wts[0];
+        u.fpos = t.wts[1];
+        u.fneg = t.wts[2];
+    }
+    return u;
+}
+
+// R += r~ (CFR+: clipped at 0; linear CFR: R += T r~; discounted CFR: R = (R + r~) times the factor
+// for its sign) for one slot; returns the slot's positive regret as a float.  V is the variant: a
+// compile-time choice, so that vanilla and CFR+ spend no FP64 operation beyond the one addition.
+template <int V>
+__device__ __forceinline__ float update_regret(double *R, double rr, float in, const UpdWeights &u) {
+    double r0;
+    if constexpr (V == CFRV_LINEAR) r0 = rr + u.T * widen(in);
+    else r0 = rr + widen(in);
+    const bool positive = __double_as_longlong(r0) > 0;      // r0 > 0 without an FP64 compare
+    if constexpr (V == CFRV_DISCOUNTED) r0 *= positive ? u.fpos : u.fneg;
+    const double r = V == CFRV_PLUS && !positive ? 0.0 : r0;
+    *R = r;
+    return positive ? __double2float_rn(r) : 0.f;
+}
+
+// sigma' of an infoset whose positive regrets sum to `sum` below FP32's normal range: FP64 division.
+__device__ __forceinline__ void regret_match_tiny(const DevTree<float> &t, int32_t qs, int na) {
+    double p = 0.0;
+    for (int a = 0; a < na; ++a) p += fmax(t.R[qs + a], 0.0);
+    for (int a = 0; a < na; ++a) t.sigma[qs + a] = (float)(fmax(t.R[qs + a], 0.0) / p);
+}
+
 // ---- per-infoset update of a wide infoset (more than 32 actions), FP32 mode ----------------------
 // The block shares the infoset's actions; the two FP64 accumulations stay FP64 (R += r~,
 // S += w pi_i sigma) and regret matching runs in FP32, the strategy's precision, with the positive
 // regrets summed over the block.  All threads of the block must call it.
-__device__ __forceinline__ void update_wide(const DevTree<float> &t, int32_t h, bool plus, float w, float *s_red) {
+template <int V>
+__device__ __forceinline__ void update_wide(const DevTree<float> &t, int32_t h, const UpdWeights &u, float *s_red) {
     const int32_t qs = t.qbase[h];
     const int32_t nq = t.qbase[h + 1] - qs;
-    const float wo = w * t.own[h];
+    const float wo = u.w * t.own[h];
     float part = 0.f;
     for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) {
         const int32_t q = qs + i;
-        double r = t.R[q] + widen(t.inst[q]);
-        if (plus) r = r > 0.0 ? r : 0.0;
-        t.R[q] = r;
+        part += update_regret<V>(t.R + q, t.R[q], t.inst[q], u);
         t.S[q] = t.S[q] + widen(wo * t.sigma[q]);
-        part += r > 0.0 ? (float)r : 0.f;
     }
     const float sum = block_sum(part, s_red);   // (its barriers also order the R writes above)
     if (sum >= 1e-30f || sum == 0.f) {
@@ -307,37 +363,17 @@ __device__ __forceinline__ void update_wide(const DevTree<float> &t, int32_t h, 
     }
 }
 
-// ---- per-infoset update, FP32 mode: one thread per infoset ---------------------------------------
-// The arithmetic of update_wide, per infoset, with no block-wide barriers: a thread loads all of its
-// infoset's R, r~ and sigma entries at once, then S where something accrues.  Infosets with more than
-// 32 actions are skipped (k_update_list takes them, one block each).
-
-// R += r~ (CFR+: clipped at 0) for one slot; returns the slot's positive regret as a float.
-__device__ __forceinline__ float update_regret(double *R, double rr, float in, bool plus) {
-    const double r0 = rr + widen(in);
-    const bool positive = __double_as_longlong(r0) > 0;      // r0 > 0 without an FP64 compare
-    const double r = plus && !positive ? 0.0 : r0;
-    *R = r;
-    return positive ? __double2float_rn(r) : 0.f;
-}
-
-// sigma' of an infoset whose positive regrets sum to `sum` below FP32's normal range: FP64 division.
-__device__ __forceinline__ void regret_match_tiny(const DevTree<float> &t, int32_t qs, int na) {
-    double p = 0.0;
-    for (int a = 0; a < na; ++a) p += fmax(t.R[qs + a], 0.0);
-    for (int a = 0; a < na; ++a) t.sigma[qs + a] = (float)(fmax(t.R[qs + a], 0.0) / p);
-}
-
-template <int NA>
-__global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t Hp, int32_t plus, int32_t linear) {
+template <int NA, int V>
+__global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t Hp, int32_t linear) {
     grid_dependency_wait();
     const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (h >= Hp) return;
+    if (t.pmask != 6 && !collects(t, t.iplayer[h])) return;      // alternating: the other player's pass
     const int32_t qs = t.qbase[h];
     const int na = t.qbase[h + 1] - qs;
     if (na > 32) return;
-    const float w = linear ? (float)*t.iter : 1.f;
-    const float wo = w * t.own[h];
+    const UpdWeights u = update_weights(t, V, linear != 0);
+    const float wo = u.w * t.own[h];
     if (na <= NA) {
         double rr[NA];
         float in[NA], sg[NA], pos[NA];
@@ -348,7 +384,7 @@ __global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t H
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
             if (a < na) {
-                pos[a] = update_regret(t.R + qs + a, rr[a], in[a], plus != 0);
+                pos[a] = update_regret<V>(t.R + qs + a, rr[a], in[a], u);
                 sg[a] = wo * sg[a];                            // the strategy-sum increment
             }
         }
@@ -379,7 +415,7 @@ __global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t H
     float pos[32];
     float sum = 0.f;
     for (int a = 0; a < na; ++a) {
-        pos[a] = update_regret(t.R + qs + a, t.R[qs + a], t.inst[qs + a], plus != 0);
+        pos[a] = update_regret<V>(t.R + qs + a, t.R[qs + a], t.inst[qs + a], u);
         const float inc = wo * t.sigma[qs + a];
         if (inc != 0.f) t.S[qs + a] = t.S[qs + a] + widen(inc);
     }
@@ -395,11 +431,13 @@ __global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t H
 }
 
 // The infosets hs[0 .. gridDim.x) (more than 32 actions), one block each (up to 1024 threads).
-__global__ void __launch_bounds__(1024) k_update_list(DevTree<float> t, const int32_t *hs, int32_t plus,
-                                                      int32_t linear) {
+template <int V>
+__global__ void __launch_bounds__(1024) k_update_list(DevTree<float> t, const int32_t *hs, int32_t linear) {
     grid_dependency_wait();
     __shared__ float s_red[32];
-    update_wide(t, hs[blockIdx.x], plus != 0, linear ? (float)*t.iter : 1.f, s_red);
+    const int32_t h = hs[blockIdx.x];
+    if (!collects(t, t.iplayer[h])) return;                      // alternating: the other player's pass
+    update_wide<V>(t, h, update_weights(t, V, linear != 0), s_red);
 }
 
 // ---- one kernel per depth and step ----------------------------------------------------------------
@@ -545,7 +583,7 @@ __device__ __forceinline__ void fused_bu(const DevTree<float> &t, FuseShared &sh
             if (a < na) ud = madd(ud, s[a], v[a]);
         sh.u[x] = ud;
         if (k == 0 || record) t.u[sh.lo[k] + i] = ud;
-        if (p == 0) return;
+        if (!collects(t, p)) return;
         const float wr = p == 1 ? sh.r1[x] : -sh.r2[x];
         if (wr == 0.f) return;
 #pragma unroll
@@ -560,7 +598,7 @@ __device__ __forceinline__ void fused_bu(const DevTree<float> &t, FuseShared &sh
     }
     sh.u[x] = ud;
     if (k == 0 || record) t.u[sh.lo[k] + i] = ud;
-    if (p == 0) return;
+    if (!collects(t, p)) return;
     const float wr = p == 1 ? sh.r1[x] : -sh.r2[x];
     if (wr == 0.f) return;
     kt = kd = 0;
@@ -681,7 +719,7 @@ __device__ __forceinline__ float tail_leaf(const DevTree<float> &t, int32_t c, f
         t.reach1[c] = q1;
         t.reach2[c] = q2;
     }
-    if (p == 0) return ud;
+    if (!collects(t, p)) return ud;
     const float wr = p == 1 ? q1 : -q2;
     if (wr == 0.f) return ud;
     if (na <= kUnroll) {
@@ -734,7 +772,7 @@ __global__ void __launch_bounds__(256) k_tail(DevTree<float> t, int32_t j0, int3
         for (int a = 0; a < kUnroll; ++a)
             if (a < na) ud = madd(ud, s[a], v[a]);
         t.u[j] = ud;
-        if (p == 0) return;
+        if (!collects(t, p)) return;
         const float wr = p == 1 ? r1 : -r2;
         if (wr == 0.f) return;
 #pragma unroll
@@ -759,7 +797,7 @@ __global__ void __launch_bounds__(256) k_tail(DevTree<float> t, int32_t j0, int3
         ud = madd(ud, s, v);
     }
     t.u[j] = ud;
-    if (p == 0) return;
+    if (!collects(t, p)) return;
     const float wr = p == 1 ? r1 : -r2;
     if (wr == 0.f) return;
     for (int a = 0; a < na; ++a) atomicAdd(&t.inst[qb + a], wr * (vd[a] - ud));
@@ -777,10 +815,10 @@ __device__ __forceinline__ void regret_match(real *sigma, const double *R, int32
 
 // Per-infoset update, one thread per infoset, FP64 operations in the oracle's order (FP64 mode).
 template <typename real, bool kDet>
-__global__ void __launch_bounds__(256) k_update(DevTree<real> t, int32_t H, int32_t plus, int32_t linear) {
+__global__ void __launch_bounds__(256) k_update(DevTree<real> t, int32_t H, int32_t variant, int32_t linear) {
     grid_dependency_wait();
     const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (h >= H || t.iplayer[h] == 0) return;
+    if (h >= H || t.iplayer[h] == 0 || !collects(t, t.iplayer[h])) return;
     const int32_t qb = t.qbase[h];
     const int na = t.qbase[h + 1] - qb;
     if (kDet) {
@@ -791,15 +829,48 @@ __global__ void __launch_bounds__(256) k_update(DevTree<real> t, int32_t H, int3
             for (int a = 0; a < na; ++a) t.inst[qb + a] += src[a];
         }
     }
-    const double w = linear ? (double)*t.iter : 1.0;
+    const double T = (double)*t.iter;
+    double w = linear ? T : 1.0;
+    if (variant == CFRV_LINEAR) w = T;
+    if (variant == CFRV_DISCOUNTED) w = t.wts[0];
     const double wo = __dmul_rn(w, (double)t.own[h]);
     for (int a = 0; a < na; ++a) {
-        double r = t.R[qb + a] + (double)t.inst[qb + a];
-        if (plus) r = r > 0.0 ? r : 0.0;
+        const double in = (double)t.inst[qb + a];
+        double r;
+        if (variant == CFRV_LINEAR) {
+            r = __dadd_rn(t.R[qb + a], __dmul_rn(T, in));
+        } else if (variant == CFRV_DISCOUNTED) {
+            const double x = __dadd_rn(t.R[qb + a], in);
+            r = __dmul_rn(x, x > 0.0 ? t.wts[1] : t.wts[2]);
+        } else {
+            r = t.R[qb + a] + in;
+            if (variant == CFRV_PLUS) r = r > 0.0 ? r : 0.0;
+        }
         t.R[qb + a] = r;
         t.S[qb + a] = madd(t.S[qb + a], wo, (double)t.sigma[qb + a]);
     }
     regret_match(t.sigma, t.R, qb, na);
+}
+
+// Linear / discounted CFR: iteration T's weights, once per iteration (T is the already counted
+// iteration): wts[0] = T^gamma, wts[1] = T^alpha / (T^alpha + 1), wts[2] = T^beta / (T^beta + 1).
+__global__ void k_weights(const int64_t *iter, double *wts, double alpha, double beta, double gamma) {
+    grid_dependency_wait();
+    const double T = (double)*iter;
+    const double ta = pow(T, alpha), tb = pow(T, beta);
+    wts[0] = pow(T, gamma);
+    wts[1] = ta / (ta + 1.0);
+    wts[2] = tb / (tb + 1.0);
+}
+
+// Alternating updates: zeroes the instantaneous regrets of the infosets [0, Hp) whose player takes
+// this pass (the other player's keep their last pass's values).
+template <typename real>
+__global__ void __launch_bounds__(256) k_zero_inst(DevTree<real> t, int32_t Hp) {
+    grid_dependency_wait();
+    const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (h >= Hp || !collects(t, t.iplayer[h])) return;
+    for (int32_t q = t.qbase[h]; q < t.qbase[h + 1]; ++q) t.inst[q] = real(0);
 }
 
 // ---- state access -----------------------------------------------------------------------------------

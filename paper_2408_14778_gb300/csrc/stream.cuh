@@ -182,7 +182,7 @@ __device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage 
         }
         t.u[ti.j0 + ii[x]] = ud;
         go[x] = false;
-        if (pl[x] == 0) continue;
+        if (!collects(t, pl[x])) continue;
         const float wr = pl[x] == 1 ? st.r1[k] : -st.r2[k];
         if (wr == 0.f) continue;
         kt = kd = 0;
@@ -227,7 +227,7 @@ __device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage 
         for (int a = 0; a < NA; ++a)
             if (a < na[x]) ud = madd(ud, s[x][a], v[x][a]);
         t.u[ti.j0 + ii[x]] = ud;
-        if (pl[x] == 0) continue;
+        if (!collects(t, pl[x])) continue;
         const float wr = pl[x] == 1 ? st.r1[k] : -st.r2[k];
         if (wr == 0.f) continue;
 #pragma unroll
@@ -657,7 +657,7 @@ struct TailTiles {
                 t.reach1[cg] = cq1;
                 t.reach2[cg] = cq2;
             }
-            if (cp == 0) continue;
+            if (!collects(t, cp)) continue;
             const float wr = cp == 1 ? cq1 : -cq2;
             if (wr == 0.f) continue;
             if (cna <= NA) {
@@ -690,7 +690,7 @@ struct TailTiles {
             for (int a = 0; a < NA; ++a)
                 if (a < na) ud = madd(ud, s[a], v[a]);
             t.u[ti.j0 + c] = ud;
-            if (p == 0) return;
+            if (!collects(t, p)) return;
             const float wr = p == 1 ? r1 : -r2;
             if (wr == 0.f) return;
 #pragma unroll
@@ -704,7 +704,7 @@ struct TailTiles {
             ud = madd(ud, __ldg(t.sigma + qb + a), val);
         }
         t.u[ti.j0 + c] = ud;
-        if (p == 0) return;
+        if (!collects(t, p)) return;
         const float wr = p == 1 ? r1 : -r2;
         if (wr == 0.f) return;
         kt = kd = 0;

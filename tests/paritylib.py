@@ -47,7 +47,7 @@ def regret_matching(g, R):
     return out
 
 
-def fp32_sigma_check(g, gs, os_, sig_g, tol=TOL32):
+def fp32_sigma_check(g, gs, os_, sig_g, tol=TOL32, players=(1, 2)):
     """Strategy parity in FP32 mode.
 
     The regrets themselves are compared elsewhere (normwise 1e-5).  Given the regrets' observed
@@ -64,7 +64,7 @@ def fp32_sigma_check(g, gs, os_, sig_g, tol=TOL32):
     R = os_["cum_regret"]
     Rg = gs["cum_regret"]
     seg = lambda x, op: op.reduceat(x, starts) if x.size else x     # noqa: E731 - per-infoset reduction
-    player = g.infoset_player > 0
+    player = np.isin(g.infoset_player, players)
     delta = seg(np.abs(Rg - R), np.maximum)
     pos = seg(np.maximum(R, 0), np.add)
     rmax = seg(R, np.maximum)
@@ -83,7 +83,7 @@ def fp32_sigma_check(g, gs, os_, sig_g, tol=TOL32):
     return float(differ.sum()) / max(int(player.sum()), 1)
 
 
-def fp32_regret_budget_check(g, gs, os_, depth):
+def fp32_regret_budget_check(g, gs, os_, depth, scale=1.0, players=(1, 2)):
     """Per-infoset bound on one FP32 step's regret error.
 
     r~(h,a) = sum_{d in h} pi-check(d) (u(child_a(d)) - u(d)) (Eq. 7).  In FP32, pi-check carries at most
@@ -92,19 +92,21 @@ def fp32_regret_budget_check(g, gs, os_, depth):
     nodes of h at most n_h eps * sum |terms|.  Hence
         |r~_gpu - r~| <= (8 D + 8 + 2 n_h) eps32 U pi~(h)      (pi~(h) of Eq. 3),
     and the same bounds the regret after one step from exact state (CFR+ clipping is 1-Lipschitz).
+    scale multiplies the bound where the step weights r~ (linear CFR: by T).
     """
     eps = 2.0 ** -24
     U = float(np.abs(g.utility).max())
     qb = qbase(g)
     nh = np.bincount(g.infoset[g.infoset >= 0], minlength=g.num_infosets)
-    budget = (8 * depth + 8 + 2 * nh) * eps * U * os_["cf_reach_sum"]
+    budget = scale * (8 * depth + 8 + 2 * nh) * eps * U * os_["cf_reach_sum"]
     dev = np.maximum.reduceat(np.abs(gs["cum_regret"] - os_["cum_regret"]), qb[:-1]) if qb[-1] else np.zeros(0)
-    bad = np.nonzero((g.infoset_player > 0) & (dev > budget * (1 + 1e-9) + 1e-300))[0]
+    bad = np.nonzero(np.isin(g.infoset_player, players) & (dev > budget * (1 + 1e-9) + 1e-300))[0]
     assert bad.size == 0, (f"infoset {bad[0]}: regret error {dev[bad[0]]:.3e} above the FP32 budget "
                            f"{budget[bad[0]]:.3e}")
 
 
-def compare_state(s, o, tol, g, what=("cum_regret", "strat_sum", "inst_regret"), max_rounding_share=1.0):
+def compare_state(s, o, tol, g, what=("cum_regret", "strat_sum", "inst_regret"), max_rounding_share=1.0,
+                  budget_scale=1.0, players=(1, 2)):
     """Regrets, sums and the strategy of the solver against the oracle.
 
     FP64: every array normwise within tol.  FP32 (one step from the oracle's state): arrays
@@ -112,16 +114,17 @@ def compare_state(s, o, tol, g, what=("cum_regret", "strat_sum", "inst_regret"),
     and strategies as in fp32_sigma_check.
     """
     gs, os_ = cfr.cfr_get_state(s), o.state()
+    keep = np.repeat(np.isin(g.infoset_player, players), g.infoset_num_actions)   # the slots compared
     for k in what:
-        e = normwise(gs[k], os_[k])
+        e = normwise(np.where(keep, gs[k], 0.0), np.where(keep, os_[k], 0.0))
         assert e <= tol, f"{k}: normwise error {e:.3e} > {tol:.0e}"
     sig = cfr.cfr_current_strategy(s)
     if tol >= TOL32:
-        fp32_regret_budget_check(g, gs, os_, cfr.cfr_get_info(s)["max_depth"])
-        share = fp32_sigma_check(g, gs, os_, sig, tol)
+        fp32_regret_budget_check(g, gs, os_, cfr.cfr_get_info(s)["max_depth"], budget_scale, players)
+        share = fp32_sigma_check(g, gs, os_, sig, tol, players)
         assert share <= max_rounding_share, f"rounding moved the strategy of {share:.2%} of infosets"
     else:
-        e = normwise(sig, os_["sigma"])
+        e = normwise(np.where(keep, sig, 0.0), np.where(keep, os_["sigma"], 0.0))
         assert e <= tol, f"sigma: normwise error {e:.3e}"
     assert gs["iteration"] == os_["iteration"]
     return gs, os_
