@@ -211,6 +211,19 @@ def time_to_exploitability(args, local: int) -> dict:
 
     out = {"target": TTT_TARGET, "check_every": TTT_CHECK, "variant": "cfr+ linear averaging, simultaneous",
            "time_includes": "iterations and the exploitability evaluations"}
+    # the variants of the same solver on the full game (GPU, FP32 mode)
+    g = gamegen.config("rank13_depth10", seed=args.seed)
+    for name, variant, mode in (("cfr+_alternating", cfr.CFR_PLUS, cfr.CFR_ALTERNATING),
+                                ("linear_cfr", cfr.CFR_LINEAR, cfr.CFR_SIMULTANEOUS),
+                                ("discounted_cfr_1.5_0_2", cfr.CFR_DISCOUNTED, cfr.CFR_SIMULTANEOUS),
+                                ("discounted_cfr_1.5_0_2_alternating", cfr.CFR_DISCOUNTED, cfr.CFR_ALTERNATING)):
+        s = cfr.cfr_load_tree(g, variant=variant, precision=cfr.CFR_FP32, update_mode=mode, device=local,
+                              dcfr=(1.5, 0.0, 2.0))
+        cfr.cfr_synchronize(s)
+        r = _ttt_run(lambda n: cfr.cfr_iterate(s, n), lambda: cfr.cfr_exploitability(s)[1], TTT_MAX_ITERS, 30.0)
+        r["nodes"] = g.num_nodes
+        out[f"gpu_rank13_depth10_{name}"] = r
+        s.close()
     for name, nodes in (("rank13_depth10", None), ("rank13_depth10_2e5", 200_000)):
         g = gamegen.config("rank13_depth10", seed=args.seed, target_nodes=nodes)
         s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, device=local)
