@@ -284,3 +284,36 @@ def permute_nodes(g: GameDesc, seed: int) -> GameDesc:
     meta["perm"] = perm
     return GameDesc(parent, action, infoset, g.infoset_player.copy(), g.infoset_num_actions.copy(),
                     g.chance_prob.copy(), util, meta)
+
+
+def batch_subgames(count: int, seed: int = 0, min_nodes: float = 1e2, max_nodes: float = 1e5,
+                   min_depth: int = 4, max_depth: int = 10) -> list:
+    """Independent seeded subgames for batched solving: sizes log-uniform in [min_nodes, max_nodes],
+    depth uniform in [min_depth, max_depth], 2..5 actions per public node, the 6-deal bucket game's deal
+    and U[-2, 2] payoffs.  A size the drawn depth cannot reach (even with every child a decision node)
+    raises the depth until it can (at most max_depth + 4).  The size fit is the continuation
+    probability's bisection (+-10%; where small trees only change size in large steps, the closest size
+    on a grid of continuation probabilities)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5B6A]))
+    out = []
+    for i in range(count):
+        target = int(round(float(np.exp(rng.uniform(np.log(min_nodes), np.log(max_nodes))))))
+        depth = int(rng.integers(min_depth, max_depth + 1))
+        sub_seed = int(rng.integers(0, 2**62))
+        kw = dict(deal_kind=DEAL_BUCKET_PAIRS, num_buckets=3, amin=2, amax=5, payoff_kind=PAY_UNIFORM, umax=2.0,
+                  p_chance=0.0, general_sum=False, first_actor=1)
+        while public_size(seed=sub_seed, depth=depth, p_cont=1.0, **kw) < target and depth < max_depth + 4:
+            depth += 1
+        full = public_size(seed=sub_seed, depth=depth, p_cont=1.0, **kw)
+        p = 1.0
+        if full > target * 1.1:
+            try:
+                p = fit_p_cont(target, seed=sub_seed, depth=depth, **kw)
+            except ValueError:       # small trees change size in steps of whole subtrees: take the closest
+                grid = np.linspace(0.0, 1.0, 201)
+                sizes = np.array([public_size(seed=sub_seed, depth=depth, p_cont=float(q), **kw) for q in grid])
+                p = float(grid[int(np.argmin(np.abs(np.log(sizes / target))))])
+        g = public_private(seed=sub_seed, depth=depth, p_cont=p, **kw)
+        g.meta.update(config="batch_subgame", target_nodes=target, batch_index=i)
+        out.append(g)
+    return out

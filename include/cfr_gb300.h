@@ -229,6 +229,68 @@ const char *cfr_last_error(const cfr_solver *s);
 /* Releases the solver and its device memory (waits for its queued work).  NULL is a no-op. */
 void cfr_free(cfr_solver *s);
 
+/* ---- batched solving (the cfg of many small independent games; no counterpart in the paper) --------
+ * Many independent games solved side by side: they are laid out as one forest and every
+ * cfr_batch_iterate call advances all of them by n iterations in ONE persistent kernel launch (a
+ * CUDA graph of the launch and two bookkeeping nodes).  A thread block takes a game from a work queue
+ * (largest games first) and runs its n iterations depth by depth (Section 3.2's steps, as
+ * cfr_iterate's kernels compute them per node and infoset), then takes the next game.  FP32 mode with
+ * FP64 accumulators, simultaneous updates, at most 32 actions per infoset; every variant.  Game g's
+ * arrays use its own caller numbering. */
+typedef struct cfr_batch cfr_batch;   /* opaque; owned by the library */
+
+typedef struct {
+    int32_t threads_per_block;  /* multiple of 32 in [32, 1024] */
+    int32_t blocks_per_sm;      /* 0 = as many as fit */
+} cfr_batch_tuning;
+
+typedef struct {
+    int32_t num_games;
+    int64_t num_nodes, num_decision, num_q;
+    int64_t iteration;          /* iterations every game has run */
+    int64_t device_bytes;
+    int32_t threads_per_block, blocks_per_sm, grid;   /* the launch shape in use */
+    int32_t tuned;              /* 1 once set by cfr_batch_set_tuning or cfr_batch_autotune */
+    int64_t kernel_launches;    /* kernels launched by cfr_batch_iterate so far */
+} cfr_batch_info;
+
+/* Validates and lays out num_games >= 1 games (each as cfr_load_tree would; the combined size must stay
+ * below 2^31 - 1 nodes).  CFR_ERR_UNSUPPORTED for FP64 mode, alternating updates or more than 32
+ * actions at an infoset.  c may be NULL (defaults: vanilla; pass variant CFR_PLUS for CFR+). */
+cfr_status cfr_batch_load(const cfr_game_desc *games, int32_t num_games, const cfr_config *c, cfr_batch **out);
+
+/* Queues n >= 0 iterations of every game (one persistent launch).  Asynchronous on the batch's stream. */
+cfr_status cfr_batch_iterate(cfr_batch *b, int32_t n);
+
+/* Sets the launch shape. */
+cfr_status cfr_batch_set_tuning(cfr_batch *b, const cfr_batch_tuning *t);
+
+/* Measures trial_iterations of every game for each block size in {128, 256, 512, 1024} and each
+ * blocks-per-SM count in {1, 2, 4, 8, 16} that fits, on a copy of the state that is restored
+ * afterwards (the iteration count does not move), and keeps the fastest.  *chosen and *best_us (time
+ * per iteration of the whole batch) may be NULL.  Synchronises. */
+cfr_status cfr_batch_autotune(cfr_batch *b, int32_t trial_iterations, cfr_batch_tuning *chosen, double *best_us);
+
+/* Per game [len >= num_games]: the microseconds per iteration of its part of the last cfr_batch_iterate
+ * call (from its first iteration's start to its last iteration's end, divided by n).  Synchronises. */
+cfr_status cfr_batch_game_times(cfr_batch *b, double *us_per_iteration, int32_t len);
+
+/* Per game [len >= num_games]: NashConv of its average strategy (Section 2.2; exploitability =
+ * NashConv / 2).  CFR_ERR_UNSUPPORTED when an infoset spans depths.  Synchronises. */
+cfr_status cfr_batch_exploitability(cfr_batch *b, double *nash_conv, int32_t len);
+
+/* Game `game`'s cumulative regrets and strategy sums (either may be NULL; len >= its num_q) and the
+ * iteration count.  Synchronises. */
+cfr_status cfr_batch_get_state(cfr_batch *b, int32_t game, double *cum_regret, double *strat_sum, int64_t len,
+                               int64_t *iteration);
+
+/* Game `game`'s average strategy (Eq. 10 normalised; len >= its num_q).  Synchronises. */
+cfr_status cfr_batch_average_strategy(cfr_batch *b, int32_t game, double *out, int64_t len);
+
+cfr_status cfr_batch_get_info(const cfr_batch *b, cfr_batch_info *info);
+const char *cfr_batch_last_error(const cfr_batch *b);   /* thread-local message if b == NULL */
+void cfr_batch_free(cfr_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

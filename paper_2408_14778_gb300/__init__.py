@@ -85,6 +85,19 @@ class _Info(ctypes.Structure):
     ]
 
 
+class _BatchTuning(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("num_games", ctypes.c_int32), ("num_nodes", ctypes.c_int64), ("num_decision", ctypes.c_int64),
+        ("num_q", ctypes.c_int64), ("iteration", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
+        ("tuned", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+    ]
+
+
 _lib_handle = None
 _P = ctypes.c_void_p
 
@@ -128,6 +141,23 @@ def lib():
         L.cfr_last_error.restype = ctypes.c_char_p
         L.cfr_free.argtypes = [_P]
         L.cfr_free.restype = None
+        L.cfr_batch_load.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(_Config), ctypes.POINTER(_P)]
+        L.cfr_batch_iterate.argtypes = [_P, ctypes.c_int32]
+        L.cfr_batch_set_tuning.argtypes = [_P, ctypes.POINTER(_BatchTuning)]
+        L.cfr_batch_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(_BatchTuning), _P]
+        L.cfr_batch_game_times.argtypes = [_P, _P, ctypes.c_int32]
+        L.cfr_batch_exploitability.argtypes = [_P, _P, ctypes.c_int32]
+        L.cfr_batch_get_state.argtypes = [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P]
+        L.cfr_batch_average_strategy.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_int64]
+        L.cfr_batch_get_info.argtypes = [_P, ctypes.POINTER(_BatchInfo)]
+        L.cfr_batch_last_error.argtypes = [_P]
+        L.cfr_batch_last_error.restype = ctypes.c_char_p
+        L.cfr_batch_free.argtypes = [_P]
+        L.cfr_batch_free.restype = None
+        for name in ("cfr_batch_load", "cfr_batch_iterate", "cfr_batch_set_tuning", "cfr_batch_autotune",
+                     "cfr_batch_game_times", "cfr_batch_exploitability", "cfr_batch_get_state",
+                     "cfr_batch_average_strategy", "cfr_batch_get_info"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("cfr_validate", "cfr_load_tree", "cfr_iterate", "cfr_synchronize", "cfr_average_strategy",
                      "cfr_current_strategy", "cfr_exploitability", "cfr_get_state", "cfr_set_state", "cfr_get_nodes",
                      "cfr_get_info", "cfr_root_value"):
@@ -362,3 +392,152 @@ class Solver:
     root_value = cfr_root_value
     phase_times = cfr_phase_times
     info = cfr_get_info
+
+
+# ---- batched solving -------------------------------------------------------------------------------
+
+def _check_batch(st: int, handle=None):
+    if st != CFR_OK:
+        msg = lib().cfr_batch_last_error(handle)
+        raise CfrError(st, msg.decode(errors="replace") if msg else "")
+
+
+class Batch:
+    """Many independent games solved side by side on the GPU (owns the C handle)."""
+
+    def __init__(self, handle, allocator, games):
+        self.handle = handle
+        self._allocator = allocator
+        self.num_games = len(games)
+        self.num_q = [int(np.sum(g.infoset_num_actions)) for g in games]
+        self.num_nodes = [int(g.num_nodes) for g in games]
+
+    def close(self):
+        if self.handle:
+            lib().cfr_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=None, stream=None,
+                   allocator: str = "torch", dcfr=(1.5, 0.0, 2.0)) -> Batch:
+    """Loads a list of games for batched solving (FP32 mode, simultaneous updates)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise CfrError(CFR_ERR_CUDA, "no CUDA device is available")
+    dev = torch.cuda.current_device() if device is None else int(device)
+    st_handle = torch.cuda.current_stream(dev).cuda_stream if stream is None else int(stream)
+    cfg = _Config()
+    lib().cfr_config_init(ctypes.byref(cfg))
+    cfg.variant, cfg.precision, cfg.avg_weight = variant, CFR_FP32, avg_weight
+    cfg.device, cfg.cuda_stream = dev, st_handle
+    cfg.dcfr_alpha, cfg.dcfr_beta, cfg.dcfr_gamma = (float(x) for x in dcfr)
+    alloc = None
+    if allocator == "torch":
+        alloc = _TorchAllocator(dev, st_handle)
+        cfg.dev_alloc, cfg.dev_free = alloc.alloc, alloc.free
+    elif allocator != "cuda":
+        raise ValueError("allocator must be 'torch' or 'cuda'")
+    descs = [_Desc(g) for g in games]
+    arr = (_GameDesc * len(descs))(*[d.c for d in descs])
+    h = _P()
+    _check_batch(lib().cfr_batch_load(arr, len(descs), ctypes.byref(cfg), ctypes.byref(h)))
+    b = Batch(h, alloc, games)
+    b._variant = int(variant)
+    return b
+
+
+def cfr_batch_iterate(b: Batch, n: int = 1):
+    _check_batch(lib().cfr_batch_iterate(b.handle, int(n)), b.handle)
+
+
+def cfr_batch_set_tuning(b: Batch, threads_per_block: int, blocks_per_sm: int = 0):
+    t = _BatchTuning(int(threads_per_block), int(blocks_per_sm))
+    _check_batch(lib().cfr_batch_set_tuning(b.handle, ctypes.byref(t)), b.handle)
+
+
+_TUNE_CACHE: dict = {}
+
+
+def _size_bucket(b: Batch) -> str:
+    """Key of the autotuner's cache: the games' count and mean size, each rounded to a power of 2."""
+    mean = float(np.mean(b.num_nodes))
+    return f"games~2^{int(round(np.log2(b.num_games)))},nodes~2^{int(round(np.log2(max(mean, 1.0))))}"
+
+
+def cfr_batch_autotune(b: Batch, trial_iterations: int = 3, cache_path: str | None = None) -> dict:
+    """Launch shape for this batch: from the cache when one was measured for this GPU and size bucket
+    (in memory, and in the JSON file cache_path when given), else measured (cfr_batch_autotune) and
+    stored.  Returns {threads_per_block, blocks_per_sm, us_per_iteration (None if cached), cached}."""
+    import json
+
+    import torch
+
+    key = f"{torch.cuda.get_device_name()}|{_size_bucket(b)}|variant={cfr_batch_get_info(b)['variant']}"
+    disk = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            disk = json.load(open(cache_path))
+        except (OSError, ValueError):
+            disk = {}
+    hit = _TUNE_CACHE.get(key) or disk.get(key)
+    if hit:
+        cfr_batch_set_tuning(b, hit["threads_per_block"], hit["blocks_per_sm"])
+        return dict(hit, us_per_iteration=None, cached=True, key=key)
+    t = _BatchTuning()
+    us = ctypes.c_double()
+    _check_batch(lib().cfr_batch_autotune(b.handle, int(trial_iterations), ctypes.byref(t), ctypes.byref(us)),
+                 b.handle)
+    rec = {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm}
+    _TUNE_CACHE[key] = rec
+    if cache_path:
+        disk[key] = rec
+        os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(disk, f, indent=1)
+        os.replace(tmp, cache_path)
+    return dict(rec, us_per_iteration=us.value, cached=False, key=key)
+
+
+def cfr_batch_game_times(b: Batch) -> np.ndarray:
+    out = np.zeros(b.num_games)
+    _check_batch(lib().cfr_batch_game_times(b.handle, out.ctypes.data, b.num_games), b.handle)
+    return out
+
+
+def cfr_batch_exploitability(b: Batch) -> np.ndarray:
+    """NashConv of every game's average strategy (exploitability = NashConv / 2)."""
+    out = np.zeros(b.num_games)
+    _check_batch(lib().cfr_batch_exploitability(b.handle, out.ctypes.data, b.num_games), b.handle)
+    return out
+
+
+def cfr_batch_get_state(b: Batch, game: int) -> dict:
+    q = b.num_q[game]
+    R, S = np.zeros(max(q, 1)), np.zeros(max(q, 1))
+    it = ctypes.c_int64()
+    _check_batch(lib().cfr_batch_get_state(b.handle, int(game), R.ctypes.data, S.ctypes.data, max(q, 1),
+                                           ctypes.byref(it)), b.handle)
+    return dict(cum_regret=R[:q], strat_sum=S[:q], iteration=it.value)
+
+
+def cfr_batch_average_strategy(b: Batch, game: int) -> np.ndarray:
+    q = b.num_q[game]
+    out = np.zeros(max(q, 1))
+    _check_batch(lib().cfr_batch_average_strategy(b.handle, int(game), out.ctypes.data, max(q, 1)), b.handle)
+    return out[:q]
+
+
+def cfr_batch_get_info(b: Batch) -> dict:
+    info = _BatchInfo()
+    _check_batch(lib().cfr_batch_get_info(b.handle, ctypes.byref(info)), b.handle)
+    d = {name: getattr(info, name) for name, _ in _BatchInfo._fields_}
+    d["variant"] = getattr(b, "_variant", None)
+    return d

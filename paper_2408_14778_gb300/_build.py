@@ -1,7 +1,7 @@
 """Builds libcfr_gb300.so in-tree with nvcc for sm_103a (GB300).
 
-Two translation units (host layout builder, CUDA kernels + C ABI) compile in parallel and link
-into one shared library next to this file.
+Three translation units (the host layout builder, the single-game kernels + C ABI, the batched
+kernels + C ABI) compile in parallel and link into one shared library next to this file.
 """
 from __future__ import annotations
 
@@ -17,8 +17,8 @@ LIB = os.path.join(HERE, "libcfr_gb300.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["cfr_api.cu", "layout.cpp"]
-HEADERS = ["kernels.cuh", "layout.hpp"]
+SOURCES = ["cfr_api.cu", "batch_api.cu", "layout.cpp"]
+HEADERS = ["kernels.cuh", "stream.cuh", "batch.cuh", "layout.hpp"]
 
 
 def _nvcc() -> str:

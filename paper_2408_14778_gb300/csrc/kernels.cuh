@@ -21,6 +21,7 @@
 #include <cstdint>
 
 namespace cfrgb {
+namespace {   // device code: internal to each translation unit that includes it
 
 // Whether action a of a node with na actions leads to a terminal (see layout.hpp).
 __device__ __forceinline__ bool is_terminal(uint32_t m, const uint32_t *wbits, int na, int a) {
@@ -363,23 +364,19 @@ __device__ __forceinline__ void update_wide(const DevTree<float> &t, int32_t h, 
     }
 }
 
-template <int NA, int V>
-__global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t Hp, int32_t linear) {
-    grid_dependency_wait();
-    const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (h >= Hp) return;
-    if (t.pmask != 6 && !collects(t, t.iplayer[h])) return;      // alternating: the other player's pass
+// The update of player infoset h (at most 32 actions) with the iteration's weights u.  C: loads
+// through L2 (the caller wrote R, S, sigma or r~ earlier in the same launch).
+template <int NA, int V, bool C>
+__device__ __forceinline__ void update_row(const DevTree<float> &t, int32_t h, const UpdWeights &u) {
     const int32_t qs = t.qbase[h];
     const int na = t.qbase[h + 1] - qs;
-    if (na > 32) return;
-    const UpdWeights u = update_weights(t, V, linear != 0);
-    const float wo = u.w * t.own[h];
+    const float wo = u.w * ldm<C>(t.own + h);
     if (na <= NA) {
         double rr[NA];
         float in[NA], sg[NA], pos[NA];
 #pragma unroll
         for (int a = 0; a < NA; ++a)
-            if (a < na) { rr[a] = t.R[qs + a]; in[a] = t.inst[qs + a]; sg[a] = t.sigma[qs + a]; }
+            if (a < na) { rr[a] = ldm<C>(t.R + qs + a); in[a] = ldm<C>(t.inst + qs + a); sg[a] = ldm<C>(t.sigma + qs + a); }
         float sum = 0.f;
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
@@ -390,7 +387,7 @@ __global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t H
         }
 #pragma unroll
         for (int a = 0; a < NA; ++a)                            // nothing accrues where own reach or sigma is 0
-            if (a < na && sg[a] != 0.f) rr[a] = t.S[qs + a];
+            if (a < na && sg[a] != 0.f) rr[a] = ldm<C>(t.S + qs + a);
 #pragma unroll
         for (int a = 0; a < NA; ++a)
             if (a < na && sg[a] != 0.f) t.S[qs + a] = rr[a] + widen(sg[a]);
@@ -405,19 +402,19 @@ __global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t H
         } else if (sum > 0.f) {
             regret_match_tiny(t, qs, na);
         } else {
-            const float u = 1.f / (float)na;                   // no positive regret: uniform (Eq. 9)
+            const float un = 1.f / (float)na;                  // no positive regret: uniform (Eq. 9)
 #pragma unroll
             for (int a = 0; a < NA; ++a)
-                if (a < na) t.sigma[qs + a] = u;
+                if (a < na) t.sigma[qs + a] = un;
         }
         return;
     }
     float pos[32];
     float sum = 0.f;
     for (int a = 0; a < na; ++a) {
-        pos[a] = update_regret<V>(t.R + qs + a, t.R[qs + a], t.inst[qs + a], u);
-        const float inc = wo * t.sigma[qs + a];
-        if (inc != 0.f) t.S[qs + a] = t.S[qs + a] + widen(inc);
+        pos[a] = update_regret<V>(t.R + qs + a, ldm<C>(t.R + qs + a), ldm<C>(t.inst + qs + a), u);
+        const float inc = wo * ldm<C>(t.sigma + qs + a);
+        if (inc != 0.f) t.S[qs + a] = ldm<C>(t.S + qs + a) + widen(inc);
     }
     for (int a = 0; a < na; ++a) sum += pos[a];
     if (sum >= 1e-30f) {
@@ -428,6 +425,16 @@ __global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t H
     } else {
         for (int a = 0; a < na; ++a) t.sigma[qs + a] = 1.f / (float)na;
     }
+}
+
+template <int NA, int V>
+__global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t Hp, int32_t linear) {
+    grid_dependency_wait();
+    const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (h >= Hp) return;
+    if (t.pmask != 6 && !collects(t, t.iplayer[h])) return;      // alternating: the other player's pass
+    if (t.qbase[h + 1] - t.qbase[h] > 32) return;
+    update_row<NA, V, false>(t, h, update_weights(t, V, linear != 0));
 }
 
 // The infosets hs[0 .. gridDim.x) (more than 32 actions), one block each (up to 1024 threads).
@@ -933,9 +940,10 @@ struct DevBR {
     int32_t *astar;            // [H]
 };
 
-__global__ void __launch_bounds__(256) k_br_topdown(DevBR b, int32_t j0, int32_t j1, int32_t player) {
-    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (j >= j1) return;
+// Best-response steps (one node or infoset each).  C: loads through L2 of the values this launch wrote.
+// Top-down: the reach of node j's decision children that excludes the best responder's own actions.
+template <bool C>
+__device__ __forceinline__ void br_topdown_node(const DevBR &b, int32_t j, int32_t player) {
     int32_t c = b.dfirst[j];
     if (c == b.dfirst[j + 1]) return;
     const int32_t h = b.dinfo[j];
@@ -943,21 +951,23 @@ __global__ void __launch_bounds__(256) k_br_topdown(DevBR b, int32_t j0, int32_t
     const int32_t qb = b.qbase[h];
     const int na = b.qbase[h + 1] - qb;
     const uint32_t m = b.kmask[j];
-    const double r = b.preach[j];
+    const double r = ldm<C>(b.preach + j);
     for (int a = 0; a < na; ++a) {
         if (is_terminal(m, b.wbits, na, a)) continue;
         b.preach[c++] = mine ? r : r * b.avg[qb + a];
     }
 }
 
+template <bool C>
 __device__ __forceinline__ double br_child(const DevBR &b, uint32_t m, int na, int a, int32_t &c, int32_t &tt,
                                            double sign) {
-    return is_terminal(m, b.wbits, na, a) ? sign * b.util[tt++] : b.val[c++];
+    return is_terminal(m, b.wbits, na, a) ? sign * b.util[tt++] : ldm<C>(b.val + c++);
 }
 
-__global__ void __launch_bounds__(256) k_br_nodes(DevBR b, int32_t j0, int32_t j1, int32_t player) {
-    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (j >= j1) return;
+// Bottom-up: the value of an opponent (or chance) node under the average strategy; at the best
+// responder's nodes, the reach-weighted action values summed per infoset (cfv).
+template <bool C>
+__device__ __forceinline__ void br_node(const DevBR &b, int32_t j, int32_t player) {
     const int32_t h = b.dinfo[j];
     const int32_t qb = b.qbase[h];
     const int na = b.qbase[h + 1] - qb;
@@ -966,41 +976,66 @@ __global__ void __launch_bounds__(256) k_br_nodes(DevBR b, int32_t j0, int32_t j
     int32_t c = b.dfirst[j], tt = b.tfirst[j];
     if (b.iplayer[h] != player) {
         double v = 0.0;
-        for (int a = 0; a < na; ++a) v += b.avg[qb + a] * br_child(b, m, na, a, c, tt, sign);
+        for (int a = 0; a < na; ++a) v += b.avg[qb + a] * br_child<C>(b, m, na, a, c, tt, sign);
         b.val[j] = v;
     } else {
-        const double r = b.preach[j];
+        const double r = ldm<C>(b.preach + j);
         if (r == 0.0) return;
         for (int a = 0; a < na; ++a) {
-            const double v = br_child(b, m, na, a, c, tt, sign);
+            const double v = br_child<C>(b, m, na, a, c, tt, sign);
             atomicAdd(&b.cfv[qb + a], r * v);
         }
     }
 }
 
-__global__ void k_br_choose(DevBR b, int32_t h0, int32_t h1, int32_t player) {
-    const int32_t h = h0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (h >= h1 || b.iplayer[h] != player) return;
+// The best action of the responder's infoset h (lowest index among ties).
+template <bool C>
+__device__ __forceinline__ void br_choose(const DevBR &b, int32_t h, int32_t player) {
+    if (b.iplayer[h] != player) return;
     const int32_t qb = b.qbase[h];
     const int na = b.qbase[h + 1] - qb;
     int best = 0;
-    for (int a = 1; a < na; ++a)
-        if (b.cfv[qb + a] > b.cfv[qb + best]) best = a;
+    double bv = ldm<C>(b.cfv + qb);
+    for (int a = 1; a < na; ++a) {
+        const double v = ldm<C>(b.cfv + qb + a);
+        if (v > bv) { best = a; bv = v; }
+    }
     b.astar[h] = best;
 }
 
-__global__ void __launch_bounds__(256) k_br_pick(DevBR b, int32_t j0, int32_t j1, int32_t player) {
-    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (j >= j1) return;
+// The value of a responder's node: that of its infoset's best action.
+template <bool C>
+__device__ __forceinline__ void br_pick(const DevBR &b, int32_t j, int32_t player) {
     const int32_t h = b.dinfo[j];
     if (b.iplayer[h] != player) return;
     const uint32_t m = b.kmask[j];
     const int na = b.qbase[h + 1] - b.qbase[h];
-    const int as = b.astar[h];
+    const int as = ldm<C>(b.astar + h);
     int32_t c = b.dfirst[j], tt = b.tfirst[j];
     double v = 0.0;
-    for (int a = 0; a <= as; ++a) v = br_child(b, m, na, a, c, tt, player == 1 ? 1.0 : -1.0);
+    for (int a = 0; a <= as; ++a) v = br_child<C>(b, m, na, a, c, tt, player == 1 ? 1.0 : -1.0);
     b.val[j] = v;
 }
 
+__global__ void __launch_bounds__(256) k_br_topdown(DevBR b, int32_t j0, int32_t j1, int32_t player) {
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j < j1) br_topdown_node<false>(b, j, player);
+}
+
+__global__ void __launch_bounds__(256) k_br_nodes(DevBR b, int32_t j0, int32_t j1, int32_t player) {
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j < j1) br_node<false>(b, j, player);
+}
+
+__global__ void k_br_choose(DevBR b, int32_t h0, int32_t h1, int32_t player) {
+    const int32_t h = h0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (h < h1) br_choose<false>(b, h, player);
+}
+
+__global__ void __launch_bounds__(256) k_br_pick(DevBR b, int32_t j0, int32_t j1, int32_t player) {
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j < j1) br_pick<false>(b, j, player);
+}
+
+}  // namespace
 }  // namespace cfrgb

@@ -22,7 +22,7 @@ cfr_status fail(std::string *err, cfr_status st, const char *fmt, ...) {
 
 }  // namespace
 
-cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, bool infoset_lists) {
+cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, bool infoset_lists, bool forest) {
     if (!g) return fail(err, CFR_ERR_INVALID, "game description is NULL");
     const int64_t n = g->num_nodes;
     if (n < 1) return fail(err, CFR_ERR_INVALID, "num_nodes must be >= 1 (got %lld)", (long long)n);
@@ -68,23 +68,24 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
             return fail(err, CFR_ERR_INVALID, "chance infoset %d: probabilities sum to %.17g, not 1", h, s);
     }
 
-    // ---- nodes: one root, ids in range, children a bijection onto actions -------------------
-    int64_t root = -1;
+    // ---- nodes: one root (a forest: any number), ids in range, children a bijection onto actions ----
+    std::vector<int32_t> roots;
     for (int64_t v = 0; v < n; ++v) {
         const int32_t par = g->parent[v];
         if (par == -1) {
-            if (root >= 0) return fail(err, CFR_ERR_INVALID, "two roots: nodes %lld and %lld", (long long)root, (long long)v);
-            root = v;
+            if (!roots.empty() && !forest)
+                return fail(err, CFR_ERR_INVALID, "two roots: nodes %d and %lld", roots[0], (long long)v);
+            roots.push_back((int32_t)v);
         } else if (par < 0 || par >= n) {
             return fail(err, CFR_ERR_INVALID, "node %lld: parent %d out of range", (long long)v, par);
         }
         const int32_t hv = g->infoset[v];
         if (hv < -1 || hv >= H) return fail(err, CFR_ERR_INVALID, "node %lld: infoset %d out of range", (long long)v, hv);
     }
-    if (root < 0) return fail(err, CFR_ERR_INVALID, "no root (no node with parent -1)");
+    if (roots.empty()) return fail(err, CFR_ERR_INVALID, "no root (no node with parent -1)");
     std::vector<int32_t> cstart((size_t)n + 1, 0);
     for (int64_t v = 0; v < n; ++v) {
-        if (v == root) continue;
+        if (g->parent[v] == -1) continue;
         const int32_t par = g->parent[v];
         if (g->infoset[par] < 0)
             return fail(err, CFR_ERR_INVALID, "node %lld: parent %d is a terminal (infoset -1)", (long long)v, par);
@@ -100,7 +101,7 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
     for (int64_t v = 0; v < n; ++v) cstart[(size_t)v + 1] += cstart[(size_t)v];
     std::vector<int32_t> child((size_t)n, -1);
     for (int64_t v = 0; v < n; ++v) {
-        if (v == root) continue;
+        if (g->parent[v] == -1) continue;
         const int32_t par = g->parent[v];
         const int32_t a = g->action[v];
         if (a < 0 || a >= g->infoset_num_actions[g->infoset[par]])
@@ -136,18 +137,20 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
         Lo.kmask.reserve((size_t)ndec); Lo.dnode_user.reserve((size_t)ndec);
         Lo.tnode_user.reserve((size_t)(n - ndec)); Lo.util.reserve((size_t)(n - ndec));
     }
-    order[0] = (int32_t)root;
-    int64_t head = 0, tail = 1;
+    int64_t head = 0, tail = 0;
     int64_t nd_proc = 0, dq = 0, tq = 0;     // decision nodes processed; decision/terminal nodes enqueued
     int32_t Hp = 0;                          // player infosets take internal ids [0, Hp), chance ones [Hp, H)
     for (int32_t h = 0; h < H; ++h) Hp += g->infoset_player[h] > 0;
     int32_t nh = 0, nhc = 0, depth = 0;
-    if (g->infoset[root] >= 0) {
-        dq = 1;
-        if (build) Lo.dnode_user.push_back((int32_t)root);
-    } else {
-        tq = 1;
-        if (build) { Lo.tnode_user.push_back((int32_t)root); Lo.util.push_back(g->utility[2 * root]); }
+    for (int32_t r : roots) {                // depth 0: the roots in id order
+        order[(size_t)tail++] = r;
+        if (g->infoset[r] >= 0) {
+            ++dq;
+            if (build) Lo.dnode_user.push_back(r);
+        } else {
+            ++tq;
+            if (build) { Lo.tnode_user.push_back(r); Lo.util.push_back(g->utility[2 * (size_t)r]); }
+        }
     }
     bool single_level = true;
     while (head < tail) {
@@ -292,21 +295,22 @@ cfr_status build_layout(const cfr_game_desc *g, Layout *out, std::string *err, b
     Lo.hnode.assign((size_t)Lo.Nd, 0);
     std::vector<int32_t> fillp(Lo.hnode_start.begin(), Lo.hnode_start.end() - 1);
     std::vector<std::pair<int32_t, int32_t>> stack;       // (node, next action)
-    if (g->infoset[root] >= 0) stack.emplace_back((int32_t)root, 0);
-    if (!stack.empty()) {
-        const int32_t j0 = dec_of_user[(size_t)root];
+    for (int32_t r : roots) {
+        if (g->infoset[r] < 0) continue;
+        stack.emplace_back(r, 0);
+        const int32_t j0 = dec_of_user[(size_t)r];
         Lo.hnode[(size_t)fillp[(size_t)Lo.dinfo[(size_t)j0]]++] = j0;
-    }
-    while (!stack.empty()) {
-        auto &top = stack.back();
-        const int32_t v = top.first;
-        const int32_t na = g->infoset_num_actions[g->infoset[v]];
-        if (top.second == na) { stack.pop_back(); continue; }
-        const int32_t c = child[(size_t)cstart[v] + top.second++];
-        if (g->infoset[c] < 0) continue;
-        const int32_t jc = dec_of_user[(size_t)c];
-        Lo.hnode[(size_t)fillp[(size_t)Lo.dinfo[(size_t)jc]]++] = jc;
-        stack.emplace_back(c, 0);
+        while (!stack.empty()) {
+            auto &top = stack.back();
+            const int32_t v = top.first;
+            const int32_t na = g->infoset_num_actions[g->infoset[v]];
+            if (top.second == na) { stack.pop_back(); continue; }
+            const int32_t c = child[(size_t)cstart[v] + top.second++];
+            if (g->infoset[c] < 0) continue;
+            const int32_t jc = dec_of_user[(size_t)c];
+            Lo.hnode[(size_t)fillp[(size_t)Lo.dinfo[(size_t)jc]]++] = jc;
+            stack.emplace_back(c, 0);
+        }
     }
     return CFR_OK;
 }

@@ -62,7 +62,10 @@ struct Layout {
 };
 
 // Validates g; if layout != nullptr also builds the layout (with the per-infoset node lists when
-// infoset_lists).  Returns CFR_OK or an error code and writes the reason into *err.
-cfr_status build_layout(const cfr_game_desc *g, Layout *layout, std::string *err, bool infoset_lists = false);
+// infoset_lists).  forest: g may have several roots (independent games side by side, all at depth 0,
+// taken in node-id order; each depth then lists its nodes game by game).  Returns CFR_OK or an error
+// code and writes the reason into *err.
+cfr_status build_layout(const cfr_game_desc *g, Layout *layout, std::string *err, bool infoset_lists = false,
+                        bool forest = false);
 
 }  // namespace cfrgb

@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 
 namespace cfrgb {
+namespace {   // device code: internal to each translation unit that includes it
 
 constexpr int kSBN = 512;                  // nodes per tile
 constexpr int kSBT = 3072;                 // staged terminal-child values per tile
@@ -729,4 +730,5 @@ __global__ void __launch_bounds__(kSBThreads) k_tail_stream(DevTree<float> t, co
 // covers its largest (non-wide) node.
 constexpr int kStreamNA[3] = {3, 5, 8};
 
+}  // namespace
 }  // namespace cfrgb

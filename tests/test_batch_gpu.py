@@ -1,0 +1,119 @@
+"""Batched solving (cfr_batch_*) against the oracle, game by game (GPU tests).
+
+Every game of a batch is an independent CFR run: its first iteration is compared with the oracle's
+under the FP32 budget of paritylib; after more iterations the batched best response is compared with
+the oracle's best response on the batch's own average strategy, and the exploitability with the oracle
+run's.
+"""
+import numpy as np
+import pytest
+
+import gamegen
+import oracle
+import paper_2408_14778_gb300 as cfr
+from paritylib import TOL32, TOL_EXPL, fp32_regret_budget_check, normwise
+
+pytestmark = pytest.mark.gpu
+
+
+def _games(n=12, seed=5, max_nodes=5e3):
+    return gamegen.batch_subgames(n, seed=seed, max_nodes=max_nodes)
+
+
+def _max_depth(g):
+    d = np.full(g.num_nodes, -1)
+    d[g.parent < 0] = 0
+    while (d < 0).any():
+        todo = np.nonzero(d < 0)[0]
+        ok = d[g.parent[todo]] >= 0
+        d[todo[ok]] = d[g.parent[todo[ok]]] + 1
+    return int(d.max())
+
+
+@pytest.mark.parametrize("variant", [cfr.CFR_VANILLA, cfr.CFR_PLUS, cfr.CFR_LINEAR, cfr.CFR_DISCOUNTED])
+def test_first_iteration_matches_oracle(variant):
+    games = _games()
+    b = cfr.cfr_batch_load(games, variant=variant)
+    cfr.cfr_batch_iterate(b, 1)
+    avg = oracle.AVG_UNIFORM if variant == cfr.CFR_VANILLA else oracle.AVG_LINEAR
+    for i, g in enumerate(games):
+        o = oracle.Oracle(g)
+        o.iterate(1, variant=variant, avg=avg, dcfr=(1.5, 0.0, 2.0))
+        gs, os_ = cfr.cfr_batch_get_state(b, i), o.state()
+        assert gs["iteration"] == os_["iteration"] == 1
+        for k in ("cum_regret", "strat_sum"):
+            assert normwise(gs[k], os_[k]) <= TOL32, (i, k)
+        fp32_regret_budget_check(g, gs, os_, _max_depth(g))
+
+
+def test_exploitability_and_convergence_track_the_oracle():
+    games = _games(10, seed=6)
+    b = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS)
+    cfr.cfr_batch_iterate(b, 150)
+    nc = cfr.cfr_batch_exploitability(b)
+    assert nc.shape == (len(games),)
+    for i, g in enumerate(games):
+        o = oracle.Oracle(g)
+        avg = cfr.cfr_batch_average_strategy(b, i)
+        nc_chk, _ = o.exploitability(avg)                 # the oracle's best response on the batch's strategy
+        assert abs(nc_chk - nc[i]) <= TOL_EXPL, (i, nc_chk, nc[i])
+        o.iterate(150, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+        nc_o, _ = o.exploitability()
+        assert nc[i] <= 1.1 * nc_o + 1e-4, (i, nc[i], nc_o)
+
+
+def test_batch_of_one_equals_the_single_game_solver():
+    g = gamegen.public_private(seed=7, num_buckets=3, depth=9, amin=2, amax=4, p_cont=0.7)   # 6-way deal
+    b = cfr.cfr_batch_load([g], variant=cfr.CFR_PLUS)
+    s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, fuse_levels=0)
+    o = oracle.Oracle(g)
+    for T in (1, 2):
+        cfr.cfr_batch_iterate(b, 1)
+        cfr.cfr_iterate(s, 1)
+        o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+        gb, gsn, os_ = cfr.cfr_batch_get_state(b, 0), cfr.cfr_get_state(s), o.state()
+        for k in ("cum_regret", "strat_sum"):
+            assert normwise(gb[k], os_[k]) <= TOL32 and normwise(gsn[k], os_[k]) <= TOL32
+    assert abs(cfr.cfr_batch_exploitability(b)[0] - cfr.cfr_exploitability(s)[0]) <= 1e-5
+
+
+def test_autotune_keeps_the_state_and_caches(tmp_path):
+    games = _games(40, seed=8)
+    b = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS)
+    cfr.cfr_batch_iterate(b, 3)
+    before = [cfr.cfr_batch_get_state(b, i) for i in (0, 17, 39)]
+    cache = str(tmp_path / "tune.json")
+    r = cfr.cfr_batch_autotune(b, trial_iterations=2, cache_path=cache)
+    assert not r["cached"] and r["threads_per_block"] in (128, 256, 512, 1024) and r["us_per_iteration"] > 0
+    after = [cfr.cfr_batch_get_state(b, i) for i in (0, 17, 39)]
+    for x, y in zip(before, after):
+        assert x["iteration"] == y["iteration"] == 3
+        np.testing.assert_array_equal(x["cum_regret"], y["cum_regret"])
+        np.testing.assert_array_equal(x["strat_sum"], y["strat_sum"])
+    info = cfr.cfr_batch_get_info(b)
+    assert info["tuned"] == 1 and info["threads_per_block"] == r["threads_per_block"]
+    b2 = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS)
+    r2 = cfr.cfr_batch_autotune(b2, cache_path=cache)
+    assert r2["cached"] and r2["threads_per_block"] == r["threads_per_block"]
+    cfr.cfr_batch_iterate(b2, 5)
+    t = cfr.cfr_batch_game_times(b2)
+    assert t.shape == (len(games),) and np.all(t > 0)
+    assert cfr.cfr_batch_get_info(b2)["iteration"] == 5
+
+
+def test_unsupported_configurations():
+    games = _games(3, seed=9)
+    for kw in (dict(precision=cfr.CFR_FP64), dict(update_mode=cfr.CFR_ALTERNATING)):
+        cfg = cfr._Config()
+        cfr.lib().cfr_config_init(cfr.ctypes.byref(cfg))
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        descs = [cfr._Desc(g) for g in games]
+        arr = (cfr._GameDesc * len(descs))(*[d.c for d in descs])
+        h = cfr._P()
+        assert cfr.lib().cfr_batch_load(arr, len(descs), cfr.ctypes.byref(cfg), cfr.ctypes.byref(h)) == \
+            cfr.CFR_ERR_UNSUPPORTED
+    wide = gamegen.matrix_game(np.ones((2, 40)))
+    with pytest.raises(cfr.CfrError) as e:
+        cfr.cfr_batch_load([wide])
+    assert e.value.status == cfr.CFR_ERR_UNSUPPORTED
