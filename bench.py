@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-exploitability-1e-3 measurement")
+    ap.add_argument("--batched-games", type=int, default=4096,
+                    help="subgames of the batched measurement (0: skip it)")
     return ap.parse_args()
 
 
@@ -241,6 +243,97 @@ def time_to_exploitability(args, local: int) -> dict:
     return out
 
 
+def batched_measurement(args, local: int) -> dict:
+    out = _batched_run(args, local, gamegen_kw=dict(min_nodes=1e2, max_nodes=1e5),
+                       label="log-uniform 1e2-1e5 nodes, depth 4-10, 2-5 actions")
+    out["small_games"] = _batched_run(args, local, gamegen_kw=dict(min_nodes=1e2, max_nodes=1e3),
+                                      label="log-uniform 1e2-1e3 nodes, depth 4-10, 2-5 actions", ttt=False)
+    return out
+
+
+def _batched_run(args, local: int, gamegen_kw: dict, label: str, ttt: bool = True) -> dict:
+    """Batched CFR+: independent subgames (log-uniform 1e2-1e5 nodes, depth 4-10, 2-5 actions) advanced
+    together by one persistent launch per call, launch shape from the autotuner.  Reports subgames/s and
+    node updates/s for 500 iterations, the p50/p99 per-subgame iteration time, the exploitability reached,
+    the time until every subgame's exploitability is at most 1e-3 (capped), and the same games run as ONE
+    tree (a uniform chance root over them) by the plain full-tree solver on the same GPU."""
+    import numpy as np
+    import torch
+
+    import gamegen
+    import paper_2408_14778_gb300 as cfr
+
+    t0 = time.perf_counter()
+    games = gamegen.batch_subgames(args.batched_games, seed=args.seed, **gamegen_kw)
+    gen_s = time.perf_counter() - t0
+    nodes = np.array([g.num_nodes for g in games], dtype=np.int64)
+    cache = os.path.join(os.path.expanduser("~"), ".cache", "paper_2408_14778_gb300", "batch_tuning.json")
+    t0 = time.perf_counter()
+    tune = cfr.cfr_batch_tune(games, variant=cfr.CFR_PLUS, device=local, cache_path=cache)
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"])
+    cfr.cfr_batch_set_tuning(b, tune["threads_per_block"], tune["blocks_per_sm"])
+    load_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(local)
+    K = 500
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cfr.cfr_batch_iterate(b, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    per_game = cfr.cfr_batch_game_times(b)
+    nc = cfr.cfr_batch_exploitability(b)
+    info = cfr.cfr_batch_get_info(b)
+    out = {"subgames": label, "games": len(games), "nodes_total": int(nodes.sum()), "nodes_min": int(nodes.min()),
+           "nodes_max": int(nodes.max()), "nodes_mean": float(nodes.mean()), "variant": "cfr+ (linear averaging)",
+           "iterations": K, "seconds": sec, "subgames_per_s": len(games) / sec,
+           "node_updates_per_s": float(nodes.sum()) * K / sec,
+           "per_subgame_us_per_iteration": {"p50": float(np.percentile(per_game, 50)),
+                                            "p99": float(np.percentile(per_game, 99)),
+                                            "max": float(per_game.max())},
+           "exploitability_after": {"median": float(np.median(nc) / 2), "max": float(nc.max() / 2)},
+           "tuning": {k: tune[k] for k in ("split_nodes", "threads_per_block", "blocks_per_sm", "cached")},
+           "tuning_trials_us_per_iteration": tune["trials"],
+           "forest_part": {"games": info["forest_games"], "nodes": info["forest_nodes"]},
+           "host_seconds": {"generate": gen_s, "tune": tune_s, "load": load_s}}
+    # time until every subgame's exploitability is at most 1e-3 (evaluations included)
+    if ttt:
+        b2 = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"])
+        cfr.cfr_batch_set_tuning(b2, tune["threads_per_block"], tune["blocks_per_sm"])
+        t0, it, worst = time.perf_counter(), 0, float("inf")
+        while it < 20000 and time.perf_counter() - t0 < 60.0:
+            cfr.cfr_batch_iterate(b2, 100)
+            it += 100
+            worst = float(cfr.cfr_batch_exploitability(b2).max() / 2)
+            if worst <= TTT_TARGET:
+                break
+        out["time_to_exploitability_1e-3_all"] = {"reached": worst <= TTT_TARGET,
+                                                  "seconds": time.perf_counter() - t0, "iterations": it,
+                                                  "worst_exploitability": worst, "check_every": 100}
+        b2.close()
+    b.close()
+    # the plain full-tree solver on the same games as one tree
+    t0 = time.perf_counter()
+    root = gamegen.with_chance_root(games)
+    s = cfr.cfr_load_tree(root, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, device=local)
+    tree_load_s = time.perf_counter() - t0
+    cfr.cfr_iterate(s, 3)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cfr.cfr_iterate(s, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec_tree = e0.elapsed_time(e1) / 1e3
+    out["plain_full_tree_same_games"] = {"seconds": sec_tree, "iterations": K, "nodes": int(root.num_nodes),
+                                         "speedup_of_batched": sec_tree / sec, "host_load_seconds": tree_load_s,
+                                         "note": "the games under one uniform chance root, cfr_load_tree + cfr_iterate"}
+    s.close()
+    return out
+
+
 def cpu_baseline(g, variant: int, seconds: float = 12.0) -> dict:
     import oracle
 
@@ -394,6 +487,9 @@ def run_ours(args, world, rank, local):
     ttt = None
     if rank == 0 and world == 1 and not args.no_ttt:
         ttt = time_to_exploitability(args, local)
+    batched = None
+    if rank == 0 and world == 1 and args.batched_games > 0:
+        batched = batched_measurement(args, local)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -404,6 +500,7 @@ def run_ours(args, world, rank, local):
                 "gpu_launches": launches - launches0, "clocks": clocks,
                 "parallelism": "replicas" if world > 1 else "single GPU"}
         line["time_to_exploitability"] = ttt
+        line["batched"] = batched
         line["phase_us"] = phase_us
         print(json.dumps(line), flush=True)
     del np

@@ -317,3 +317,34 @@ def batch_subgames(count: int, seed: int = 0, min_nodes: float = 1e2, max_nodes:
         g.meta.update(config="batch_subgame", target_nodes=target, batch_index=i)
         out.append(g)
     return out
+
+
+def with_chance_root(games: list) -> GameDesc:
+    """The games under one uniform chance root (one tree): a plain single-tree solver then runs them
+    all at once, each game's regrets scaled by the root's probability (which regret matching ignores)."""
+    k = len(games)
+    sizes = [g.num_nodes for g in games]
+    hs = [g.num_infosets for g in games]
+    N = 1 + sum(sizes)
+    parent = np.empty(N, np.int32)
+    action = np.empty(N, np.int32)
+    infoset = np.empty(N, np.int32)
+    util = np.zeros((N, 2))
+    parent[0], action[0], infoset[0] = -1, -1, 0
+    players, nacts, probs = [np.array([0], np.int8)], [np.array([k], np.int32)], [np.full(k, 1.0 / k)]
+    off, hoff = 1, 1
+    for i, g in enumerate(games):
+        n = g.num_nodes
+        p = g.parent.astype(np.int64)
+        parent[off:off + n] = np.where(p < 0, 0, p + off)
+        action[off:off + n] = np.where(p < 0, i, g.action)
+        infoset[off:off + n] = np.where(g.infoset < 0, -1, g.infoset + hoff)
+        util[off:off + n] = g.utility
+        players.append(g.infoset_player)
+        nacts.append(g.infoset_num_actions)
+        probs.append(g.chance_prob)
+        off += n
+        hoff += g.num_infosets
+    return GameDesc(parent, action, infoset, np.concatenate(players).astype(np.int8),
+                    np.concatenate(nacts).astype(np.int32), np.concatenate(probs), util,
+                    meta=dict(config="chance_root_of_batch", games=k))

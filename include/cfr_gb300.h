@@ -102,6 +102,9 @@ typedef struct {
     double dcfr_alpha;      /* CFR_DISCOUNTED: alpha, beta, gamma (defaults 1.5, 0, 2); finite */
     double dcfr_beta;
     double dcfr_gamma;
+    int64_t batch_split_nodes;  /* cfr_batch_load: games of at least this many nodes run as one forest
+                                   through the per-depth kernels, the rest in the persistent kernel
+                                   (0 = default 16384; negative = all in the persistent kernel) */
 } cfr_config;
 
 /* Sizes and accounting of a loaded solver. */
@@ -229,14 +232,15 @@ const char *cfr_last_error(const cfr_solver *s);
 /* Releases the solver and its device memory (waits for its queued work).  NULL is a no-op. */
 void cfr_free(cfr_solver *s);
 
-/* ---- batched solving (the cfg of many small independent games; no counterpart in the paper) --------
- * Many independent games solved side by side: they are laid out as one forest and every
- * cfr_batch_iterate call advances all of them by n iterations in ONE persistent kernel launch (a
- * CUDA graph of the launch and two bookkeeping nodes).  A thread block takes a game from a work queue
- * (largest games first) and runs its n iterations depth by depth (Section 3.2's steps, as
- * cfr_iterate's kernels compute them per node and infoset), then takes the next game.  FP32 mode with
- * FP64 accumulators, simultaneous updates, at most 32 actions per infoset; every variant.  Game g's
- * arrays use its own caller numbering. */
+/* ---- batched solving (many independent games; no counterpart in the paper) -------------------------
+ * Many independent games solved side by side; every cfr_batch_iterate call advances all of them by n
+ * iterations.  Games below a size split (cfr_config.batch_split_nodes) run in ONE persistent kernel
+ * launch (a CUDA graph of the launch and two bookkeeping nodes): a thread block takes a game from a
+ * work queue (largest first) and runs its n iterations depth by depth (Section 3.2's steps, as
+ * cfr_iterate's kernels compute them per node and infoset), then takes the next game.  The larger
+ * games run as one forest (one root per game) through cfr_iterate's per-depth kernels on a second
+ * stream, concurrently.  FP32 mode with FP64 accumulators, simultaneous updates, at most 32 actions per
+ * infoset in the persistent part; every variant.  Game g's arrays use its own caller numbering. */
 typedef struct cfr_batch cfr_batch;   /* opaque; owned by the library */
 
 typedef struct {
@@ -252,6 +256,9 @@ typedef struct {
     int32_t threads_per_block, blocks_per_sm, grid;   /* the launch shape in use */
     int32_t tuned;              /* 1 once set by cfr_batch_set_tuning or cfr_batch_autotune */
     int64_t kernel_launches;    /* kernels launched by cfr_batch_iterate so far */
+    int32_t forest_games;       /* games at or above the size split, run as one forest */
+    int64_t forest_nodes;
+    int64_t split_nodes;
 } cfr_batch_info;
 
 /* Validates and lays out num_games >= 1 games (each as cfr_load_tree would; the combined size must stay

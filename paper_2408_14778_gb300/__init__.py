@@ -70,6 +70,7 @@ class _Config(ctypes.Structure):
         ("dcfr_alpha", ctypes.c_double),
         ("dcfr_beta", ctypes.c_double),
         ("dcfr_gamma", ctypes.c_double),
+        ("batch_split_nodes", ctypes.c_int64),
     ]
 
 
@@ -94,7 +95,8 @@ class _BatchInfo(ctypes.Structure):
         ("num_games", ctypes.c_int32), ("num_nodes", ctypes.c_int64), ("num_decision", ctypes.c_int64),
         ("num_q", ctypes.c_int64), ("iteration", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
         ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
-        ("tuned", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+        ("tuned", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("forest_games", ctypes.c_int32),
+        ("forest_nodes", ctypes.c_int64), ("split_nodes", ctypes.c_int64),
     ]
 
 
@@ -425,8 +427,9 @@ class Batch:
 
 
 def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=None, stream=None,
-                   allocator: str = "torch", dcfr=(1.5, 0.0, 2.0)) -> Batch:
-    """Loads a list of games for batched solving (FP32 mode, simultaneous updates)."""
+                   allocator: str = "torch", dcfr=(1.5, 0.0, 2.0), split_nodes: int = 0) -> Batch:
+    """Loads a list of games for batched solving (FP32 mode, simultaneous updates).  split_nodes:
+    cfr_config.batch_split_nodes (0 default, negative: every game in the persistent kernel)."""
     import torch
 
     if not torch.cuda.is_available():
@@ -438,6 +441,7 @@ def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=N
     cfg.variant, cfg.precision, cfg.avg_weight = variant, CFR_FP32, avg_weight
     cfg.device, cfg.cuda_stream = dev, st_handle
     cfg.dcfr_alpha, cfg.dcfr_beta, cfg.dcfr_gamma = (float(x) for x in dcfr)
+    cfg.batch_split_nodes = int(split_nodes)
     alloc = None
     if allocator == "torch":
         alloc = _TorchAllocator(dev, st_handle)
@@ -541,3 +545,56 @@ def cfr_batch_get_info(b: Batch) -> dict:
     d = {name: getattr(info, name) for name, _ in _BatchInfo._fields_}
     d["variant"] = getattr(b, "_variant", None)
     return d
+
+
+def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 4096, 16384, 65536, -1), trial_iterations: int = 10,
+                   device=None, cache_path: str | None = None, dcfr=(1.5, 0.0, 2.0)) -> dict:
+    """The batch's size split (which games run as one forest through the per-depth kernels, which in the
+    persistent kernel) and the persistent launch shape: for each candidate split the batch is loaded,
+    the launch shape measured (cfr_batch_autotune), and trial_iterations timed; the fastest is kept and
+    cached per GPU and size bucket (in memory, and in the JSON file cache_path when given).  split 1 runs
+    every game as one forest, -1 every game in the persistent kernel.  Returns {split_nodes,
+    threads_per_block, blocks_per_sm, us_per_iteration (None if cached), cached, trials}."""
+    import json
+
+    import torch
+
+    probe = Batch(None, None, games)
+    key = f"{torch.cuda.get_device_name()}|{_size_bucket(probe)}|variant={int(variant)}|split"
+    disk = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            disk = json.load(open(cache_path))
+        except (OSError, ValueError):
+            disk = {}
+    hit = _TUNE_CACHE.get(key) or disk.get(key)
+    if hit:
+        return dict(hit, us_per_iteration=None, cached=True, trials=None, key=key)
+    trials = []
+    for split in splits:
+        b = cfr_batch_load(games, variant=variant, device=device, dcfr=dcfr, split_nodes=split)
+        t = _BatchTuning()                               # measured for this split (no cache lookup)
+        _check_batch(lib().cfr_batch_autotune(b.handle, 2, ctypes.byref(t), None), b.handle)
+        shape = {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm}
+        cfr_batch_iterate(b, 2)                       # warm-up (graph capture)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cfr_batch_iterate(b, trial_iterations)
+        e1.record()
+        torch.cuda.synchronize()
+        us = 1e3 * e0.elapsed_time(e1) / trial_iterations
+        trials.append({"split_nodes": split, "threads_per_block": shape["threads_per_block"],
+                       "blocks_per_sm": shape["blocks_per_sm"], "us_per_iteration": us})
+        b.close()
+    best = min(trials, key=lambda r: r["us_per_iteration"])
+    rec = {k: best[k] for k in ("split_nodes", "threads_per_block", "blocks_per_sm")}
+    _TUNE_CACHE[key] = rec
+    if cache_path:
+        disk[key] = rec
+        os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(disk, f, indent=1)
+        os.replace(tmp, cache_path)
+    return dict(rec, us_per_iteration=best["us_per_iteration"], cached=False, trials=trials, key=key)

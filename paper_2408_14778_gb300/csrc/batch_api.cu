@@ -1,6 +1,7 @@
-// C ABI of batched solving (include/cfr_gb300.h, cfr_batch_*): many independent games laid out as one
-// forest and advanced together by one persistent launch per call (batch.cuh), with the launch shape
-// picked by a measured sweep (cfr_batch_autotune).
+// C ABI of batched solving (include/cfr_gb300.h, cfr_batch_*): many independent games advanced together.
+// Games below a size split run in one persistent launch per call (batch.cuh), its shape picked by a
+// measured sweep (cfr_batch_autotune); the larger ones as one forest through the single-game solver's
+// per-depth kernels on a second stream, concurrently.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,12 +16,15 @@
 #include "batch.cuh"
 #include "cfr_gb300.h"
 #include "layout.hpp"
+#include "solver_internal.hpp"
 
 using namespace cfrgb;
 
 namespace {
 
 thread_local std::string g_batch_err;
+
+constexpr int64_t kBatchSplitDefault = 16384;   // games of at least this many nodes run as one forest
 
 struct BDeviceGuard {
     int prev = -1;
@@ -42,7 +46,20 @@ struct cfr_batch {
     int device = 0, sms = 0;
     cudaStream_t stream = nullptr;   // borrowed
     cudaStream_t cap = nullptr;      // private, for graph capture
-    int32_t G = 0, stride = 0, Hp = 0, H = 0, hp_na = 0;
+    // The games split by size: the small ones run in the persistent kernel (the fields below), those of
+    // at least split_nodes nodes as one forest through the single-game solver's per-depth kernels
+    // (`big`, on `side`), concurrently.
+    int32_t n_games = 0;
+    int64_t split_nodes = 0;
+    std::vector<int8_t> part;            // per game: 0 persistent, 1 forest
+    std::vector<int32_t> idx;            // per game: its index within its part
+    std::vector<int64_t> big_q_off;      // forest part: per game, its first slot in the forest's numbering
+    std::vector<int64_t> big_nodes;
+    cfr_solver *big = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_b0 = nullptr, ev_b1 = nullptr;
+    bool big_timed = false;
+    int32_t G = 0, stride = 0, Hp = 0, H = 0, hp_na = 0;   // the persistent part
     int64_t N = 0, Nd = 0, Nt = 0, Q = 0;
     bool single_level = true;
     // host: per game, its first node / infoset / infoset-action slot in the caller's numbering (+ total)
@@ -223,6 +240,8 @@ cfr_status build_batch_graph(cfr_batch *b, int32_t K) {
     return CFR_OK;
 }
 
+cfr_status small_exploitability(cfr_batch *b, double *nash_conv);
+
 cfr_status bsync(cfr_batch *b) {
     BCK(cudaStreamSynchronize(b->stream));
     return CFR_OK;
@@ -401,12 +420,66 @@ cfr_status cfr_batch_load(const cfr_game_desc *games, int32_t num_games, const c
 
     std::unique_ptr<cfr_batch> b(new cfr_batch());
     b->cfg = cfg;
-    b->G = num_games;
+    b->n_games = num_games;
+    b->split_nodes = cfg.batch_split_nodes == 0 ? kBatchSplitDefault : cfg.batch_split_nodes;
+    std::vector<cfr_game_desc> small, large;
+    b->part.assign((size_t)num_games, 0);
+    b->idx.assign((size_t)num_games, 0);
+    for (int32_t i = 0; i < num_games; ++i) {
+        const bool big = b->split_nodes > 0 && games[i].num_nodes >= b->split_nodes;
+        b->part[(size_t)i] = big;
+        b->idx[(size_t)i] = (int32_t)(big ? large.size() : small.size());
+        (big ? large : small).push_back(games[i]);
+    }
+    b->G = (int32_t)small.size();
     std::vector<int32_t> parent, action, infoset, nact;
     std::vector<int8_t> player;
     std::vector<double> cprob, util;
-    cfr_status st = combine(games, num_games, b.get(), parent, action, infoset, player, nact, cprob, util);
-    if (st != CFR_OK) return st;
+    cfr_status st = CFR_OK;
+    if (!large.empty()) {
+        // the forest part: the large games combined in order, loaded by the single-game solver
+        cfr_batch tmp;
+        st = combine(large.data(), (int32_t)large.size(), &tmp, parent, action, infoset, player, nact, cprob, util);
+        if (st != CFR_OK) return st;
+        b->big_q_off = tmp.q_off;
+        b->big_nodes = tmp.game_nodes;
+        cfr_game_desc all{};
+        all.num_nodes = tmp.node_off.back();
+        all.parent = parent.data(); all.action = action.data(); all.infoset = infoset.data();
+        all.num_infosets = (int32_t)tmp.h_off.back();
+        all.infoset_player = player.data(); all.infoset_num_actions = nact.data();
+        all.chance_prob = cprob.data(); all.num_chance_prob = (int64_t)cprob.size(); all.utility = util.data();
+        BDeviceGuard dg0(cfg.device);
+        if (!dg0.ok) return berr(nullptr, CFR_ERR_CUDA, "cannot select CUDA device %d", cfg.device);
+        cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+        for (cudaEvent_t *ev : {&b->ev_fork, &b->ev_join})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        for (cudaEvent_t *ev : {&b->ev_b0, &b->ev_b1})
+            if (e == cudaSuccess) e = cudaEventCreate(ev);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cfr_batch_free(b.release());
+            return berr(nullptr, CFR_ERR_CUDA, "stream/event creation: %s", cudaGetErrorString(e));
+        }
+        cfr_config fc = cfg;
+        fc.cuda_stream = b->side;
+        st = cfrgb::load_tree_impl(&all, &fc, true, &b->big);
+        if (st != CFR_OK) {
+            std::string msg = cfr_last_error(nullptr);
+            cfr_batch_free(b.release());
+            return berr(nullptr, st, "%s", msg.c_str());
+        }
+        parent.clear(); action.clear(); infoset.clear(); player.clear(); nact.clear(); cprob.clear(); util.clear();
+    }
+    if (b->G == 0) {
+        BDeviceGuard dg1(cfg.device);
+        cudaGetDevice(&b->device);
+        b->stream = static_cast<cudaStream_t>(cfg.cuda_stream);
+        *out = b.release();
+        return CFR_OK;
+    }
+    st = combine(small.data(), b->G, b.get(), parent, action, infoset, player, nact, cprob, util);
+    if (st != CFR_OK) { cfr_batch_free(b.release()); return st; }
     cfr_game_desc all{};
     all.num_nodes = b->node_off.back();
     all.parent = parent.data(); all.action = action.data(); all.infoset = infoset.data();
@@ -416,17 +489,18 @@ cfr_status cfr_batch_load(const cfr_game_desc *games, int32_t num_games, const c
     std::unique_ptr<Layout> Lo(new Layout());
     std::string err;
     st = build_layout(&all, Lo.get(), &err, false, true);
-    if (st != CFR_OK) return berr(nullptr, st, "%s", err.c_str());
+    if (st != CFR_OK) { cfr_batch_free(b.release()); return berr(nullptr, st, "%s", err.c_str()); }
     parent.clear(); parent.shrink_to_fit(); action.clear(); action.shrink_to_fit();
     infoset.clear(); infoset.shrink_to_fit(); util.clear(); util.shrink_to_fit();
 
     BDeviceGuard dg(cfg.device);
-    if (!dg.ok) return berr(nullptr, CFR_ERR_CUDA, "cannot select CUDA device %d", cfg.device);
+    if (!dg.ok) { cfr_batch_free(b.release()); return berr(nullptr, CFR_ERR_CUDA, "cannot select CUDA device %d", cfg.device); }
     cudaGetDevice(&b->device);
     b->stream = static_cast<cudaStream_t>(cfg.cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        cfr_batch_free(b.release());
         return berr(nullptr, CFR_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
     }
     st = load_batch(b.get(), *Lo);
@@ -444,10 +518,22 @@ cfr_status cfr_batch_iterate(cfr_batch *b, int32_t n) {
     if (n < 0) return berr(b, CFR_ERR_INVALID, "n must be >= 0");
     if (n == 0) return CFR_OK;
     BDeviceGuard dg(b->device);
-    if (!b->graph_exec || b->graph_K != n) BTRY(build_batch_graph(b, n));
-    BCK(cudaGraphLaunch(b->graph_exec, b->stream));
+    if (b->big) {                                      // the forest part, on its stream, after earlier work
+        BCK(cudaEventRecord(b->ev_fork, b->stream));
+        BCK(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+        BCK(cudaEventRecord(b->ev_b0, b->side));
+        if (cfr_iterate(b->big, n) != CFR_OK) return berr(b, CFR_ERR_CUDA, "forest part: %s", cfr_last_error(b->big));
+        BCK(cudaEventRecord(b->ev_b1, b->side));
+        BCK(cudaEventRecord(b->ev_join, b->side));
+        b->big_timed = true;
+    }
+    if (b->G > 0) {
+        if (!b->graph_exec || b->graph_K != n) BTRY(build_batch_graph(b, n));
+        BCK(cudaGraphLaunch(b->graph_exec, b->stream));
+        b->kernel_launches += 2;
+    }
+    if (b->big) BCK(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
     b->iteration += n;
-    b->kernel_launches += 2;
     b->last_K = n;
     return CFR_OK;
 }
@@ -457,7 +543,7 @@ cfr_status cfr_batch_set_tuning(cfr_batch *b, const cfr_batch_tuning *t) {
     if (!t || t->threads_per_block < 32 || t->threads_per_block > 1024 || t->threads_per_block % 32 || t->blocks_per_sm < 0)
         return berr(b, CFR_ERR_INVALID, "threads_per_block must be a multiple of 32 in [32, 1024], blocks_per_sm >= 0");
     BDeviceGuard dg(b->device);
-    if (occupancy(b, t->threads_per_block) < 1) return berr(b, CFR_ERR_INVALID, "no block of %d threads fits an SM", t->threads_per_block);
+    if (b->G > 0 && occupancy(b, t->threads_per_block) < 1) return berr(b, CFR_ERR_INVALID, "no block of %d threads fits an SM", t->threads_per_block);
     b->threads = t->threads_per_block;
     b->blocks_per_sm = t->blocks_per_sm;
     b->tuned = true;
@@ -468,6 +554,11 @@ cfr_status cfr_batch_set_tuning(cfr_batch *b, const cfr_batch_tuning *t) {
 cfr_status cfr_batch_autotune(cfr_batch *b, int32_t trial_iterations, cfr_batch_tuning *chosen, double *best_us) {
     BTRY(busable(b));
     if (trial_iterations < 1) return berr(b, CFR_ERR_INVALID, "trial_iterations must be >= 1");
+    if (b->G == 0) {                                   // only the forest part: nothing to tune
+        if (chosen) { chosen->threads_per_block = b->threads; chosen->blocks_per_sm = b->blocks_per_sm; }
+        if (best_us) *best_us = 0.0;
+        return CFR_OK;
+    }
     BDeviceGuard dg(b->device);
     // the trials run real iterations on a snapshot of the state, restored afterwards
     if (!b->snapR) {
@@ -519,23 +610,51 @@ cfr_status cfr_batch_autotune(cfr_batch *b, int32_t trial_iterations, cfr_batch_
 
 cfr_status cfr_batch_game_times(cfr_batch *b, double *us_per_iteration, int32_t len) {
     BTRY(busable(b));
-    if (!us_per_iteration || len < b->G) return berr(b, CFR_ERR_INVALID, "output needs %d entries", b->G);
+    if (!us_per_iteration || len < b->n_games) return berr(b, CFR_ERR_INVALID, "output needs %d entries", b->n_games);
     if (b->last_K <= 0) return berr(b, CFR_ERR_STATE, "no cfr_batch_iterate call yet");
     BDeviceGuard dg(b->device);
     BTRY(bsync(b));
-    std::vector<unsigned long long> t0((size_t)b->G), t1((size_t)b->G);
-    BCK(cudaMemcpy(t0.data(), b->t_start, sizeof(unsigned long long) * (size_t)b->G, cudaMemcpyDeviceToHost));
-    BCK(cudaMemcpy(t1.data(), b->t_end, sizeof(unsigned long long) * (size_t)b->G, cudaMemcpyDeviceToHost));
-    for (int32_t g = 0; g < b->G; ++g) us_per_iteration[g] = (double)(t1[(size_t)g] - t0[(size_t)g]) * 1e-3 / b->last_K;
+    std::vector<unsigned long long> t0((size_t)std::max(b->G, 1)), t1((size_t)std::max(b->G, 1));
+    if (b->G > 0) {
+        BCK(cudaMemcpy(t0.data(), b->t_start, sizeof(unsigned long long) * (size_t)b->G, cudaMemcpyDeviceToHost));
+        BCK(cudaMemcpy(t1.data(), b->t_end, sizeof(unsigned long long) * (size_t)b->G, cudaMemcpyDeviceToHost));
+    }
+    float big_ms = 0.f;
+    if (b->big && b->big_timed) BCK(cudaEventElapsedTime(&big_ms, b->ev_b0, b->ev_b1));
+    for (int32_t g = 0; g < b->n_games; ++g) {
+        const size_t k = (size_t)b->idx[(size_t)g];
+        us_per_iteration[g] = b->part[(size_t)g] ? 1e3 * (double)big_ms / b->last_K     // the forest advances together
+                                                 : (double)(t1[k] - t0[k]) * 1e-3 / b->last_K;
+    }
     return CFR_OK;
 }
 
 cfr_status cfr_batch_exploitability(cfr_batch *b, double *nash_conv, int32_t len) {
     BTRY(busable(b));
-    if (!nash_conv || len < b->G) return berr(b, CFR_ERR_INVALID, "output needs %d entries", b->G);
+    if (!nash_conv || len < b->n_games) return berr(b, CFR_ERR_INVALID, "output needs %d entries", b->n_games);
     if (!b->single_level)
         return berr(b, CFR_ERR_UNSUPPORTED, "the GPU best response needs every infoset at a single depth");
     BDeviceGuard dg(b->device);
+    std::vector<double> big_nc(b->big_nodes.size());
+    if (b->big) {
+        BTRY(bsync(b));
+        if (cfrgb::root_nash_conv(b->big, big_nc.data(), (int32_t)big_nc.size()) != CFR_OK)
+            return berr(b, CFR_ERR_CUDA, "forest part: %s", cfr_last_error(b->big));
+    }
+    std::vector<double> small_nc((size_t)b->G);
+    BTRY(small_exploitability(b, small_nc.data()));
+    for (int32_t g = 0; g < b->n_games; ++g)
+        nash_conv[g] = b->part[(size_t)g] ? big_nc[(size_t)b->idx[(size_t)g]] : small_nc[(size_t)b->idx[(size_t)g]];
+    return CFR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// NashConv of every game of the persistent part.
+cfr_status small_exploitability(cfr_batch *b, double *nash_conv) {
+    if (b->G == 0) return CFR_OK;
     if (!b->avg) {
         BTRY(balloc(b, &b->avg, b->Q)); BTRY(balloc(b, &b->cfv, b->Q)); BTRY(balloc(b, &b->preach, b->Nd));
         BTRY(balloc(b, &b->val, b->Nd)); BTRY(balloc(b, &b->astar, b->H)); BTRY(balloc(b, &b->br_out, 2 * (int64_t)b->G));
@@ -560,9 +679,13 @@ cfr_status cfr_batch_exploitability(cfr_batch *b, double *nash_conv, int32_t len
     return CFR_OK;
 }
 
-// Per game: R and S (and the average strategy) in the game's own infoset-major order.
-static cfr_status game_slots(cfr_batch *b, int32_t game, const double *dev, double *out, int64_t len) {
-    if (game < 0 || game >= b->G) return berr(b, CFR_ERR_INVALID, "game %d out of range", game);
+}  // namespace
+
+extern "C" {
+
+// Per game of the persistent part: R and S (and the average strategy) in the game's own infoset-major
+// order.
+static cfr_status small_slots(cfr_batch *b, int32_t game, const double *dev, double *out, int64_t len) {
     const int64_t q0 = b->q_off[(size_t)game], q1 = b->q_off[(size_t)game + 1];
     if (!out || len < q1 - q0) return berr(b, CFR_ERR_INVALID, "output needs %lld entries", (long long)(q1 - q0));
     std::vector<double> all((size_t)std::max<int64_t>(b->Q, 1));
@@ -574,43 +697,77 @@ static cfr_status game_slots(cfr_batch *b, int32_t game, const double *dev, doub
     return CFR_OK;
 }
 
+// A forest-part game's slice of a whole-forest array (the forest's own caller numbering).
+static cfr_status big_slice(cfr_batch *b, int32_t k, const std::vector<double> &all, double *out, int64_t len) {
+    const int64_t q0 = b->big_q_off[(size_t)k], q1 = b->big_q_off[(size_t)k + 1];
+    if (!out || len < q1 - q0) return berr(b, CFR_ERR_INVALID, "output needs %lld entries", (long long)(q1 - q0));
+    std::copy(all.begin() + q0, all.begin() + q1, out);
+    return CFR_OK;
+}
+
 cfr_status cfr_batch_get_state(cfr_batch *b, int32_t game, double *cum_regret, double *strat_sum, int64_t len,
                                int64_t *iteration) {
     BTRY(busable(b));
+    if (game < 0 || game >= b->n_games) return berr(b, CFR_ERR_INVALID, "game %d out of range", game);
     BDeviceGuard dg(b->device);
     BTRY(bsync(b));
-    if (cum_regret) BTRY(game_slots(b, game, b->R, cum_regret, len));
-    if (strat_sum) BTRY(game_slots(b, game, b->S, strat_sum, len));
+    const int32_t k = b->idx[(size_t)game];
+    if (b->part[(size_t)game]) {
+        const int64_t Qb = b->big_q_off.back();
+        std::vector<double> R((size_t)std::max<int64_t>(Qb, 1)), S((size_t)std::max<int64_t>(Qb, 1));
+        if (cfr_get_state(b->big, R.data(), S.data(), nullptr, std::max<int64_t>(Qb, 1), nullptr, 0, nullptr) != CFR_OK)
+            return berr(b, CFR_ERR_CUDA, "forest part: %s", cfr_last_error(b->big));
+        if (cum_regret) BTRY(big_slice(b, k, R, cum_regret, len));
+        if (strat_sum) BTRY(big_slice(b, k, S, strat_sum, len));
+    } else {
+        if (cum_regret) BTRY(small_slots(b, k, b->R, cum_regret, len));
+        if (strat_sum) BTRY(small_slots(b, k, b->S, strat_sum, len));
+    }
     if (iteration) *iteration = b->iteration;
     return CFR_OK;
 }
 
 cfr_status cfr_batch_average_strategy(cfr_batch *b, int32_t game, double *out, int64_t len) {
     BTRY(busable(b));
+    if (game < 0 || game >= b->n_games) return berr(b, CFR_ERR_INVALID, "game %d out of range", game);
     BDeviceGuard dg(b->device);
+    BTRY(bsync(b));
+    const int32_t k = b->idx[(size_t)game];
+    if (b->part[(size_t)game]) {
+        const int64_t Qb = b->big_q_off.back();
+        std::vector<double> A((size_t)std::max<int64_t>(Qb, 1));
+        if (cfr_average_strategy(b->big, A.data(), std::max<int64_t>(Qb, 1)) != CFR_OK)
+            return berr(b, CFR_ERR_CUDA, "forest part: %s", cfr_last_error(b->big));
+        return big_slice(b, k, A, out, len);
+    }
     if (!b->avg) BTRY(balloc(b, &b->avg, b->Q));
     if (b->H > 0) {
         k_average<<<(b->H + 255) / 256, 256, 0, b->stream>>>(b->S, b->sigma064, b->qbase, b->iplayer, b->avg, b->H);
         BCK(cudaGetLastError());
     }
     BTRY(bsync(b));
-    return game_slots(b, game, b->avg, out, len);
+    return small_slots(b, k, b->avg, out, len);
 }
 
 cfr_status cfr_batch_get_info(const cfr_batch *b, cfr_batch_info *info) {
     if (!b || !info) return berr(nullptr, CFR_ERR_INVALID, "batch or info is NULL");
     std::memset(info, 0, sizeof *info);
-    info->num_games = b->G;
-    info->num_nodes = b->N;
-    info->num_decision = b->Nd;
-    info->num_q = b->Q;
+    info->num_games = b->n_games;
+    cfr_info fi{};
+    if (b->big) cfr_get_info(b->big, &fi);
+    info->num_nodes = b->N + fi.num_nodes;
+    info->num_decision = b->Nd + fi.num_decision;
+    info->num_q = b->Q + fi.num_q;
+    info->forest_games = (int32_t)b->big_nodes.size();
+    info->forest_nodes = fi.num_nodes;
+    info->split_nodes = b->split_nodes;
+    info->device_bytes = b->device_bytes + fi.device_bytes;
     info->iteration = b->iteration;
-    info->device_bytes = b->device_bytes;
     info->threads_per_block = b->threads;
     info->blocks_per_sm = b->blocks_per_sm;
-    info->grid = grid_of(b, b->threads, b->blocks_per_sm);
+    info->grid = b->G > 0 ? grid_of(b, b->threads, b->blocks_per_sm) : 0;
     info->tuned = b->tuned;
-    info->kernel_launches = b->kernel_launches;
+    info->kernel_launches = b->kernel_launches + fi.kernel_launches;
     return CFR_OK;
 }
 
@@ -621,11 +778,16 @@ void cfr_batch_free(cfr_batch *b) {
     BDeviceGuard dg(b->device);
     if (b->stream || b->cap) cudaStreamSynchronize(b->stream);
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->side) cudaStreamSynchronize(b->side);
+    if (b->big) cfr_free(b->big);
     for (void *p : b->blocks) {
         if (b->cfg.dev_free) b->cfg.dev_free(p, b->cfg.alloc_ctx);
         else cudaFree(p);
     }
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->side) cudaStreamDestroy(b->side);
+    for (cudaEvent_t ev : {b->ev_fork, b->ev_join, b->ev_b0, b->ev_b1})
+        if (ev) cudaEventDestroy(ev);
     delete b;
 }
 

@@ -15,6 +15,7 @@
 #include "cfr_gb300.h"
 #include "kernels.cuh"
 #include "layout.hpp"
+#include "solver_internal.hpp"
 #include "stream.cuh"
 
 using namespace cfrgb;
@@ -747,13 +748,16 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
             s->level_na[(size_t)l] = maxa <= kStreamNA[0] ? 0 : maxa <= kStreamNA[1] ? 1 : 2;
         }
     }
-    // The root's counterfactual reaches are 1 (Eq. 2, v = v_0) and never change.
+    // The root's counterfactual reaches are 1 (Eq. 2, v = v_0) and never change (every root's, for a
+    // forest of independent games).
     if (s->Nd > 0) {
-        const double one64 = 1.0;
-        const float one32 = 1.0f;
-        const void *one = fp64 ? (const void *)&one64 : (const void *)&one32;
-        CK(cudaMemcpyAsync(s->reach1, one, rs, cudaMemcpyHostToDevice, s->stream));
-        CK(cudaMemcpyAsync(s->reach2, one, rs, cudaMemcpyHostToDevice, s->stream));
+        const size_t nroots = (size_t)s->dlevel[1];
+        std::vector<double> one64(nroots, 1.0);
+        std::vector<float> one32(nroots, 1.0f);
+        const void *one = fp64 ? (const void *)one64.data() : (const void *)one32.data();
+        CK(cudaMemcpyAsync(s->reach1, one, rs * nroots, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->reach2, one, rs * nroots, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
     }
     if (s->H > 0) {
         if (fp64) regret_match_all<double>(s); else regret_match_all<float>(s);
@@ -786,8 +790,8 @@ cfr_status best_response(cfr_solver *s, int player, double *value) {
     b.util = s->util64; b.qbase = s->qbase; b.iplayer = s->iplayer; b.avg = s->avg;
     b.preach = s->br_reach; b.val = s->br_val; b.cfv = s->br_cfv; b.astar = s->astar;
     cudaStream_t st = s->stream;
-    const double one = 1.0;
-    CK(cudaMemcpyAsync(s->br_reach, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    const std::vector<double> ones((size_t)s->dlevel[1], 1.0);     // the root (every root of a forest)
+    CK(cudaMemcpyAsync(s->br_reach, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s->br_cfv, 0, sizeof(double) * (size_t)std::max<int64_t>(s->Q, 1), st));
     for (int32_t l = 0; l + 1 < s->L; ++l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
@@ -827,6 +831,7 @@ void cfr_config_init(cfr_config *c) {
     c->dcfr_alpha = 1.5;
     c->dcfr_beta = 0.0;
     c->dcfr_gamma = 2.0;
+    c->batch_split_nodes = 0;
 }
 
 cfr_status cfr_validate(const cfr_game_desc *g, char *msg, size_t msg_len) {
@@ -838,6 +843,13 @@ cfr_status cfr_validate(const cfr_game_desc *g, char *msg, size_t msg_len) {
 }
 
 cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver **out) {
+    return cfrgb::load_tree_impl(g, c, false, out);
+}
+
+}  // extern "C"
+
+// cfr_load_tree, or (forest) several independent games side by side: one root per game at depth 0.
+cfr_status cfrgb::load_tree_impl(const cfr_game_desc *g, const cfr_config *c, bool forest, cfr_solver **out) {
     if (!out) return set_err(nullptr, CFR_ERR_INVALID, "out is NULL");
     *out = nullptr;
     cfr_config cfg;
@@ -859,7 +871,7 @@ cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver
 
     std::unique_ptr<Layout> Lo(new Layout());
     std::string err;
-    cfr_status st = build_layout(g, Lo.get(), &err, cfg.precision == CFR_FP64);
+    cfr_status st = build_layout(g, Lo.get(), &err, cfg.precision == CFR_FP64, forest);
     if (st != CFR_OK) return set_err(nullptr, st, "%s", err.c_str());
 
     DeviceGuard dg(cfg.device);
@@ -889,6 +901,39 @@ cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver
     *out = s.release();
     return CFR_OK;
 }
+
+// NashConv of every root's game (a forest; single-depth infosets): both best responses, each root's
+// value read after each.  per_root[k] for the k-th decision root (decision nodes of depth 0 in order).
+cfr_status cfrgb::root_nash_conv(cfr_solver *s, double *per_root, int32_t n) {
+    TRY(check_usable(s));
+    if (!s->single_level)
+        return set_err(s, CFR_ERR_UNSUPPORTED, "the GPU best response needs every infoset at a single depth");
+    if (s->Nd == 0 || n < s->dlevel[1]) return set_err(s, CFR_ERR_INVALID, "need %d root entries", s->Nd ? s->dlevel[1] : 0);
+    DeviceGuard dg(s->device);
+    const int32_t nr = s->dlevel[1];
+    if (!s->avg) TRY(alloc_n(s, &s->avg, s->Q));
+    if (!s->br_reach) {
+        TRY(alloc_n(s, &s->br_reach, s->Nd));
+        TRY(alloc_n(s, &s->br_val, s->Nd));
+        TRY(alloc_n(s, &s->br_cfv, s->Q));
+        TRY(alloc_n(s, &s->astar, s->H));
+    }
+    if (s->H > 0) {
+        k_average<<<nblocks(s->H), kBlock, 0, s->stream>>>(s->S, s->sigma064, s->qbase, s->iplayer, s->avg, s->H);
+        CK_LAUNCH();
+    }
+    std::vector<double> v((size_t)nr);
+    for (int32_t k = 0; k < nr; ++k) per_root[k] = 0.0;
+    for (int player = 1; player <= 2; ++player) {
+        double dummy = 0.0;
+        TRY(best_response(s, player, &dummy));
+        CK(cudaMemcpy(v.data(), s->br_val, sizeof(double) * nr, cudaMemcpyDeviceToHost));
+        for (int32_t k = 0; k < nr; ++k) per_root[k] += v[(size_t)k];
+    }
+    return CFR_OK;
+}
+
+extern "C" {
 
 cfr_status cfr_iterate(cfr_solver *s, int32_t n) {
     TRY(check_usable(s));

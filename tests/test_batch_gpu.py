@@ -117,3 +117,29 @@ def test_unsupported_configurations():
     with pytest.raises(cfr.CfrError) as e:
         cfr.cfr_batch_load([wide])
     assert e.value.status == cfr.CFR_ERR_UNSUPPORTED
+
+
+def test_size_split_runs_both_parts_like_the_oracle():
+    # games of >= 1500 nodes go to the forest part, the rest to the persistent kernel
+    games = gamegen.batch_subgames(14, seed=10, max_nodes=2e4)
+    sizes = np.array([g.num_nodes for g in games])
+    assert (sizes >= 1500).any() and (sizes < 1500).any()
+    b = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, split_nodes=1500)
+    info = cfr.cfr_batch_get_info(b)
+    assert info["forest_games"] == int((sizes >= 1500).sum()) and info["num_games"] == len(games)
+    cfr.cfr_batch_iterate(b, 1)
+    for i, g in enumerate(games):
+        o = oracle.Oracle(g)
+        o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+        gs, os_ = cfr.cfr_batch_get_state(b, i), o.state()
+        for k in ("cum_regret", "strat_sum"):
+            assert normwise(gs[k], os_[k]) <= TOL32, (i, k)
+        fp32_regret_budget_check(g, gs, os_, _max_depth(g))
+    cfr.cfr_batch_iterate(b, 60)
+    nc = cfr.cfr_batch_exploitability(b)
+    for i, g in enumerate(games):
+        nc_chk, _ = oracle.Oracle(g).exploitability(cfr.cfr_batch_average_strategy(b, i))
+        assert abs(nc_chk - nc[i]) <= TOL_EXPL, (i, nc_chk, nc[i])
+    t = cfr.cfr_batch_game_times(b)
+    assert np.all(t > 0)
+    assert len(set(np.round(t[sizes >= 1500], 6))) == 1          # the forest part advances together
