@@ -234,17 +234,19 @@ void cfr_free(cfr_solver *s);
 
 /* ---- batched solving (many independent games; no counterpart in the paper) -------------------------
  * Many independent games solved side by side; every cfr_batch_iterate call advances all of them by n
- * iterations.  Games below a size split (cfr_config.batch_split_nodes) run in ONE persistent kernel
- * launch (a CUDA graph of the launch and two bookkeeping nodes): a thread block takes a game from a
- * work queue (largest first) and runs its n iterations depth by depth (Section 3.2's steps, as
- * cfr_iterate's kernels compute them per node and infoset), then takes the next game.  The larger
- * games run as one forest (one root per game) through cfr_iterate's per-depth kernels on a second
- * stream, concurrently.  FP32 mode with FP64 accumulators, simultaneous updates, at most 32 actions per
- * infoset in the persistent part; every variant.  Game g's arrays use its own caller numbering. */
+ * iterations.  A game below the size split (cfr_config.batch_split_nodes) whose image fits in shared
+ * memory (its structure, reaches, values, r~, sigma, R and S; at most 200 KB, about 5000 nodes) runs in
+ * ONE persistent kernel launch (a CUDA graph of the launch and two bookkeeping nodes): a thread block
+ * takes a game from a work queue (largest first), copies it into its shared memory, runs its n
+ * iterations there depth by depth (Section 3.2's steps, as cfr_iterate's kernels compute them per node
+ * and infoset), writes R, S and sigma back and takes the next game.  Every other game (larger, or with
+ * a node of more than 32 actions) runs in one forest (one root per game) through cfr_iterate's
+ * per-depth kernels on a second stream, concurrently.  FP32 mode with FP64 accumulators, simultaneous
+ * updates, every variant.  Game g's arrays use its own caller numbering. */
 typedef struct cfr_batch cfr_batch;   /* opaque; owned by the library */
 
 typedef struct {
-    int32_t threads_per_block;  /* multiple of 32 in [32, 1024] */
+    int32_t threads_per_block;  /* multiple of 32 in [32, 256] */
     int32_t blocks_per_sm;      /* 0 = as many as fit */
 } cfr_batch_tuning;
 
@@ -256,14 +258,15 @@ typedef struct {
     int32_t threads_per_block, blocks_per_sm, grid;   /* the launch shape in use */
     int32_t tuned;              /* 1 once set by cfr_batch_set_tuning or cfr_batch_autotune */
     int64_t kernel_launches;    /* kernels launched by cfr_batch_iterate so far */
-    int32_t forest_games;       /* games at or above the size split, run as one forest */
+    int32_t forest_games;       /* games run as one forest (at or above the split, too large or too wide) */
     int64_t forest_nodes;
     int64_t split_nodes;
+    int64_t smem_bytes;         /* dynamic shared memory of a persistent block (its largest game's image) */
 } cfr_batch_info;
 
 /* Validates and lays out num_games >= 1 games (each as cfr_load_tree would; the combined size must stay
- * below 2^31 - 1 nodes).  CFR_ERR_UNSUPPORTED for FP64 mode, alternating updates or more than 32
- * actions at an infoset.  c may be NULL (defaults: vanilla; pass variant CFR_PLUS for CFR+). */
+ * below 2^31 - 1 nodes).  CFR_ERR_UNSUPPORTED for FP64 mode or alternating updates.  c may be NULL
+ * (defaults: vanilla; pass variant CFR_PLUS for CFR+). */
 cfr_status cfr_batch_load(const cfr_game_desc *games, int32_t num_games, const cfr_config *c, cfr_batch **out);
 
 /* Queues n >= 0 iterations of every game (one persistent launch).  Asynchronous on the batch's stream. */
@@ -272,7 +275,7 @@ cfr_status cfr_batch_iterate(cfr_batch *b, int32_t n);
 /* Sets the launch shape. */
 cfr_status cfr_batch_set_tuning(cfr_batch *b, const cfr_batch_tuning *t);
 
-/* Measures trial_iterations of every game for each block size in {128, 256, 512, 1024} and each
+/* Measures trial_iterations of every game for each block size in {64, 128, 256} and each
  * blocks-per-SM count in {1, 2, 4, 8, 16} that fits, on a copy of the state that is restored
  * afterwards (the iteration count does not move), and keeps the fastest.  *chosen and *best_us (time
  * per iteration of the whole batch) may be NULL.  Synchronises. */

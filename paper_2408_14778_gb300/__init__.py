@@ -96,7 +96,7 @@ class _BatchInfo(ctypes.Structure):
         ("num_q", ctypes.c_int64), ("iteration", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
         ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
         ("tuned", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("forest_games", ctypes.c_int32),
-        ("forest_nodes", ctypes.c_int64), ("split_nodes", ctypes.c_int64),
+        ("forest_nodes", ctypes.c_int64), ("split_nodes", ctypes.c_int64), ("smem_bytes", ctypes.c_int64),
     ]
 
 
@@ -547,14 +547,15 @@ def cfr_batch_get_info(b: Batch) -> dict:
     return d
 
 
-def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 4096, 16384, 65536, -1), trial_iterations: int = 10,
+def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 512, 2048, -1), trial_iterations: int = 10,
                    device=None, cache_path: str | None = None, dcfr=(1.5, 0.0, 2.0)) -> dict:
     """The batch's size split (which games run as one forest through the per-depth kernels, which in the
     persistent kernel) and the persistent launch shape: for each candidate split the batch is loaded,
     the launch shape measured (cfr_batch_autotune), and trial_iterations timed; the fastest is kept and
     cached per GPU and size bucket (in memory, and in the JSON file cache_path when given).  split 1 runs
-    every game as one forest, -1 every game in the persistent kernel.  Returns {split_nodes,
-    threads_per_block, blocks_per_sm, us_per_iteration (None if cached), cached, trials}."""
+    every game as one forest, -1 every game whose image fits shared memory in the persistent kernel.
+    Returns {split_nodes, threads_per_block, blocks_per_sm, us_per_iteration (None if cached), cached,
+    trials}."""
     import json
 
     import torch

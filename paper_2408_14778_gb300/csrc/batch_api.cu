@@ -1,7 +1,8 @@
 // C ABI of batched solving (include/cfr_gb300.h, cfr_batch_*): many independent games advanced together.
-// Games below a size split run in one persistent launch per call (batch.cuh), its shape picked by a
-// measured sweep (cfr_batch_autotune); the larger ones as one forest through the single-game solver's
-// per-depth kernels on a second stream, concurrently.
+// Games below a size split whose image fits shared memory run in one persistent launch per call, each
+// solved by one block in its shared memory (batch.cuh), the launch shape picked by a measured sweep
+// (cfr_batch_autotune); the others as one forest through the single-game solver's per-depth kernels on
+// a second stream, concurrently.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,7 +25,60 @@ namespace {
 
 thread_local std::string g_batch_err;
 
-constexpr int64_t kBatchSplitDefault = 16384;   // games of at least this many nodes run as one forest
+constexpr int64_t kBatchSplitDefault = 4096;    // games of at least this many nodes run as one forest
+constexpr int64_t kSmemCap = 200 * 1024;        // shared memory a resident game may take, at most
+
+// A game's shared-memory image (batch.cuh) from its own single-game layout; the slot map is filled
+// once the batch's layout is known.  False when the game cannot be resident (a node with more than 32
+// actions, or more than kSmemCap bytes); *err explains an invalid game.
+struct GameImage {
+    std::vector<int32_t> w;
+    std::vector<int32_t> q_int2user, qplayer;   // per local slot: the game's caller slot, its player
+    int64_t bytes = 0;
+};
+
+cfr_status make_image(const cfr_game_desc &g, GameImage &img, bool *fits, std::string *err) {
+    Layout Lg;
+    const cfr_status st = build_layout(&g, &Lg, err);
+    if (st != CFR_OK) return st;
+    *fits = Lg.wide.empty();
+    if (!*fits) return CFR_OK;
+    std::vector<int32_t> &w = img.w;
+    w.assign(kImgHeader, 0);
+    auto put = [&](const void *data, size_t bytes) -> int32_t {
+        while (w.size() % 4) w.push_back(0);
+        const int32_t off = (int32_t)w.size();
+        const size_t nw = (bytes + 3) / 4;
+        w.resize(w.size() + nw, 0);
+        if (data && bytes) std::memcpy(w.data() + off, data, bytes);
+        return off;
+    };
+    const std::vector<float> util(Lg.util.begin(), Lg.util.end()), sigma0(Lg.sigma0.begin(), Lg.sigma0.end());
+    w[kImgNd] = (int32_t)Lg.Nd; w[kImgNt] = (int32_t)Lg.Nt; w[kImgH] = Lg.H; w[kImgHp] = Lg.Hp;
+    w[kImgQ] = (int32_t)Lg.Q; w[kImgL] = Lg.L;
+    w[kImgDlevel] = put(Lg.dlevel.data(), 4 * Lg.dlevel.size());
+    w[kImgHlevel] = put(Lg.hlevel.data(), 4 * Lg.hlevel.size());
+    w[kImgDfirst] = put(Lg.dfirst.data(), 4 * Lg.dfirst.size());
+    w[kImgTfirst] = put(Lg.tfirst.data(), 4 * Lg.tfirst.size());
+    w[kImgKmask] = put(Lg.kmask.data(), 4 * Lg.kmask.size());
+    w[kImgQp] = put(Lg.qp.data(), 4 * Lg.qp.size());
+    w[kImgUtil] = put(util.data(), 4 * util.size());
+    w[kImgQbase] = put(Lg.qbase.data(), 4 * Lg.qbase.size());
+    w[kImgPseq] = put(Lg.pseq.data(), 4 * Lg.pseq.size());
+    w[kImgPseqH] = put(Lg.pseq_h.data(), 4 * Lg.pseq_h.size());
+    w[kImgIplayer] = put(Lg.iplayer.data(), Lg.iplayer.size());
+    w[kImgSigma0] = put(sigma0.data(), 4 * sigma0.size());
+    w[kImgQmap] = put(nullptr, 4 * (size_t)Lg.Q);
+    while (w.size() % 4) w.push_back(0);
+    w[kImgWords] = (int32_t)w.size();
+    img.q_int2user = Lg.q_int2user;
+    img.qplayer.assign((size_t)Lg.Q, 0);
+    for (int32_t h = 0; h < Lg.H; ++h)
+        for (int32_t q = Lg.qbase[(size_t)h]; q < Lg.qbase[(size_t)h + 1]; ++q) img.qplayer[(size_t)q] = Lg.iplayer[(size_t)h];
+    img.bytes = smem_game_bytes((int64_t)w.size(), Lg.Nd, Lg.H, Lg.Q);
+    *fits = img.bytes <= kSmemCap;
+    return CFR_OK;
+}
 
 struct BDeviceGuard {
     int prev = -1;
@@ -60,6 +114,9 @@ struct cfr_batch {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_b0 = nullptr, ev_b1 = nullptr;
     bool big_timed = false;
     int32_t G = 0, stride = 0, Hp = 0, H = 0, hp_na = 0;   // the persistent part
+    int32_t *images = nullptr;           // per game of the persistent part, its shared-memory image
+    int64_t *img_off = nullptr;          // word offset of each image
+    int64_t smem_bytes = 0;              // dynamic shared memory of a block (the largest game's need)
     int64_t N = 0, Nd = 0, Nt = 0, Q = 0;
     bool single_level = true;
     // host: per game, its first node / infoset / infoset-action slot in the caller's numbering (+ total)
@@ -67,12 +124,11 @@ struct cfr_batch {
     std::vector<int32_t> q_int2user;     // internal slot -> caller slot of the combined game
     std::vector<int64_t> game_nodes;
     // device
-    int32_t *dfirst = nullptr, *tfirst = nullptr, *dinfo = nullptr, *qbase = nullptr, *pseq = nullptr,
-            *pseq_h = nullptr, *astar = nullptr;
+    // (the forest's structure serves the best response; the iterations run on the images)
+    int32_t *dfirst = nullptr, *tfirst = nullptr, *dinfo = nullptr, *qbase = nullptr, *astar = nullptr;
     int8_t *iplayer = nullptr;
-    uint32_t *kmask = nullptr, *qp = nullptr;
-    float *util = nullptr, *sigma = nullptr, *inst = nullptr, *reach1 = nullptr, *reach2 = nullptr, *u = nullptr,
-          *own = nullptr;
+    uint32_t *kmask = nullptr;
+    float *sigma = nullptr;
     double *util64 = nullptr, *sigma064 = nullptr, *R = nullptr, *S = nullptr, *avg = nullptr, *cfv = nullptr,
            *preach = nullptr, *val = nullptr, *br_out = nullptr, *snapR = nullptr, *snapS = nullptr;
     float *snapSigma = nullptr;
@@ -150,16 +206,6 @@ cfr_status bupload(cfr_batch *b, T *dst, const std::vector<T> &src) {
     return CFR_OK;
 }
 
-DevTree<float> batch_tree(const cfr_batch *b) {
-    DevTree<float> t{};
-    t.dfirst = b->dfirst; t.tfirst = b->tfirst; t.dinfo = b->dinfo; t.kmask = b->kmask; t.wbits = nullptr;
-    t.qp = b->qp; t.util = b->util; t.qbase = b->qbase; t.iplayer = b->iplayer; t.pseq = b->pseq;
-    t.pseq_h = b->pseq_h; t.sigma = b->sigma; t.inst = b->inst; t.reach1 = b->reach1; t.reach2 = b->reach2;
-    t.u = b->u; t.own = b->own; t.R = b->R; t.S = b->S; t.iter = b->d_iter; t.contrib = nullptr;
-    t.hnode_start = nullptr; t.hnode = nullptr; t.pmask = 6; t.wts = nullptr;
-    return t;
-}
-
 BatchDesc batch_desc(const cfr_batch *b) {
     BatchDesc d;
     d.order = b->order; d.dlo = b->dlo; d.dhi = b->dhi; d.hlo = b->hlo; d.hhi = b->hhi; d.nlev = b->nlev;
@@ -167,48 +213,55 @@ BatchDesc batch_desc(const cfr_batch *b) {
     return d;
 }
 
-// The persistent launch of K iterations for the batch's variant and action count.
-template <int NA>
-cudaError_t launch_iterate_na(cfr_batch *b, cudaStream_t st, int32_t K, int grid, int threads) {
-    const DevTree<float> t = batch_tree(b);
-    const BatchDesc d = batch_desc(b);
-    const int32_t linear = b->cfg.avg_weight == CFR_AVG_LINEAR;
-    const double3 dc = make_double3(b->cfg.dcfr_alpha, b->cfg.dcfr_beta, b->cfg.dcfr_gamma);
-    const int64_t *T0 = b->d_iter;
-    switch (b->cfg.variant) {
-    case CFR_VANILLA: k_batch_iterate<NA, CFRV_VANILLA><<<grid, threads, 0, st>>>(t, d, T0, K, linear, dc); break;
-    case CFR_PLUS: k_batch_iterate<NA, CFRV_PLUS><<<grid, threads, 0, st>>>(t, d, T0, K, linear, dc); break;
-    case CFR_LINEAR: k_batch_iterate<NA, CFRV_LINEAR><<<grid, threads, 0, st>>>(t, d, T0, K, linear, dc); break;
-    default: k_batch_iterate<NA, CFRV_DISCOUNTED><<<grid, threads, 0, st>>>(t, d, T0, K, linear, dc); break;
+// The persistent launch of K iterations (games resident in shared memory) for the batch's variant and
+// action count.
+template <int NA, int V>
+void *smem_kernel() { return reinterpret_cast<void *>(k_batch_smem<NA, V>); }
+
+void *smem_kernel_for(const cfr_batch *b) {
+    const int na = b->hp_na <= 3 ? 0 : b->hp_na <= 5 ? 1 : 2;
+    switch (b->cfg.variant * 3 + na) {
+    case 0: return smem_kernel<3, CFRV_VANILLA>();
+    case 1: return smem_kernel<5, CFRV_VANILLA>();
+    case 2: return smem_kernel<8, CFRV_VANILLA>();
+    case 3: return smem_kernel<3, CFRV_PLUS>();
+    case 4: return smem_kernel<5, CFRV_PLUS>();
+    case 5: return smem_kernel<8, CFRV_PLUS>();
+    case 6: return smem_kernel<3, CFRV_LINEAR>();
+    case 7: return smem_kernel<5, CFRV_LINEAR>();
+    case 8: return smem_kernel<8, CFRV_LINEAR>();
+    case 9: return smem_kernel<3, CFRV_DISCOUNTED>();
+    case 10: return smem_kernel<5, CFRV_DISCOUNTED>();
+    default: return smem_kernel<8, CFRV_DISCOUNTED>();
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_iterate(cfr_batch *b, cudaStream_t st, int32_t K, int grid, int threads) {
-    if (b->hp_na <= 3) return launch_iterate_na<3>(b, st, K, grid, threads);
-    if (b->hp_na <= 5) return launch_iterate_na<5>(b, st, K, grid, threads);
-    return launch_iterate_na<8>(b, st, K, grid, threads);
+    const int32_t linear = b->cfg.avg_weight == CFR_AVG_LINEAR;
+    const double3 dc = make_double3(b->cfg.dcfr_alpha, b->cfg.dcfr_beta, b->cfg.dcfr_gamma);
+    const int32_t *images = b->images;
+    const int64_t *img_off = b->img_off;
+    const int32_t *order = b->order;
+    int32_t G = b->G;
+    int32_t *next = b->next;
+    double *gR = b->R, *gS = b->S;
+    float *gs = b->sigma;
+    const int64_t *T0 = b->d_iter;
+    unsigned long long *t0 = b->t_start, *t1 = b->t_end;
+    void *args[] = {&images, &img_off, &order, &G, &next, &gR, &gS, &gs, &T0, &K, (void *)&linear, (void *)&dc, &t0, &t1};
+    return cudaLaunchKernel(smem_kernel_for(b), dim3((unsigned)grid), dim3((unsigned)threads), args,
+                            (size_t)b->smem_bytes, st);
 }
 
 // Resident blocks per SM of the iteration kernel at a block size.
-template <int NA>
-int occupancy_na(const cfr_batch *b, int threads) {
-    int per_sm = 0;
-    cudaError_t e;
-    switch (b->cfg.variant) {
-    case CFR_VANILLA: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iterate<NA, CFRV_VANILLA>, threads, 0); break;
-    case CFR_PLUS: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iterate<NA, CFRV_PLUS>, threads, 0); break;
-    case CFR_LINEAR: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iterate<NA, CFRV_LINEAR>, threads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iterate<NA, CFRV_DISCOUNTED>, threads, 0); break;
-    }
-    if (e != cudaSuccess) { cudaGetLastError(); return 0; }
-    return per_sm;
-}
-
 int occupancy(const cfr_batch *b, int threads) {
-    if (b->hp_na <= 3) return occupancy_na<3>(b, threads);
-    if (b->hp_na <= 5) return occupancy_na<5>(b, threads);
-    return occupancy_na<8>(b, threads);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smem_kernel_for(b), threads, (size_t)b->smem_bytes) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
 }
 
 int grid_of(const cfr_batch *b, int threads, int bps) {
@@ -351,48 +404,61 @@ cfr_status load_batch(cfr_batch *b, Layout &Lo) {
     if (!Lo.wide.empty()) return berr(nullptr, CFR_ERR_UNSUPPORTED, "batched solving handles at most 32 actions per node");
 
     BTRY(balloc(b, &b->dfirst, b->Nd + 1)); BTRY(balloc(b, &b->tfirst, b->Nd + 1)); BTRY(balloc(b, &b->dinfo, b->Nd));
-    BTRY(balloc(b, &b->kmask, b->Nd)); BTRY(balloc(b, &b->qp, b->Nd));
-    BTRY(balloc(b, &b->util, b->Nt)); BTRY(balloc(b, &b->util64, b->Nt));
+    BTRY(balloc(b, &b->kmask, b->Nd)); BTRY(balloc(b, &b->util64, b->Nt));
     BTRY(balloc(b, &b->qbase, (int64_t)b->H + 1)); BTRY(balloc(b, &b->iplayer, b->H));
-    BTRY(balloc(b, &b->pseq, b->H)); BTRY(balloc(b, &b->pseq_h, b->H));
-    BTRY(balloc(b, &b->sigma, b->Q)); BTRY(balloc(b, &b->sigma064, b->Q)); BTRY(balloc(b, &b->inst, b->Q));
-    BTRY(balloc(b, &b->reach1, b->Nd)); BTRY(balloc(b, &b->reach2, b->Nd)); BTRY(balloc(b, &b->u, b->Nd));
-    BTRY(balloc(b, &b->own, b->H)); BTRY(balloc(b, &b->R, b->Q)); BTRY(balloc(b, &b->S, b->Q));
+    BTRY(balloc(b, &b->sigma, b->Q)); BTRY(balloc(b, &b->sigma064, b->Q));
+    BTRY(balloc(b, &b->R, b->Q)); BTRY(balloc(b, &b->S, b->Q));
     BTRY(balloc(b, &b->order, G)); BTRY(balloc(b, &b->dlo, (int64_t)dlo.size())); BTRY(balloc(b, &b->dhi, (int64_t)dhi.size()));
     BTRY(balloc(b, &b->hlo, (int64_t)hlo.size())); BTRY(balloc(b, &b->hhi, (int64_t)hhi.size()));
     BTRY(balloc(b, &b->nlev, G)); BTRY(balloc(b, &b->next, 1));
     BTRY(balloc(b, &b->t_start, G)); BTRY(balloc(b, &b->t_end, G)); BTRY(balloc(b, &b->d_iter, 1));
 
     BTRY(bupload(b, b->dfirst, Lo.dfirst)); BTRY(bupload(b, b->tfirst, Lo.tfirst)); BTRY(bupload(b, b->dinfo, Lo.dinfo));
-    BTRY(bupload(b, b->kmask, Lo.kmask)); BTRY(bupload(b, b->qp, Lo.qp));
+    BTRY(bupload(b, b->kmask, Lo.kmask));
     BTRY(bupload(b, b->util64, Lo.util));
-    BTRY(bupload(b, b->util, std::vector<float>(Lo.util.begin(), Lo.util.end())));
     BTRY(bupload(b, b->qbase, Lo.qbase)); BTRY(bupload(b, b->iplayer, Lo.iplayer));
-    BTRY(bupload(b, b->pseq, Lo.pseq)); BTRY(bupload(b, b->pseq_h, Lo.pseq_h));
     BTRY(bupload(b, b->sigma064, Lo.sigma0));
     BTRY(bupload(b, b->sigma, std::vector<float>(Lo.sigma0.begin(), Lo.sigma0.end())));
     BTRY(bupload(b, b->order, order)); BTRY(bupload(b, b->dlo, dlo)); BTRY(bupload(b, b->dhi, dhi));
     BTRY(bupload(b, b->hlo, hlo)); BTRY(bupload(b, b->hhi, hhi)); BTRY(bupload(b, b->nlev, nlev));
-    BCK(cudaMemsetAsync(b->inst, 0, sizeof(float) * (size_t)std::max<int64_t>(b->Q, 1), b->stream));
     BCK(cudaMemsetAsync(b->R, 0, sizeof(double) * (size_t)std::max<int64_t>(b->Q, 1), b->stream));
     BCK(cudaMemsetAsync(b->S, 0, sizeof(double) * (size_t)std::max<int64_t>(b->Q, 1), b->stream));
-    BCK(cudaMemsetAsync(b->own, 0, sizeof(float) * (size_t)std::max<int32_t>(b->H, 1), b->stream));
-    BCK(cudaMemsetAsync(b->u, 0, sizeof(float) * (size_t)std::max<int64_t>(b->Nd, 1), b->stream));
     BCK(cudaMemsetAsync(b->d_iter, 0, sizeof(int64_t), b->stream));
-    // every game's root has counterfactual reaches 1 (Eq. 2 at v_0)
-    if (L > 0) {
-        const std::vector<float> ones((size_t)Lo.dlevel[1], 1.f);
-        BTRY(bupload(b, b->reach1, ones));
-        BTRY(bupload(b, b->reach2, ones));
-    }
     if (b->H > 0) {
         k_regret_match_all<float><<<(b->H + 255) / 256, 256, 0, b->stream>>>(b->sigma, b->R, b->qbase, b->iplayer, b->H);
         BCK(cudaGetLastError());
     }
     BCK(cudaStreamSynchronize(b->stream));
     BCK(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device));
-    b->threads = 256;
     b->blocks_per_sm = 0;
+    return CFR_OK;
+}
+
+// The resident games' images with their slot maps (local slot -> the batch layout's slot, -1 for
+// chance), uploaded; the kernel's shared memory sized for the largest.
+cfr_status load_images(cfr_batch *b, std::vector<GameImage> &imgs) {
+    std::vector<int64_t> user2int((size_t)std::max<int64_t>(b->Q, 1), -1);
+    for (int64_t qi = 0; qi < b->Q; ++qi) user2int[(size_t)b->q_int2user[(size_t)qi]] = qi;
+    std::vector<int32_t> all;
+    std::vector<int64_t> off((size_t)b->G, 0);
+    b->smem_bytes = 0;
+    for (int32_t k = 0; k < b->G; ++k) {
+        GameImage &img = imgs[(size_t)k];
+        int32_t *qmap = img.w.data() + img.w[kImgQmap];
+        for (size_t q = 0; q < img.q_int2user.size(); ++q)
+            qmap[q] = img.qplayer[q] > 0 ? (int32_t)user2int[(size_t)(b->q_off[(size_t)k] + img.q_int2user[q])] : -1;
+        off[(size_t)k] = (int64_t)all.size();
+        all.insert(all.end(), img.w.begin(), img.w.end());
+        b->smem_bytes = std::max(b->smem_bytes, img.bytes);
+        img = GameImage();
+    }
+    BTRY(balloc(b, &b->images, (int64_t)all.size()));
+    BTRY(balloc(b, &b->img_off, (int64_t)b->G));
+    BTRY(bupload(b, b->images, all));
+    BTRY(bupload(b, b->img_off, off));
+    // the kernel's limit is every batch's cap (a batch of smaller games must not lower it for another)
+    BCK(cudaFuncSetAttribute(smem_kernel_for(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
+    b->threads = 128;
     return CFR_OK;
 }
 
@@ -423,13 +489,23 @@ cfr_status cfr_batch_load(const cfr_game_desc *games, int32_t num_games, const c
     b->n_games = num_games;
     b->split_nodes = cfg.batch_split_nodes == 0 ? kBatchSplitDefault : cfg.batch_split_nodes;
     std::vector<cfr_game_desc> small, large;
+    std::vector<GameImage> imgs;
     b->part.assign((size_t)num_games, 0);
     b->idx.assign((size_t)num_games, 0);
     for (int32_t i = 0; i < num_games; ++i) {
-        const bool big = b->split_nodes > 0 && games[i].num_nodes >= b->split_nodes;
+        bool big = b->split_nodes > 0 && games[i].num_nodes >= b->split_nodes;
+        GameImage img;
+        if (!big) {                                    // resident in shared memory if its image fits
+            bool fits = false;
+            std::string err;
+            const cfr_status st = make_image(games[i], img, &fits, &err);
+            if (st != CFR_OK) return berr(nullptr, st, "game %d: %s", i, err.c_str());
+            big = !fits;
+        }
         b->part[(size_t)i] = big;
         b->idx[(size_t)i] = (int32_t)(big ? large.size() : small.size());
         (big ? large : small).push_back(games[i]);
+        if (!big) imgs.push_back(std::move(img));
     }
     b->G = (int32_t)small.size();
     std::vector<int32_t> parent, action, infoset, nact;
@@ -504,6 +580,7 @@ cfr_status cfr_batch_load(const cfr_game_desc *games, int32_t num_games, const c
         return berr(nullptr, CFR_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
     }
     st = load_batch(b.get(), *Lo);
+    if (st == CFR_OK) st = load_images(b.get(), imgs);
     if (st != CFR_OK) {
         std::string msg = b->err.empty() ? g_batch_err : b->err;
         cfr_batch_free(b.release());
@@ -540,8 +617,8 @@ cfr_status cfr_batch_iterate(cfr_batch *b, int32_t n) {
 
 cfr_status cfr_batch_set_tuning(cfr_batch *b, const cfr_batch_tuning *t) {
     BTRY(busable(b));
-    if (!t || t->threads_per_block < 32 || t->threads_per_block > 1024 || t->threads_per_block % 32 || t->blocks_per_sm < 0)
-        return berr(b, CFR_ERR_INVALID, "threads_per_block must be a multiple of 32 in [32, 1024], blocks_per_sm >= 0");
+    if (!t || t->threads_per_block < 32 || t->threads_per_block > 256 || t->threads_per_block % 32 || t->blocks_per_sm < 0)
+        return berr(b, CFR_ERR_INVALID, "threads_per_block must be a multiple of 32 in [32, 256], blocks_per_sm >= 0");
     BDeviceGuard dg(b->device);
     if (b->G > 0 && occupancy(b, t->threads_per_block) < 1) return berr(b, CFR_ERR_INVALID, "no block of %d threads fits an SM", t->threads_per_block);
     b->threads = t->threads_per_block;
@@ -578,7 +655,7 @@ cfr_status cfr_batch_autotune(cfr_batch *b, int32_t trial_iterations, cfr_batch_
     BCK(cudaEventCreate(&e1));
     double best = 1e300;
     int best_threads = b->threads, best_bps = b->blocks_per_sm;
-    for (int threads : {128, 256, 512, 1024}) {
+    for (int threads : {64, 128, 256}) {
         const int occ = occupancy(b, threads);
         for (int bps : {1, 2, 4, 8, 16}) {
             if (bps > occ) break;
@@ -761,6 +838,7 @@ cfr_status cfr_batch_get_info(const cfr_batch *b, cfr_batch_info *info) {
     info->forest_games = (int32_t)b->big_nodes.size();
     info->forest_nodes = fi.num_nodes;
     info->split_nodes = b->split_nodes;
+    info->smem_bytes = b->smem_bytes;
     info->device_bytes = b->device_bytes + fi.device_bytes;
     info->iteration = b->iteration;
     info->threads_per_block = b->threads;
