@@ -27,6 +27,10 @@ thread_local std::string g_batch_err;
 
 constexpr int64_t kBatchSplitDefault = 4096;    // games of at least this many nodes run as one forest
 constexpr int64_t kSmemCap = 200 * 1024;        // shared memory a resident game may take, at most
+// Resident games are launched in classes by footprint, each with the shared memory of its largest
+// game, so that a few large games do not lower every block's occupancy.
+constexpr int kClasses = 4;
+constexpr int64_t kClassCap[kClasses] = {24 * 1024, 48 * 1024, 100 * 1024, kSmemCap};
 
 // A game's shared-memory image (batch.cuh) from its own single-game layout; the slot map is filled
 // once the batch's layout is known.  False when the game cannot be resident (a node with more than 32
@@ -117,6 +121,12 @@ struct cfr_batch {
     int32_t *images = nullptr;           // per game of the persistent part, its shared-memory image
     int64_t *img_off = nullptr;          // word offset of each image
     int64_t smem_bytes = 0;              // dynamic shared memory of a block (the largest game's need)
+    // footprint classes: class c's games are order[cls_off[c] .. cls_off[c + 1]), launched with
+    // cls_smem[c] bytes per block, each class but the first on its own stream (graph branch)
+    std::vector<int32_t> cls_off;
+    std::vector<int64_t> cls_smem;
+    cudaStream_t aux[kClasses] = {};
+    cudaEvent_t cls_fork = nullptr, cls_join[kClasses] = {};
     int64_t N = 0, Nd = 0, Nt = 0, Q = 0;
     bool single_level = true;
     // host: per game, its first node / infoset / infoset-action slot in the caller's numbering (+ total)
@@ -236,43 +246,72 @@ void *smem_kernel_for(const cfr_batch *b) {
     }
 }
 
-cudaError_t launch_iterate(cfr_batch *b, cudaStream_t st, int32_t K, int grid, int threads) {
+int32_t class_games(const cfr_batch *b, int c) { return b->cls_off[(size_t)c + 1] - b->cls_off[(size_t)c]; }
+
+cudaError_t launch_class(cfr_batch *b, cudaStream_t st, int c, int32_t K, int grid, int threads) {
     const int32_t linear = b->cfg.avg_weight == CFR_AVG_LINEAR;
     const double3 dc = make_double3(b->cfg.dcfr_alpha, b->cfg.dcfr_beta, b->cfg.dcfr_gamma);
     const int32_t *images = b->images;
     const int64_t *img_off = b->img_off;
-    const int32_t *order = b->order;
-    int32_t G = b->G;
-    int32_t *next = b->next;
+    const int32_t *order = b->order + b->cls_off[(size_t)c];
+    int32_t G = class_games(b, c);
+    int32_t *next = b->next + c;
     double *gR = b->R, *gS = b->S;
     float *gs = b->sigma;
     const int64_t *T0 = b->d_iter;
     unsigned long long *t0 = b->t_start, *t1 = b->t_end;
     void *args[] = {&images, &img_off, &order, &G, &next, &gR, &gS, &gs, &T0, &K, (void *)&linear, (void *)&dc, &t0, &t1};
     return cudaLaunchKernel(smem_kernel_for(b), dim3((unsigned)grid), dim3((unsigned)threads), args,
-                            (size_t)b->smem_bytes, st);
+                            (size_t)b->cls_smem[(size_t)c], st);
 }
 
-// Resident blocks per SM of the iteration kernel at a block size.
-int occupancy(const cfr_batch *b, int threads) {
+// Resident blocks per SM of class c's launch at a block size.
+int occupancy(const cfr_batch *b, int c, int threads) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smem_kernel_for(b), threads, (size_t)b->smem_bytes) !=
-        cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smem_kernel_for(b), threads,
+                                                      (size_t)b->cls_smem[(size_t)c]) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return per_sm;
 }
 
-int grid_of(const cfr_batch *b, int threads, int bps) {
-    const int per_sm = std::max(1, std::min(bps > 0 ? bps : occupancy(b, threads), occupancy(b, threads)));
-    return std::max(1, std::min(b->G, per_sm * b->sms));
+// The most blocks per SM any non-empty class can hold, and the fewest (0: no class fits).
+int occupancy_max(const cfr_batch *b, int threads) {
+    int m = 0;
+    for (int c = 0; c < kClasses; ++c)
+        if (class_games(b, c) > 0) m = std::max(m, occupancy(b, c, threads));
+    return m;
+}
+int occupancy_min(const cfr_batch *b, int threads) {
+    int m = 1 << 30;
+    for (int c = 0; c < kClasses; ++c)
+        if (class_games(b, c) > 0) m = std::min(m, occupancy(b, c, threads));
+    return m == 1 << 30 ? 0 : m;
+}
+
+int grid_of(const cfr_batch *b, int c, int threads, int bps) {
+    const int occ = occupancy(b, c, threads);
+    const int per_sm = std::max(1, bps > 0 ? std::min(bps, occ) : occ);
+    return std::max(1, std::min(class_games(b, c), per_sm * b->sms));
 }
 
 // Queues K iterations: the work counter reset, the persistent launch, the iteration count advanced.
+// Class 0 (or the first non-empty class) runs on st, the others on their own streams forked from and
+// joined back to it.
 cfr_status enqueue_batch(cfr_batch *b, cudaStream_t st, int32_t K, int threads, int bps) {
-    BCK(cudaMemsetAsync(b->next, 0, sizeof(int32_t), st));
-    BCK(launch_iterate(b, st, K, grid_of(b, threads, bps), threads));
+    BCK(cudaMemsetAsync(b->next, 0, sizeof(int32_t) * kClasses, st));
+    int first = -1;
+    for (int c = 0; c < kClasses; ++c) {
+        if (class_games(b, c) == 0) continue;
+        if (first < 0) { first = c; BCK(cudaEventRecord(b->cls_fork, st)); continue; }
+        BCK(cudaStreamWaitEvent(b->aux[c], b->cls_fork, 0));
+        BCK(launch_class(b, b->aux[c], c, K, grid_of(b, c, threads, bps), threads));
+        BCK(cudaEventRecord(b->cls_join[c], b->aux[c]));
+    }
+    if (first >= 0) BCK(launch_class(b, st, first, K, grid_of(b, first, threads, bps), threads));
+    for (int c = first + 1; c < kClasses && first >= 0; ++c)
+        if (class_games(b, c) > 0) BCK(cudaStreamWaitEvent(st, b->cls_join[c], 0));
     k_batch_advance<<<1, 1, 0, st>>>(b->d_iter, K);
     BCK(cudaGetLastError());
     return CFR_OK;
@@ -410,7 +449,7 @@ cfr_status load_batch(cfr_batch *b, Layout &Lo) {
     BTRY(balloc(b, &b->R, b->Q)); BTRY(balloc(b, &b->S, b->Q));
     BTRY(balloc(b, &b->order, G)); BTRY(balloc(b, &b->dlo, (int64_t)dlo.size())); BTRY(balloc(b, &b->dhi, (int64_t)dhi.size()));
     BTRY(balloc(b, &b->hlo, (int64_t)hlo.size())); BTRY(balloc(b, &b->hhi, (int64_t)hhi.size()));
-    BTRY(balloc(b, &b->nlev, G)); BTRY(balloc(b, &b->next, 1));
+    BTRY(balloc(b, &b->nlev, G)); BTRY(balloc(b, &b->next, kClasses));
     BTRY(balloc(b, &b->t_start, G)); BTRY(balloc(b, &b->t_end, G)); BTRY(balloc(b, &b->d_iter, 1));
 
     BTRY(bupload(b, b->dfirst, Lo.dfirst)); BTRY(bupload(b, b->tfirst, Lo.tfirst)); BTRY(bupload(b, b->dinfo, Lo.dinfo));
@@ -435,13 +474,15 @@ cfr_status load_batch(cfr_batch *b, Layout &Lo) {
 }
 
 // The resident games' images with their slot maps (local slot -> the batch layout's slot, -1 for
-// chance), uploaded; the kernel's shared memory sized for the largest.
+// chance), uploaded; the games ordered by footprint class, then largest first, each class's shared
+// memory sized for its largest game; the classes' streams and events.
 cfr_status load_images(cfr_batch *b, std::vector<GameImage> &imgs) {
     std::vector<int64_t> user2int((size_t)std::max<int64_t>(b->Q, 1), -1);
     for (int64_t qi = 0; qi < b->Q; ++qi) user2int[(size_t)b->q_int2user[(size_t)qi]] = qi;
-    std::vector<int32_t> all;
-    std::vector<int64_t> off((size_t)b->G, 0);
+    std::vector<int32_t> all, cls((size_t)b->G);
+    std::vector<int64_t> off((size_t)b->G, 0), bytes((size_t)b->G);
     b->smem_bytes = 0;
+    b->cls_smem.assign(kClasses, 0);
     for (int32_t k = 0; k < b->G; ++k) {
         GameImage &img = imgs[(size_t)k];
         int32_t *qmap = img.w.data() + img.w[kImgQmap];
@@ -449,15 +490,34 @@ cfr_status load_images(cfr_batch *b, std::vector<GameImage> &imgs) {
             qmap[q] = img.qplayer[q] > 0 ? (int32_t)user2int[(size_t)(b->q_off[(size_t)k] + img.q_int2user[q])] : -1;
         off[(size_t)k] = (int64_t)all.size();
         all.insert(all.end(), img.w.begin(), img.w.end());
+        bytes[(size_t)k] = img.bytes;
+        int c = 0;
+        while (img.bytes > kClassCap[c]) ++c;
+        cls[(size_t)k] = c;
+        b->cls_smem[(size_t)c] = std::max(b->cls_smem[(size_t)c], img.bytes);
         b->smem_bytes = std::max(b->smem_bytes, img.bytes);
         img = GameImage();
     }
+    std::vector<int32_t> order((size_t)b->G);
+    for (int32_t g = 0; g < b->G; ++g) order[(size_t)g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return cls[(size_t)x] != cls[(size_t)y] ? cls[(size_t)x] < cls[(size_t)y] : bytes[(size_t)x] > bytes[(size_t)y];
+    });
+    b->cls_off.assign(kClasses + 1, 0);
+    for (int32_t g = 0; g < b->G; ++g) ++b->cls_off[(size_t)cls[(size_t)g] + 1];
+    for (int c = 0; c < kClasses; ++c) b->cls_off[(size_t)c + 1] += b->cls_off[(size_t)c];
     BTRY(balloc(b, &b->images, (int64_t)all.size()));
     BTRY(balloc(b, &b->img_off, (int64_t)b->G));
     BTRY(bupload(b, b->images, all));
     BTRY(bupload(b, b->img_off, off));
+    BTRY(bupload(b, b->order, order));
     // the kernel's limit is every batch's cap (a batch of smaller games must not lower it for another)
     BCK(cudaFuncSetAttribute(smem_kernel_for(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
+    BCK(cudaEventCreateWithFlags(&b->cls_fork, cudaEventDisableTiming));
+    for (int c = 0; c < kClasses; ++c) {
+        BCK(cudaStreamCreateWithFlags(&b->aux[c], cudaStreamNonBlocking));
+        BCK(cudaEventCreateWithFlags(&b->cls_join[c], cudaEventDisableTiming));
+    }
     b->threads = 128;
     return CFR_OK;
 }
@@ -620,7 +680,8 @@ cfr_status cfr_batch_set_tuning(cfr_batch *b, const cfr_batch_tuning *t) {
     if (!t || t->threads_per_block < 32 || t->threads_per_block > 256 || t->threads_per_block % 32 || t->blocks_per_sm < 0)
         return berr(b, CFR_ERR_INVALID, "threads_per_block must be a multiple of 32 in [32, 256], blocks_per_sm >= 0");
     BDeviceGuard dg(b->device);
-    if (b->G > 0 && occupancy(b, t->threads_per_block) < 1) return berr(b, CFR_ERR_INVALID, "no block of %d threads fits an SM", t->threads_per_block);
+    if (b->G > 0 && occupancy_min(b, t->threads_per_block) < 1)
+        return berr(b, CFR_ERR_INVALID, "no block of %d threads fits an SM", t->threads_per_block);
     b->threads = t->threads_per_block;
     b->blocks_per_sm = t->blocks_per_sm;
     b->tuned = true;
@@ -656,7 +717,8 @@ cfr_status cfr_batch_autotune(cfr_batch *b, int32_t trial_iterations, cfr_batch_
     double best = 1e300;
     int best_threads = b->threads, best_bps = b->blocks_per_sm;
     for (int threads : {64, 128, 256}) {
-        const int occ = occupancy(b, threads);
+        if (occupancy_min(b, threads) < 1) continue;
+        const int occ = occupancy_max(b, threads);
         for (int bps : {1, 2, 4, 8, 16}) {
             if (bps > occ) break;
             BCK(cudaMemcpy(b->d_iter, &T0, sizeof T0, cudaMemcpyHostToDevice));
@@ -843,7 +905,9 @@ cfr_status cfr_batch_get_info(const cfr_batch *b, cfr_batch_info *info) {
     info->iteration = b->iteration;
     info->threads_per_block = b->threads;
     info->blocks_per_sm = b->blocks_per_sm;
-    info->grid = b->G > 0 ? grid_of(b, b->threads, b->blocks_per_sm) : 0;
+    info->grid = 0;
+    for (int c = 0; c < kClasses && b->G > 0; ++c)
+        if (class_games(b, c) > 0) info->grid += grid_of(b, c, b->threads, b->blocks_per_sm);
     info->tuned = b->tuned;
     info->kernel_launches = b->kernel_launches + fi.kernel_launches;
     return CFR_OK;
@@ -864,8 +928,12 @@ void cfr_batch_free(cfr_batch *b) {
     }
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->side) cudaStreamDestroy(b->side);
-    for (cudaEvent_t ev : {b->ev_fork, b->ev_join, b->ev_b0, b->ev_b1})
+    for (cudaEvent_t ev : {b->ev_fork, b->ev_join, b->ev_b0, b->ev_b1, b->cls_fork})
         if (ev) cudaEventDestroy(ev);
+    for (int c = 0; c < kClasses; ++c) {
+        if (b->aux[c]) { cudaStreamSynchronize(b->aux[c]); cudaStreamDestroy(b->aux[c]); }
+        if (b->cls_join[c]) cudaEventDestroy(b->cls_join[c]);
+    }
     delete b;
 }
 
