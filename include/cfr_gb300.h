@@ -301,6 +301,50 @@ cfr_status cfr_batch_get_info(const cfr_batch *b, cfr_batch_info *info);
 const char *cfr_batch_last_error(const cfr_batch *b);   /* thread-local message if b == NULL */
 void cfr_batch_free(cfr_batch *b);
 
+/* ---- learned leaf values: a BF16 multilayer perceptron (no counterpart in the paper) ---------------
+ * Depth-limited solving replaces the subtrees below a depth cutoff by a value network: a multilayer
+ * perceptron of num_layers linear layers with ReLU between them, y = W_L(...ReLU(W_1 x + b_1)...) + b_L,
+ * mapping (public-state embedding, both players' ranges) to both players' counterfactual values.  The
+ * matrix products run on the tensor cores with BF16 operands and FP32 accumulation; the parameters are
+ * kept in FP32 (the master copy, updated by Adam) with a BF16 copy for the products; hidden activations
+ * and backpropagated gradients are BF16 between layers.  Loss: mean squared error over the batch and
+ * the outputs, L = (1 / (B n_out)) sum (y - t)^2.
+ * Parameter layout (host arrays of cfr_mlp_num_params floats): layer by layer, W_l row-major
+ * [dims[l + 1]][dims[l]], then b_l [dims[l + 1]].
+ * Device arrays (x, y, target, loss) belong to the caller and must stay valid until the queued work is
+ * done; every call is asynchronous on the network's stream unless it says it synchronises. */
+typedef struct cfr_mlp cfr_mlp;   /* opaque; owned by the library */
+
+/* dims[0 .. num_layers]: input width, hidden widths, output width (each in [1, 8192]); 1 <= num_layers
+ * <= 8.  Parameters start at zero (set them with cfr_mlp_set_params). */
+cfr_status cfr_mlp_create(const int32_t *dims, int32_t num_layers, int32_t device, void *cuda_stream, cfr_mlp **out);
+int64_t cfr_mlp_num_params(const cfr_mlp *m);
+
+/* Host copies of the FP32 parameters / of the gradients of the last cfr_mlp_backward (layout above).
+ * Synchronise. */
+cfr_status cfr_mlp_set_params(cfr_mlp *m, const float *params, int64_t len);
+cfr_status cfr_mlp_get_params(cfr_mlp *m, float *params, int64_t len);
+cfr_status cfr_mlp_get_grads(cfr_mlp *m, float *grads, int64_t len);
+
+/* y [batch][dims[L]] = the network at x [batch][dims[0]] (device, FP32, row-major); batch >= 1. */
+cfr_status cfr_mlp_forward(cfr_mlp *m, const float *x, int32_t batch, float *y);
+
+/* Forward and backward pass at (x, target [batch][dims[L]]): leaves dL/dparams in the network's
+ * gradient buffer and, if loss != NULL, writes L to *loss (device, one double). */
+cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int32_t batch, double *loss);
+
+/* One Adam step (Kingma and Ba, 2015, bias-corrected) on the gradients of the last cfr_mlp_backward:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+cfr_status cfr_mlp_adam(cfr_mlp *m, float lr, float beta1, float beta2, float eps);
+
+/* The time of one pass of each of the last cfr_mlp_forward and cfr_mlp_backward calls' matrix
+ * products (microseconds, summed over layers) and their FLOPs (2 M N K over the padded shapes); NULLs
+ * skip.  Synchronises. */
+cfr_status cfr_mlp_gemm_stats(cfr_mlp *m, double *fwd_us, double *fwd_flops, double *bwd_us, double *bwd_flops);
+
+const char *cfr_mlp_last_error(const cfr_mlp *m);   /* thread-local message if m == NULL */
+void cfr_mlp_free(cfr_mlp *m);
+
 #ifdef __cplusplus
 }
 #endif

@@ -156,6 +156,22 @@ def lib():
         L.cfr_batch_last_error.restype = ctypes.c_char_p
         L.cfr_batch_free.argtypes = [_P]
         L.cfr_batch_free.restype = None
+        L.cfr_mlp_create.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.POINTER(_P)]
+        L.cfr_mlp_num_params.argtypes = [_P]
+        L.cfr_mlp_num_params.restype = ctypes.c_int64
+        for name in ("cfr_mlp_set_params", "cfr_mlp_get_params", "cfr_mlp_get_grads"):
+            getattr(L, name).argtypes = [_P, _P, ctypes.c_int64]
+        L.cfr_mlp_forward.argtypes = [_P, _P, ctypes.c_int32, _P]
+        L.cfr_mlp_backward.argtypes = [_P, _P, _P, ctypes.c_int32, _P]
+        L.cfr_mlp_adam.argtypes = [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+        L.cfr_mlp_gemm_stats.argtypes = [_P, _P, _P, _P, _P]
+        L.cfr_mlp_last_error.argtypes = [_P]
+        L.cfr_mlp_last_error.restype = ctypes.c_char_p
+        L.cfr_mlp_free.argtypes = [_P]
+        L.cfr_mlp_free.restype = None
+        for name in ("cfr_mlp_create", "cfr_mlp_set_params", "cfr_mlp_get_params", "cfr_mlp_get_grads",
+                     "cfr_mlp_forward", "cfr_mlp_backward", "cfr_mlp_adam", "cfr_mlp_gemm_stats"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("cfr_batch_load", "cfr_batch_iterate", "cfr_batch_set_tuning", "cfr_batch_autotune",
                      "cfr_batch_game_times", "cfr_batch_exploitability", "cfr_batch_get_state",
                      "cfr_batch_average_strategy", "cfr_batch_get_info"):
@@ -599,3 +615,110 @@ def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 512, 2048, -1), trial_ite
             json.dump(disk, f, indent=1)
         os.replace(tmp, cache_path)
     return dict(rec, us_per_iteration=best["us_per_iteration"], cached=False, trials=trials, key=key)
+
+
+# ---- learned leaf values: the BF16 value network (cfr_mlp_*) ---------------------------------------------
+
+def _check_mlp(st: int, handle=None):
+    if st != CFR_OK:
+        msg = lib().cfr_mlp_last_error(handle)
+        raise CfrError(st, msg.decode(errors="replace") if msg else "")
+
+
+class Mlp:
+    """A value network on the GPU (owns the C handle).  dims: input, hidden..., output widths."""
+
+    def __init__(self, handle, dims, device):
+        self.handle = handle
+        self.dims = list(dims)
+        self.device = device
+
+    @property
+    def num_params(self) -> int:
+        return int(lib().cfr_mlp_num_params(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().cfr_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def cfr_mlp_create(dims, device=None, stream=None) -> Mlp:
+    """A network of len(dims) - 1 linear layers (ReLU between them), parameters zero.  stream: None =
+    PyTorch's current stream on the device."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise CfrError(CFR_ERR_CUDA, "no CUDA device is available")
+    dev = torch.cuda.current_device() if device is None else int(device)
+    st_handle = torch.cuda.current_stream(dev).cuda_stream if stream is None else int(stream)
+    d = _arr(dims, np.int32)
+    h = _P()
+    _check_mlp(lib().cfr_mlp_create(d.ctypes.data, len(d) - 1, dev, st_handle, ctypes.byref(h)))
+    return Mlp(h, d.tolist(), dev)
+
+
+def cfr_mlp_set_params(m: Mlp, params):
+    p = _arr(params, np.float32)
+    _check_mlp(lib().cfr_mlp_set_params(m.handle, p.ctypes.data, p.size), m.handle)
+
+
+def cfr_mlp_get_params(m: Mlp) -> np.ndarray:
+    out = np.zeros(m.num_params, np.float32)
+    _check_mlp(lib().cfr_mlp_get_params(m.handle, out.ctypes.data, out.size), m.handle)
+    return out
+
+
+def cfr_mlp_get_grads(m: Mlp) -> np.ndarray:
+    out = np.zeros(m.num_params, np.float32)
+    _check_mlp(lib().cfr_mlp_get_grads(m.handle, out.ctypes.data, out.size), m.handle)
+    return out
+
+
+def _dev_f32(x, m: Mlp, width: int):
+    import torch
+
+    t = torch.as_tensor(x, dtype=torch.float32, device=f"cuda:{m.device}").contiguous()
+    if t.ndim != 2 or t.shape[1] != width:
+        raise ValueError(f"expected shape (batch, {width}), got {tuple(t.shape)}")
+    return t
+
+
+def cfr_mlp_forward(m: Mlp, x, out=None):
+    """y = the network at x (batch x dims[0]); x and the result are FP32 CUDA tensors."""
+    import torch
+
+    xt = _dev_f32(x, m, m.dims[0])
+    y = out if out is not None else torch.empty((xt.shape[0], m.dims[-1]), dtype=torch.float32, device=xt.device)
+    _check_mlp(lib().cfr_mlp_forward(m.handle, xt.data_ptr(), xt.shape[0], y.data_ptr()), m.handle)
+    return y
+
+
+def cfr_mlp_backward(m: Mlp, x, target, loss=None):
+    """Gradients of the mean squared error at (x, target) into the network's buffer; returns the loss
+    as a one-element FP64 CUDA tensor (not synchronised)."""
+    import torch
+
+    xt, tt = _dev_f32(x, m, m.dims[0]), _dev_f32(target, m, m.dims[-1])
+    if xt.shape[0] != tt.shape[0]:
+        raise ValueError("x and target need the same batch")
+    lt = loss if loss is not None else torch.zeros(1, dtype=torch.float64, device=xt.device)
+    _check_mlp(lib().cfr_mlp_backward(m.handle, xt.data_ptr(), tt.data_ptr(), xt.shape[0], lt.data_ptr()), m.handle)
+    return lt
+
+
+def cfr_mlp_adam(m: Mlp, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    _check_mlp(lib().cfr_mlp_adam(m.handle, float(lr), float(beta1), float(beta2), float(eps)), m.handle)
+
+
+def cfr_mlp_gemm_stats(m: Mlp) -> dict:
+    """Time (us) and FLOPs of the matrix products of the last forward and backward calls."""
+    v = [ctypes.c_double() for _ in range(4)]
+    _check_mlp(lib().cfr_mlp_gemm_stats(m.handle, *[ctypes.byref(x) for x in v]), m.handle)
+    return dict(fwd_us=v[0].value, fwd_flops=v[1].value, bwd_us=v[2].value, bwd_flops=v[3].value)

@@ -1,7 +1,8 @@
 """Builds libcfr_gb300.so in-tree with nvcc for sm_103a (GB300).
 
-Three translation units (the host layout builder, the single-game kernels + C ABI, the batched
-kernels + C ABI) compile in parallel and link into one shared library next to this file.
+Four translation units (the host layout builder, the single-game kernels + C ABI, the batched
+kernels + C ABI, the value-network kernels + C ABI) compile in parallel and link into one shared
+library next to this file.
 """
 from __future__ import annotations
 
@@ -17,7 +18,7 @@ LIB = os.path.join(HERE, "libcfr_gb300.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["cfr_api.cu", "batch_api.cu", "layout.cpp"]
+SOURCES = ["cfr_api.cu", "batch_api.cu", "mlp.cu", "layout.cpp"]
 HEADERS = ["kernels.cuh", "stream.cuh", "batch.cuh", "layout.hpp"]
 
 

@@ -1,0 +1,571 @@
+// Learned leaf values: the BF16 multilayer perceptron of include/cfr_gb300.h (cfr_mlp_*), trained and
+// evaluated with this file's kernels.
+//
+// Matrix products: one tiled tensor-core GEMM, C[M][N] = sum_k A(m, k) B(k, n), BF16 operands and FP32
+// accumulation (mma.sync m16n8k16), 128 x 128 x 32 block tiles staged through shared memory by cp.async
+// in a three-stage pipeline, eight warps of 64 x 32.  Each operand is read from global memory in its
+// stored orientation - the reduction index contiguous ("K-major") or the output index contiguous - and
+// ldmatrix (with .trans for the second case) builds the fragments, so the three products of a layer
+// need no transposed copies:
+//   forward        Z[b][o]  = sum_i X[b][i] W[o][i]      A K-major, B K-major ([o][i])
+//   weight grad    dW[o][i] = sum_b dZ[b][o] X[b][i]     A and B with the output index contiguous
+//   data grad      dX[b][i] = sum_o dZ[b][o] W[o][i]     A K-major, B with the output index contiguous
+// Every dimension is padded to a multiple of 128 (the batch too): padded weights and inputs are zero and
+// padded rows of the output gradient are zero, so padding never reaches a real result.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cfr_gb300.h"
+
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 32, kStages = 3, kThreads = 256;
+constexpr int kTileBytes = kBM * kBK * 2;   // one operand tile of one stage (both orientations)
+constexpr int kPad = 128;
+
+__host__ __device__ inline int64_t pad_to(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+// ---- shared-memory tile addressing (16-byte chunks XOR-swizzled so ldmatrix rows hit distinct banks)
+// K-major tile: 128 rows x 32 bf16 (64 bytes, 4 chunks per row).
+__device__ __forceinline__ uint32_t km_off(int row, int chunk) { return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4)); }
+// Output-index-contiguous tile: 32 rows (reduction) x 128 bf16 (256 bytes, 16 chunks per row).
+__device__ __forceinline__ uint32_t mm_off(int row, int chunk) { return (uint32_t)(row * 256 + ((chunk ^ (row & 7)) << 4)); }
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One operand tile (rows r0.., reduction k0..) of stage buffer `s` from global memory.  K-major: tile
+// rows are 128 output rows of 32 reduction values at &G[(r0 + r) ld + k0]; otherwise 32 reduction rows
+// of 128 output values at &G[(k0 + r) ld + r0].
+template <bool KM>
+__device__ __forceinline__ void load_tile(uint32_t s, const __nv_bfloat16 *G, int64_t ld, int64_t r0, int64_t k0) {
+#pragma unroll
+    for (int it = 0; it < (kBM * kBK / 8) / kThreads; ++it) {
+        const int i = (int)threadIdx.x + it * kThreads;
+        if (KM) {
+            const int r = i >> 2, c = i & 3;
+            cp_async16(s + km_off(r, c), G + (r0 + r) * ld + k0 + c * 8);
+        } else {
+            const int r = i >> 4, c = i & 15;
+            cp_async16(s + mm_off(r, c), G + (k0 + r) * ld + r0 + c * 8);
+        }
+    }
+}
+
+enum Epi { kEpiHidden = 0, kEpiOut = 1, kEpiStore = 2, kEpiMask = 3 };
+
+// C = A B over M x N (multiples of 128), reduction K (multiple of 32).  AKM / BKM: whether A / B is
+// stored K-major.  Epilogues: kEpiHidden bf16(ReLU(acc + bias[n])); kEpiOut acc + bias[n] (FP32);
+// kEpiStore acc (FP32); kEpiMask bf16(acc if mask[m][n] > 0 else 0).
+template <bool AKM, bool BKM, int EPI>
+__global__ void __launch_bounds__(kThreads) k_gemm(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B,
+                                                   int64_t ldb, void *C, int64_t ldc, int32_t K, const float *bias,
+                                                   const __nv_bfloat16 *mask) {
+    __shared__ __align__(128) unsigned char smem[kStages * 2 * kTileBytes];
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+    const int64_t m0 = (int64_t)blockIdx.y * kBM, n0 = (int64_t)blockIdx.x * kBN;
+    const int nk = K / kBK;
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+    auto sa = [&](int st) { return sbase + (uint32_t)(st * 2 * kTileBytes); };
+    auto sb = [&](int st) { return sbase + (uint32_t)(st * 2 * kTileBytes + kTileBytes); };
+#pragma unroll
+    for (int st = 0; st < kStages - 1; ++st) {
+        if (st < nk) {
+            load_tile<AKM>(sa(st), A, lda, m0, (int64_t)st * kBK);
+            load_tile<BKM>(sb(st), B, ldb, n0, (int64_t)st * kBK);
+        }
+        cp_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        cp_wait<kStages - 2>();
+        __syncthreads();
+        {   // prefetch kStages - 1 tiles ahead into the buffer computed on in the previous step
+            const int kn = kt + kStages - 1;
+            if (kn < nk) {
+                load_tile<AKM>(sa(kn % kStages), A, lda, m0, (int64_t)kn * kBK);
+                load_tile<BKM>(sb(kn % kStages), B, ldb, n0, (int64_t)kn * kBK);
+            }
+            cp_commit();
+        }
+        const uint32_t ta = sa(kt % kStages), tb = sb(kt % kStages);
+#pragma unroll
+        for (int kk = 0; kk < kBK; kk += 16) {
+            uint32_t af[4][4], bf[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi) {
+                if (AKM) {
+                    const int row = wm + mi * 16 + (lane & 15), chunk = (kk >> 3) + (lane >> 4);
+                    ldsm_x4(ta + km_off(row, chunk), af[mi][0], af[mi][1], af[mi][2], af[mi][3]);
+                } else {
+                    const int i = lane >> 3;
+                    const int row = kk + (i >> 1) * 8 + (lane & 7), chunk = (wm + mi * 16 + (i & 1) * 8) >> 3;
+                    ldsm_x4_t(ta + mm_off(row, chunk), af[mi][0], af[mi][1], af[mi][2], af[mi][3]);
+                }
+            }
+#pragma unroll
+            for (int nj = 0; nj < 2; ++nj) {
+                const int i = lane >> 3;
+                if (BKM) {
+                    const int row = wn + nj * 16 + (i >> 1) * 8 + (lane & 7), chunk = (kk >> 3) + (i & 1);
+                    ldsm_x4(tb + km_off(row, chunk), bf[2 * nj][0], bf[2 * nj][1], bf[2 * nj + 1][0], bf[2 * nj + 1][1]);
+                } else {
+                    const int row = kk + (i & 1) * 8 + (lane & 7), chunk = (wn + nj * 16 + (i >> 1) * 8) >> 3;
+                    ldsm_x4_t(tb + mm_off(row, chunk), bf[2 * nj][0], bf[2 * nj][1], bf[2 * nj + 1][0], bf[2 * nj + 1][1]);
+                }
+            }
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bf[ni][0], bf[ni][1]);
+        }
+    }
+    cp_wait<0>();
+    // epilogue: thread holds rows g, g + 8 and columns 2 t, 2 t + 1 of each 16 x 8 tile
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t m = m0 + wm + mi * 16 + g + h * 8, n = n0 + wn + ni * 8 + 2 * t;
+                float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+                if (EPI == kEpiHidden || EPI == kEpiOut) { v0 += bias[n]; v1 += bias[n + 1]; }
+                if (EPI == kEpiHidden) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                if (EPI == kEpiMask) {
+                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + m * ldc + n);
+                    if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                }
+                if (EPI == kEpiHidden || EPI == kEpiMask)
+                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + m * ldc + n) =
+                        __floats2bfloat162_rn(v0, v1);
+                else
+                    *reinterpret_cast<float2 *>(static_cast<float *>(C) + m * ldc + n) = make_float2(v0, v1);
+            }
+}
+
+// x [B][n] FP32 -> xp [Bp][np] BF16, zero outside.
+__global__ void k_pack_input(const float *x, int32_t B, int32_t n, __nv_bfloat16 *xp, int64_t Bp, int64_t np) {
+    const int64_t total = Bp * np;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / np, c = i % np;
+        xp[i] = __float2bfloat16_rn(r < B && c < n ? x[r * n + c] : 0.f);
+    }
+}
+
+// yp [Bp][np] -> y [B][n].
+__global__ void k_unpack_output(const float *yp, int64_t np, int32_t B, int32_t n, float *y) {
+    const int64_t total = (int64_t)B * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = yp[(i / n) * np + i % n];
+}
+
+// Mean squared error: dY = bf16(2 (y - t) / (B n)) on the real entries, 0 elsewhere; *loss += sum (y - t)^2
+// / (B n) (zeroed beforehand).
+__global__ void k_mse(const float *yp, int64_t np, const float *t, int32_t B, int32_t n, int64_t Bp,
+                      __nv_bfloat16 *dy, double *loss) {
+    __shared__ double red[32];
+    const int64_t total = Bp * np;
+    const double scale = 1.0 / ((double)B * n);
+    double part = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / np, c = i % np;
+        float d = 0.f;
+        if (r < B && c < n) {
+            d = yp[i] - t[r * n + c];
+            part += (double)d * d;
+        }
+        dy[i] = __float2bfloat16_rn((float)(2.0 * scale) * d);
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        part = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (threadIdx.x == 0 && loss) atomicAdd(loss, part * scale);
+    }
+}
+
+// db[c] = sum over the Bp rows of dz[r][c] (one thread per column; rows strided over blockDim.y).
+__global__ void k_bias_grad(const __nv_bfloat16 *dz, int64_t Bp, int64_t np, float *db) {
+    __shared__ float red[8][32];
+    const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    float s = 0.f;
+    for (int64_t r = threadIdx.y; r < Bp; r += blockDim.y) s += __bfloat162float(dz[r * np + c]);
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        for (int k = 1; k < (int)blockDim.y; ++k) s += red[k][threadIdx.x];
+        db[c] = s;
+    }
+}
+
+// Adam over the flat (padded) parameter array; the BF16 mirror follows the FP32 parameters.
+__global__ void k_adam(float *p, const float *g, float *m1, float *m2, __nv_bfloat16 *pb, int64_t n, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float a = b1 * m1[i] + (1.f - b1) * gi;
+        const float b = b2 * m2[i] + (1.f - b2) * gi * gi;
+        m1[i] = a;
+        m2[i] = b;
+        const float q = p[i] - lr * (a / c1) / (sqrtf(b / c2) + eps);
+        p[i] = q;
+        pb[i] = __float2bfloat16_rn(q);
+    }
+}
+
+__global__ void k_to_bf16(const float *p, __nv_bfloat16 *pb, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+thread_local std::string g_mlp_err;
+
+}  // namespace
+
+struct cfr_mlp {
+    int L = 0;
+    std::vector<int32_t> dims;       // real widths
+    std::vector<int64_t> pdims;      // padded widths
+    std::vector<int64_t> w_off, b_off;   // per layer: offsets of W [pdims[l+1]][pdims[l]] and b in the flat arrays
+    int64_t P = 0, num_params = 0;   // flat padded size, real parameter count
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
+    __nv_bfloat16 *pb = nullptr;
+    int64_t steps = 0;
+    // activations for the largest batch seen: acts[0] input, acts[l] hidden output of layer l - 1
+    int64_t cap = 0;
+    std::vector<__nv_bfloat16 *> acts, grads;   // grads[l]: dL/dZ of layer l (BF16, [cap][pdims[l + 1]])
+    float *yp = nullptr;
+    cudaEvent_t ev[4] = {};
+    double fwd_flops = 0, bwd_flops = 0;
+    bool fwd_timed = false, bwd_timed = false;
+    std::string err;
+    bool poisoned = false;
+};
+
+namespace {
+
+cfr_status merr(cfr_mlp *m, cfr_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (m) m->err = buf;
+    else g_mlp_err = buf;
+    return st;
+}
+
+#define MCK(call)                                                                                         \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) {                                                                          \
+            m->poisoned = true;                                                                           \
+            return merr(m, e_ == cudaErrorMemoryAllocation ? CFR_ERR_OOM : CFR_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                      \
+        }                                                                                                 \
+    } while (0)
+
+struct MDeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit MDeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+        if (dev >= 0 && dev != prev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~MDeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+cfr_status usable(cfr_mlp *m) {
+    if (!m) return merr(nullptr, CFR_ERR_INVALID, "network is NULL");
+    if (m->poisoned) return merr(m, CFR_ERR_STATE, "network is unusable after an earlier CUDA error: %s", m->err.c_str());
+    return CFR_OK;
+}
+
+int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
+cfr_status ensure_batch(cfr_mlp *m, int64_t Bp) {
+    if (Bp <= m->cap) return CFR_OK;
+    for (auto *a : m->acts) cudaFree(a);
+    for (auto *a : m->grads) cudaFree(a);
+    cudaFree(m->yp);
+    m->acts.assign((size_t)m->L, nullptr);
+    m->grads.assign((size_t)m->L, nullptr);
+    m->yp = nullptr;
+    m->cap = 0;
+    for (int l = 0; l < m->L; ++l) {
+        MCK(cudaMalloc(&m->acts[(size_t)l], sizeof(__nv_bfloat16) * (size_t)(Bp * m->pdims[(size_t)l])));
+        MCK(cudaMalloc(&m->grads[(size_t)l], sizeof(__nv_bfloat16) * (size_t)(Bp * m->pdims[(size_t)l + 1])));
+    }
+    MCK(cudaMalloc(&m->yp, sizeof(float) * (size_t)(Bp * m->pdims[(size_t)m->L])));
+    m->cap = Bp;
+    return CFR_OK;
+}
+
+template <bool AKM, bool BKM, int EPI>
+cudaError_t gemm(cudaStream_t st, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, void *C,
+                 int64_t ldc, int64_t M, int64_t N, int64_t K, const float *bias, const __nv_bfloat16 *mask) {
+    const dim3 grid((unsigned)(N / kBN), (unsigned)(M / kBM));
+    k_gemm<AKM, BKM, EPI><<<grid, kThreads, 0, st>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask);
+    return cudaGetLastError();
+}
+
+// The forward pass over Bp padded rows (input already packed into acts[0]); output in yp.
+cfr_status forward_padded(cfr_mlp *m, int64_t Bp, double *flops) {
+    double f = 0;
+    for (int l = 0; l < m->L; ++l) {
+        const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
+        const __nv_bfloat16 *W = m->pb + m->w_off[(size_t)l];
+        const float *b = m->p + m->b_off[(size_t)l];
+        if (l + 1 < m->L)
+            MCK((gemm<true, true, kEpiHidden>(m->stream, m->acts[(size_t)l], K, W, K, m->acts[(size_t)l + 1], N, Bp, N, K, b, nullptr)));
+        else
+            MCK((gemm<true, true, kEpiOut>(m->stream, m->acts[(size_t)l], K, W, K, m->yp, N, Bp, N, K, b, nullptr)));
+        f += 2.0 * (double)Bp * N * K;
+    }
+    *flops = f;
+    return CFR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cfr_status cfr_mlp_create(const int32_t *dims, int32_t num_layers, int32_t device, void *cuda_stream, cfr_mlp **out) {
+    if (!out) return merr(nullptr, CFR_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!dims || num_layers < 1 || num_layers > 8) return merr(nullptr, CFR_ERR_INVALID, "num_layers must be in [1, 8]");
+    for (int l = 0; l <= num_layers; ++l)
+        if (dims[l] < 1 || dims[l] > 8192) return merr(nullptr, CFR_ERR_INVALID, "dims[%d] = %d is outside [1, 8192]", l, dims[l]);
+    MDeviceGuard dg(device);
+    if (!dg.ok) return merr(nullptr, CFR_ERR_CUDA, "cannot select CUDA device %d", device);
+    cfr_mlp *m = new cfr_mlp();
+    cudaGetDevice(&m->device);
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    m->L = num_layers;
+    m->dims.assign(dims, dims + num_layers + 1);
+    for (int l = 0; l <= num_layers; ++l) m->pdims.push_back(pad_to(dims[l], kPad));
+    for (int l = 0; l < num_layers; ++l) {
+        m->w_off.push_back(m->P);
+        m->P += m->pdims[(size_t)l + 1] * m->pdims[(size_t)l];
+        m->b_off.push_back(m->P);
+        m->P += m->pdims[(size_t)l + 1];
+        m->num_params += (int64_t)dims[l + 1] * dims[l] + dims[l + 1];
+    }
+    auto fail = [&](cudaError_t e) {
+        std::string msg = cudaGetErrorString(e);
+        cudaGetLastError();
+        cfr_mlp_free(m);
+        return merr(nullptr, e == cudaErrorMemoryAllocation ? CFR_ERR_OOM : CFR_ERR_CUDA, "network allocation: %s", msg.c_str());
+    };
+    cudaError_t e = cudaSuccess;
+    for (float **a : {&m->p, &m->g, &m->m1, &m->m2})
+        if (e == cudaSuccess) e = cudaMalloc(a, sizeof(float) * (size_t)m->P);
+    if (e == cudaSuccess) e = cudaMalloc(&m->pb, sizeof(__nv_bfloat16) * (size_t)m->P);
+    for (float *a : {m->p, m->g, m->m1, m->m2})
+        if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, sizeof(float) * (size_t)m->P, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->pb, 0, sizeof(__nv_bfloat16) * (size_t)m->P, m->stream);
+    for (cudaEvent_t &ev : m->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return fail(e);
+    *out = m;
+    return CFR_OK;
+}
+
+int64_t cfr_mlp_num_params(const cfr_mlp *m) { return m ? m->num_params : 0; }
+
+cfr_status cfr_mlp_set_params(cfr_mlp *m, const float *params, int64_t len) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    if (!params || len < m->num_params) return merr(m, CFR_ERR_INVALID, "params needs %lld entries", (long long)m->num_params);
+    MDeviceGuard dg(m->device);
+    std::vector<float> flat((size_t)m->P, 0.f);
+    int64_t k = 0;
+    for (int l = 0; l < m->L; ++l) {
+        const int64_t in = m->dims[(size_t)l], o = m->dims[(size_t)l + 1], ld = m->pdims[(size_t)l];
+        for (int64_t r = 0; r < o; ++r)
+            for (int64_t c = 0; c < in; ++c) flat[(size_t)(m->w_off[(size_t)l] + r * ld + c)] = params[k++];
+        for (int64_t r = 0; r < o; ++r) flat[(size_t)(m->b_off[(size_t)l] + r)] = params[k++];
+    }
+    MCK(cudaMemcpyAsync(m->p, flat.data(), sizeof(float) * flat.size(), cudaMemcpyHostToDevice, m->stream));
+    k_to_bf16<<<grid_for(m->P), 256, 0, m->stream>>>(m->p, m->pb, m->P);
+    MCK(cudaGetLastError());
+    for (float *a : {m->m1, m->m2}) MCK(cudaMemsetAsync(a, 0, sizeof(float) * (size_t)m->P, m->stream));
+    m->steps = 0;
+    MCK(cudaStreamSynchronize(m->stream));
+    return CFR_OK;
+}
+
+static cfr_status get_flat(cfr_mlp *m, const float *dev, float *out, int64_t len) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    if (!out || len < m->num_params) return merr(m, CFR_ERR_INVALID, "output needs %lld entries", (long long)m->num_params);
+    MDeviceGuard dg(m->device);
+    std::vector<float> flat((size_t)m->P);
+    MCK(cudaMemcpyAsync(flat.data(), dev, sizeof(float) * flat.size(), cudaMemcpyDeviceToHost, m->stream));
+    MCK(cudaStreamSynchronize(m->stream));
+    int64_t k = 0;
+    for (int l = 0; l < m->L; ++l) {
+        const int64_t in = m->dims[(size_t)l], o = m->dims[(size_t)l + 1], ld = m->pdims[(size_t)l];
+        for (int64_t r = 0; r < o; ++r)
+            for (int64_t c = 0; c < in; ++c) out[k++] = flat[(size_t)(m->w_off[(size_t)l] + r * ld + c)];
+        for (int64_t r = 0; r < o; ++r) out[k++] = flat[(size_t)(m->b_off[(size_t)l] + r)];
+    }
+    return CFR_OK;
+}
+
+cfr_status cfr_mlp_get_params(cfr_mlp *m, float *params, int64_t len) { return get_flat(m, m ? m->p : nullptr, params, len); }
+cfr_status cfr_mlp_get_grads(cfr_mlp *m, float *grads, int64_t len) { return get_flat(m, m ? m->g : nullptr, grads, len); }
+
+cfr_status cfr_mlp_forward(cfr_mlp *m, const float *x, int32_t batch, float *y) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    if (!x || !y || batch < 1) return merr(m, CFR_ERR_INVALID, "x and y must be device arrays and batch >= 1");
+    MDeviceGuard dg(m->device);
+    const int64_t Bp = pad_to(batch, kPad);
+    if ((st = ensure_batch(m, Bp)) != CFR_OK) return st;
+    k_pack_input<<<grid_for(Bp * m->pdims[0]), 256, 0, m->stream>>>(x, batch, m->dims[0], m->acts[0], Bp, m->pdims[0]);
+    MCK(cudaGetLastError());
+    MCK(cudaEventRecord(m->ev[0], m->stream));
+    if ((st = forward_padded(m, Bp, &m->fwd_flops)) != CFR_OK) return st;
+    MCK(cudaEventRecord(m->ev[1], m->stream));
+    m->fwd_timed = true;
+    k_unpack_output<<<grid_for((int64_t)batch * m->dims[(size_t)m->L]), 256, 0, m->stream>>>(
+        m->yp, m->pdims[(size_t)m->L], batch, m->dims[(size_t)m->L], y);
+    MCK(cudaGetLastError());
+    return CFR_OK;
+}
+
+cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int32_t batch, double *loss) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    if (!x || !target || batch < 1) return merr(m, CFR_ERR_INVALID, "x and target must be device arrays and batch >= 1");
+    MDeviceGuard dg(m->device);
+    const int64_t Bp = pad_to(batch, kPad);
+    if ((st = ensure_batch(m, Bp)) != CFR_OK) return st;
+    const int L = m->L;
+    k_pack_input<<<grid_for(Bp * m->pdims[0]), 256, 0, m->stream>>>(x, batch, m->dims[0], m->acts[0], Bp, m->pdims[0]);
+    MCK(cudaGetLastError());
+    double f = 0;
+    if ((st = forward_padded(m, Bp, &f)) != CFR_OK) return st;
+    if (loss) MCK(cudaMemsetAsync(loss, 0, sizeof(double), m->stream));
+    const int64_t nL = m->pdims[(size_t)L];
+    k_mse<<<grid_for(Bp * nL), 256, 0, m->stream>>>(m->yp, nL, target, batch, m->dims[(size_t)L], Bp,
+                                                    m->grads[(size_t)L - 1], loss);
+    MCK(cudaGetLastError());
+    MCK(cudaEventRecord(m->ev[2], m->stream));
+    double fb = 0;
+    for (int l = L - 1; l >= 0; --l) {
+        const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
+        const __nv_bfloat16 *dz = m->grads[(size_t)l];
+        // dW[o][i] = sum_b dZ[b][o] X[b][i]
+        MCK((gemm<false, false, kEpiStore>(m->stream, dz, N, m->acts[(size_t)l], K, m->g + m->w_off[(size_t)l], K, N, K, Bp,
+                                           nullptr, nullptr)));
+        fb += 2.0 * (double)N * K * Bp;
+        if (l > 0) {   // dZ of layer l - 1 = (dZ W) masked where its ReLU output was 0
+            MCK((gemm<true, false, kEpiMask>(m->stream, dz, N, m->pb + m->w_off[(size_t)l], K, m->grads[(size_t)l - 1], K, Bp, K,
+                                             N, nullptr, m->acts[(size_t)l])));
+            fb += 2.0 * (double)Bp * K * N;
+        }
+    }
+    MCK(cudaEventRecord(m->ev[3], m->stream));
+    m->bwd_flops = fb;
+    m->bwd_timed = true;
+    for (int l = 0; l < L; ++l) {
+        const int64_t N = m->pdims[(size_t)l + 1];
+        k_bias_grad<<<(unsigned)(N / 32), dim3(32, 8), 0, m->stream>>>(m->grads[(size_t)l], Bp, N, m->g + m->b_off[(size_t)l]);
+        MCK(cudaGetLastError());
+    }
+    return CFR_OK;
+}
+
+cfr_status cfr_mlp_adam(cfr_mlp *m, float lr, float beta1, float beta2, float eps) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return merr(m, CFR_ERR_INVALID, "need lr >= 0, beta1 and beta2 in [0, 1), eps > 0");
+    MDeviceGuard dg(m->device);
+    m->steps += 1;
+    const float c1 = (float)(1.0 - std::pow((double)beta1, (double)m->steps));
+    const float c2 = (float)(1.0 - std::pow((double)beta2, (double)m->steps));
+    k_adam<<<grid_for(m->P), 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, m->pb, m->P, lr, beta1, beta2, eps, c1, c2);
+    MCK(cudaGetLastError());
+    return CFR_OK;
+}
+
+cfr_status cfr_mlp_gemm_stats(cfr_mlp *m, double *fwd_us, double *fwd_flops, double *bwd_us, double *bwd_flops) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    MDeviceGuard dg(m->device);
+    MCK(cudaStreamSynchronize(m->stream));
+    float a = 0.f, b = 0.f;
+    if (m->fwd_timed) MCK(cudaEventElapsedTime(&a, m->ev[0], m->ev[1]));
+    if (m->bwd_timed) MCK(cudaEventElapsedTime(&b, m->ev[2], m->ev[3]));
+    if (fwd_us) *fwd_us = 1e3 * a;
+    if (fwd_flops) *fwd_flops = m->fwd_timed ? m->fwd_flops : 0.0;
+    if (bwd_us) *bwd_us = 1e3 * b;
+    if (bwd_flops) *bwd_flops = m->bwd_timed ? m->bwd_flops : 0.0;
+    return CFR_OK;
+}
+
+const char *cfr_mlp_last_error(const cfr_mlp *m) { return m ? m->err.c_str() : g_mlp_err.c_str(); }
+
+void cfr_mlp_free(cfr_mlp *m) {
+    if (!m) return;
+    MDeviceGuard dg(m->device);
+    cudaStreamSynchronize(m->stream);
+    for (void *a : {(void *)m->p, (void *)m->g, (void *)m->m1, (void *)m->m2, (void *)m->pb, (void *)m->yp})
+        if (a) cudaFree(a);
+    for (auto *a : m->acts) if (a) cudaFree(a);
+    for (auto *a : m->grads) if (a) cudaFree(a);
+    for (cudaEvent_t ev : m->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete m;
+}
+
+}  // extern "C"
