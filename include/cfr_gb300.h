@@ -205,6 +205,33 @@ cfr_status cfr_set_state(cfr_solver *s, const double *cum_regret, const double *
  * depths are fused and the solver was loaded without cfr_config.record_nodes.  Test hook. */
 cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *cf_reach2, int64_t len);
 
+/* ---- depth-limited solving: leaves whose utility is refreshed between iterations -------------------
+ * A depth-limited game ends in "leaves": terminals standing for the subtrees cut below them, whose
+ * player-1 utility is set from outside (a value network) as the strategies change.  These calls keep
+ * the refresh on the device: cfr_gather_ranges writes both players' ranges at the cut (products of
+ * current-strategy probabilities along each public path, Eq. 4) into the network's input, and
+ * cfr_set_leaf_values copies the network's output into the leaves' utilities.  Both are queued on the
+ * solver's stream and take effect from the next iteration. */
+
+/* Registers the range program: segment k (a range vector: one player at one cut public node) has
+ * entries seg_entries[k] .. seg_entries[k + 1] - 1, written to out[seg_dst[k] + 0, 1, ...] by
+ * cfr_gather_ranges; entry e is the product of the current strategy over the caller slots
+ * slots[entry_prod[e] .. entry_prod[e + 1] - 1] (empty: 1), and each segment is divided by its sum
+ * (uniform if 0).  seg_entries and entry_prod start at 0 and do not decrease.  Host arrays, copied. */
+cfr_status cfr_set_range_program(cfr_solver *s, int64_t num_segments, const int64_t *seg_dst, const int64_t *seg_entries,
+                                 const int64_t *entry_prod, const int32_t *slots);
+
+/* Runs the range program on the current strategy; out is a DEVICE FP32 array. */
+cfr_status cfr_gather_ranges(cfr_solver *s, float *out);
+
+/* Registers num_leaves terminal nodes (caller ids) and, per leaf, the index of its value in the array
+ * cfr_set_leaf_values reads.  Host arrays, copied.  CFR_ERR_INVALID if a node is not a terminal. */
+cfr_status cfr_set_leaves(cfr_solver *s, const int32_t *nodes, const int64_t *src_index, int64_t num_leaves);
+
+/* Sets each registered leaf's player-1 utility to scale * src[src_index] (src: DEVICE FP32 array);
+ * player 2's is its negation. */
+cfr_status cfr_set_leaf_values(cfr_solver *s, const float *src, double scale);
+
 /* Expected payoff of player 1 under the last iteration's profile sigma^(T): u-check(sigma^(T), v_0, 1)
  * of Eq. 1 at the root, which equals u-hat(sigma^(T), 1) of Section 2.2.  One scalar; synchronises
  * the stream (a per-iteration progress read).  0 before the first iteration. */

@@ -156,6 +156,12 @@ def lib():
         L.cfr_batch_last_error.restype = ctypes.c_char_p
         L.cfr_batch_free.argtypes = [_P]
         L.cfr_batch_free.restype = None
+        L.cfr_set_range_program.argtypes = [_P, ctypes.c_int64, _P, _P, _P, _P]
+        L.cfr_gather_ranges.argtypes = [_P, _P]
+        L.cfr_set_leaves.argtypes = [_P, _P, _P, ctypes.c_int64]
+        L.cfr_set_leaf_values.argtypes = [_P, _P, ctypes.c_double]
+        for name in ("cfr_set_range_program", "cfr_gather_ranges", "cfr_set_leaves", "cfr_set_leaf_values"):
+            getattr(L, name).restype = ctypes.c_int
         L.cfr_mlp_create.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.POINTER(_P)]
         L.cfr_mlp_num_params.argtypes = [_P]
         L.cfr_mlp_num_params.restype = ctypes.c_int64
@@ -365,6 +371,32 @@ def cfr_phase_times(s: "Solver") -> list:
              CFR_PHASE_FUSED: "fused depths {}+", CFR_PHASE_UPDATE: "update", CFR_PHASE_OWN: "own reaches"}
     return [dict(name=names[int(k)].format(int(d)), kind=int(k), depth=int(d), us=float(u), bytes=float(b))
             for k, d, u, b in zip(kind, depth, us, by)]
+
+
+def cfr_set_range_program(s: "Solver", seg_dst, seg_entries, entry_prod, slots):
+    """Registers the range program of cfr_gather_ranges (include/cfr_gb300.h)."""
+    d, e, p = _arr(seg_dst, np.int64), _arr(seg_entries, np.int64), _arr(entry_prod, np.int64)
+    sl = _arr(slots, np.int32)
+    _check(lib().cfr_set_range_program(s.handle, d.size, d.ctypes.data, e.ctypes.data, p.ctypes.data,
+                                       sl.ctypes.data if sl.size else None), s.handle)
+
+
+def cfr_gather_ranges(s: "Solver", out):
+    """Writes the range program's output into out (an FP32 CUDA tensor), queued on the solver's stream."""
+    _check(lib().cfr_gather_ranges(s.handle, out.data_ptr()), s.handle)
+
+
+def cfr_set_leaves(s: "Solver", nodes, src_index):
+    n, si = _arr(nodes, np.int32), _arr(src_index, np.int64)
+    if n.size != si.size:
+        raise ValueError("nodes and src_index need the same length")
+    _check(lib().cfr_set_leaves(s.handle, n.ctypes.data if n.size else None, si.ctypes.data if si.size else None,
+                                n.size), s.handle)
+
+
+def cfr_set_leaf_values(s: "Solver", src, scale: float = 1.0):
+    """Leaf utilities from src (an FP32 CUDA tensor), queued on the solver's stream."""
+    _check(lib().cfr_set_leaf_values(s.handle, src.data_ptr(), float(scale)), s.handle)
 
 
 def cfr_get_info(s: "Solver") -> dict:

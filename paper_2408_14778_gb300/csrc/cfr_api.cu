@@ -92,6 +92,10 @@ struct cfr_solver {
     int32_t *tail_tiles = nullptr;                        // k_tail_stream: 8 words per tile (TailTiles::tm)
     int32_t ntail_tiles = 0, tl_grid[3] = {0, 0, 0};
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
+    // depth-limited solving (cfr_set_range_program, cfr_set_leaves)
+    int64_t rp_nseg = 0, nleaves = 0;
+    int64_t *rp_dst = nullptr, *rp_ent = nullptr, *rp_prod = nullptr, *leaf_src = nullptr;
+    int32_t *rp_slots = nullptr, *leaf_t = nullptr;
     int64_t kernel_launches = 0;
     int64_t iteration = 0;
     cudaGraph_t graph = nullptr;
@@ -1093,6 +1097,108 @@ cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *c
         for (int64_t j = 0; j < s->Nd; ++j) outs[i][s->dnode_user[j]] = tmp[j];
         for (int64_t k = 0; k < s->Nt; ++k) outs[i][s->tnode_user[k]] = nan;
     }
+    return CFR_OK;
+}
+
+static bool nondecreasing_from_zero(const int64_t *a, int64_t n) {
+    if (a[0] != 0) return false;
+    for (int64_t i = 0; i < n; ++i)
+        if (a[i + 1] < a[i]) return false;
+    return true;
+}
+
+cfr_status cfr_set_range_program(cfr_solver *s, int64_t num_segments, const int64_t *seg_dst, const int64_t *seg_entries,
+                                 const int64_t *entry_prod, const int32_t *slots) {
+    TRY(check_usable(s));
+    if (num_segments < 0 || (num_segments > 0 && (!seg_dst || !seg_entries || !entry_prod)))
+        return set_err(s, CFR_ERR_INVALID, "range program: malformed arrays");
+    if (num_segments == 0) { s->rp_nseg = 0; return CFR_OK; }
+    if (!nondecreasing_from_zero(seg_entries, num_segments))
+        return set_err(s, CFR_ERR_INVALID, "range program: seg_entries must start at 0 and not decrease");
+    const int64_t E = seg_entries[num_segments];
+    if (!nondecreasing_from_zero(entry_prod, E))
+        return set_err(s, CFR_ERR_INVALID, "range program: entry_prod must start at 0 and not decrease");
+    const int64_t nslots = entry_prod[E];
+    if (nslots > 0 && !slots) return set_err(s, CFR_ERR_INVALID, "range program: slots is NULL");
+    for (int64_t k = 0; k < num_segments; ++k)
+        if (seg_dst[k] < 0) return set_err(s, CFR_ERR_INVALID, "range program: seg_dst[%lld] < 0", (long long)k);
+    DeviceGuard dg(s->device);
+    std::vector<int32_t> q2u((size_t)std::max<int64_t>(s->Q, 1)), u2q((size_t)std::max<int64_t>(s->Q, 1), -1);
+    CK(cudaMemcpyAsync(q2u.data(), s->q_int2user, sizeof(int32_t) * (size_t)s->Q, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int64_t q = 0; q < s->Q; ++q) u2q[(size_t)q2u[(size_t)q]] = (int32_t)q;
+    std::vector<int32_t> sl((size_t)nslots);
+    for (int64_t i = 0; i < nslots; ++i) {
+        if (slots[i] < 0 || slots[i] >= s->Q) return set_err(s, CFR_ERR_INVALID, "range program: slot %d out of range", slots[i]);
+        sl[(size_t)i] = u2q[(size_t)slots[i]];
+    }
+    TRY(alloc_n(s, &s->rp_dst, num_segments)); TRY(alloc_n(s, &s->rp_ent, num_segments + 1));
+    TRY(alloc_n(s, &s->rp_prod, E + 1)); TRY(alloc_n(s, &s->rp_slots, nslots));
+    TRY(upload(s, s->rp_dst, std::vector<int64_t>(seg_dst, seg_dst + num_segments)));
+    TRY(upload(s, s->rp_ent, std::vector<int64_t>(seg_entries, seg_entries + num_segments + 1)));
+    TRY(upload(s, s->rp_prod, std::vector<int64_t>(entry_prod, entry_prod + E + 1)));
+    TRY(upload(s, s->rp_slots, sl));
+    CK(cudaStreamSynchronize(s->stream));
+    s->rp_nseg = num_segments;
+    return CFR_OK;
+}
+
+cfr_status cfr_gather_ranges(cfr_solver *s, float *out) {
+    TRY(check_usable(s));
+    if (s->rp_nseg == 0) return CFR_OK;
+    if (!out) return set_err(s, CFR_ERR_INVALID, "out is NULL");
+    DeviceGuard dg(s->device);
+    const int grid = (int)std::min<int64_t>((s->rp_nseg + 127) / 128, 4096);
+    if (s->cfg.precision == CFR_FP64)
+        k_ranges<double><<<grid, 128, 0, s->stream>>>(static_cast<const double *>(s->sigma), s->rp_dst, s->rp_ent, s->rp_prod,
+                                                      s->rp_slots, s->rp_nseg, out);
+    else
+        k_ranges<float><<<grid, 128, 0, s->stream>>>(static_cast<const float *>(s->sigma), s->rp_dst, s->rp_ent, s->rp_prod,
+                                                     s->rp_slots, s->rp_nseg, out);
+    CK_LAUNCH();
+    s->kernel_launches += 1;
+    return CFR_OK;
+}
+
+cfr_status cfr_set_leaves(cfr_solver *s, const int32_t *nodes, const int64_t *src_index, int64_t num_leaves) {
+    TRY(check_usable(s));
+    if (num_leaves < 0 || (num_leaves > 0 && (!nodes || !src_index)))
+        return set_err(s, CFR_ERR_INVALID, "leaves: malformed arrays");
+    std::vector<int32_t> node2t((size_t)std::max<int64_t>(s->N, 1), -1);
+    for (int64_t k = 0; k < s->Nt; ++k) node2t[(size_t)s->tnode_user[(size_t)k]] = (int32_t)k;
+    std::vector<int32_t> t((size_t)num_leaves);
+    for (int64_t i = 0; i < num_leaves; ++i) {
+        if (nodes[i] < 0 || nodes[i] >= s->N || node2t[(size_t)nodes[i]] < 0)
+            return set_err(s, CFR_ERR_INVALID, "leaves: node %d is not a terminal", nodes[i]);
+        if (src_index[i] < 0) return set_err(s, CFR_ERR_INVALID, "leaves: src_index[%lld] < 0", (long long)i);
+        t[(size_t)i] = node2t[(size_t)nodes[i]];
+    }
+    DeviceGuard dg(s->device);
+    s->nleaves = 0;
+    if (num_leaves == 0) return CFR_OK;
+    TRY(alloc_n(s, &s->leaf_t, num_leaves));
+    TRY(alloc_n(s, &s->leaf_src, num_leaves));
+    TRY(upload(s, s->leaf_t, t));
+    TRY(upload(s, s->leaf_src, std::vector<int64_t>(src_index, src_index + num_leaves)));
+    CK(cudaStreamSynchronize(s->stream));
+    s->nleaves = num_leaves;
+    return CFR_OK;
+}
+
+cfr_status cfr_set_leaf_values(cfr_solver *s, const float *src, double scale) {
+    TRY(check_usable(s));
+    if (s->nleaves == 0) return CFR_OK;
+    if (!src) return set_err(s, CFR_ERR_INVALID, "src is NULL");
+    DeviceGuard dg(s->device);
+    const int grid = (int)std::min<int64_t>((s->nleaves + 255) / 256, 4096);
+    if (s->cfg.precision == CFR_FP64)
+        k_set_leaves<double><<<grid, 256, 0, s->stream>>>(static_cast<double *>(s->util), s->util64, s->leaf_t, s->leaf_src,
+                                                          src, scale, s->nleaves);
+    else
+        k_set_leaves<float><<<grid, 256, 0, s->stream>>>(static_cast<float *>(s->util), s->util64, s->leaf_t, s->leaf_src,
+                                                         src, scale, s->nleaves);
+    CK_LAUNCH();
+    s->kernel_launches += 1;
     return CFR_OK;
 }
 

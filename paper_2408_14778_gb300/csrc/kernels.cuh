@@ -890,6 +890,42 @@ __global__ void k_regret_match_all(real *sigma, const double *R, const int32_t *
     regret_match(sigma, R, qbase[h], qbase[h + 1] - qbase[h]);
 }
 
+// ---- depth-limited solving: leaf refresh ----------------------------------------------------------
+// Range program: segment s writes its entries e in [ent[s], ent[s + 1]) to out[dst[s] + e - ent[s]],
+// each the product of sigma over the internal slots slots[prod[e] .. prod[e + 1]) (a player's own
+// reach of one private state at one public node, Eq. 4), then divides the segment by its sum (uniform
+// when the sum is 0).  One thread per segment.
+template <typename real>
+__global__ void k_ranges(const real *sigma, const int64_t *dst, const int64_t *ent, const int64_t *prod,
+                         const int32_t *slots, int64_t nseg, float *out) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = ent[s], e1 = ent[s + 1];
+        double sum = 0.0;
+        for (int64_t e = e0; e < e1; ++e) {
+            double p = 1.0;
+            for (int64_t i = prod[e]; i < prod[e + 1]; ++i) p *= (double)sigma[slots[i]];
+            sum += p;
+        }
+        for (int64_t e = e0; e < e1; ++e) {
+            double p = 1.0;
+            for (int64_t i = prod[e]; i < prod[e + 1]; ++i) p *= (double)sigma[slots[i]];
+            out[dst[s] + (e - e0)] = sum > 0.0 ? (float)(p / sum) : (float)(1.0 / (double)(e1 - e0));
+        }
+    }
+}
+
+// Leaf refresh: the utility of registered terminal t[i] becomes scale * src[src_index[i]] (both the
+// working-precision copy and the FP64 one the best response reads).
+template <typename real>
+__global__ void k_set_leaves(real *util, double *util64, const int32_t *t, const int64_t *src_index, const float *src,
+                             double scale, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = scale * (double)src[src_index[i]];
+        util[t[i]] = (real)v;
+        util64[t[i]] = v;
+    }
+}
+
 // out[user slot] = src[internal slot], widened to double.
 template <typename T>
 __global__ void k_gather_q(const T *src, const int32_t *q_int2user, double *out, int32_t Q) {
