@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-exploitability-1e-3 measurement")
+    ap.add_argument("--no-leaf", action="store_true", help="skip the learned-leaf depth-limited measurement")
+    ap.add_argument("--leaf-samples-per-node", type=int, default=64)
+    ap.add_argument("--leaf-train-steps", type=int, default=3000)
     ap.add_argument("--batched-games", type=int, default=4096,
                     help="subgames of the batched measurement (0: skip it)")
     return ap.parse_args()
@@ -188,6 +191,7 @@ TTT_TARGET = 1e-3          # exploitability (NashConv / 2), absolute, payoff uni
 TTT_CHECK = 25             # iterations between exploitability evaluations
 TTT_MAX_ITERS = 100000
 TTT_ORACLE_SECONDS = 60.0
+LEAF_BLUEPRINT_ITERS = 4000
 
 
 def _ttt_run(step, expl, max_iters: int, max_seconds: float) -> dict:
@@ -240,6 +244,92 @@ def time_to_exploitability(args, local: int) -> dict:
                          lambda: o.exploitability()[1], TTT_MAX_ITERS, TTT_ORACLE_SECONDS)
             r.update(nodes=g.num_nodes, cores=1, capped_at_seconds=TTT_ORACLE_SECONDS)
             out[f"oracle_{name}"] = r
+    return out
+
+
+def measured_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = json.load(open(p)).get("bf16_tflops")
+        if v:
+            return float(v), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except (OSError, ValueError):
+        pass
+    return 1900.0, "fallback (1.9 PFLOP/s bf16 burst, earlier GB300 measurement)"
+
+
+def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
+    """Depth-limited CFR+ with the learned leaf network on the 13-rank fold/showdown game (2e6 nodes) cut
+    at game depth 6: training samples from full-depth GPU CFR+ solves of the cut subgames under random
+    ranges, the network (402 -> 3 x 1024 ReLU -> 338, BF16 tensor-core kernels) trained by the library,
+    then the depth-limited solve with the leaves refreshed on the device every iteration.  Its
+    exploitability is measured in the depth-limited game and, in the full game, with the strategy of a
+    full-depth CFR+ solve below the cut; an untrained network of the same shape is the baseline."""
+    import numpy as np
+    import torch
+
+    import gamegen
+    import paper_2408_14778_gb300 as cfr
+    from paper_2408_14778_gb300 import depth_limited as dl
+
+    out = {"game": "rank13_depth10 (13-rank fold/showdown, 156 deals, depth 10)", "cut_game_depth": 6,
+           "variant": "cfr+ linear averaging, simultaneous", "target": TTT_TARGET, "check_every": TTT_CHECK}
+    g = gamegen.config("rank13_depth10", seed=args.seed)
+    t0 = time.perf_counter()
+    cut = dl.cut_game(g, depth=5, seed=args.seed)
+    out["cut"] = {"full_nodes": g.num_nodes, "depth_limited_nodes": int(cut.game.parent.shape[0]),
+                  "cut_public_nodes": int(cut.cut_nodes.size), "leaves": int(cut.leaf_nodes.size),
+                  "host_seconds": time.perf_counter() - t0}
+    # full-depth CFR+: the strategy below the cut (and the full-depth reference for the comparison)
+    s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, device=local)
+    cfr.cfr_synchronize(s)
+    t0 = time.perf_counter()
+    cfr.cfr_iterate(s, LEAF_BLUEPRINT_ITERS)
+    ex_full = cfr.cfr_exploitability(s)[1]
+    out["full_depth"] = {"iterations": LEAF_BLUEPRINT_ITERS, "seconds": time.perf_counter() - t0,
+                         "exploitability": ex_full,
+                         "time_to_1e-3": (ttt or {}).get("gpu_rank13_depth10")}
+    below = cfr.cfr_average_strategy(s)
+    s.close()
+    t0 = time.perf_counter()
+    X, Y = dl.generate_samples(cut, per_node=args.leaf_samples_per_node, iterations=300, seed=args.seed,
+                               device=local)
+    out["samples"] = {"count": int(X.shape[0]), "per_cut_node": args.leaf_samples_per_node,
+                      "solver_iterations": 300, "seconds": time.perf_counter() - t0,
+                      "source": "full-depth GPU CFR+ on the cut subgames under random (Dirichlet) ranges"}
+    net = dl.make_network(seed=args.seed, device=local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = dl.train(net, X, Y, steps=args.leaf_train_steps, batch=1024, lr=1e-3, seed=args.seed, device=local)
+    torch.cuda.synchronize()
+    out["training"] = {"steps": args.leaf_train_steps, "batch": 1024, "optimizer": "adam, lr 1e-3 decaying to 1e-4",
+                       "seconds": time.perf_counter() - t0, "mse_first": hist[0], "mse_last": hist[-1]}
+    # the network's matrix products at a batch of 4096
+    xb = torch.randn(4096, 402, device=f"cuda:{local}")
+    tb = torch.randn(4096, 338, device=f"cuda:{local}")
+    for _ in range(5):
+        cfr.cfr_mlp_forward(net, xb)
+        cfr.cfr_mlp_backward(net, xb, tb)
+    st = cfr.cfr_mlp_gemm_stats(net)
+    peak, src = measured_bf16_peak()
+    fwd, bwd = st["fwd_flops"] / st["fwd_us"] / 1e6, st["bwd_flops"] / st["bwd_us"] / 1e6
+    out["network_gemm"] = {"batch": 4096, "forward_tflops": fwd, "backward_tflops": bwd, "peak_tflops": peak,
+                           "peak_source": src, "forward_frac": fwd / peak, "backward_frac": bwd / peak,
+                           "instruction": "mma.sync m16n8k16 bf16, fp32 accumulate"}
+    untrained = dl.make_network(seed=args.seed + 1, device=local)
+    for name, model, ranges in (("trained", net, cfr.CFR_AVERAGE_STRATEGY),
+                                ("trained_current_ranges", net, cfr.CFR_CURRENT_STRATEGY),
+                                ("untrained", untrained, cfr.CFR_AVERAGE_STRATEGY)):
+        d = dl.DepthLimitedSolver(cut, model, refresh=1, device=local, ranges=ranges)
+        cfr.cfr_synchronize(d.s)
+        r = _ttt_run(d.iterate, d.exploitability, TTT_MAX_ITERS, 20.0)
+        r["full_game_exploitability"] = dl.full_game_exploitability(
+            g, dl.combined_strategy(cut, d.average_strategy(), below), device=local)
+        r["leaf_ranges"] = "average strategy" if ranges == cfr.CFR_AVERAGE_STRATEGY else "current strategy"
+        r["note"] = ("exploitability: in the depth-limited game with the leaves' current values; "
+                     "full_game_exploitability: in the full game, full-depth strategy below the cut")
+        out[f"depth_limited_{name}"] = r
+        d.close()
     return out
 
 
@@ -490,6 +580,9 @@ def run_ours(args, world, rank, local):
     batched = None
     if rank == 0 and world == 1 and args.batched_games > 0:
         batched = batched_measurement(args, local)
+    leaf = None
+    if rank == 0 and world == 1 and not args.no_leaf:
+        leaf = learned_leaf_measurement(args, local, ttt)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -501,6 +594,7 @@ def run_ours(args, world, rank, local):
                 "parallelism": "replicas" if world > 1 else "single GPU"}
         line["time_to_exploitability"] = ttt
         line["batched"] = batched
+        line["learned_leaf"] = leaf
         line["phase_us"] = phase_us
         print(json.dumps(line), flush=True)
     del np

@@ -209,7 +209,7 @@ cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *c
  * A depth-limited game ends in "leaves": terminals standing for the subtrees cut below them, whose
  * player-1 utility is set from outside (a value network) as the strategies change.  These calls keep
  * the refresh on the device: cfr_gather_ranges writes both players' ranges at the cut (products of
- * current-strategy probabilities along each public path, Eq. 4) into the network's input, and
+ * strategy probabilities along each public path, Eq. 4) into the network's input, and
  * cfr_set_leaf_values copies the network's output into the leaves' utilities.  Both are queued on the
  * solver's stream and take effect from the next iteration. */
 
@@ -221,8 +221,11 @@ cfr_status cfr_get_nodes(cfr_solver *s, double *u1, double *cf_reach1, double *c
 cfr_status cfr_set_range_program(cfr_solver *s, int64_t num_segments, const int64_t *seg_dst, const int64_t *seg_entries,
                                  const int64_t *entry_prod, const int32_t *slots);
 
-/* Runs the range program on the current strategy; out is a DEVICE FP32 array. */
-cfr_status cfr_gather_ranges(cfr_solver *s, float *out);
+/* Runs the range program on the current strategy sigma^(T+1) (CFR_CURRENT_STRATEGY) or on the average
+ * strategy (CFR_AVERAGE_STRATEGY, Eq. 15); out is a DEVICE FP32 array. */
+#define CFR_CURRENT_STRATEGY 0
+#define CFR_AVERAGE_STRATEGY 1
+cfr_status cfr_gather_ranges(cfr_solver *s, float *out, int32_t strategy);
 
 /* Registers num_leaves terminal nodes (caller ids) and, per leaf, the index of its value in the array
  * cfr_set_leaf_values reads.  Host arrays, copied.  CFR_ERR_INVALID if a node is not a terminal. */

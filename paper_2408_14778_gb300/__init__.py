@@ -157,7 +157,7 @@ def lib():
         L.cfr_batch_free.argtypes = [_P]
         L.cfr_batch_free.restype = None
         L.cfr_set_range_program.argtypes = [_P, ctypes.c_int64, _P, _P, _P, _P]
-        L.cfr_gather_ranges.argtypes = [_P, _P]
+        L.cfr_gather_ranges.argtypes = [_P, _P, ctypes.c_int32]
         L.cfr_set_leaves.argtypes = [_P, _P, _P, ctypes.c_int64]
         L.cfr_set_leaf_values.argtypes = [_P, _P, ctypes.c_double]
         for name in ("cfr_set_range_program", "cfr_gather_ranges", "cfr_set_leaves", "cfr_set_leaf_values"):
@@ -381,9 +381,13 @@ def cfr_set_range_program(s: "Solver", seg_dst, seg_entries, entry_prod, slots):
                                        sl.ctypes.data if sl.size else None), s.handle)
 
 
-def cfr_gather_ranges(s: "Solver", out):
-    """Writes the range program's output into out (an FP32 CUDA tensor), queued on the solver's stream."""
-    _check(lib().cfr_gather_ranges(s.handle, out.data_ptr()), s.handle)
+CFR_CURRENT_STRATEGY, CFR_AVERAGE_STRATEGY = 0, 1
+
+
+def cfr_gather_ranges(s: "Solver", out, strategy: int = CFR_CURRENT_STRATEGY):
+    """Writes the range program's output into out (an FP32 CUDA tensor), queued on the solver's stream,
+    from the current (CFR_CURRENT_STRATEGY) or the average strategy (CFR_AVERAGE_STRATEGY)."""
+    _check(lib().cfr_gather_ranges(s.handle, out.data_ptr(), int(strategy)), s.handle)
 
 
 def cfr_set_leaves(s: "Solver", nodes, src_index):

@@ -1143,12 +1143,25 @@ cfr_status cfr_set_range_program(cfr_solver *s, int64_t num_segments, const int6
     return CFR_OK;
 }
 
-cfr_status cfr_gather_ranges(cfr_solver *s, float *out) {
+cfr_status cfr_gather_ranges(cfr_solver *s, float *out, int32_t strategy) {
     TRY(check_usable(s));
+    if (strategy != CFR_CURRENT_STRATEGY && strategy != CFR_AVERAGE_STRATEGY)
+        return set_err(s, CFR_ERR_INVALID, "strategy must be CFR_CURRENT_STRATEGY or CFR_AVERAGE_STRATEGY");
     if (s->rp_nseg == 0) return CFR_OK;
     if (!out) return set_err(s, CFR_ERR_INVALID, "out is NULL");
     DeviceGuard dg(s->device);
     const int grid = (int)std::min<int64_t>((s->rp_nseg + 127) / 128, 4096);
+    if (strategy == CFR_AVERAGE_STRATEGY) {
+        if (!s->avg) TRY(alloc_n(s, &s->avg, s->Q));
+        if (s->H > 0) {
+            k_average<<<nblocks(s->H), kBlock, 0, s->stream>>>(s->S, s->sigma064, s->qbase, s->iplayer, s->avg, s->H);
+            CK_LAUNCH();
+        }
+        k_ranges<double><<<grid, 128, 0, s->stream>>>(s->avg, s->rp_dst, s->rp_ent, s->rp_prod, s->rp_slots, s->rp_nseg, out);
+        CK_LAUNCH();
+        s->kernel_launches += 2;
+        return CFR_OK;
+    }
     if (s->cfg.precision == CFR_FP64)
         k_ranges<double><<<grid, 128, 0, s->stream>>>(static_cast<const double *>(s->sigma), s->rp_dst, s->rp_ent, s->rp_prod,
                                                       s->rp_slots, s->rp_nseg, out);

@@ -31,7 +31,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (CFR_FP32, CFR_PLUS, cfr_average_strategy, cfr_exploitability, cfr_gather_ranges, cfr_get_nodes,
+from . import (CFR_AVERAGE_STRATEGY, CFR_FP32, CFR_PLUS, cfr_average_strategy, cfr_exploitability, cfr_gather_ranges, cfr_get_nodes,
                cfr_get_state, cfr_iterate, cfr_load_tree, cfr_mlp_adam, cfr_mlp_backward, cfr_mlp_create,
                cfr_mlp_forward, cfr_mlp_set_params, cfr_set_leaf_values, cfr_set_leaves, cfr_set_range_program,
                cfr_set_state)
@@ -365,12 +365,14 @@ def train(net, X, Y, steps: int = 2000, batch: int = 1024, lr: float = 1e-3, see
 
 class DepthLimitedSolver:
     """CFR+ on the depth-limited game, its leaves refreshed from the network every `refresh` iterations
-    (device-side: ranges -> network -> leaf utilities)."""
+    (device-side: ranges -> network -> leaf utilities).  ranges: CFR_AVERAGE_STRATEGY (default; the
+    leaves then settle as the average strategy converges) or CFR_CURRENT_STRATEGY."""
 
-    def __init__(self, cut: Cut, net, refresh: int = 1, device=None, fuse_levels: int = -1):
+    def __init__(self, cut: Cut, net, refresh: int = 1, device=None, fuse_levels: int = -1,
+                 ranges: int = CFR_AVERAGE_STRATEGY):
         import torch
 
-        self.cut, self.net, self.refresh = cut, net, int(refresh)
+        self.cut, self.net, self.refresh, self.ranges = cut, net, int(refresh), int(ranges)
         self.s = cfr_load_tree(cut.game, variant=CFR_PLUS, precision=CFR_FP32, device=device, fuse_levels=fuse_levels)
         dev = f"cuda:{device if device is not None else torch.cuda.current_device()}"
         rows = cut.cut_nodes.size
@@ -386,7 +388,7 @@ class DepthLimitedSolver:
     def _refresh(self):
         if self.cut.cut_nodes.size == 0:
             return
-        cfr_gather_ranges(self.s, self.x)
+        cfr_gather_ranges(self.s, self.x, self.ranges)
         cfr_mlp_forward(self.net, self.x, out=self.y)
         cfr_set_leaf_values(self.s, self.y, self.umax)
 

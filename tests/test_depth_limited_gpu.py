@@ -61,6 +61,32 @@ def test_gathered_ranges_are_the_oracles_own_reaches(game):
             assert not got[r, lo + 13:lo + 169].any()
 
 
+def test_average_strategy_ranges_are_the_oracles(game):
+    cut = dl.cut_game(game, depth=3)
+    v = cut.view
+    top = cut.game
+    s = cfr.cfr_load_tree(top, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32)
+    cfr.cfr_iterate(s, 7)
+    cfr.cfr_set_range_program(s, cut.seg_dst, cut.seg_entries, cut.entry_prod, cut.slots)
+    x = torch.zeros((cut.cut_nodes.size, 402), dtype=torch.float32, device="cuda")
+    cfr.cfr_gather_ranges(s, x, cfr.CFR_AVERAGE_STRATEGY)
+    got = x.cpu().numpy().astype(np.float64)
+    avg = cfr.cfr_average_strategy(s)
+    o = oracle.Oracle(top, record=True)                 # the oracle's own reaches under that profile
+    o.set_state(avg, np.zeros_like(avg), 0)
+    o.iterate(1)
+    nodes = o.nodes()
+    Pt = cut.top_public.size
+    for r, c in enumerate(cut.cut_nodes):
+        j = np.searchsorted(cut.top_public, c)
+        for p in (1, 2):
+            own = np.zeros(13)
+            for k in range(v.K):
+                own[v.x[p][k]] = nodes[f"own{p}"][1 + k * Pt + j]
+            lo = 64 + (p - 1) * 169
+            assert normwise(got[r, lo:lo + 13], own / own.sum()) <= TOL32
+
+
 def test_leaf_values_and_one_iteration_match_the_oracle(game):
     cut = dl.cut_game(game, depth=3)
     top = cut.game
@@ -90,10 +116,10 @@ def test_device_refresh_equals_a_host_refresh(game):
     cut = dl.cut_game(game, depth=3)
     net = dl.make_network(hidden=(64, 64), seed=2)
     d = dl.DepthLimitedSolver(cut, net, refresh=1, fuse_levels=0)
-    d.iterate(3)                           # refreshed after each iteration, from the strategy it produced
+    d.iterate(3)                           # refreshed after each iteration, from the average strategy
     x = torch.zeros((cut.cut_nodes.size, 402), dtype=torch.float32, device="cuda")
     x[:, :64] = torch.tensor(cut.embed, dtype=torch.float32, device="cuda")
-    cfr.cfr_gather_ranges(d.s, x)
+    cfr.cfr_gather_ranges(d.s, x, cfr.CFR_AVERAGE_STRATEGY)
     y = cfr.cfr_mlp_forward(net, x).cpu().numpy().astype(np.float64)
     u1 = cfr.cfr_get_nodes(d.s)["u1"]
     np.testing.assert_allclose(u1[cut.leaf_nodes], d.umax * y.ravel()[cut.leaf_src], rtol=1e-6, atol=1e-6)
