@@ -103,8 +103,8 @@ typedef struct {
     double dcfr_beta;
     double dcfr_gamma;
     int64_t batch_split_nodes;  /* cfr_batch_load: games of at least this many nodes run as one forest
-                                   through the per-depth kernels, the rest in the persistent kernel
-                                   (0 = default 16384; negative = all in the persistent kernel) */
+                                   through the per-depth kernels, the rest in the persistent kernel if
+                                   their image fits shared memory (0 = default 4096; negative = no split) */
 } cfr_config;
 
 /* Sizes and accounting of a loaded solver. */
