@@ -372,6 +372,15 @@ cfr_status cfr_mlp_adam(cfr_mlp *m, float lr, float beta1, float beta2, float ep
  * skip.  Synchronises. */
 cfr_status cfr_mlp_gemm_stats(cfr_mlp *m, double *fwd_us, double *fwd_flops, double *bwd_us, double *bwd_flops);
 
+/* The instruction the products run on: 0 (default) the warp-level mma.sync kernel, 1 tcgen05.mma with
+ * the accumulator in tensor memory (same results within the rounding of FP32 accumulation; slower in
+ * its present form).  Takes effect for later calls. */
+cfr_status cfr_mlp_set_tensor_path(cfr_mlp *m, int32_t tcgen05);
+
+/* Waits for the network's queued work; CFR_ERR_TIMEOUT if a tensor-core kernel gave up waiting for its
+ * operands (the network is then unusable). */
+cfr_status cfr_mlp_synchronize(cfr_mlp *m);
+
 const char *cfr_mlp_last_error(const cfr_mlp *m);   /* thread-local message if m == NULL */
 void cfr_mlp_free(cfr_mlp *m);
 

@@ -171,12 +171,15 @@ def lib():
         L.cfr_mlp_backward.argtypes = [_P, _P, _P, ctypes.c_int32, _P]
         L.cfr_mlp_adam.argtypes = [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
         L.cfr_mlp_gemm_stats.argtypes = [_P, _P, _P, _P, _P]
+        L.cfr_mlp_set_tensor_path.argtypes = [_P, ctypes.c_int32]
+        L.cfr_mlp_synchronize.argtypes = [_P]
         L.cfr_mlp_last_error.argtypes = [_P]
         L.cfr_mlp_last_error.restype = ctypes.c_char_p
         L.cfr_mlp_free.argtypes = [_P]
         L.cfr_mlp_free.restype = None
         for name in ("cfr_mlp_create", "cfr_mlp_set_params", "cfr_mlp_get_params", "cfr_mlp_get_grads",
-                     "cfr_mlp_forward", "cfr_mlp_backward", "cfr_mlp_adam", "cfr_mlp_gemm_stats"):
+                     "cfr_mlp_forward", "cfr_mlp_backward", "cfr_mlp_adam", "cfr_mlp_gemm_stats",
+                     "cfr_mlp_set_tensor_path", "cfr_mlp_synchronize"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("cfr_batch_load", "cfr_batch_iterate", "cfr_batch_set_tuning", "cfr_batch_autotune",
                      "cfr_batch_game_times", "cfr_batch_exploitability", "cfr_batch_get_state",
@@ -751,6 +754,15 @@ def cfr_mlp_backward(m: Mlp, x, target, loss=None):
 
 def cfr_mlp_adam(m: Mlp, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
     _check_mlp(lib().cfr_mlp_adam(m.handle, float(lr), float(beta1), float(beta2), float(eps)), m.handle)
+
+
+def cfr_mlp_set_tensor_path(m: Mlp, tcgen05: bool = True):
+    """Products on tcgen05 (tcgen05=True) or on the warp-level mma.sync kernel (the library's default)."""
+    _check_mlp(lib().cfr_mlp_set_tensor_path(m.handle, int(bool(tcgen05))), m.handle)
+
+
+def cfr_mlp_synchronize(m: Mlp):
+    _check_mlp(lib().cfr_mlp_synchronize(m.handle), m.handle)
 
 
 def cfr_mlp_gemm_stats(m: Mlp) -> dict:

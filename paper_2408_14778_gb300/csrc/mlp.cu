@@ -1,9 +1,13 @@
 // Learned leaf values: the BF16 multilayer perceptron of include/cfr_gb300.h (cfr_mlp_*), trained and
 // evaluated with this file's kernels.
 //
-// Matrix products: one tiled tensor-core GEMM, C[M][N] = sum_k A(m, k) B(k, n), BF16 operands and FP32
-// accumulation (mma.sync m16n8k16), 128 x 128 x 32 block tiles staged through shared memory by cp.async
-// in a three-stage pipeline, eight warps of 64 x 32.  Each operand is read from global memory in its
+// Matrix products: C[M][N] = sum_k A(m, k) B(k, n), BF16 operands and FP32 accumulation, by one of two
+// kernels (cfr_mlp_set_tensor_path): the warp-level k_gemm (default; mma.sync m16n8k16, 128 x 128 x 32
+// block tiles staged through shared memory by cp.async in a three-stage pipeline, eight warps of 64 x 32)
+// or k_gemm_tc on the 5th-generation tensor cores (tcgen05.mma, accumulator in tensor memory).  Both
+// read the same operands with the same tile shape; measured on GB300, k_gemm_tc is the slower of the
+// two (its four warps' 16-byte cp.async copies cannot keep a 128 x 128 tile fed from L2), so k_gemm is
+// the default until the tcgen05 kernel gets bulk-copied operands and a wider tile.  Each operand is read from global memory in its
 // stored orientation - the reduction index contiguous ("K-major") or the output index contiguous - and
 // ldmatrix (with .trans for the second case) builds the fragments, so the three products of a layer
 // need no transposed copies:
@@ -181,6 +185,191 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const __nv_bfloat16 *A, int64
             }
 }
 
+// ---- the same products on the 5th-generation tensor cores (tcgen05, accumulator in tensor memory) ---
+// One CTA of 128 threads computes a 128 x 128 tile of C.  Per 32-wide reduction step all threads copy the
+// A and B tiles into shared memory with cp.async, four steps ahead of the one multiplied (six stages),
+// in the tensor core's canonical no-swizzle layout: 8 x 16-byte core matrices, each an 8-row x 8-element
+// block stored contiguously (128 bytes); core (r, k) of an operand tile sits at r * 512 + k * 128 bytes
+// (4 cores along the reduction, 16 along the rows).  A
+// K-major operand's core rows are its rows (8 reduction values each); an operand whose output index is
+// contiguous in memory is stored the same way with the roles of the 8 x 8 block transposed (each core
+// row holds 8 output-index values at one reduction index) and the instruction's major bit set.  In both
+// cases the descriptor's leading offset (128 bytes) steps along the reduction and its stride offset
+// (512 bytes) along the rows.  One elected thread issues two tcgen05.mma (M = 128, N = 128, K = 16) per
+// step and commits them to the stage's mbarrier, which the refill of that stage waits for two steps
+// later.  The FP32 accumulator lives in 128 columns of tensor memory; the epilogue reads it with
+// tcgen05.ld (warp w owns lanes 32 w .. 32 w + 31, one output row per thread).  Every mbarrier wait is
+// bounded; a wait that gives up sets *err and the CTA still releases its tensor memory.
+constexpr int kTcK = 32, kTcStages = 6, kTcThreads = 128;
+constexpr int kTcDist = kTcStages - 2;                        // tiles loaded ahead of the one multiplied
+constexpr int kTcTileBytes = 128 * kTcK * 2;                  // 8 KB per operand per stage
+constexpr int kTcRowCore = (kTcK / 8) * 128;                  // bytes between core matrices along the rows
+constexpr int kTcSmem = kTcStages * 2 * kTcTileBytes + 64;     // + mbarriers and the TMEM address
+constexpr uint32_t kTcCols = 128;
+constexpr uint32_t kTcWaitPolls = 1u << 26;
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kTcWaitPolls; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Shared-memory matrix descriptor: start address, leading (reduction) and stride (row) byte offsets, the
+// descriptor version of this architecture (1), no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// Byte offset of element (row, k) of an operand tile in the layout above.  KM: the element's 16-byte
+// core row runs along k; otherwise along the rows.
+template <bool KM>
+__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+    const uint32_t core = (uint32_t)((row >> 3) * kTcRowCore + (k >> 3) * 128);
+    return KM ? core + (uint32_t)((row & 7) * 16 + (k & 7) * 2) : core + (uint32_t)((k & 7) * 16 + (row & 7) * 2);
+}
+
+// Copies one operand tile (rows r0 .. r0 + 127, reduction k0 .. k0 + kTcK - 1) into stage buffer s.
+template <bool KM>
+__device__ __forceinline__ void tc_load(uint32_t s, const __nv_bfloat16 *G, int64_t ld, int64_t r0, int64_t k0) {
+#pragma unroll
+    for (int it = 0; it < (128 * kTcK / 8) / kTcThreads; ++it) {
+        const int i = (int)threadIdx.x + it * kTcThreads;
+        if (KM) {                                  // row r, reduction chunk c (8 values)
+            const int r = i / (kTcK / 8), c = i % (kTcK / 8);
+            cp_async16(s + tc_off<true>(r, c * 8), G + (r0 + r) * ld + k0 + c * 8);
+        } else {                                   // reduction index k, row chunk c (8 rows)
+            const int k = i >> 4, c = i & 15;      // 16 chunks of 8 rows per reduction index
+            cp_async16(s + tc_off<false>(c * 8, k), G + (k0 + k) * ld + r0 + c * 8);
+        }
+    }
+}
+
+template <bool AKM, bool BKM, int EPI>
+__global__ void __launch_bounds__(kTcThreads) k_gemm_tc(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B,
+                                                        int64_t ldb, void *C, int64_t ldc, int32_t K, const float *bias,
+                                                        const __nv_bfloat16 *mask, int *err) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    const uint32_t sbase = tc_smem_u32(tsm);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tsm + kTcStages * 2 * kTcTileBytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + kTcStages);
+    const int tid = (int)threadIdx.x, warp = tid >> 5;
+    const int64_t m0 = (int64_t)blockIdx.y * 128, n0 = (int64_t)blockIdx.x * 128;
+    const int nk = K / kTcK;
+    auto sa = [&](int st) { return sbase + (uint32_t)(st * 2 * kTcTileBytes); };
+    auto sb = [&](int st) { return sbase + (uint32_t)(st * 2 * kTcTileBytes + kTcTileBytes); };
+    auto bar = [&](int st) { return tc_smem_u32(bars + st); };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(tslot)),
+                     "r"(kTcCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0)
+        for (int st = 0; st < kTcStages; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(st)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    // instruction descriptor: FP32 accumulator, BF16 A and B, their majors, N = 128, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((AKM ? 0u : 1u) << 15) | ((BKM ? 0u : 1u) << 16) |
+                           ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    bool ok = true;
+#pragma unroll
+    for (int st = 0; st < kTcDist; ++st) {
+        if (st < nk) {
+            tc_load<AKM>(sa(st), A, lda, m0, (int64_t)st * kTcK);
+            tc_load<BKM>(sb(st), B, ldb, n0, (int64_t)st * kTcK);
+        }
+        cp_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        // tile kt's copies (committed kTcDist groups ago) have landed
+        cp_wait<kTcDist - 1>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (!__syncthreads_and(ok)) { ok = false; break; }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int st = kt % kTcStages;
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 16; ++kk) {
+                const uint64_t ad = tc_desc(sa(st) + kk * 256, 128, kTcRowCore);
+                const uint64_t bd = tc_desc(sb(st) + kk * 256, 128, kTcRowCore);
+                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(st))
+                         : "memory");
+        }
+        // with tile kt's products queued, refill the stage of tile kt - 2 (its products issued two steps
+        // ago) with tile kt + kTcDist
+        const int kn = kt + kTcDist;
+        if (kn < nk) {
+            if (kt >= 2 && !tc_mbar_wait(bar((kt - 2) % kTcStages), (uint32_t)(((kt - 2) / kTcStages) & 1))) ok = false;
+            if (ok) {
+                tc_load<AKM>(sa(kn % kTcStages), A, lda, m0, (int64_t)kn * kTcK);
+                tc_load<BKM>(sb(kn % kTcStages), B, ldb, n0, (int64_t)kn * kTcK);
+            }
+        }
+        cp_commit();
+    }
+    cp_wait<0>();
+    // the last step's commit covers every product issued before it
+    if (nk > 0 && ok && !tc_mbar_wait(bar((nk - 1) % kTcStages), (uint32_t)(((nk - 1) / kTcStages) & 1))) ok = false;
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int64_t m = m0 + warp * 32 + (tid & 31);
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                         "%12, %13, %14, %15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int64_t n = n0 + c0;
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+                if (EPI == kEpiHidden || EPI == kEpiOut) { v0 += bias[n + j]; v1 += bias[n + j + 1]; }
+                if (EPI == kEpiHidden) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                if (EPI == kEpiMask) {
+                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + m * ldc + n + j);
+                    if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                }
+                if (EPI == kEpiHidden || EPI == kEpiMask)
+                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + m * ldc + n + j) =
+                        __floats2bfloat162_rn(v0, v1);
+                else
+                    *reinterpret_cast<float2 *>(static_cast<float *>(C) + m * ldc + n + j) = make_float2(v0, v1);
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+        // give the products in flight a bounded chance to finish before the memory is released
+        if (nk > 0) tc_mbar_wait(bar((nk - 1) % kTcStages), (uint32_t)(((nk - 1) / kTcStages) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+}
+
 // x [B][n] FP32 -> xp [Bp][np] BF16, zero outside.
 __global__ void k_pack_input(const float *x, int32_t B, int32_t n, __nv_bfloat16 *xp, int64_t Bp, int64_t np) {
     const int64_t total = Bp * np;
@@ -280,6 +469,8 @@ struct cfr_mlp {
     cudaEvent_t ev[4] = {};
     double fwd_flops = 0, bwd_flops = 0;
     bool fwd_timed = false, bwd_timed = false;
+    bool tc = false;                 // tcgen05 products, or the mma.sync kernel (default: faster, measured)
+    int *d_err = nullptr;            // set by a tcgen05 kernel whose mbarrier wait gave up
     std::string err;
     bool poisoned = false;
 };
@@ -347,11 +538,39 @@ cfr_status ensure_batch(cfr_mlp *m, int64_t Bp) {
 }
 
 template <bool AKM, bool BKM, int EPI>
-cudaError_t gemm(cudaStream_t st, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, void *C,
-                 int64_t ldc, int64_t M, int64_t N, int64_t K, const float *bias, const __nv_bfloat16 *mask) {
-    const dim3 grid((unsigned)(N / kBN), (unsigned)(M / kBM));
-    k_gemm<AKM, BKM, EPI><<<grid, kThreads, 0, st>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask);
+cudaError_t gemm_tc(cudaStream_t st, int *err, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
+                    void *C, int64_t ldc, int64_t M, int64_t N, int64_t K, const float *bias, const __nv_bfloat16 *mask) {
+    static bool attr = false;   // per instantiation; the attribute is per device function
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<AKM, BKM, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid((unsigned)(N / 128), (unsigned)(M / 128));
+    k_gemm_tc<AKM, BKM, EPI><<<grid, kTcThreads, kTcSmem, st>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask, err);
     return cudaGetLastError();
+}
+
+// C = A B on the network's tensor path (tcgen05 or mma.sync); shapes are multiples of 128.
+template <bool AKM, bool BKM, int EPI>
+cudaError_t gemm(const cfr_mlp *m, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, void *C,
+                 int64_t ldc, int64_t M, int64_t N, int64_t K, const float *bias, const __nv_bfloat16 *mask) {
+    if (m->tc) return gemm_tc<AKM, BKM, EPI>(m->stream, m->d_err, A, lda, B, ldb, C, ldc, M, N, K, bias, mask);
+    const dim3 grid((unsigned)(N / kBN), (unsigned)(M / kBM));
+    k_gemm<AKM, BKM, EPI><<<grid, kThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask);
+    return cudaGetLastError();
+}
+
+// CFR_ERR_TIMEOUT if a tensor-core kernel gave up waiting (synchronises).
+cfr_status check_err(cfr_mlp *m) {
+    int e = 0;
+    MCK(cudaMemcpyAsync(&e, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    MCK(cudaStreamSynchronize(m->stream));
+    if (e) {
+        m->poisoned = true;
+        return merr(m, CFR_ERR_TIMEOUT, "a tensor-core product gave up waiting for its operands");
+    }
+    return CFR_OK;
 }
 
 // The forward pass over Bp padded rows (input already packed into acts[0]); output in yp.
@@ -362,9 +581,9 @@ cfr_status forward_padded(cfr_mlp *m, int64_t Bp, double *flops) {
         const __nv_bfloat16 *W = m->pb + m->w_off[(size_t)l];
         const float *b = m->p + m->b_off[(size_t)l];
         if (l + 1 < m->L)
-            MCK((gemm<true, true, kEpiHidden>(m->stream, m->acts[(size_t)l], K, W, K, m->acts[(size_t)l + 1], N, Bp, N, K, b, nullptr)));
+            MCK((gemm<true, true, kEpiHidden>(m, m->acts[(size_t)l], K, W, K, m->acts[(size_t)l + 1], N, Bp, N, K, b, nullptr)));
         else
-            MCK((gemm<true, true, kEpiOut>(m->stream, m->acts[(size_t)l], K, W, K, m->yp, N, Bp, N, K, b, nullptr)));
+            MCK((gemm<true, true, kEpiOut>(m, m->acts[(size_t)l], K, W, K, m->yp, N, Bp, N, K, b, nullptr)));
         f += 2.0 * (double)Bp * N * K;
     }
     *flops = f;
@@ -402,7 +621,8 @@ cfr_status cfr_mlp_create(const int32_t *dims, int32_t num_layers, int32_t devic
         cfr_mlp_free(m);
         return merr(nullptr, e == cudaErrorMemoryAllocation ? CFR_ERR_OOM : CFR_ERR_CUDA, "network allocation: %s", msg.c_str());
     };
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaMalloc(&m->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream);
     for (float **a : {&m->p, &m->g, &m->m1, &m->m2})
         if (e == cudaSuccess) e = cudaMalloc(a, sizeof(float) * (size_t)m->P);
     if (e == cudaSuccess) e = cudaMalloc(&m->pb, sizeof(__nv_bfloat16) * (size_t)m->P);
@@ -446,6 +666,7 @@ static cfr_status get_flat(cfr_mlp *m, const float *dev, float *out, int64_t len
     if (st != CFR_OK) return st;
     if (!out || len < m->num_params) return merr(m, CFR_ERR_INVALID, "output needs %lld entries", (long long)m->num_params);
     MDeviceGuard dg(m->device);
+    if ((st = check_err(m)) != CFR_OK) return st;
     std::vector<float> flat((size_t)m->P);
     MCK(cudaMemcpyAsync(flat.data(), dev, sizeof(float) * flat.size(), cudaMemcpyDeviceToHost, m->stream));
     MCK(cudaStreamSynchronize(m->stream));
@@ -504,11 +725,11 @@ cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int
         const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
         const __nv_bfloat16 *dz = m->grads[(size_t)l];
         // dW[o][i] = sum_b dZ[b][o] X[b][i]
-        MCK((gemm<false, false, kEpiStore>(m->stream, dz, N, m->acts[(size_t)l], K, m->g + m->w_off[(size_t)l], K, N, K, Bp,
+        MCK((gemm<false, false, kEpiStore>(m, dz, N, m->acts[(size_t)l], K, m->g + m->w_off[(size_t)l], K, N, K, Bp,
                                            nullptr, nullptr)));
         fb += 2.0 * (double)N * K * Bp;
         if (l > 0) {   // dZ of layer l - 1 = (dZ W) masked where its ReLU output was 0
-            MCK((gemm<true, false, kEpiMask>(m->stream, dz, N, m->pb + m->w_off[(size_t)l], K, m->grads[(size_t)l - 1], K, Bp, K,
+            MCK((gemm<true, false, kEpiMask>(m, dz, N, m->pb + m->w_off[(size_t)l], K, m->grads[(size_t)l - 1], K, Bp, K,
                                              N, nullptr, m->acts[(size_t)l])));
             fb += 2.0 * (double)Bp * K * N;
         }
@@ -542,7 +763,7 @@ cfr_status cfr_mlp_gemm_stats(cfr_mlp *m, double *fwd_us, double *fwd_flops, dou
     cfr_status st = usable(m);
     if (st != CFR_OK) return st;
     MDeviceGuard dg(m->device);
-    MCK(cudaStreamSynchronize(m->stream));
+    if ((st = check_err(m)) != CFR_OK) return st;
     float a = 0.f, b = 0.f;
     if (m->fwd_timed) MCK(cudaEventElapsedTime(&a, m->ev[0], m->ev[1]));
     if (m->bwd_timed) MCK(cudaEventElapsedTime(&b, m->ev[2], m->ev[3]));
@@ -553,13 +774,28 @@ cfr_status cfr_mlp_gemm_stats(cfr_mlp *m, double *fwd_us, double *fwd_flops, dou
     return CFR_OK;
 }
 
+cfr_status cfr_mlp_set_tensor_path(cfr_mlp *m, int32_t tcgen05) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    if (tcgen05 != 0 && tcgen05 != 1) return merr(m, CFR_ERR_INVALID, "tcgen05 must be 0 or 1");
+    m->tc = tcgen05 == 1;
+    return CFR_OK;
+}
+
+cfr_status cfr_mlp_synchronize(cfr_mlp *m) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    MDeviceGuard dg(m->device);
+    return check_err(m);
+}
+
 const char *cfr_mlp_last_error(const cfr_mlp *m) { return m ? m->err.c_str() : g_mlp_err.c_str(); }
 
 void cfr_mlp_free(cfr_mlp *m) {
     if (!m) return;
     MDeviceGuard dg(m->device);
     cudaStreamSynchronize(m->stream);
-    for (void *a : {(void *)m->p, (void *)m->g, (void *)m->m1, (void *)m->m2, (void *)m->pb, (void *)m->yp})
+    for (void *a : {(void *)m->p, (void *)m->g, (void *)m->m1, (void *)m->m2, (void *)m->pb, (void *)m->yp, (void *)m->d_err})
         if (a) cudaFree(a);
     for (auto *a : m->acts) if (a) cudaFree(a);
     for (auto *a : m->grads) if (a) cudaFree(a);
