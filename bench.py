@@ -152,11 +152,12 @@ def measured_hbm_peak():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources that define the single-game iteration's kernels, their launch and the layout
+    they read (the batch and value-network sources do not change its traffic)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2408_14778_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("kernels.cuh", "stream.cuh", "cfr_api.cu", "layout.cpp", "layout.hpp"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -528,7 +529,9 @@ def run_ours(args, world, rank, local):
     names = [p["name"] for p in ph[0]]
     us = np.mean([[p["us"] for p in run] for run in ph], axis=0)
     by = np.array([p["bytes"] for p in ph[0]])
-    kernel_of = {cfr.CFR_PHASE_TOPDOWN: "k_topdown", cfr.CFR_PHASE_BOTTOMUP: "k_bottomup", cfr.CFR_PHASE_FUSED: "k_fused",
+    nfused = info["num_levels"] - info["fused_from_depth"]
+    kernel_of = {cfr.CFR_PHASE_TOPDOWN: "k_topdown", cfr.CFR_PHASE_BOTTOMUP: "k_bottomup",
+                 cfr.CFR_PHASE_FUSED: "k_tail_stream" if nfused == 2 else "k_fused",
                  cfr.CFR_PHASE_OWN: "k_own",
                  cfr.CFR_PHASE_UPDATE: "k_update_rows" if args.precision == "fp32" else "k_update"}
     k = int(np.argmax(us))
