@@ -454,6 +454,7 @@ def workload_config(args, g, info=None):
         c.update(decision_nodes=info["num_decision"], terminals=info["num_terminal"], infosets=info["num_infosets"],
                  infoset_actions=info["num_q"], levels=info["num_levels"], device_bytes=info["device_bytes"],
                  fused_from_depth=info["fused_from_depth"], fused_tiles=info["fused_tiles"],
+                 head_depths=info["head_depths"],
                  kernels_per_iteration=info["kernels_per_iteration"])
     return c
 

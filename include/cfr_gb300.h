@@ -102,6 +102,11 @@ typedef struct {
     double dcfr_alpha;      /* CFR_DISCOUNTED: alpha, beta, gamma (defaults 1.5, 0, 2); finite */
     double dcfr_beta;
     double dcfr_gamma;
+    int32_t head_levels;    /* FP32 mode: the shallowest depths (each at most 32768 nodes) run in one
+                               thread-block-cluster launch per direction instead of one launch per depth.
+                               0 = none (default: measured slower than the per-depth launches on the 1e8-
+                               node tree), -1 = as many as qualify (at least 2), k >= 2 = at most k.
+                               Ignored in FP64 mode. */
     int64_t batch_split_nodes;  /* cfr_batch_load: games of at least this many nodes run as one forest
                                    through the per-depth kernels, the rest in the persistent kernel if
                                    their image fits shared memory (0 = default 4096; negative = no split) */
@@ -127,6 +132,7 @@ typedef struct {
     int64_t kernel_launches;      /* kernel launches made by cfr_iterate so far */
     int32_t fused_from_depth;     /* first depth run by the fused kernel (num_levels: none) */
     int32_t fused_tiles;          /* thread blocks of the fused kernel that process nodes */
+    int32_t head_depths;          /* FP32 mode: leading depths run in one cluster launch per direction */
 } cfr_info;
 
 /* Fills *c with defaults: vanilla, FP32, simultaneous, default averaging, current device,

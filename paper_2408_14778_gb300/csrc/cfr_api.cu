@@ -28,6 +28,8 @@ constexpr int kBlock = 256;
 constexpr int kWideBlock = 1024;   // nodes and infosets with more than 32 actions: one block each
 constexpr int32_t kFuseAuto = 2;   // fused depths when cfr_config.fuse_levels < 0
 constexpr int32_t kStreamMinNodes = 32768;   // FP32 bottom-up depths this large use k_bottomup_stream
+constexpr int32_t kHeadMaxNodes = 32768;     // FP32: leading depths at most this large run in the cluster head
+constexpr int32_t kHeadMaxWide = 64;         // ... with at most this many nodes of more than 32 actions
 
 inline int32_t nblocks(int64_t n) { return (int32_t)((n + kBlock - 1) / kBlock); }
 
@@ -92,6 +94,9 @@ struct cfr_solver {
     int32_t *tail_tiles = nullptr;                        // k_tail_stream: 8 words per tile (TailTiles::tm)
     int32_t ntail_tiles = 0, tl_grid[3] = {0, 0, 0};
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
+    // FP32 mode: depths 0 .. head_n - 1 run in one cluster launch per direction (k_head_*) of head_ctas
+    // blocks; head_n == 0: per-depth launches
+    int32_t head_n = 0, head_ctas = 0;
     // depth-limited solving (cfr_set_range_program, cfr_set_leaves)
     int64_t rp_nseg = 0, nleaves = 0;
     int64_t *rp_dst = nullptr, *rp_ent = nullptr, *rp_prod = nullptr, *leaf_src = nullptr;
@@ -221,7 +226,39 @@ struct Launcher {
         if (!follows_kernel(st) && nchained < 2) chained[nchained++] = st;
         return e;
     }
+    // One thread-block cluster of `ctas` blocks.
+    template <typename... P, typename... A>
+    cudaError_t cluster(void (*k)(P...), int ctas, int block, cudaStream_t st, A... args) {
+        cudaLaunchConfig_t c = {};
+        c.gridDim = dim3((unsigned)ctas);
+        c.blockDim = dim3((unsigned)block);
+        c.stream = st;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)ctas;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
+        c.attrs = at;
+        c.numAttrs = pdl && follows_kernel(st) ? 2 : 1;
+        const cudaError_t e = cudaLaunchKernelEx(&c, k, args...);
+        if (!follows_kernel(st) && nchained < 2) chained[nchained++] = st;
+        return e;
+    }
 };
+
+HeadArgs head_args(const cfr_solver *s, bool bump) {
+    HeadArgs a{};
+    a.n = s->head_n;
+    a.bump = bump;
+    a.wide = s->wide;
+    for (int32_t l = 0; l <= s->head_n; ++l) {
+        a.dlevel[l] = s->dlevel[(size_t)l];
+        a.wlevel[l] = s->wlevel[(size_t)l];
+    }
+    return a;
+}
 
 // Whether the top-down step from depth l launches anything: a depth whose nodes have no decision
 // children (the last one) has none, except depth 0, whose first thread counts the iteration, and
@@ -336,7 +373,13 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         go.cut(os);
     }
     if (s->Hp > 0) TRY(mark());
-    for (int32_t l = 0; l < r; ++l) {
+    // the shallowest depths in one cluster launch (the graph's iteration only: the phase timer keeps
+    // one launch per depth)
+    const int32_t head = (!det && ev == nullptr) ? s->head_n : 0;
+    if constexpr (!det) {
+        if (head > 0) CK(go.cluster(k_head_topdown, s->head_ctas, kHeadThreads, st, t, head_args(s, first)));
+    }
+    for (int32_t l = head; l < r; ++l) {
         if (!topdown_launches(s, l)) continue;
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         if (s->ddepth_children[l] || l == 0) {
@@ -379,7 +422,7 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
             TRY(mark());
         }
     }
-    for (int32_t l = r - 1; l >= 0; --l) {
+    for (int32_t l = r - 1; l >= head; --l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         bool streamed = false;
         if constexpr (!det) {
@@ -390,6 +433,9 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         const int32_t nw = s->wlevel[l + 1] - s->wlevel[l];
         if (!det && nw > 0) CK(go(k_bottomup_wide<real>, nw, kWideBlock, 0, st, t, (const int32_t *)s->wide, s->wlevel[l]));
         TRY(mark());
+    }
+    if constexpr (!det) {
+        if (head > 0) CK(go.cluster(k_head_bottomup, s->head_ctas, kHeadThreads, st, t, head_args(s, false)));
     }
     if (branch) {
         CK(cudaStreamWaitEvent(st, s->join[pi], 0));
@@ -493,13 +539,61 @@ int32_t launches_per_iteration(const cfr_solver *s) {
 int32_t launches_per_pass(const cfr_solver *s) {
     const bool det = s->cfg.precision == CFR_FP64;
     const int32_t r = fused_from(s);
-    int32_t n = r + 1 + (r < s->L);                           // bottom-up depths, fused, update
+    const int32_t head = det ? 0 : s->head_n;
+    int32_t n = (r - head) + 1 + (r < s->L);                  // bottom-up depths, fused, update
     for (int32_t l = 0; l < s->L; ++l) n += s->hlevel[l + 1] > s->hlevel[l];   // own reaches
-    for (int32_t l = 0; l < r; ++l) {
+    if (head > 0) n += 2;                                     // the head's two cluster launches
+    for (int32_t l = head; l < r; ++l) {
         n += s->ddepth_children[l] || l == 0;                 // top-down
         if (!det) n += 2 * (s->wlevel[l + 1] > s->wlevel[l]);
     }
     return n;
+}
+
+// FP32 mode: the leading depths that one cluster can run faster than one launch each (at most
+// kHeadMaxNodes nodes and kHeadMaxWide wide nodes per depth, below the fused depths); used when there
+// are at least two and a cluster of 16 (or else 8) blocks of kHeadThreads fits.
+cfr_status plan_head(cfr_solver *s) {
+    s->head_n = 0;
+    s->head_ctas = 0;
+    const int32_t r = fused_from(s);
+    const int32_t cap = s->cfg.head_levels < 0 ? kHeadMaxDepths : std::min(s->cfg.head_levels, (int32_t)kHeadMaxDepths);
+    int32_t n = 0;
+    while (n < std::min(r, cap) && s->dlevel[(size_t)n + 1] - s->dlevel[(size_t)n] <= kHeadMaxNodes &&
+           s->wlevel[(size_t)n + 1] - s->wlevel[(size_t)n] <= kHeadMaxWide)
+        ++n;
+    if (n < 2) return CFR_OK;
+    for (const void *k : {(const void *)k_head_topdown, (const void *)k_head_bottomup})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            cudaGetLastError();
+            return CFR_OK;
+        }
+    for (int ctas : {16, 8}) {
+        bool fits = true;
+        for (const void *k : {(const void *)k_head_topdown, (const void *)k_head_bottomup}) {
+            cudaLaunchConfig_t c = {};
+            c.gridDim = dim3((unsigned)ctas);
+            c.blockDim = dim3((unsigned)kHeadThreads);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)ctas;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            c.attrs = at;
+            c.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, k, &c) != cudaSuccess || clusters < 1) {
+                cudaGetLastError();
+                fits = false;
+            }
+        }
+        if (fits) {
+            s->head_n = n;
+            s->head_ctas = ctas;
+            return CFR_OK;
+        }
+    }
+    return CFR_OK;
 }
 
 cfr_status build_graph(cfr_solver *s) {
@@ -689,6 +783,7 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     TRY(upload(s, s->wide, Lo.wide));
     if (!fp64) {
         TRY(plan_fusion(s, Lo));
+        TRY(plan_head(s));
         {
             std::vector<int32_t> wh;
             for (int32_t h = 0; h < s->Hp; ++h) {
@@ -832,6 +927,7 @@ void cfr_config_init(cfr_config *c) {
     c->avg_weight = CFR_AVG_DEFAULT;
     c->device = -1;
     c->fuse_levels = -1;
+    c->head_levels = 0;
     c->dcfr_alpha = 1.5;
     c->dcfr_beta = 0.0;
     c->dcfr_gamma = 2.0;
@@ -1286,6 +1382,7 @@ cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info) {
     info->kernels_per_iteration = launches_per_iteration(s);
     info->kernel_launches = s->kernel_launches;
     info->fused_from_depth = fused_from(s);
+    info->head_depths = s->cfg.precision == CFR_FP64 ? 0 : s->head_n;
     info->fused_tiles = fused_from(s) == s->L ? 0
                         : !s->fuse_tail ? s->fuse_ntiles
                         : s->ntail_tiles > 0 ? s->ntail_tiles : nblocks(s->dlevel[s->fuse_r + 1] - s->dlevel[s->fuse_r]);

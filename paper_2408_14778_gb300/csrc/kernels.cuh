@@ -486,6 +486,54 @@ __global__ void __launch_bounds__(1024) k_bottomup_wide(DevTree<real> t, const i
     bu_wide<real, false>(t, wide[w0 + blockIdx.x], s_red);
 }
 
+// ---- the shallowest depths in one launch, FP32 mode ------------------------------------------------
+// Depths 0 .. n-1 of a large tree hold few nodes (the deal, its first actions): one launch per depth
+// spends its time in launch and dependency latency, not in memory traffic.  k_head_topdown and
+// k_head_bottomup run them all in one launch of a single thread-block cluster, depth by depth, with a
+// cluster barrier (release / acquire at cluster scope, which orders the global writes of one depth
+// before the reads of the next) between depths.  Nodes with more than 32 actions go one per block, to
+// the block-cooperative td_wide / bu_wide.  Data written in this launch is read through L2.
+constexpr int kHeadMaxDepths = 16;
+constexpr int kHeadThreads = 1024;
+
+struct HeadArgs {
+    int32_t n;                                 // depths 0 .. n - 1
+    int32_t bump;                              // count the iteration (first pass of an iteration)
+    const int32_t *wide;                       // nodes with more than 32 actions, by depth
+    int32_t dlevel[kHeadMaxDepths + 1];
+    int32_t wlevel[kHeadMaxDepths + 1];
+};
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kHeadThreads) k_head_topdown(DevTree<float> t, HeadArgs a) {
+    grid_dependency_wait();
+    if (a.bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
+    const int32_t stride = (int32_t)(gridDim.x * blockDim.x);
+    for (int l = 0; l < a.n; ++l) {
+        for (int32_t j = a.dlevel[l] + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); j < a.dlevel[l + 1]; j += stride)
+            td_node<float, true, true>(t, j);
+        for (int32_t w = a.wlevel[l] + (int32_t)blockIdx.x; w < a.wlevel[l + 1]; w += (int32_t)gridDim.x)
+            td_wide<float, true>(t, a.wide[w]);
+        cluster_barrier();
+    }
+}
+
+__global__ void __launch_bounds__(kHeadThreads) k_head_bottomup(DevTree<float> t, HeadArgs a) {
+    grid_dependency_wait();
+    __shared__ float s_red[32];
+    const int32_t stride = (int32_t)(gridDim.x * blockDim.x);
+    for (int l = a.n - 1; l >= 0; --l) {
+        for (int32_t j = a.dlevel[l] + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); j < a.dlevel[l + 1]; j += stride)
+            bu_node<float, false, true>(t, j);
+        for (int32_t w = a.wlevel[l] + (int32_t)blockIdx.x; w < a.wlevel[l + 1]; w += (int32_t)gridDim.x)
+            bu_wide<float, true>(t, a.wide[w], s_red);   // every thread of the block takes part
+        cluster_barrier();
+    }
+}
+
 // ---- fused deepest depths, FP32 mode ----------------------------------------------------------------
 // The depths r .. L-1, which hold most of the nodes, in one launch.  Block b takes a tile of
 // consecutive depth-r nodes with all their decision descendants - consecutive at every depth, since
