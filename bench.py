@@ -316,7 +316,8 @@ def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
     fwd, bwd = st["fwd_flops"] / st["fwd_us"] / 1e6, st["bwd_flops"] / st["bwd_us"] / 1e6
     out["network_gemm"] = {"batch": 4096, "forward_tflops": fwd, "backward_tflops": bwd, "peak_tflops": peak,
                            "peak_source": src, "forward_frac": fwd / peak, "backward_frac": bwd / peak,
-                           "instruction": "mma.sync m16n8k16 bf16, fp32 accumulate"}
+                           "instruction": "forward: tcgen05.mma kind::f16 (bf16, fp32 accumulator in tensor memory, "
+                                          "TMA operands); backward: mma.sync m16n8k16 bf16"}
     untrained = dl.make_network(seed=args.seed + 1, device=local)
     for name, model, ranges in (("trained", net, cfr.CFR_AVERAGE_STRATEGY),
                                 ("trained_current_ranges", net, cfr.CFR_CURRENT_STRATEGY),

@@ -378,10 +378,12 @@ cfr_status cfr_mlp_adam(cfr_mlp *m, float lr, float beta1, float beta2, float ep
  * skip.  Synchronises. */
 cfr_status cfr_mlp_gemm_stats(cfr_mlp *m, double *fwd_us, double *fwd_flops, double *bwd_us, double *bwd_flops);
 
-/* The instruction the products run on: 0 (default) the warp-level mma.sync kernel, 1 tcgen05.mma with
- * the accumulator in tensor memory (same results within the rounding of FP32 accumulation; slower in
- * its present form).  Takes effect for later calls. */
-cfr_status cfr_mlp_set_tensor_path(cfr_mlp *m, int32_t tcgen05);
+/* The instructions the products run on: 2 (default) the forward products on tcgen05.mma (accumulator in
+ * tensor memory, TMA-loaded operands) and the backward ones on the warp-level mma.sync kernel - the
+ * fastest measured for each; 0 mma.sync for every product; 1 tcgen05.mma for every product (the backward
+ * ones with per-thread operand copies).  Results agree within the rounding of FP32 accumulation.  Takes
+ * effect for later calls. */
+cfr_status cfr_mlp_set_tensor_path(cfr_mlp *m, int32_t path);
 
 /* Waits for the network's queued work; CFR_ERR_TIMEOUT if a tensor-core kernel gave up waiting for its
  * operands (the network is then unusable). */

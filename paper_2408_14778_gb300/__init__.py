@@ -759,9 +759,13 @@ def cfr_mlp_adam(m: Mlp, lr: float, beta1: float = 0.9, beta2: float = 0.999, ep
     _check_mlp(lib().cfr_mlp_adam(m.handle, float(lr), float(beta1), float(beta2), float(eps)), m.handle)
 
 
-def cfr_mlp_set_tensor_path(m: Mlp, tcgen05: bool = True):
-    """Products on tcgen05 (tcgen05=True) or on the warp-level mma.sync kernel (the library's default)."""
-    _check_mlp(lib().cfr_mlp_set_tensor_path(m.handle, int(bool(tcgen05))), m.handle)
+MLP_PATH_MMA_SYNC, MLP_PATH_TCGEN05, MLP_PATH_MIXED = 0, 1, 2
+
+
+def cfr_mlp_set_tensor_path(m: Mlp, path: int = MLP_PATH_MIXED):
+    """0: mma.sync for every product; 1: tcgen05 for every product; 2 (default): tcgen05 with TMA operands
+    for the forward products, mma.sync for the backward ones."""
+    _check_mlp(lib().cfr_mlp_set_tensor_path(m.handle, int(path)), m.handle)
 
 
 def cfr_mlp_synchronize(m: Mlp):

@@ -1,13 +1,18 @@
 // Learned leaf values: the BF16 multilayer perceptron of include/cfr_gb300.h (cfr_mlp_*), trained and
 // evaluated with this file's kernels.
 //
-// Matrix products: C[M][N] = sum_k A(m, k) B(k, n), BF16 operands and FP32 accumulation, by one of two
-// kernels (cfr_mlp_set_tensor_path): the warp-level k_gemm (default; mma.sync m16n8k16, 128 x 128 x 32
-// block tiles staged through shared memory by cp.async in a three-stage pipeline, eight warps of 64 x 32)
-// or k_gemm_tc on the 5th-generation tensor cores (tcgen05.mma, accumulator in tensor memory).  Both
-// read the same operands with the same tile shape; measured on GB300, k_gemm_tc is the slower of the
-// two (its four warps' 16-byte cp.async copies cannot keep a 128 x 128 tile fed from L2), so k_gemm is
-// the default until the tcgen05 kernel gets bulk-copied operands and a wider tile.  Each operand is read from global memory in its
+// Matrix products: C[M][N] = sum_k A(m, k) B(k, n), BF16 operands and FP32 accumulation, by three
+// kernels (cfr_mlp_set_tensor_path chooses):
+//   k_gemm_tma  forward products on the 5th-generation tensor cores (tcgen05.mma, accumulator in tensor
+//               memory) with TMA-loaded, 128-byte-swizzled operands and warp-specialised copy / MMA
+//               issue (both operands of the forward product are K-major);
+//   k_gemm      the warp-level kernel (mma.sync m16n8k16, 128 x 128 x 32 block tiles staged through
+//               shared memory by cp.async in a three-stage pipeline, eight warps of 64 x 32), any
+//               operand orientation;
+//   k_gemm_tc   tcgen05.mma with operands copied by every thread with cp.async into the canonical
+//               no-swizzle layout, any orientation.
+// The default (path 2) runs the forward products on k_gemm_tma and the backward ones on k_gemm, the
+// fastest measured on GB300 for each; path 0 is k_gemm everywhere, path 1 tcgen05 everywhere.  Each operand is read from global memory in its
 // stored orientation - the reduction index contiguous ("K-major") or the output index contiguous - and
 // ldmatrix (with .trans for the second case) builds the fragments, so the three products of a layer
 // need no transposed copies:
@@ -16,8 +21,10 @@
 //   data grad      dX[b][i] = sum_o dZ[b][o] W[o][i]     A K-major, B with the output index contiguous
 // Every dimension is padded to a multiple of 128 (the batch too): padded weights and inputs are zero and
 // padded rows of the output gradient are zero, so padding never reaches a real result.
+#include <cuda.h>   // CUtensorMap and its enums; the encoder is fetched through the runtime's entry point
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -370,6 +377,146 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(const __nv_bfloat16 *A, 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
+// ---- forward products on tcgen05 with TMA-fed, 128-byte-swizzled operands -------------------------
+// Both operands of the forward product are K-major (activations [batch][in], weights [out][in]), so
+// each stage's tiles are two TMA boxes: 128 rows x 64 reduction values of A and BN x 64 of B, written
+// by the copy engine in the 128-byte swizzled layout that the tensor core's descriptor names (8-row
+// groups 1024 bytes apart; a 16-wide reduction step is a 32-byte advance inside the swizzle row).
+// Warp 0's first lane issues the copies into two (BN = 256) or three (BN = 128) stages, warp 1's first lane issues four tcgen05.mma
+// (M = 128, N = BN, K = 16) per stage and commits each stage back to the copier and, at the end, to the
+// epilogue; all four warps then read the FP32 accumulator (BN tensor-memory columns) and write the
+// result.  Every mbarrier wait is bounded; one that gives up sets *err.
+constexpr int kTmK = 64, kTmThreads = 128;
+
+// Two blocks per SM (one's epilogue overlaps the other's products): 96 KB of stages each.
+template <int BN>
+struct TmShape {
+    static constexpr int kStages = BN == 256 ? 2 : 3;
+    static constexpr int kA = 128 * kTmK * 2, kB = BN * kTmK * 2, kStage = kA + kB;
+    static constexpr int kSmem = kStages * kStage + 1024 + 128;   // + alignment slack, barriers
+};
+
+__device__ __forceinline__ uint64_t tm_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void tm_load(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y, uint32_t bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                 "[%4];" ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constant__ CUtensorMap ta,
+                                                            const __grid_constant__ CUtensorMap tb, void *C, int64_t ldc,
+                                                            int32_t K, const float *bias, int *err) {
+    using S = TmShape<BN>;
+    extern __shared__ unsigned char raw[];
+    const uint32_t raw_s = tc_smem_u32(raw);
+    const uint32_t base = (raw_s + 1023u) & ~1023u;              // swizzled tiles: 1024-byte aligned
+    const uint32_t bars = base + S::kStages * S::kStage;           // full[stages], empty[stages], acc
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(raw + (bars - raw_s) + (2 * S::kStages + 1) * 8);
+    auto full = [&](int st) { return bars + 8u * st; };
+    auto empty = [&](int st) { return bars + 8u * (S::kStages + st); };
+    const uint32_t accb = bars + 8u * (2 * S::kStages);
+    const int tid = (int)threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int32_t m0 = (int32_t)blockIdx.y * 128, n0 = (int32_t)blockIdx.x * BN;
+    const int nk = K / kTmK;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(tslot)),
+                     "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < 2 * S::kStages + 1; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8u * st) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((128u >> 4) << 24);
+
+    if (warp == 0 && lane == 0) {                       // the copier
+        int issued = 0;
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int st = kt % S::kStages;
+            if (kt >= S::kStages && !tc_mbar_wait(empty(st), (uint32_t)((kt / S::kStages - 1) & 1))) { ok = false; break; }
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"((uint32_t)S::kStage)
+                         : "memory");
+            const uint32_t sa = base + (uint32_t)(st * S::kStage);
+            tm_load(sa, &ta, kt * kTmK, m0, full(st));
+            tm_load(sa + S::kA, &tb, kt * kTmK, n0, full(st));
+            ++issued;
+        }
+        // no copy may still be landing when the block exits
+        for (int j = issued > S::kStages ? issued - S::kStages : 0; j < issued; ++j)
+            if (!tc_mbar_wait(full(j % S::kStages), (uint32_t)((j / S::kStages) & 1))) ok = false;
+        if (!ok) atomicExch(err, 1);
+    } else if (warp == 1 && lane == 0) {                // the tensor-core issuer
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int st = kt % S::kStages;
+            if (!tc_mbar_wait(full(st), (uint32_t)((kt / S::kStages) & 1))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = base + (uint32_t)(st * S::kStage);
+#pragma unroll
+            for (int kk = 0; kk < kTmK / 16; ++kk) {
+                const uint64_t ad = tm_desc_sw128(sa + kk * 32), bd = tm_desc_sw128(sa + S::kA + kk * 32);
+                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty(st))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accb) : "memory");
+        if (!ok) atomicExch(err, 1);
+    }
+    __syncwarp();
+    const bool done = tc_mbar_wait(accb, 0);
+    if (!done && lane == 0) atomicExch(err, 1);
+    if (__all_sync(0xffffffffu, done)) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int64_t m = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                         "%12, %13, %14, %15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int64_t n = n0 + c0;
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                float v0 = __uint_as_float(r[j]) + bias[n + j], v1 = __uint_as_float(r[j + 1]) + bias[n + j + 1];
+                if (EPI == kEpiHidden) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + m * ldc + n + j) =
+                        __floats2bfloat162_rn(v0, v1);
+                } else {
+                    *reinterpret_cast<float2 *>(static_cast<float *>(C) + m * ldc + n + j) = make_float2(v0, v1);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
 // x [B][n] FP32 -> xp [Bp][np] BF16, zero outside.
 __global__ void k_pack_input(const float *x, int32_t B, int32_t n, __nv_bfloat16 *xp, int64_t Bp, int64_t np) {
     const int64_t total = Bp * np;
@@ -469,7 +616,7 @@ struct cfr_mlp {
     cudaEvent_t ev[4] = {};
     double fwd_flops = 0, bwd_flops = 0;
     bool fwd_timed = false, bwd_timed = false;
-    bool tc = false;                 // tcgen05 products, or the mma.sync kernel (default: faster, measured)
+    int32_t path = 2;                // cfr_mlp_set_tensor_path: 0 mma.sync, 1 tcgen05, 2 (default) mixed
     int *d_err = nullptr;            // set by a tcgen05 kernel whose mbarrier wait gave up
     std::string err;
     bool poisoned = false;
@@ -555,9 +702,70 @@ cudaError_t gemm_tc(cudaStream_t st, int *err, const __nv_bfloat16 *A, int64_t l
 template <bool AKM, bool BKM, int EPI>
 cudaError_t gemm(const cfr_mlp *m, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, void *C,
                  int64_t ldc, int64_t M, int64_t N, int64_t K, const float *bias, const __nv_bfloat16 *mask) {
-    if (m->tc) return gemm_tc<AKM, BKM, EPI>(m->stream, m->d_err, A, lda, B, ldb, C, ldc, M, N, K, bias, mask);
+    if (m->path == 1) return gemm_tc<AKM, BKM, EPI>(m->stream, m->d_err, A, lda, B, ldb, C, ldc, M, N, K, bias, mask);
     const dim3 grid((unsigned)(N / kBN), (unsigned)(M / kBM));
     k_gemm<AKM, BKM, EPI><<<grid, kThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask);
+    return cudaGetLastError();
+}
+
+// The driver's tensor-map encoder, fetched once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// A 2-D K-major BF16 operand [rows][K] (row stride K elements) in boxes of box_rows x 64, 128-byte swizzle.
+bool encode_operand(CUtensorMap *map, const __nv_bfloat16 *g, int64_t rows, int64_t K, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kTmK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(g), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The forward product on tcgen05 with TMA operands: BN = 256 where N allows, else 128.
+template <int EPI>
+cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bfloat16 *W, void *C, int64_t M, int64_t N,
+                         int64_t K, const float *bias) {
+    CUtensorMap ta, tb;
+    // 256-wide tiles where they still give two blocks per SM, else 128-wide
+    const int bn = (N % 256 == 0 && (N / 256) * (M / 128) >= 2 * 152) ? 256 : 128;
+    if (!encode_operand(&ta, A, M, K, 128) || !encode_operand(&tb, W, N, K, bn)) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)(N / bn), (unsigned)(M / 128));
+    if (bn == 256) {
+        static bool attr = false;
+        if (!attr) {
+            const cudaError_t e = cudaFuncSetAttribute(k_gemm_tma<256, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       TmShape<256>::kSmem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_gemm_tma<256, EPI><<<grid, kTmThreads, TmShape<256>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, m->d_err);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            const cudaError_t e = cudaFuncSetAttribute(k_gemm_tma<128, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       TmShape<128>::kSmem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_gemm_tma<128, EPI><<<grid, kTmThreads, TmShape<128>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, m->d_err);
+    }
     return cudaGetLastError();
 }
 
@@ -580,10 +788,14 @@ cfr_status forward_padded(cfr_mlp *m, int64_t Bp, double *flops) {
         const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
         const __nv_bfloat16 *W = m->pb + m->w_off[(size_t)l];
         const float *b = m->p + m->b_off[(size_t)l];
-        if (l + 1 < m->L)
+        if (m->path != 0) {   // tcgen05 with TMA operands
+            if (l + 1 < m->L) MCK(gemm_fwd_tma<kEpiHidden>(m, m->acts[(size_t)l], W, m->acts[(size_t)l + 1], Bp, N, K, b));
+            else MCK(gemm_fwd_tma<kEpiOut>(m, m->acts[(size_t)l], W, m->yp, Bp, N, K, b));
+        } else if (l + 1 < m->L) {
             MCK((gemm<true, true, kEpiHidden>(m, m->acts[(size_t)l], K, W, K, m->acts[(size_t)l + 1], N, Bp, N, K, b, nullptr)));
-        else
+        } else {
             MCK((gemm<true, true, kEpiOut>(m, m->acts[(size_t)l], K, W, K, m->yp, N, Bp, N, K, b, nullptr)));
+        }
         f += 2.0 * (double)Bp * N * K;
     }
     *flops = f;
@@ -774,11 +986,11 @@ cfr_status cfr_mlp_gemm_stats(cfr_mlp *m, double *fwd_us, double *fwd_flops, dou
     return CFR_OK;
 }
 
-cfr_status cfr_mlp_set_tensor_path(cfr_mlp *m, int32_t tcgen05) {
+cfr_status cfr_mlp_set_tensor_path(cfr_mlp *m, int32_t path) {
     cfr_status st = usable(m);
     if (st != CFR_OK) return st;
-    if (tcgen05 != 0 && tcgen05 != 1) return merr(m, CFR_ERR_INVALID, "tcgen05 must be 0 or 1");
-    m->tc = tcgen05 == 1;
+    if (path < 0 || path > 2) return merr(m, CFR_ERR_INVALID, "path must be 0, 1 or 2");
+    m->path = path;
     return CFR_OK;
 }
 

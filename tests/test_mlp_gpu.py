@@ -22,24 +22,29 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
 
 
-def _net(dims, seed, tcgen05=True):
+def _net(dims, seed, path=cfr.MLP_PATH_MIXED):
     rng = np.random.default_rng(seed)
     params = mlp.init_params(dims, rng)
     m = cfr.cfr_mlp_create(dims)
-    cfr.cfr_mlp_set_tensor_path(m, tcgen05)
+    cfr.cfr_mlp_set_tensor_path(m, path)
     cfr.cfr_mlp_set_params(m, mlp.flatten(params).astype(np.float32))
     # the oracle uses the FP32 parameters the network holds
     params = mlp.unflatten(cfr.cfr_mlp_get_params(m).astype(np.float64), dims)
     return m, params, rng
 
 
-@pytest.mark.parametrize("tcgen05", [True, False], ids=["tcgen05", "mma_sync"])
+PATHS = pytest.mark.parametrize("path", [cfr.MLP_PATH_MMA_SYNC, cfr.MLP_PATH_TCGEN05, cfr.MLP_PATH_MIXED],
+                                ids=["mma_sync", "tcgen05", "mixed"])
+
+
+@PATHS
 @pytest.mark.parametrize("dims,batch", [(LEAF_DIMS, 300), ([5, 7, 3], 1), ([130, 200, 129], 128), ([1, 1], 3),
-                                        ([33, 300, 300, 17], 257)])
-def test_forward_matches_oracle(dims, batch, tcgen05):
+                                        ([33, 300, 300, 17], 257), ([64, 512, 512, 64], 4096),
+                                        ([128, 1024, 256], 9728)])   # the last: 256-wide tcgen05 tiles
+def test_forward_matches_oracle(dims, batch, path):
     import torch
 
-    m, params, rng = _net(dims, seed=len(dims) * 1000 + batch, tcgen05=tcgen05)
+    m, params, rng = _net(dims, seed=len(dims) * 1000 + batch, path=path)
     x = rng.normal(size=(batch, dims[0])).astype(np.float32)
     y = cfr.cfr_mlp_forward(m, torch.tensor(x, device="cuda")).cpu().numpy().astype(np.float64)
     cfr.cfr_mlp_synchronize(m)
@@ -48,13 +53,13 @@ def test_forward_matches_oracle(dims, batch, tcgen05):
     assert np.max(np.abs(y - ref)) <= 2e-2 * np.max(np.abs(ref)) + 1e-6
 
 
-@pytest.mark.parametrize("tcgen05", [True, False], ids=["tcgen05", "mma_sync"])
+@PATHS
 @pytest.mark.parametrize("dims,batch", [(LEAF_DIMS, 300), ([5, 7, 3], 2), ([130, 200, 129], 128),
                                         ([33, 300, 300, 17], 257)])
-def test_gradients_match_oracle(dims, batch, tcgen05):
+def test_gradients_match_oracle(dims, batch, path):
     import torch
 
-    m, params, rng = _net(dims, seed=7 + batch, tcgen05=tcgen05)
+    m, params, rng = _net(dims, seed=7 + batch, path=path)
     x = rng.normal(size=(batch, dims[0])).astype(np.float32)
     t = rng.normal(size=(batch, dims[-1])).astype(np.float32)
     loss = cfr.cfr_mlp_backward(m, torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")).item()
