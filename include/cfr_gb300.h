@@ -147,6 +147,11 @@ void cfr_config_init(cfr_config *c);
  * non-NULL, a NUL-terminated reason of at most msg_len bytes is written. */
 cfr_status cfr_validate(const cfr_game_desc *g, char *msg, size_t msg_len);
 
+/* Test hook: builds the host layout of g with the one-thread builder (builder 0) or the multi-threaded
+ * one (builder 1; cfr_load_tree uses it from 2^20 nodes on) and returns a 64-bit hash of every layout
+ * array, so that the two can be compared; forest != 0 accepts several roots.  Errors as cfr_validate. */
+cfr_status cfr_layout_digest(const cfr_game_desc *g, int32_t builder, int32_t forest, uint64_t *digest);
+
 /* Validates the game (as cfr_validate), builds the level-ordered layout on the host (nodes sorted
  * by depth, children of a node contiguous and in action order - the level graphs L^(l) of
  * Section 3.1 made implicit), uploads it once and sets sigma^(1) to uniform (Section 3.1).

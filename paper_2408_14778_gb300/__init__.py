@@ -126,6 +126,9 @@ def lib():
         L.cfr_config_init.argtypes = [ctypes.POINTER(_Config)]
         L.cfr_config_init.restype = None
         L.cfr_validate.argtypes = [ctypes.POINTER(_GameDesc), ctypes.c_char_p, ctypes.c_size_t]
+        L.cfr_layout_digest.argtypes = [ctypes.POINTER(_GameDesc), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_uint64)]
+        L.cfr_layout_digest.restype = ctypes.c_int
         L.cfr_load_tree.argtypes = [ctypes.POINTER(_GameDesc), ctypes.POINTER(_Config), ctypes.POINTER(_P)]
         L.cfr_iterate.argtypes = [_P, ctypes.c_int32]
         L.cfr_synchronize.argtypes = [_P]
@@ -232,6 +235,15 @@ def cfr_validate(game) -> tuple[int, str]:
     buf = ctypes.create_string_buffer(512)
     st = lib().cfr_validate(ctypes.byref(d.c), buf, len(buf))
     return st, buf.value.decode(errors="replace")
+
+
+def cfr_layout_digest(game, builder: int, forest: bool = False) -> tuple[int, int, str]:
+    """(status, hash of the host layout, message) from the one-thread (0) or multi-threaded (1) builder."""
+    d = _Desc(game)
+    h = ctypes.c_uint64()
+    st = lib().cfr_layout_digest(ctypes.byref(d.c), int(builder), int(bool(forest)), ctypes.byref(h))
+    msg = lib().cfr_last_error(None)
+    return st, h.value, (msg.decode(errors="replace") if (st and msg) else "")
 
 
 class _TorchAllocator:

@@ -946,6 +946,36 @@ cfr_status cfr_load_tree(const cfr_game_desc *g, const cfr_config *c, cfr_solver
     return cfrgb::load_tree_impl(g, c, false, out);
 }
 
+cfr_status cfr_layout_digest(const cfr_game_desc *g, int32_t builder, int32_t forest, uint64_t *digest) {
+    if (!digest || (builder != 0 && builder != 1)) return set_err(nullptr, CFR_ERR_INVALID, "digest is NULL or builder not 0/1");
+    Layout Lo;
+    std::string err;
+    const cfr_status st = builder == 0 ? build_layout_serial(g, &Lo, &err, true, forest != 0)
+                                       : build_layout_parallel(g, &Lo, &err, true, forest != 0);
+    if (st != CFR_OK) {
+        g_thread_err = err;
+        return st;
+    }
+    uint64_t h = 1469598103934665603ull;   // FNV-1a over every field, in declaration order
+    auto mix = [&](const void *p, size_t bytes) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < bytes; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+    };
+    auto vec = [&](const auto &v) {
+        const uint64_t n = v.size();
+        mix(&n, sizeof n);
+        if (n) mix(v.data(), sizeof(v[0]) * v.size());
+    };
+    const int64_t sizes[] = {Lo.N, Lo.Nd, Lo.Nt, Lo.Q, Lo.H, Lo.L, Lo.max_depth, Lo.max_actions, Lo.single_level, Lo.Hp};
+    mix(sizes, sizeof sizes);
+    vec(Lo.dfirst); vec(Lo.tfirst); vec(Lo.dinfo); vec(Lo.kmask); vec(Lo.wbits); vec(Lo.qp); vec(Lo.dlevel);
+    vec(Lo.hlevel); vec(Lo.wide); vec(Lo.wlevel); vec(Lo.util); vec(Lo.qbase); vec(Lo.iplayer); vec(Lo.pseq);
+    vec(Lo.pseq_h); vec(Lo.sigma0); vec(Lo.q_int2user); vec(Lo.h_int2user); vec(Lo.dnode_user); vec(Lo.tnode_user);
+    vec(Lo.hnode_start); vec(Lo.hnode);
+    *digest = h;
+    return CFR_OK;
+}
+
 }  // extern "C"
 
 // cfr_load_tree, or (forest) several independent games side by side: one root per game at depth 0.

@@ -68,4 +68,11 @@ struct Layout {
 cfr_status build_layout(const cfr_game_desc *g, Layout *layout, std::string *err, bool infoset_lists = false,
                         bool forest = false);
 
+// The two builders build_layout chooses between (by size): one thread, and several host threads from
+// kParallelLayoutNodes nodes on.  Same results, same errors.
+constexpr int64_t kParallelLayoutNodes = 1 << 20;
+cfr_status build_layout_serial(const cfr_game_desc *g, Layout *layout, std::string *err, bool infoset_lists, bool forest);
+cfr_status build_layout_parallel(const cfr_game_desc *g, Layout *layout, std::string *err, bool infoset_lists,
+                                 bool forest);
+
 }  // namespace cfrgb
