@@ -71,6 +71,8 @@ struct cfr_solver {
          *u = nullptr, *own = nullptr;
     double *util64 = nullptr, *sigma064 = nullptr, *R = nullptr, *S = nullptr, *stage = nullptr;
     double *br_reach = nullptr, *br_val = nullptr, *br_cfv = nullptr, *avg = nullptr, *br_out = nullptr;
+    double *br_reach2 = nullptr, *br_val2 = nullptr;   // player 2's, beside player 1's in br_reach / br_val
+    cudaGraphExec_t br_exec = nullptr;                   // the average strategy and both best responses
     int64_t *d_iter = nullptr;
     int *d_err = nullptr;                                 // set by a device-side wait that expired
     int32_t sb_grid[3] = {0, 0, 0}, td_grid[3] = {0, 0, 0};   // streamed kernels: resident blocks, per
@@ -882,35 +884,69 @@ cfr_status gather_q_to_host(cfr_solver *s, const T *src, double *out) {
     return sync_and_check(s);
 }
 
-cfr_status best_response(cfr_solver *s, int player, double *value) {
-    DevBR b;
-    b.dfirst = s->dfirst; b.tfirst = s->tfirst; b.dinfo = s->dinfo;
-    b.kmask = s->kmask; b.wbits = s->wbits;
-    b.util = s->util64; b.qbase = s->qbase; b.iplayer = s->iplayer; b.avg = s->avg;
-    b.preach = s->br_reach; b.val = s->br_val; b.cfv = s->br_cfv; b.astar = s->astar;
-    cudaStream_t st = s->stream;
-    const std::vector<double> ones((size_t)s->dlevel[1], 1.0);     // the root (every root of a forest)
-    CK(cudaMemcpyAsync(s->br_reach, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, st));
+// The average strategy (Eq. 10 normalised) and both players' best responses against it in one pass
+// (k_br2_*, one launch per step and depth), captured once into a graph; afterwards br_val[0 .. roots)
+// and br_val2[0 .. roots) hold each responder's value at every root.
+cfr_status enqueue_best_responses(cfr_solver *s, cudaStream_t st) {
+    DevBR b1;
+    b1.dfirst = s->dfirst; b1.tfirst = s->tfirst; b1.dinfo = s->dinfo;
+    b1.kmask = s->kmask; b1.wbits = s->wbits;
+    b1.util = s->util64; b1.qbase = s->qbase; b1.iplayer = s->iplayer; b1.avg = s->avg;
+    b1.preach = s->br_reach; b1.val = s->br_val; b1.cfv = s->br_cfv; b1.astar = s->astar;
+    DevBR b2 = b1;
+    b2.preach = s->br_reach2;
+    b2.val = s->br_val2;
+    Launcher go;
+    go.pdl = false;          // the set-up kernels do not wait on a predecessor: plain ordering
+    if (s->H > 0) CK(go(k_average, nblocks(s->H), kBlock, 0, st, (const double *)s->S, (const double *)s->sigma064,
+                        (const int32_t *)s->qbase, (const int8_t *)s->iplayer, s->avg, s->H));
+    const int32_t nr = s->dlevel[1];
+    CK(go(k_fill, nblocks(nr), kBlock, 0, st, s->br_reach, nr, 1.0));
+    CK(go(k_fill, nblocks(nr), kBlock, 0, st, s->br_reach2, nr, 1.0));
     CK(cudaMemsetAsync(s->br_cfv, 0, sizeof(double) * (size_t)std::max<int64_t>(s->Q, 1), st));
+    go.cut(st);
+    go.pdl = true;           // the k_br2_* kernels wait (griddepcontrol.wait) before touching memory
     for (int32_t l = 0; l + 1 < s->L; ++l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
-        k_br_topdown<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
-        CK_LAUNCH();
+        CK(go(k_br2_topdown, nblocks(j1 - j0), kBlock, 0, st, b1, b2, j0, j1));
     }
     for (int32_t l = s->L - 1; l >= 0; --l) {
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
-        k_br_nodes<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
-        CK_LAUNCH();
-        if (h1 > h0) {
-            k_br_choose<<<nblocks(h1 - h0), kBlock, 0, st>>>(b, h0, h1, player);
-            CK_LAUNCH();
-        }
-        k_br_pick<<<nblocks(j1 - j0), kBlock, 0, st>>>(b, j0, j1, player);
-        CK_LAUNCH();
+        CK(go(k_br2_nodes, nblocks(j1 - j0), kBlock, 0, st, b1, b2, j0, j1));
+        if (h1 > h0) CK(go(k_br2_choose, nblocks(h1 - h0), kBlock, 0, st, b1, b2, h0, h1));
+        CK(go(k_br2_pick, nblocks(j1 - j0), kBlock, 0, st, b1, b2, j0, j1));
     }
-    CK(cudaMemcpyAsync(value, s->br_val, sizeof(double), cudaMemcpyDeviceToHost, st));
-    return sync_and_check(s);
+    return CFR_OK;
+}
+
+// Runs the captured best-response pass; the per-root values are then read from br_val / br_val2.
+cfr_status best_responses(cfr_solver *s) {
+    if (!s->avg) TRY(alloc_n(s, &s->avg, s->Q));
+    if (!s->br_reach2) {
+        if (!s->br_reach) {
+            TRY(alloc_n(s, &s->br_reach, s->Nd));
+            TRY(alloc_n(s, &s->br_val, s->Nd));
+            TRY(alloc_n(s, &s->br_cfv, s->Q));
+            TRY(alloc_n(s, &s->astar, s->H));
+        }
+        TRY(alloc_n(s, &s->br_reach2, s->Nd));
+        TRY(alloc_n(s, &s->br_val2, s->Nd));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    if (!s->br_exec) {
+        CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+        const cfr_status st = enqueue_best_responses(s, s->cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+        if (st != CFR_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) { s->poisoned = true; return set_err(s, CFR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)); }
+        const cudaError_t ie = cudaGraphInstantiate(&s->br_exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(ie);
+    }
+    CK(cudaGraphLaunch(s->br_exec, s->stream));
+    return CFR_OK;
 }
 
 }  // namespace
@@ -1041,25 +1077,12 @@ cfr_status cfrgb::root_nash_conv(cfr_solver *s, double *per_root, int32_t n) {
     if (s->Nd == 0 || n < s->dlevel[1]) return set_err(s, CFR_ERR_INVALID, "need %d root entries", s->Nd ? s->dlevel[1] : 0);
     DeviceGuard dg(s->device);
     const int32_t nr = s->dlevel[1];
-    if (!s->avg) TRY(alloc_n(s, &s->avg, s->Q));
-    if (!s->br_reach) {
-        TRY(alloc_n(s, &s->br_reach, s->Nd));
-        TRY(alloc_n(s, &s->br_val, s->Nd));
-        TRY(alloc_n(s, &s->br_cfv, s->Q));
-        TRY(alloc_n(s, &s->astar, s->H));
-    }
-    if (s->H > 0) {
-        k_average<<<nblocks(s->H), kBlock, 0, s->stream>>>(s->S, s->sigma064, s->qbase, s->iplayer, s->avg, s->H);
-        CK_LAUNCH();
-    }
-    std::vector<double> v((size_t)nr);
-    for (int32_t k = 0; k < nr; ++k) per_root[k] = 0.0;
-    for (int player = 1; player <= 2; ++player) {
-        double dummy = 0.0;
-        TRY(best_response(s, player, &dummy));
-        CK(cudaMemcpy(v.data(), s->br_val, sizeof(double) * nr, cudaMemcpyDeviceToHost));
-        for (int32_t k = 0; k < nr; ++k) per_root[k] += v[(size_t)k];
-    }
+    TRY(best_responses(s));
+    std::vector<double> v1((size_t)nr), v2((size_t)nr);
+    CK(cudaMemcpyAsync(v1.data(), s->br_val, sizeof(double) * nr, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(v2.data(), s->br_val2, sizeof(double) * nr, cudaMemcpyDeviceToHost, s->stream));
+    TRY(sync_and_check(s));
+    for (int32_t k = 0; k < nr; ++k) per_root[k] = v1[(size_t)k] + v2[(size_t)k];   // zero-sum
     return CFR_OK;
 }
 
@@ -1110,20 +1133,12 @@ cfr_status cfr_exploitability(cfr_solver *s, double *nash_conv, double *exploita
     DeviceGuard dg(s->device);
     double nc = 0.0;
     if (s->Nd > 0) {
-        if (!s->avg) TRY(alloc_n(s, &s->avg, s->Q));
-        if (!s->br_reach) {
-            TRY(alloc_n(s, &s->br_reach, s->Nd));
-            TRY(alloc_n(s, &s->br_val, s->Nd));
-            TRY(alloc_n(s, &s->br_cfv, s->Q));
-            TRY(alloc_n(s, &s->astar, s->H));
-        }
-        k_average<<<nblocks(s->H), kBlock, 0, s->stream>>>(s->S, s->sigma064, s->qbase, s->iplayer, s->avg, s->H);
-        CK_LAUNCH();
-        for (int p = 1; p <= 2; ++p) {
-            double v = 0.0;
-            TRY(best_response(s, p, &v));
-            nc += v;   // zero-sum: u_1(avg) + u_2(avg) = 0
-        }
+        TRY(best_responses(s));
+        double v[2] = {0.0, 0.0};
+        CK(cudaMemcpyAsync(&v[0], s->br_val, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(&v[1], s->br_val2, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        TRY(sync_and_check(s));
+        nc = v[0] + v[1];   // zero-sum: u_1(avg) + u_2(avg) = 0
     }
     if (nash_conv) *nash_conv = nc;
     if (exploitability) *exploitability = nc / 2.0;
@@ -1426,6 +1441,7 @@ void cfr_free(cfr_solver *s) {
     DeviceGuard dg(s->device);
     if (s->stream || s->cap) cudaStreamSynchronize(s->stream);
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->br_exec) cudaGraphExecDestroy(s->br_exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     for (auto &b : s->blocks) {
         if (s->cfg.dev_free) s->cfg.dev_free(b.first, s->cfg.alloc_ctx);

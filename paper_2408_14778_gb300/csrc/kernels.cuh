@@ -1121,5 +1121,44 @@ __global__ void __launch_bounds__(256) k_br_pick(DevBR b, int32_t j0, int32_t j1
     if (j < j1) br_pick<false>(b, j, player);
 }
 
+// Both players' best responses in one pass: b1 and b2 hold each responder's reaches and values and
+// share cfv and astar, which each responder writes at its own infosets only.
+__global__ void __launch_bounds__(256) k_br2_topdown(DevBR b1, DevBR b2, int32_t j0, int32_t j1) {
+    grid_dependency_wait();
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j >= j1) return;
+    br_topdown_node<false>(b1, j, 1);
+    br_topdown_node<false>(b2, j, 2);
+}
+
+__global__ void __launch_bounds__(256) k_br2_nodes(DevBR b1, DevBR b2, int32_t j0, int32_t j1) {
+    grid_dependency_wait();
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j >= j1) return;
+    br_node<false>(b1, j, 1);
+    br_node<false>(b2, j, 2);
+}
+
+__global__ void __launch_bounds__(256) k_br2_choose(DevBR b1, DevBR b2, int32_t h0, int32_t h1) {
+    grid_dependency_wait();
+    const int32_t h = h0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (h >= h1) return;
+    if (b1.iplayer[h] == 1) br_choose<false>(b1, h, 1);
+    else br_choose<false>(b2, h, 2);
+}
+
+__global__ void __launch_bounds__(256) k_br2_pick(DevBR b1, DevBR b2, int32_t j0, int32_t j1) {
+    grid_dependency_wait();
+    const int32_t j = j0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j >= j1) return;
+    br_pick<false>(b1, j, 1);
+    br_pick<false>(b2, j, 2);
+}
+
+__global__ void k_fill(double *p, int32_t n, double v) {
+    const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (i < n) p[i] = v;
+}
+
 }  // namespace
 }  // namespace cfrgb
