@@ -193,6 +193,8 @@ TTT_CHECK = 25             # iterations between exploitability evaluations
 TTT_MAX_ITERS = 100000
 TTT_ORACLE_SECONDS = 60.0
 LEAF_BLUEPRINT_ITERS = 4000
+LEAF_REFRESH = 10            # depth-limited solving: iterations between leaf refreshes
+LEAF_MAX_ITERS = 20000
 
 
 def _ttt_run(step, expl, max_iters: int, max_seconds: float) -> dict:
@@ -291,7 +293,16 @@ def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
                          "exploitability": ex_full,
                          "time_to_1e-3": (ttt or {}).get("gpu_rank13_depth10")}
     below = cfr.cfr_average_strategy(s)
+    blueprint_S = cfr.cfr_get_state(s)["strat_sum"]
     s.close()
+    # the pipeline with perfect leaves: the full solve's own values at the cut, fixed
+    t0 = time.perf_counter()
+    y_exact = dl.blueprint_leaf_values(cut, blueprint_S, device=local)
+    top = dl.solve_with_fixed_leaves(cut, y_exact, LEAF_BLUEPRINT_ITERS, device=local)
+    out["depth_limited_exact_leaves"] = {
+        "iterations": LEAF_BLUEPRINT_ITERS, "seconds": time.perf_counter() - t0,
+        "full_game_exploitability": dl.full_game_exploitability(g, dl.combined_strategy(cut, top, below), device=local),
+        "note": "leaves fixed to the full-depth solve's deal values at the cut: what a perfect network gives"}
     t0 = time.perf_counter()
     X, Y = dl.generate_samples(cut, per_node=args.leaf_samples_per_node, iterations=300, seed=args.seed,
                                device=local)
@@ -322,9 +333,10 @@ def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
     for name, model, ranges in (("trained", net, cfr.CFR_AVERAGE_STRATEGY),
                                 ("trained_current_ranges", net, cfr.CFR_CURRENT_STRATEGY),
                                 ("untrained", untrained, cfr.CFR_AVERAGE_STRATEGY)):
-        d = dl.DepthLimitedSolver(cut, model, refresh=1, device=local, ranges=ranges)
+        d = dl.DepthLimitedSolver(cut, model, refresh=LEAF_REFRESH, device=local, ranges=ranges)
         cfr.cfr_synchronize(d.s)
-        r = _ttt_run(d.iterate, d.exploitability, TTT_MAX_ITERS, 20.0)
+        r = _ttt_run(d.iterate, d.exploitability, LEAF_MAX_ITERS, 20.0)
+        r["leaf_refresh_every"] = LEAF_REFRESH
         r["full_game_exploitability"] = dl.full_game_exploitability(
             g, dl.combined_strategy(cut, d.average_strategy(), below), device=local)
         r["leaf_ranges"] = "average strategy" if ranges == cfr.CFR_AVERAGE_STRATEGY else "current strategy"

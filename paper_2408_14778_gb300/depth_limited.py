@@ -413,6 +413,46 @@ class DepthLimitedSolver:
         self.s.close()
 
 
+def blueprint_leaf_values(cut: Cut, strat_sum: np.ndarray, device=None):
+    """The leaves' values in the network's output layout ([rows][338], FP32 CUDA tensor, divided by the
+    payoff bound) when the full game is played by the average strategy of strat_sum (a full-game solve's
+    strategy sums): each cut node's deal values under that play.  With these fixed leaves the
+    depth-limited game's solution should reproduce the full solve above the cut - the check of the cut,
+    the leaf indices and the combination, and the bound on what a perfect network could give."""
+    import torch
+
+    v = cut.view
+    g = v.g
+    s = cfr_load_tree(g, variant=CFR_PLUS, precision=CFR_FP32, fuse_levels=0, device=device)
+    S = np.asarray(strat_sum, dtype=np.float64)
+    cfr_set_state(s, S, S, 1)                  # sigma := the average strategy
+    cfr_iterate(s, 1)
+    u1 = cfr_get_nodes(s)["u1"]
+    s.close()
+    umax = float(np.max(np.abs(g.utility))) or 1.0
+    rows = cut.cut_nodes.size
+    y = np.zeros(rows * 2 * RANGE, np.float32)
+    Pt = cut.top_public.size
+    k = (cut.leaf_nodes.astype(np.int64) - 1) // Pt
+    j = (cut.leaf_nodes.astype(np.int64) - 1) % Pt
+    y[cut.leaf_src] = u1[v.node(k, cut.top_public[j])] / umax
+    dev = f"cuda:{device if device is not None else torch.cuda.current_device()}"
+    return torch.tensor(y.reshape(rows, 2 * RANGE), device=dev)
+
+
+def solve_with_fixed_leaves(cut: Cut, y, iterations: int, device=None):
+    """CFR+ on the depth-limited game with the leaves set once from y (the network output layout);
+    returns the average strategy (depth-limited caller slots)."""
+    s = cfr_load_tree(cut.game, variant=CFR_PLUS, precision=CFR_FP32, device=device)
+    cfr_set_leaves(s, cut.leaf_nodes, cut.leaf_src)
+    umax = float(np.max(np.abs(cut.view.g.utility))) or 1.0
+    cfr_set_leaf_values(s, y, umax)
+    cfr_iterate(s, iterations)
+    avg = cfr_average_strategy(s)
+    s.close()
+    return avg
+
+
 def combined_strategy(cut: Cut, top_avg: np.ndarray, below_avg: np.ndarray) -> np.ndarray:
     """A full-game strategy (caller slots of the full game): the depth-limited game's average strategy
     above the cut, below_avg (for instance a full-depth solve's) everywhere else."""

@@ -145,3 +145,19 @@ def test_trained_network_beats_an_untrained_one():
         expl[name] = dl.full_game_exploitability(game, dl.combined_strategy(cut, d.average_strategy(), below))
         d.close()
     assert expl["trained"] < 0.5 * expl["untrained"], expl
+
+
+def test_exact_leaves_reproduce_the_full_solve():
+    # leaves fixed to the full solve's own deal values at the cut: the depth-limited solution, completed
+    # below the cut by the full solve, is as unexploitable as the full solve (checks the cut game, the
+    # leaf indices and the strategy combination end to end)
+    game = gamegen.config("rank13_depth10", seed=3, target_nodes=60_000)
+    cut = dl.cut_game(game, depth=4)
+    full = cfr.cfr_load_tree(game, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32)
+    cfr.cfr_iterate(full, 3000)
+    below = cfr.cfr_average_strategy(full)
+    ex_full = cfr.cfr_exploitability(full)[1]
+    y = dl.blueprint_leaf_values(cut, cfr.cfr_get_state(full)["strat_sum"])
+    top = dl.solve_with_fixed_leaves(cut, y, 3000)
+    ex = dl.full_game_exploitability(game, dl.combined_strategy(cut, top, below))
+    assert ex <= 2.0 * ex_full + 2e-3, (ex, ex_full)
