@@ -65,3 +65,18 @@ def test_full_size_exploitability(full):
     assert abs(nc_g - nc_o) <= 1e-5 * max(1.0, abs(nc_o)), (nc_g, nc_o)
     nc_chk, ex_chk = o.exploitability(cfr.cfr_average_strategy(s))
     assert abs(nc_g - nc_chk) <= TOL_EXPL and abs(ex_g - ex_chk) <= TOL_EXPL
+
+
+def test_fp64_bit_identical_above_the_parallel_layout_threshold():
+    # 2.0e6 nodes: the multi-threaded host layout builder (2^20 nodes and more) feeds FP64 mode, whose
+    # deterministic regret sums walk the per-infoset node lists; three iterations equal the oracle's bit for bit
+    g = gamegen.config("rank13_depth10", seed=5)
+    assert g.num_nodes >= 1 << 20
+    o = oracle.Oracle(g)
+    s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP64)
+    o.iterate(3, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+    cfr.cfr_iterate(s, 3)
+    gs, os_ = cfr.cfr_get_state(s), o.state()
+    for k in ("cum_regret", "strat_sum"):
+        np.testing.assert_array_equal(gs[k], os_[k])
+    s.close()
