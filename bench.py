@@ -348,35 +348,48 @@ def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
 
 
 def batched_measurement(args, local: int) -> dict:
-    out = _batched_run(args, local, gamegen_kw=dict(min_nodes=1e2, max_nodes=1e5),
-                       label="log-uniform 1e2-1e5 nodes, depth 4-10, 2-5 actions")
-    out["small_games"] = _batched_run(args, local, gamegen_kw=dict(min_nodes=1e2, max_nodes=1e3),
-                                      label="log-uniform 1e2-1e3 nodes, depth 4-10, 2-5 actions", ttt=False)
+    import paper_2408_14778_gb300 as cfr
+
+    cfg4 = _subgames(args, dict(min_nodes=1e2, max_nodes=1e5))
+    label = "log-uniform 1e2-1e5 nodes, depth 4-10, 2-5 actions"
+    out = _batched_run(args, local, cfg4, label)
+    out["alternating"] = _batched_run(args, local, cfg4, label, update_mode=cfr.CFR_ALTERNATING)
+    small = _subgames(args, dict(min_nodes=1e2, max_nodes=1e3))
+    out["small_games"] = _batched_run(args, local, small, "log-uniform 1e2-1e3 nodes, depth 4-10, 2-5 actions",
+                                      ttt=False)
     return out
 
 
-def _batched_run(args, local: int, gamegen_kw: dict, label: str, ttt: bool = True) -> dict:
+def _subgames(args, kw: dict):
+    import gamegen
+
+    t0 = time.perf_counter()
+    games = gamegen.batch_subgames(args.batched_games, seed=args.seed, **kw)
+    return games, time.perf_counter() - t0
+
+
+def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, update_mode: int = 0) -> dict:
     """Batched CFR+: independent subgames (log-uniform 1e2-1e5 nodes, depth 4-10, 2-5 actions) advanced
     together by one persistent launch per call, launch shape from the autotuner.  Reports subgames/s and
     node updates/s for 500 iterations, the p50/p99 per-subgame iteration time, the exploitability reached,
     the time until every subgame's exploitability is at most 1e-3 (capped), and the same games run as ONE
-    tree (a uniform chance root over them) by the plain full-tree solver on the same GPU."""
+    tree (a uniform chance root over them) by the plain full-tree solver on the same GPU; update_mode:
+    simultaneous (0) or alternating (1) updates, for both."""
     import numpy as np
     import torch
 
     import gamegen
     import paper_2408_14778_gb300 as cfr
 
-    t0 = time.perf_counter()
-    games = gamegen.batch_subgames(args.batched_games, seed=args.seed, **gamegen_kw)
-    gen_s = time.perf_counter() - t0
+    games, gen_s = games_gen
     nodes = np.array([g.num_nodes for g in games], dtype=np.int64)
     cache = os.path.join(os.path.expanduser("~"), ".cache", "paper_2408_14778_gb300", "batch_tuning.json")
     t0 = time.perf_counter()
-    tune = cfr.cfr_batch_tune(games, variant=cfr.CFR_PLUS, device=local, cache_path=cache)
+    tune = cfr.cfr_batch_tune(games, variant=cfr.CFR_PLUS, device=local, cache_path=cache, update_mode=update_mode)
     tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    b = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"])
+    b = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"],
+                           update_mode=update_mode)
     cfr.cfr_batch_set_tuning(b, tune["threads_per_block"], tune["blocks_per_sm"])
     load_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(local)
@@ -393,6 +406,7 @@ def _batched_run(args, local: int, gamegen_kw: dict, label: str, ttt: bool = Tru
     info = cfr.cfr_batch_get_info(b)
     out = {"subgames": label, "games": len(games), "nodes_total": int(nodes.sum()), "nodes_min": int(nodes.min()),
            "nodes_max": int(nodes.max()), "nodes_mean": float(nodes.mean()), "variant": "cfr+ (linear averaging)",
+           "updates": "alternating" if update_mode else "simultaneous",
            "iterations": K, "seconds": sec, "subgames_per_s": len(games) / sec,
            "node_updates_per_s": float(nodes.sum()) * K / sec,
            "per_subgame_us_per_iteration": {"p50": float(np.percentile(per_game, 50)),
@@ -405,7 +419,8 @@ def _batched_run(args, local: int, gamegen_kw: dict, label: str, ttt: bool = Tru
            "host_seconds": {"generate": gen_s, "tune": tune_s, "load": load_s}}
     # time until every subgame's exploitability is at most 1e-3 (evaluations included)
     if ttt:
-        b2 = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"])
+        b2 = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"],
+                                update_mode=update_mode)
         cfr.cfr_batch_set_tuning(b2, tune["threads_per_block"], tune["blocks_per_sm"])
         t0, it, worst = time.perf_counter(), 0, float("inf")
         while it < 20000 and time.perf_counter() - t0 < 60.0:
@@ -422,7 +437,7 @@ def _batched_run(args, local: int, gamegen_kw: dict, label: str, ttt: bool = Tru
     # the plain full-tree solver on the same games as one tree
     t0 = time.perf_counter()
     root = gamegen.with_chance_root(games)
-    s = cfr.cfr_load_tree(root, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, device=local)
+    s = cfr.cfr_load_tree(root, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, device=local, update_mode=update_mode)
     tree_load_s = time.perf_counter() - t0
     cfr.cfr_iterate(s, 3)
     torch.cuda.synchronize()

@@ -282,8 +282,8 @@ void cfr_free(cfr_solver *s);
  * iterations there depth by depth (Section 3.2's steps, as cfr_iterate's kernels compute them per node
  * and infoset), writes R, S and sigma back and takes the next game.  Every other game (larger, or with
  * a node of more than 32 actions) runs in one forest (one root per game) through cfr_iterate's
- * per-depth kernels on a second stream, concurrently.  FP32 mode with FP64 accumulators, simultaneous
- * updates, every variant.  Game g's arrays use its own caller numbering. */
+ * per-depth kernels on a second stream, concurrently.  FP32 mode with FP64 accumulators, simultaneous or
+ * alternating updates, every variant.  Game g's arrays use its own caller numbering. */
 typedef struct cfr_batch cfr_batch;   /* opaque; owned by the library */
 
 typedef struct {
@@ -306,8 +306,8 @@ typedef struct {
 } cfr_batch_info;
 
 /* Validates and lays out num_games >= 1 games (each as cfr_load_tree would; the combined size must stay
- * below 2^31 - 1 nodes).  CFR_ERR_UNSUPPORTED for FP64 mode or alternating updates.  c may be NULL
- * (defaults: vanilla; pass variant CFR_PLUS for CFR+). */
+ * below 2^31 - 1 nodes).  CFR_ERR_UNSUPPORTED for FP64 mode.  c may be NULL (defaults: vanilla; pass
+ * variant CFR_PLUS for CFR+). */
 cfr_status cfr_batch_load(const cfr_game_desc *games, int32_t num_games, const cfr_config *c, cfr_batch **out);
 
 /* Queues n >= 0 iterations of every game (one persistent launch).  Asynchronous on the batch's stream. */

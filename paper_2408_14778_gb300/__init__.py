@@ -497,9 +497,10 @@ class Batch:
 
 
 def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=None, stream=None,
-                   allocator: str = "torch", dcfr=(1.5, 0.0, 2.0), split_nodes: int = 0) -> Batch:
-    """Loads a list of games for batched solving (FP32 mode, simultaneous updates).  split_nodes:
-    cfr_config.batch_split_nodes (0 default, negative: every game in the persistent kernel)."""
+                   allocator: str = "torch", dcfr=(1.5, 0.0, 2.0), split_nodes: int = 0,
+                   update_mode=CFR_SIMULTANEOUS) -> Batch:
+    """Loads a list of games for batched solving (FP32 mode).  split_nodes: cfr_config.batch_split_nodes
+    (0 default, negative: every game whose image fits shared memory in the persistent kernel)."""
     import torch
 
     if not torch.cuda.is_available():
@@ -512,6 +513,7 @@ def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=N
     cfg.device, cfg.cuda_stream = dev, st_handle
     cfg.dcfr_alpha, cfg.dcfr_beta, cfg.dcfr_gamma = (float(x) for x in dcfr)
     cfg.batch_split_nodes = int(split_nodes)
+    cfg.update_mode = int(update_mode)
     alloc = None
     if allocator == "torch":
         alloc = _TorchAllocator(dev, st_handle)
@@ -524,6 +526,7 @@ def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=N
     _check_batch(lib().cfr_batch_load(arr, len(descs), ctypes.byref(cfg), ctypes.byref(h)))
     b = Batch(h, alloc, games)
     b._variant = int(variant)
+    b._update_mode = int(update_mode)
     return b
 
 
@@ -553,7 +556,8 @@ def cfr_batch_autotune(b: Batch, trial_iterations: int = 3, cache_path: str | No
 
     import torch
 
-    key = f"{torch.cuda.get_device_name()}|{_size_bucket(b)}|variant={cfr_batch_get_info(b)['variant']}"
+    key = (f"{torch.cuda.get_device_name()}|{_size_bucket(b)}|variant={cfr_batch_get_info(b)['variant']}"
+           f"|mode={getattr(b, '_update_mode', 0)}")
     disk = {}
     if cache_path and os.path.exists(cache_path):
         try:
@@ -618,7 +622,8 @@ def cfr_batch_get_info(b: Batch) -> dict:
 
 
 def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 512, 2048, -1), trial_iterations: int = 10,
-                   device=None, cache_path: str | None = None, dcfr=(1.5, 0.0, 2.0)) -> dict:
+                   device=None, cache_path: str | None = None, dcfr=(1.5, 0.0, 2.0),
+                   update_mode=CFR_SIMULTANEOUS) -> dict:
     """The batch's size split (which games run as one forest through the per-depth kernels, which in the
     persistent kernel) and the persistent launch shape: for each candidate split the batch is loaded,
     the launch shape measured (cfr_batch_autotune), and trial_iterations timed; the fastest is kept and
@@ -631,7 +636,7 @@ def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 512, 2048, -1), trial_ite
     import torch
 
     probe = Batch(None, None, games)
-    key = f"{torch.cuda.get_device_name()}|{_size_bucket(probe)}|variant={int(variant)}|split"
+    key = f"{torch.cuda.get_device_name()}|{_size_bucket(probe)}|variant={int(variant)}|mode={int(update_mode)}|split"
     disk = {}
     if cache_path and os.path.exists(cache_path):
         try:
@@ -643,7 +648,7 @@ def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 512, 2048, -1), trial_ite
         return dict(hit, us_per_iteration=None, cached=True, trials=None, key=key)
     trials = []
     for split in splits:
-        b = cfr_batch_load(games, variant=variant, device=device, dcfr=dcfr, split_nodes=split)
+        b = cfr_batch_load(games, variant=variant, device=device, dcfr=dcfr, split_nodes=split, update_mode=update_mode)
         t = _BatchTuning()                               # measured for this split (no cache lookup)
         _check_batch(lib().cfr_batch_autotune(b.handle, 2, ctypes.byref(t), None), b.handle)
         shape = {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm}

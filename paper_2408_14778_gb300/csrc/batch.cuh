@@ -111,7 +111,8 @@ template <int NA, int V>
 __global__ void __launch_bounds__(256) k_batch_smem(const int32_t *images, const int64_t *img_off, const int32_t *order,
                                                     int32_t G, int32_t *next, double *gR, double *gS, float *gsigma,
                                                     const int64_t *T0p, int32_t K, int32_t linear, double3 dcfr,
-                                                    unsigned long long *t_start, unsigned long long *t_end) {
+                                                    int32_t alternating, unsigned long long *t_start,
+                                                    unsigned long long *t_end) {
     grid_dependency_wait();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t slot;
@@ -188,21 +189,27 @@ __global__ void __launch_bounds__(256) k_batch_smem(const int32_t *images, const
                 u.fneg = tb / (tb + 1.0);
                 u.w = (float)pow(T, dcfr.z);
             }
-            for (int l = 0; l < L; ++l) {
-                for (int32_t h = hlevel[l] + tid; h < hlevel[l + 1]; h += bs) {
-                    for (int32_t q = t.qbase[h]; q < t.qbase[h + 1]; ++q) t.inst[q] = 0.f;
-                    own_infoset<float, false>(t, h);
+            // one pass for both players, or (alternating updates) player 1's and then player 2's under
+            // player 1's new strategy, with the same iteration weights
+            for (int pass = 0; pass < (alternating ? 2 : 1); ++pass) {
+                t.pmask = alternating ? (pass == 0 ? 2 : 4) : 6;
+                for (int l = 0; l < L; ++l) {
+                    for (int32_t h = hlevel[l] + tid; h < hlevel[l + 1]; h += bs) {
+                        for (int32_t q = t.qbase[h]; q < t.qbase[h + 1]; ++q) t.inst[q] = 0.f;
+                        own_infoset<float, false>(t, h);
+                    }
+                    if (l + 1 < L)
+                        for (int32_t j = dlevel[l] + tid; j < dlevel[l + 1]; j += bs) td_node<float, true, false>(t, j);
+                    __syncthreads();
                 }
-                if (l + 1 < L)
-                    for (int32_t j = dlevel[l] + tid; j < dlevel[l + 1]; j += bs) td_node<float, true, false>(t, j);
+                for (int l = L - 1; l >= 0; --l) {
+                    for (int32_t j = dlevel[l] + tid; j < dlevel[l + 1]; j += bs) bu_node<float, false, false>(t, j);
+                    __syncthreads();
+                }
+                for (int32_t h = tid; h < Hp; h += bs)
+                    if (collects(t, t.iplayer[h])) update_row<NA, V, false>(t, h, u);
                 __syncthreads();
             }
-            for (int l = L - 1; l >= 0; --l) {
-                for (int32_t j = dlevel[l] + tid; j < dlevel[l + 1]; j += bs) bu_node<float, false, false>(t, j);
-                __syncthreads();
-            }
-            for (int32_t h = tid; h < Hp; h += bs) update_row<NA, V, false>(t, h, u);
-            __syncthreads();
         }
         if (tid == 0) t_end[g] = batch_clock();
         for (int32_t q = tid; q < Q; q += bs) {

@@ -260,7 +260,9 @@ cudaError_t launch_class(cfr_batch *b, cudaStream_t st, int c, int32_t K, int gr
     float *gs = b->sigma;
     const int64_t *T0 = b->d_iter;
     unsigned long long *t0 = b->t_start, *t1 = b->t_end;
-    void *args[] = {&images, &img_off, &order, &G, &next, &gR, &gS, &gs, &T0, &K, (void *)&linear, (void *)&dc, &t0, &t1};
+    int32_t alternating = b->cfg.update_mode == CFR_ALTERNATING;
+    void *args[] = {&images, &img_off, &order, &G, &next, &gR, &gS, &gs, &T0, &K, (void *)&linear, (void *)&dc,
+                    &alternating, &t0, &t1};
     return cudaLaunchKernel(smem_kernel_for(b), dim3((unsigned)grid), dim3((unsigned)threads), args,
                             (size_t)b->cls_smem[(size_t)c], st);
 }
@@ -536,8 +538,8 @@ cfr_status cfr_batch_load(const cfr_game_desc *games, int32_t num_games, const c
         return berr(nullptr, CFR_ERR_INVALID, "variant %d unknown", cfg.variant);
     if (cfg.precision != CFR_FP32)
         return berr(nullptr, CFR_ERR_UNSUPPORTED, "batched solving runs in FP32 mode (FP64 accumulators)");
-    if (cfg.update_mode != CFR_SIMULTANEOUS)
-        return berr(nullptr, CFR_ERR_UNSUPPORTED, "batched solving runs simultaneous updates");
+    if (cfg.update_mode != CFR_SIMULTANEOUS && cfg.update_mode != CFR_ALTERNATING)
+        return berr(nullptr, CFR_ERR_INVALID, "update_mode %d unknown", cfg.update_mode);
     if (cfg.avg_weight == CFR_AVG_DEFAULT) cfg.avg_weight = cfg.variant == CFR_VANILLA ? CFR_AVG_UNIFORM : CFR_AVG_LINEAR;
     if (cfg.avg_weight != CFR_AVG_UNIFORM && cfg.avg_weight != CFR_AVG_LINEAR)
         return berr(nullptr, CFR_ERR_INVALID, "avg_weight %d unknown", cfg.avg_weight);
