@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-exploitability-1e-3 measurement")
     ap.add_argument("--no-leaf", action="store_true", help="skip the learned-leaf depth-limited measurement")
-    ap.add_argument("--leaf-samples-per-node", type=int, default=64)
-    ap.add_argument("--leaf-train-steps", type=int, default=3000)
+    ap.add_argument("--leaf-samples-per-node", type=int, default=256)
+    ap.add_argument("--leaf-train-steps", type=int, default=10000)
     ap.add_argument("--batched-games", type=int, default=4096,
                     help="subgames of the batched measurement (0: skip it)")
     return ap.parse_args()
@@ -310,12 +310,21 @@ def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
                       "solver_iterations": 300, "seconds": time.perf_counter() - t0,
                       "source": "full-depth GPU CFR+ on the cut subgames under random (Dirichlet) ranges"}
     net = dl.make_network(seed=args.seed, device=local)
+    # a random tenth of the samples is held out of training
+    perm = np.random.default_rng(args.seed).permutation(X.shape[0])
+    nh = max(1, X.shape[0] // 10)
+    Xh, Yh = X[perm[:nh]], Y[perm[:nh]]
+    Xt, Yt = X[perm[nh:]], Y[perm[nh:]]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = dl.train(net, X, Y, steps=args.leaf_train_steps, batch=1024, lr=1e-3, seed=args.seed, device=local)
+    hist = dl.train(net, Xt, Yt, steps=args.leaf_train_steps, batch=1024, lr=1e-3, seed=args.seed, device=local)
     torch.cuda.synchronize()
+    held = float(cfr.cfr_mlp_backward(net, torch.tensor(Xh, device=f"cuda:{local}"),
+                                      torch.tensor(Yh, device=f"cuda:{local}")).item())
     out["training"] = {"steps": args.leaf_train_steps, "batch": 1024, "optimizer": "adam, lr 1e-3 decaying to 1e-4",
-                       "seconds": time.perf_counter() - t0, "mse_first": hist[0], "mse_last": hist[-1]}
+                       "samples_trained": int(Xt.shape[0]), "samples_held_out": int(nh),
+                       "seconds": time.perf_counter() - t0, "mse_first": hist[0], "mse_last": hist[-1],
+                       "mse_held_out": held, "note": "mean squared error of values divided by the payoff bound"}
     # the network's matrix products at a batch of 4096
     xb = torch.randn(4096, 402, device=f"cuda:{local}")
     tb = torch.randn(4096, 338, device=f"cuda:{local}")
