@@ -359,10 +359,10 @@ def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
 def batched_measurement(args, local: int) -> dict:
     import paper_2408_14778_gb300 as cfr
 
-    cfg4 = _subgames(args, dict(min_nodes=1e2, max_nodes=1e5))
+    wide_range = _subgames(args, dict(min_nodes=1e2, max_nodes=1e5))
     label = "log-uniform 1e2-1e5 nodes, depth 4-10, 2-5 actions"
-    out = _batched_run(args, local, cfg4, label)
-    out["alternating"] = _batched_run(args, local, cfg4, label, update_mode=cfr.CFR_ALTERNATING)
+    out = _batched_run(args, local, wide_range, label)
+    out["alternating"] = _batched_run(args, local, wide_range, label, update_mode=cfr.CFR_ALTERNATING)
     small = _subgames(args, dict(min_nodes=1e2, max_nodes=1e3))
     out["small_games"] = _batched_run(args, local, small, "log-uniform 1e2-1e3 nodes, depth 4-10, 2-5 actions",
                                       ttt=False)

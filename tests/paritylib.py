@@ -1,6 +1,6 @@
 """Comparison helpers for the GPU-vs-oracle parity tests.
 
-Tolerances (the benchmark spec): FP64 mode 1e-12, FP32 mode 1e-5 (normwise relative, per array:
+Tolerances: FP64 mode 1e-12, FP32 mode 1e-5 (normwise relative, per array:
 max_i |x_i - y_i| / max_i |y_i|), exploitability 1e-6 absolute.
 """
 import numpy as np
