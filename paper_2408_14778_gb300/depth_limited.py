@@ -26,7 +26,6 @@ CFR, range and network computation runs in the library's kernels.
 """
 from __future__ import annotations
 
-import time
 from dataclasses import dataclass
 
 import numpy as np
@@ -469,9 +468,3 @@ def full_game_exploitability(game, strategy: np.ndarray, device=None) -> float:
     nc = cfr_exploitability(s)[0]
     s.close()
     return nc / 2.0
-
-
-def timed(fn):
-    t0 = time.perf_counter()
-    out = fn()
-    return out, time.perf_counter() - t0
