@@ -60,8 +60,9 @@ __device__ __forceinline__ int terminals_before(const uint32_t *wb, int a) {
 }
 
 // Exact float -> double by bit manipulation (integer pipe); zero keeps its sign, and subnormal,
-// infinite or NaN inputs take the hardware conversion.  GB300's FP64 pipe is narrow, so the update
-// keeps it for the two FP64 additions.
+// infinite or NaN inputs take the hardware conversion.  GB300's FP64 pipe is narrow (ncu: the row update
+// had it 80% busy with two additions and a conversion per slot); with narrow and add_nonneg below, the
+// update's only FP64 operation per slot is the regret addition.
 __device__ __forceinline__ double widen(float x) {
     const uint32_t b = __float_as_uint(x);
     if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
@@ -69,6 +70,47 @@ __device__ __forceinline__ double widen(float x) {
     if (e == 0u || e == 0xffu) return (double)x;
     const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
     return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// double -> float rounded to nearest, ties to even, by integer operations where the result is a normal
+// FP32 number (biased double exponent 897 .. 1150): the top 23 of the 52 fraction bits are kept and the
+// 29 dropped bits round them (above half, or exactly half with an odd kept part, adds one; a carry out of
+// the fraction moves into the exponent, and past the largest finite value gives infinity, as the
+// rounding rule does).  Zero, subnormal results, overflow of the exponent range, infinities and NaN take
+// the hardware conversion, which would otherwise occupy the FP64 pipe once per slot.
+__device__ __forceinline__ float narrow(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    if (e - 897u > 253u) return __double2float_rn(x);
+    const uint32_t m = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+    const uint32_t up = ((lo & 0x1fffffffu) + (m & 1u)) > 0x10000000u;
+    return __uint_as_float((hi & 0x80000000u) | (m + up));
+}
+
+// a + b for a, b >= 0, rounded to nearest, ties to even, by integer operations (the average-strategy
+// sum S and its increment are never negative).  With A >= B as bit patterns, B's significand is shifted
+// right by the exponent gap, the bits shifted out kept as a sticky bit below the two guard bits; the
+// sum is normalised by at most one place (a carry), then rounded on the three low bits, a carry out of
+// the significand moving into the exponent and past the largest finite value giving infinity.  A zero
+// or subnormal smaller operand, and any infinity, NaN or negative input, take the FP64 addition.
+__device__ __forceinline__ double add_nonneg(double a, double b) {
+    uint64_t A = (uint64_t)__double_as_longlong(a), B = (uint64_t)__double_as_longlong(b);
+    if (A < B) { const uint64_t t = A; A = B; B = t; }
+    const uint32_t ea = (uint32_t)(A >> 52), eb = (uint32_t)(B >> 52);
+    if (eb == 0u || ea >= 0x7ffu) return a + b;
+    const uint64_t F = (1ull << 52) - 1ull, H = 1ull << 52;
+    const uint64_t ma = ((A & F) | H) << 3;
+    uint64_t mb = ((B & F) | H) << 3;
+    const uint32_t d = ea - eb;
+    mb = d >= 56u ? 1ull : (mb >> d) | (uint64_t)((mb & ((1ull << d) - 1ull)) != 0ull);
+    uint64_t sum = ma + mb;
+    uint32_t e = ea;
+    if (sum >> 56) { sum = (sum >> 1) | (sum & 1ull); ++e; }
+    const uint32_t low = (uint32_t)sum & 7u;
+    uint64_t sig = sum >> 3;
+    sig += (low > 4u) || (low == 4u && (sig & 1ull));
+    if (sig >> 53) { sig >>= 1; ++e; }
+    return __longlong_as_double((long long)(e >= 0x7ffu ? 0x7ff0000000000000ull : ((uint64_t)e << 52) | (sig & F)));
 }
 
 // Sum over the block (every thread gets it); scratch32 holds one value per warp.
@@ -326,7 +368,7 @@ __device__ __forceinline__ float update_regret(double *R, double rr, float in, c
     if constexpr (V == CFRV_DISCOUNTED) r0 *= positive ? u.fpos : u.fneg;
     const double r = V == CFRV_PLUS && !positive ? 0.0 : r0;
     *R = r;
-    return positive ? __double2float_rn(r) : 0.f;
+    return positive ? narrow(r) : 0.f;
 }
 
 // sigma' of an infoset whose positive regrets sum to `sum` below FP32's normal range: FP64 division.
@@ -390,7 +432,7 @@ __device__ __forceinline__ void update_row(const DevTree<float> &t, int32_t h, c
             if (a < na && sg[a] != 0.f) rr[a] = ldm<C>(t.S + qs + a);
 #pragma unroll
         for (int a = 0; a < NA; ++a)
-            if (a < na && sg[a] != 0.f) t.S[qs + a] = rr[a] + widen(sg[a]);
+            if (a < na && sg[a] != 0.f) t.S[qs + a] = add_nonneg(rr[a], widen(sg[a]));
 #pragma unroll
         for (int a = 0; a < NA; ++a)
             if (a < na) sum += pos[a];
@@ -414,7 +456,7 @@ __device__ __forceinline__ void update_row(const DevTree<float> &t, int32_t h, c
     for (int a = 0; a < na; ++a) {
         pos[a] = update_regret<V>(t.R + qs + a, ldm<C>(t.R + qs + a), ldm<C>(t.inst + qs + a), u);
         const float inc = wo * ldm<C>(t.sigma + qs + a);
-        if (inc != 0.f) t.S[qs + a] = ldm<C>(t.S + qs + a) + widen(inc);
+        if (inc != 0.f) t.S[qs + a] = add_nonneg(ldm<C>(t.S + qs + a), widen(inc));
     }
     for (int a = 0; a < na; ++a) sum += pos[a];
     if (sum >= 1e-30f) {
