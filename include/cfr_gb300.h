@@ -251,6 +251,14 @@ cfr_status cfr_set_leaf_values(cfr_solver *s, const float *src, double scale);
  * the stream (a per-iteration progress read).  0 before the first iteration. */
 cfr_status cfr_root_value(cfr_solver *s, double *u1);
 
+/* cfr_root_value without waiting: enqueues on the solver's stream, after the work queued so far, the
+ * write of that value (as an FP64 number) to *u1, and returns.  u1 is caller-owned PAGE-LOCKED host
+ * memory (cudaHostAlloc or cudaHostRegister; PyTorch's pin_memory) that the GPU can address; it holds
+ * the value once the stream has passed this point (cfr_synchronize, or an event recorded on the stream
+ * after this call).  For a loop that reads each iteration's value while the next one runs.
+ * CFR_ERR_INVALID if u1 is NULL or not page-locked. */
+cfr_status cfr_root_value_async(cfr_solver *s, double *u1);
+
 /* Runs ONE iteration (it counts: T advances by 1) as individually launched kernels on the solver's
  * stream with CUDA events between its phases, and returns per phase the elapsed time in
  * microseconds (us), the phase's algorithmic bytes (bytes), its kind (CFR_PHASE_*) and depth (depth;

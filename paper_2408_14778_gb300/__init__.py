@@ -140,6 +140,7 @@ def lib():
         L.cfr_get_nodes.argtypes = [_P, _P, _P, _P, ctypes.c_int64]
         L.cfr_get_info.argtypes = [_P, ctypes.POINTER(_Info)]
         L.cfr_root_value.argtypes = [_P, _P]
+        L.cfr_root_value_async.argtypes = [_P, _P]
         L.cfr_phase_times.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int32, _P]
         L.cfr_phase_times.restype = ctypes.c_int
         L.cfr_exploitability_static.argtypes = [_P, _P, _P]
@@ -192,7 +193,7 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         for name in ("cfr_validate", "cfr_load_tree", "cfr_iterate", "cfr_synchronize", "cfr_average_strategy",
                      "cfr_current_strategy", "cfr_exploitability", "cfr_get_state", "cfr_set_state", "cfr_get_nodes",
-                     "cfr_get_info", "cfr_root_value"):
+                     "cfr_get_info", "cfr_root_value", "cfr_root_value_async"):
             getattr(L, name).restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
@@ -374,6 +375,13 @@ def cfr_root_value(s: "Solver") -> float:
     return v.value
 
 
+def cfr_root_value_async(s: "Solver", dst: int):
+    """Enqueues the write of u-check(sigma^T, v_0, 1) as a float64 to dst (the address of page-locked host
+    memory, e.g. a pinned torch tensor's data_ptr()) on the solver's stream; it is there once the stream
+    has passed this point."""
+    _check(lib().cfr_root_value_async(s.handle, ctypes.c_void_p(int(dst))), s.handle)
+
+
 def cfr_phase_times(s: "Solver") -> list:
     """Runs one iteration as individually timed kernels (it counts as an iteration) and returns its
     phases in launch order, each a dict: name, kind (CFR_PHASE_*), depth, us and algorithmic bytes."""
@@ -462,6 +470,7 @@ class Solver:
     set_state = cfr_set_state
     get_nodes = cfr_get_nodes
     root_value = cfr_root_value
+    root_value_async = cfr_root_value_async
     phase_times = cfr_phase_times
     info = cfr_get_info
 

@@ -1376,6 +1376,23 @@ cfr_status cfr_root_value(cfr_solver *s, double *u1) {
     return CFR_OK;
 }
 
+cfr_status cfr_root_value_async(cfr_solver *s, double *u1) {
+    TRY(check_usable(s));
+    if (!u1) return set_err(s, CFR_ERR_INVALID, "u1 is NULL");
+    DeviceGuard dg(s->device);
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, u1) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer) {
+        cudaGetLastError();
+        return set_err(s, CFR_ERR_INVALID, "u1 is not page-locked host memory");
+    }
+    double *dst = static_cast<double *>(a.devicePointer);
+    if (s->Nd == 0) k_root_out<double><<<1, 1, 0, s->stream>>>(static_cast<const double *>(s->util64), dst);
+    else if (s->cfg.precision == CFR_FP64) k_root_out<double><<<1, 1, 0, s->stream>>>(static_cast<const double *>(s->u), dst);
+    else k_root_out<float><<<1, 1, 0, s->stream>>>(static_cast<const float *>(s->u), dst);
+    CK_LAUNCH();
+    return CFR_OK;
+}
+
 cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t *kind, int32_t *depth, int32_t len,
                            int32_t *nphases) {
     TRY(check_usable(s));

@@ -1197,6 +1197,10 @@ __global__ void __launch_bounds__(256) k_br2_pick(DevBR b1, DevBR b2, int32_t j0
     br_pick<false>(b2, j, 2);
 }
 
+// The root's value u(v_0) (or the terminal root's utility) as FP64 into page-locked host memory.
+template <typename real>
+__global__ void k_root_out(const real *u, double *out) { out[0] = (double)u[0]; }
+
 __global__ void k_fill(double *p, int32_t n, double v) {
     const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (i < n) p[i] = v;

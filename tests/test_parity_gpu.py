@@ -324,6 +324,23 @@ def test_root_value_is_expected_payoff():
         assert cfr.cfr_root_value(s) == rv[0]
 
 
+def test_root_value_async_matches_the_synchronous_read():
+    import torch
+
+    buf = torch.zeros(2, dtype=torch.float64, pin_memory=True)
+    g = gamegen.config("bucket3_depth6", seed=5)
+    for precision in (cfr.CFR_FP64, cfr.CFR_FP32):
+        s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=precision)
+        for t in range(4):
+            cfr.cfr_iterate(s, 1)
+            cfr.cfr_root_value_async(s, buf.data_ptr() + 8 * (t % 2))
+            cfr.cfr_synchronize(s)
+            assert buf[t % 2].item() == cfr.cfr_root_value(s)
+        with pytest.raises(cfr.CfrError):                  # pageable host memory is refused
+            cfr.cfr_root_value_async(s, np.zeros(1).ctypes.data)
+        s.close()
+
+
 def test_bad_arguments_raise():
     g = gamegen.config("bucket3_depth6", seed=4)
     s = cfr.cfr_load_tree(g)
