@@ -605,8 +605,9 @@ def run_ours(args, world, rank, local):
             if t > 0:
                 ready[(t - 1) % 2].synchronize()
                 values[t - 1] = root_buf[(t - 1) % 2].item()
-        ready[(args.steps - 1) % 2].synchronize()
-        values[args.steps - 1] = root_buf[(args.steps - 1) % 2].item()
+        if args.steps > 0:
+            ready[(args.steps - 1) % 2].synchronize()
+            values[args.steps - 1] = root_buf[(args.steps - 1) % 2].item()
         avg = cfr.cfr_average_strategy(s2)
         el = time.perf_counter() - t0
         el = max_over_ranks(el, world, device=f"cuda:{local}")
@@ -618,7 +619,7 @@ def run_ours(args, world, rank, local):
                "includes": "cfr_load_tree from host arrays (validation, layout, upload) + per step cfr_iterate(1) + "
                            "cfr_root_value_async into page-locked memory, each step's value read on the host while "
                            "the next step runs, then cfr_average_strategy",
-               "root_value_last": float(values[-1]),
+               "root_value_last": float(values[-1]) if args.steps > 0 else None,
                "seconds": el}
         s2.close()
         del avg
