@@ -480,13 +480,26 @@ def cpu_baseline(g, variant: int, seconds: float = 12.0) -> dict:
                       f"{iters} full iterations in {el:.1f} s, single-threaded recursive FP64 oracle"}
 
 
+WORKLOAD_TEXT = {
+    "bucket3_depth6": "6 ordered deals of 2 of 3 buckets, depth 6, |A| 2-3, u1~U[-2,2]",
+    "rank13_depth10": "156 ordered deals of 2 of 13 ranks, depth 10, |A| 3-4, fold/showdown payoffs, pot in {1,2,4,8}",
+    "holdem169_depth12": "1326-way deal bucketed to 169, depth 12, |A| 4-5, u1~U[-100,100]",
+}
+L2_BYTES = 129e6   # GB300's L2
+
+
 def workload_config(args, g, info=None):
-    c = {"workload": f"{args.workload} (seed {args.seed}): 1326-way deal bucketed to 169, depth 12, |A| 4-5, "
-                     "u1~U[-100,100]",
+    if info is None:
+        l2 = "not applicable (host cores)"
+    elif info["device_bytes"] > L2_BYTES:
+        l2 = "resident state larger than L2 (no flush needed)"
+    else:
+        l2 = "resident state fits in L2 (iterations run from L2; not a full-size measurement)"
+    c = {"workload": f"{args.workload} (seed {args.seed}): {WORKLOAD_TEXT.get(args.workload, 'seeded synthetic game')}",
          "nodes": g.num_nodes, "variant": "cfr+" if args.variant == "plus" else "vanilla",
          "averaging": "linear" if args.variant == "plus" else "uniform",
          "precision": "fp32 reach/values/regrets, fp64 cumulative sums" if args.precision == "fp32" else "fp64",
-         "update": "simultaneous", "l2": "resident state larger than L2 (no flush needed)"}
+         "update": "simultaneous", "l2": l2}
     if info:
         c.update(decision_nodes=info["num_decision"], terminals=info["num_terminal"], infosets=info["num_infosets"],
                  infoset_actions=info["num_q"], levels=info["num_levels"], device_bytes=info["device_bytes"],
