@@ -24,3 +24,11 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["gpu_launches"] == 0
+
+
+def test_every_named_workload_has_its_description():
+    sys.path.insert(0, ROOT)
+    import bench
+    import gamegen
+
+    assert set(bench.WORKLOAD_TEXT) == set(gamegen.CONFIGS)
