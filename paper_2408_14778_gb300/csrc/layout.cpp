@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <functional>
+#include <memory>
 #include <limits>
 #include <mutex>
 #include <thread>
@@ -32,6 +33,28 @@ void parallel_ranges(int64_t n, F f) {
     for (int64_t c = 1; c < T; ++c) th.emplace_back([&f, c, n, T] { f(c, n * c / T, n * (c + 1) / T); });
     f((int64_t)0, (int64_t)0, n / T);
     for (auto &t : th) t.join();
+}
+
+// x[i] += x[i - 1] for i = 1 .. n in place (a running sum over x[1 .. n] starting from x[0]), in
+// parallel: each range's total, the totals' running sum as the ranges' offsets, then each range's own
+// running sum from its offset.  The ranges are parallel_ranges' (the same split in both passes).
+void running_sum(std::vector<int32_t> &x, int64_t n) {
+    const int64_t T = nchunks(n);
+    std::vector<int64_t> off((size_t)T + 1, 0);
+    parallel_ranges(n, [&](int64_t c, int64_t b, int64_t e) {
+        int64_t t = 0;
+        for (int64_t i = b + 1; i <= e; ++i) t += x[(size_t)i];
+        off[(size_t)c + 1] = t;
+    });
+    off[0] = x[0];
+    for (int64_t c = 0; c < T; ++c) off[(size_t)c + 1] += off[(size_t)c];
+    parallel_ranges(n, [&](int64_t c, int64_t b, int64_t e) {
+        int64_t t = off[(size_t)c];
+        for (int64_t i = b + 1; i <= e; ++i) {
+            t += x[(size_t)i];
+            x[(size_t)i] = (int32_t)t;
+        }
+    });
 }
 
 // The first failure of a parallel pass: the lowest node index wins.
@@ -464,10 +487,15 @@ cfr_status build_layout_parallel(const cfr_game_desc *g, Layout *out, std::strin
     if (roots.empty()) return fail(err, CFR_ERR_INVALID, "no root (no node with parent -1)");
 
     // ---- children: counts, a bijection onto actions ------------------------------------------
-    std::vector<int32_t> cstart, child, order, seq1, seq2;
-    run_concurrently({[&] { cstart.assign((size_t)n + 1, 0); }, [&] { child.assign((size_t)n, -1); },
-                      [&] { order.assign((size_t)n, 0); }, [&] { seq1.assign((size_t)n, -1); },
-                      [&] { seq2.assign((size_t)n, -1); }});
+    // seq1 / seq2: each node's last own slot of player 1 / 2 (-1: none yet), kept by breadth-first position
+    // (the node order[i] at i), so that the numbering pass reads and writes them in order.  order, seq1 and
+    // seq2 are written before they are read (the roots' entries when they are placed), so they are left
+    // uninitialised: their pages are first touched by the parallel numbering pass.
+    std::vector<int32_t> cstart, child;
+    std::unique_ptr<int32_t[]> order(new int32_t[(size_t)std::max<int64_t>(n, 1)]);
+    std::unique_ptr<int32_t[]> seq1(new int32_t[(size_t)std::max<int64_t>(n, 1)]);
+    std::unique_ptr<int32_t[]> seq2(new int32_t[(size_t)std::max<int64_t>(n, 1)]);
+    run_concurrently({[&] { cstart.assign((size_t)n + 1, 0); }, [&] { child.assign((size_t)n, -1); }});
     {
         FirstError fe;
         parallel_ranges(n, [&](int64_t, int64_t b, int64_t e) {
@@ -492,7 +520,7 @@ cfr_status build_layout_parallel(const cfr_game_desc *g, Layout *out, std::strin
         });
         if (fe.st != CFR_OK) return fe.report(err);
     }
-    for (int64_t v = 0; v < n; ++v) cstart[(size_t)v + 1] += cstart[(size_t)v];
+    running_sum(cstart, n);
     {
         FirstError fe;
         parallel_ranges(n, [&](int64_t, int64_t b, int64_t e) {
@@ -561,6 +589,7 @@ cfr_status build_layout_parallel(const cfr_game_desc *g, Layout *out, std::strin
                           [&] { Lo.util.assign((size_t)(n - ndec), 0.0); }});
         int64_t tail = 0, dq = 0, tq = 0, nd_proc = 0;
         for (int32_t r : roots) {
+            seq1[(size_t)tail] = seq2[(size_t)tail] = -1;
             order[(size_t)tail++] = r;
             if (inf[r] >= 0) Lo.dnode_user[(size_t)dq++] = r;
             else { Lo.tnode_user[(size_t)tq] = r; Lo.util[(size_t)tq++] = g->utility[2 * (size_t)r]; }
@@ -615,8 +644,9 @@ cfr_status build_layout_parallel(const cfr_game_desc *g, Layout *out, std::strin
                     const int32_t hu = inf[v];
                     if (hu < 0) continue;
                     const int p = g->infoset_player[hu];
+                    const int32_t s1v = seq1[(size_t)i], s2v = seq2[(size_t)i];
                     if (p > 0) {
-                        const int64_t sq = p == 1 ? seq1[(size_t)v] : seq2[(size_t)v];
+                        const int64_t sq = p == 1 ? s1v : s2v;
                         int64_t expect = -2;
                         if (!__atomic_compare_exchange_n(&rep[(size_t)hu], &expect, sq, false, __ATOMIC_RELAXED, __ATOMIC_RELAXED) &&
                             expect != sq)
@@ -633,10 +663,11 @@ cfr_status build_layout_parallel(const cfr_game_desc *g, Layout *out, std::strin
                     const size_t woff = wbase + (size_t)ww;
                     for (int32_t a = 0; a < na; ++a) {
                         const int32_t cv = child[(size_t)cstart[v] + a];
-                        order[(size_t)(child_base + ch++)] = cv;
+                        const int64_t pos = child_base + ch++;
+                        order[(size_t)pos] = cv;
                         const int32_t q = (int32_t)(qbase_user[(size_t)hu] + a);
-                        seq1[(size_t)cv] = p == 1 ? q : seq1[(size_t)v];
-                        seq2[(size_t)cv] = p == 2 ? q : seq2[(size_t)v];
+                        seq1[(size_t)pos] = p == 1 ? q : s1v;
+                        seq2[(size_t)pos] = p == 2 ? q : s2v;
                         if (inf[cv] >= 0) {
                             Lo.dnode_user[(size_t)(dq_base + dc++)] = cv;
                         } else {
