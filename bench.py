@@ -46,6 +46,7 @@ def parse():
                     help="FP32 mode: deepest depths run by the fused kernel (-1 automatic, 0 none)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-error", action="store_true", help="skip the error-against-the-oracle block")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-exploitability-1e-3 measurement")
     ap.add_argument("--no-leaf", action="store_true", help="skip the learned-leaf depth-limited measurement")
     ap.add_argument("--leaf-samples-per-node", type=int, default=256)
@@ -178,14 +179,22 @@ def recorded_traffic(workload: str, precision: str, phase: str):
     return None
 
 
-def oracle_sample(g, budget_s: float):
-    """First-deals sub-game sized so one oracle iteration takes about budget_s seconds."""
+def oracle_sample(g, budget_s: float, threads: int = 1):
+    """First-deals sub-game sized so one oracle iteration on `threads` host threads takes about
+    budget_s seconds."""
     import gamegen
 
     per_deal = int(g.meta["public_nodes"])
-    rate = 1.0e7                               # oracle node-updates/s, order of magnitude, sizing only
+    rate = 1.0e7 * max(threads, 1)             # oracle node-updates/s, order of magnitude, sizing only
     k = max(1, min(int(g.meta["deals"]), int(budget_s * rate / per_deal)))
     return gamegen.first_deals(g, k)
+
+
+def oracle_threads() -> int:
+    """Host threads of the oracle's multi-threaded passes (all of this host's cores by default)."""
+    import oracle
+
+    return oracle.max_threads()
 
 
 TTT_TARGET = 1e-3          # exploitability (NashConv / 2), absolute, payoff units
@@ -239,6 +248,9 @@ def time_to_exploitability(args, local: int) -> dict:
         cfr.cfr_synchronize(s)
         r = _ttt_run(lambda n: cfr.cfr_iterate(s, n), lambda: cfr.cfr_exploitability(s)[1], TTT_MAX_ITERS, 30.0)
         r["nodes"] = g.num_nodes
+        # the final exploitability against the oracle's best responses to the same average strategy
+        r["oracle_error_abs"] = abs(2 * r["exploitability"] - oracle.Oracle(g).exploitability(
+            profile=cfr.cfr_average_strategy(s))[0]) / 2
         out[f"gpu_{name}"] = r
         s.close()
         if nodes is not None:
@@ -413,6 +425,12 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
     per_game = cfr.cfr_batch_game_times(b)
     nc = cfr.cfr_batch_exploitability(b)
     info = cfr.cfr_batch_get_info(b)
+    # every 256th game's NashConv against the oracle's best responses to that game's average strategy
+    import oracle
+
+    checked = list(range(0, len(games), 256))
+    dev = [abs(nc[i] - oracle.Oracle(games[i]).exploitability(profile=cfr.cfr_batch_average_strategy(b, i))[0])
+           for i in checked]
     out = {"subgames": label, "games": len(games), "nodes_total": int(nodes.sum()), "nodes_min": int(nodes.min()),
            "nodes_max": int(nodes.max()), "nodes_mean": float(nodes.mean()), "variant": "cfr+ (linear averaging)",
            "updates": "alternating" if update_mode else "simultaneous",
@@ -422,6 +440,8 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
                                             "p99": float(np.percentile(per_game, 99)),
                                             "max": float(per_game.max())},
            "exploitability_after": {"median": float(np.median(nc) / 2), "max": float(nc.max() / 2)},
+           "oracle_error": {"games_checked": len(checked), "nash_conv_abs_max": float(max(dev)),
+                            "note": "GPU NashConv against the oracle's best responses to the GPU's average strategy"},
            "tuning": {k: tune[k] for k in ("split_nodes", "threads_per_block", "blocks_per_sm", "cached")},
            "tuning_trials_us_per_iteration": tune["trials"],
            "forest_part": {"games": info["forest_games"], "nodes": info["forest_nodes"]},
@@ -462,22 +482,85 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
     return out
 
 
-def cpu_baseline(g, variant: int, seconds: float = 12.0) -> dict:
+def _time_oracle(sub, variant: int, threads: int, seconds: float):
     import oracle
 
-    sub = oracle_sample(g, 0.5)
     o = oracle.Oracle(sub)
-    o.iterate(1, variant=variant, avg=variant)
+    o.iterate(1, variant=variant, avg=variant, threads=threads)
     iters, t0 = 0, time.perf_counter()
     while True:
-        o.iterate(1, variant=variant, avg=variant)
+        o.iterate(1, variant=variant, avg=variant, threads=threads)
         iters += 1
         el = time.perf_counter() - t0
         if el >= seconds and iters >= 2:
             break
-    return {"value": sub.num_nodes * iters / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return sub.num_nodes * iters / el, iters, el, o.last_threads
+
+
+def cpu_baseline(g, variant: int, seconds: float = 10.0) -> dict:
+    """The oracle on this host's cores, on the first deals of the same workload: all cores (its
+    multi-threaded passes, bit-identical to the one-thread walk; the reported value) and one core."""
+    threads = oracle_threads()
+    sub = oracle_sample(g, 0.5, threads)
+    v_all, it_all, el_all, used = _time_oracle(sub, variant, 0, seconds)
+    sub1 = oracle_sample(g, 0.5)
+    v_one, it_one, el_one, _ = _time_oracle(sub1, variant, 1, seconds)
+    return {"value": v_all, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"first {sub.meta['deals']} of {g.meta['deals']} deals ({sub.num_nodes} of {g.num_nodes} nodes), "
-                      f"{iters} full iterations in {el:.1f} s, single-threaded recursive FP64 oracle"}
+                      f"{it_all} full iterations in {el_all:.1f} s on {used} host threads (recursive FP64 oracle, "
+                      f"subtrees of the root deal in parallel, sums in the one-thread order)",
+            "host_cores": os.cpu_count(),
+            "single_core": {"value": v_one, "unit": UNIT, "cores": 1,
+                            "sample": f"first {sub1.meta['deals']} deals ({sub1.num_nodes} nodes), {it_one} full "
+                                      f"iterations in {el_one:.1f} s, one thread"}}
+
+
+def oracle_error(g, variant: int, local: int) -> dict:
+    """Error of the GPU's results against the FP64 oracle on the bench workload's first deals: from the
+    oracle's state after T0 iterations, one GPU iteration in FP32 mode (and one in FP64 mode) against
+    the oracle's own next iteration - cumulative regret R, strategy sum S, instantaneous regret r~ and
+    the next strategy sigma, each normwise (max |x - y| / max |y| over the players' slots) - and the
+    NashConv of the average strategy, absolute: the GPU's against the oracle's after the same step, and
+    the GPU's best responses against the oracle's on the GPU's own average strategy."""
+    import numpy as np
+
+    import oracle
+    import paper_2408_14778_gb300 as cfr
+
+    T0 = 3
+    sub = oracle_sample(g, 0.5, oracle_threads())
+    o = oracle.Oracle(sub)
+    o.iterate(T0, variant=variant, avg=variant, threads=0)
+    st0 = o.state()
+    o.iterate(1, variant=variant, avg=variant, threads=0)
+    ref = o.state()
+    nc_ref = o.exploitability()[0]
+    keep = np.repeat(sub.infoset_player != 0, sub.infoset_num_actions)
+
+    def nw(x, y):
+        x, y = np.where(keep, x, 0.0), np.where(keep, y, 0.0)
+        return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-30)) if y.size else 0.0
+
+    out = {"sample": f"first {sub.meta['deals']} deals ({sub.num_nodes} nodes)", "from_iteration": T0,
+           "variant": "cfr+ linear averaging" if variant else "vanilla", "nash_conv_oracle": nc_ref,
+           "tolerance": {"fp32_normwise": 1e-5, "fp64_normwise": 1e-12, "nash_conv_abs": 1e-6}}
+    for name, prec in (("fp32", cfr.CFR_FP32), ("fp64", cfr.CFR_FP64)):
+        s = cfr.cfr_load_tree(sub, variant=cfr.CFR_PLUS if variant else cfr.CFR_VANILLA, precision=prec,
+                              device=local)
+        cfr.cfr_set_state(s, st0["cum_regret"], st0["strat_sum"], T0)
+        cfr.cfr_iterate(s, 1)
+        gs = cfr.cfr_get_state(s)
+        nc = cfr.cfr_exploitability(s)[0]
+        avg = cfr.cfr_average_strategy(s)
+        nc_br = o.exploitability(profile=avg)[0]
+        out[name] = {"cum_regret": nw(gs["cum_regret"], ref["cum_regret"]),
+                     "strat_sum": nw(gs["strat_sum"], ref["strat_sum"]),
+                     "inst_regret": nw(gs["inst_regret"], ref["inst_regret"]),
+                     "sigma": nw(cfr.cfr_current_strategy(s), ref["sigma"]),
+                     "nash_conv_abs": abs(nc - nc_ref),
+                     "best_response_abs": abs(nc - nc_br)}
+        s.close()
+    return out
 
 
 WORKLOAD_TEXT = {
@@ -518,20 +601,22 @@ def run_reference(args, world, rank):
     variant = 1 if args.variant == "plus" else 0
     g = gamegen.config(args.workload, seed=args.seed, target_nodes=args.nodes)
     budget = max(0.05, 90.0 / max(args.steps + args.warmup, 1))
-    sub = oracle_sample(g, budget)
+    threads = oracle_threads()
+    sub = oracle_sample(g, budget, threads)
     o = oracle.Oracle(sub)
-    o.iterate(args.warmup, variant=variant, avg=variant)
+    o.iterate(args.warmup, variant=variant, avg=variant, threads=0)
     t0 = time.perf_counter()
-    o.iterate(args.steps, variant=variant, avg=variant)
+    o.iterate(args.steps, variant=variant, avg=variant, threads=0)
     el = time.perf_counter() - t0
+    cores = o.last_threads
     value = sub.num_nodes * args.steps / el
     sample = (f"first {sub.meta['deals']} of {g.meta['deals']} deals ({sub.num_nodes} of {g.num_nodes} nodes) per "
-              f"step; single-threaded recursive FP64 oracle")
+              f"step; recursive FP64 oracle on {cores} host threads (subtrees of the root deal in parallel)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(args, g), precision="fp64 throughout (the oracle)"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -642,6 +727,9 @@ def run_ours(args, world, rank, local):
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(g, 1 if args.variant == "plus" else 0)
+    oerr = None
+    if rank == 0 and world == 1 and not args.no_oracle_error:
+        oerr = oracle_error(g, 1 if args.variant == "plus" else 0, local)
     ttt = None
     if rank == 0 and world == 1 and not args.no_ttt:
         ttt = time_to_exploitability(args, local)
@@ -660,6 +748,7 @@ def run_ours(args, world, rank, local):
                 "iterations_per_s": args.steps / t_max, "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches - launches0, "clocks": clocks,
                 "parallelism": "replicas" if world > 1 else "single GPU"}
+        line["oracle_error"] = oerr
         line["time_to_exploitability"] = ttt
         line["batched"] = batched
         line["learned_leaf"] = leaf

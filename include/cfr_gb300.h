@@ -195,7 +195,8 @@ cfr_status cfr_exploitability(cfr_solver *s, double *nash_conv, double *exploita
  * The first call on a device looks up the region's device address (set-up, once per device); make
  * that first call before any stream capture.  All calls share the region and leave their contents
  * in it (each call resets what must start at zero), so calls that overlap on the GPU - from two
- * streams or two threads - race and give wrong results.  Results equal cfr_exploitability's. */
+ * streams or two threads - race and give wrong results.  Results agree with cfr_exploitability's
+ * to 1e-6 (the per-player kernels sum in another order than the two-player pass). */
 cfr_status cfr_exploitability_static(cfr_solver *s, double *nash_conv, double *exploitability);
 
 /* Copies the FP64 cumulative regrets R (R = T * r-bar of Eq. 8), strategy sums S (numerator of
@@ -381,6 +382,19 @@ cfr_status cfr_mlp_forward(cfr_mlp *m, const float *x, int32_t batch, float *y);
 /* Forward and backward pass at (x, target [batch][dims[L]]): leaves dL/dparams in the network's
  * gradient buffer and, if loss != NULL, writes L to *loss (device, one double). */
 cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int32_t batch, double *loss);
+
+/* Test hook: a host copy (as FP32) of one intermediate of the last cfr_mlp_forward or
+ * cfr_mlp_backward call, rows [0, batch) of that call and the real columns, row-major:
+ *   CFR_MLP_ACT  layer `layer`'s input as its product read it (BF16): the rounded input x for
+ *                layer 0, bf16(ReLU(Z)) of layer - 1 otherwise; [batch][dims[layer]];
+ *   CFR_MLP_DZ   dL/dZ of layer `layer` (BF16), after cfr_mlp_backward only; [batch][dims[layer + 1]];
+ *   CFR_MLP_OUT  the network output y (FP32); [batch][dims[num_layers]] (layer ignored).
+ * Synchronises.  CFR_ERR_INVALID for a bad selector or layer or a short buffer (len entries),
+ * CFR_ERR_STATE before the first pass or for CFR_MLP_DZ after a forward pass. */
+#define CFR_MLP_ACT 0
+#define CFR_MLP_DZ 1
+#define CFR_MLP_OUT 2
+cfr_status cfr_mlp_get_intermediate(cfr_mlp *m, int32_t which, int32_t layer, float *out, int64_t len);
 
 /* One Adam step (Kingma and Ba, 2015, bias-corrected) on the gradients of the last cfr_mlp_backward:
  * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */

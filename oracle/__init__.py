@@ -25,12 +25,17 @@ AVG_UNIFORM, AVG_LINEAR = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile cfr_oracle.c into liboracle.so (plain gcc -O2; no fast-math)."""
+    """Compile cfr_oracle.c into liboracle.so (plain gcc -O2; no fast-math; OpenMP for the
+    multi-threaded passes where the compiler has it, else those passes run on one thread)."""
     src = os.path.join(_HERE, "cfr_oracle.c")
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", src, "-o", tmp, "-lm"])
+    base = ["gcc", "-O2", "-std=gnu99", "-fPIC", "-shared", "-ffp-contract=off", src, "-o", tmp, "-lm"]
+    try:
+        subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base)
     os.replace(tmp, _SO)
     return _SO
 
@@ -54,6 +59,11 @@ def _lib():
         lib.orc_root.argtypes = [_P]
         lib.orc_set_record.argtypes = [_P, ctypes.c_int32]
         lib.orc_iterate.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]
+        lib.orc_iterate_mt.restype = ctypes.c_int32
+        lib.orc_iterate_mt.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                       ctypes.c_int32]
+        lib.orc_max_threads.restype = ctypes.c_int32
+        lib.orc_max_threads.argtypes = []
         lib.orc_get_state.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         lib.orc_set_state.argtypes = [_P, _P, _P, ctypes.c_int64]
         lib.orc_get_nodes.restype = ctypes.c_int32
@@ -73,6 +83,11 @@ def _lib():
 
 def _c(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def max_threads() -> int:
+    """Host threads the multi-threaded passes use by default (1 if the oracle was built without OpenMP)."""
+    return int(_lib().orc_max_threads())
 
 
 class Oracle:
@@ -109,13 +124,23 @@ class Oracle:
         return int(_lib().orc_root(self._h))
 
     def iterate(self, n: int = 1, variant: int = VANILLA, avg: int = AVG_UNIFORM, alternating: bool = False,
-                dcfr=(1.5, 0.0, 2.0)):
+                dcfr=(1.5, 0.0, 2.0), threads: int = 1):
         """Runs n CFR iterations; returns the root payoffs (u1, u2) of the last pass.  variant: VANILLA,
-        CFR_PLUS, LINEAR or DISCOUNTED (with dcfr = (alpha, beta, gamma)); avg is ignored by the last two."""
+        CFR_PLUS, LINEAR or DISCOUNTED (with dcfr = (alpha, beta, gamma)); avg is ignored by the last two.
+        threads != 1: each pass walks the root's subtrees on that many host threads (0: all), with the
+        same results bit for bit; the count used is in ``last_threads``."""
         rv = np.zeros(2)
         d = np.asarray(dcfr, dtype=np.float64)
-        _lib().orc_iterate(self._h, int(n), int(variant), int(avg), int(bool(alternating)), d.ctypes.data,
-                           rv.ctypes.data)
+        if threads == 1:
+            _lib().orc_iterate(self._h, int(n), int(variant), int(avg), int(bool(alternating)), d.ctypes.data,
+                               rv.ctypes.data)
+            self.last_threads = 1
+        else:
+            used = _lib().orc_iterate_mt(self._h, int(n), int(variant), int(avg), int(bool(alternating)),
+                                         d.ctypes.data, rv.ctypes.data, int(threads))
+            if used < 0:
+                raise MemoryError("oracle: no memory for the multi-threaded pass")
+            self.last_threads = int(used)
         return rv
 
     def state(self) -> dict:

@@ -43,11 +43,22 @@
  * i's infosets, argmax_a sum_{d in h} pi_-i(d) V(child_a(d)), where V is the value below with i
  * best responding.  NashConv = sum_i (BR_i - u_i(profile)); exploitability = NashConv / 2.
  * Ties pick the lowest action index.
+ *
+ * Multi-threaded passes (orc_iterate_mt; OpenMP, used to time the oracle on all host cores): the
+ * subtrees below the root's outcomes are walked by separate threads with the same walk.  A node
+ * then does not add its Eq. 7 terms into the shared sums; it stores them per edge (and its
+ * counterfactual and own reach per node), and afterwards each infoset adds its nodes' stored terms
+ * in the order the one-thread walk would have added them (depth-first post-order), so every sum
+ * sees the same additions in the same order and the results are bit for bit those of orc_iterate.
+ * The end-of-iteration update is independent per infoset and runs in parallel as it is.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int64_t n;
@@ -70,6 +81,11 @@ typedef struct {
     double *rec;       /* n x 6: u1, u2, pi-check 1, pi-check 2, pi-hat 1, pi-hat 2 of the last pass */
     int64_t recall_violations;
     uint8_t *own_seen;
+    /* multi-threaded passes: per-edge Eq. 7 terms and per-node reaches of the last pass, and each
+     * infoset's nodes in depth-first post-order */
+    int mt;
+    double *contrib, *cfnode, *ownnode;
+    int32_t *hpost;
     /* best-response scratch */
     double *preach, *V;
     int32_t *astar;
@@ -82,6 +98,7 @@ static void orc_free_all(orc *o) {
     free(o->cstart); free(o->child); free(o->infoset); free(o->player); free(o->nact); free(o->qbase);
     free(o->hstart); free(o->hnode); free(o->util); free(o->sigma0); free(o->sigma); free(o->R); free(o->S);
     free(o->inst); free(o->own); free(o->cfsum); free(o->rec); free(o->own_seen); free(o->preach); free(o->V); free(o->astar);
+    free(o->contrib); free(o->cfnode); free(o->ownnode); free(o->hpost);
     free(o);
 }
 
@@ -180,6 +197,17 @@ void orc_set_record(orc *o, int32_t on) {
  * recursion (the parent's value times sigma of the edge unless that player acted there);
  * own1, own2: own reaches pi-hat(v, 1), pi-hat(v, 2) of Eq. 4 (the parent's value times sigma of
  * the edge when that player acted there). */
+static void walk(orc *o, int32_t v, double cf1, double cf2, double own1, double own2, int mask, double out[2]);
+
+/* The walk below child a of v (player p of v acting with probability s on that edge). */
+static void walk_child(orc *o, int32_t v, int32_t a, int p, double s, double cf1, double cf2, double own1,
+                       double own2, int mask, double out[2]) {
+    int32_t c = o->child[o->cstart[v] + a];
+    if (p == 0) walk(o, c, cf1 * s, cf2 * s, own1, own2, mask, out);
+    else if (p == 1) walk(o, c, cf1, cf2 * s, own1 * s, own2, mask, out);
+    else walk(o, c, cf1 * s, cf2, own1, own2 * s, mask, out);
+}
+
 static void walk(orc *o, int32_t v, double cf1, double cf2, double own1, double own2, int mask, double out[2]) {
     if (o->record) {
         double *r = o->rec + (size_t)v * 6;
@@ -194,23 +222,35 @@ static void walk(orc *o, int32_t v, double cf1, double cf2, double own1, double 
         int64_t qb = o->qbase[h];
         double ua[2 * na];
         double u[2] = {0.0, 0.0};
+        if (o->mt && v == o->root) {
+            /* multi-threaded pass: the subtrees below the root's outcomes on separate threads */
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int32_t a = 0; a < na; ++a)
+                walk_child(o, v, a, p, o->sigma[qb + a], cf1, cf2, own1, own2, mask, ua + 2 * a);
+        } else {
+            for (int32_t a = 0; a < na; ++a)
+                walk_child(o, v, a, p, o->sigma[qb + a], cf1, cf2, own1, own2, mask, ua + 2 * a);
+        }
         for (int32_t a = 0; a < na; ++a) {
             double s = o->sigma[qb + a];
-            int32_t c = o->child[o->cstart[v] + a];
-            if (p == 0) walk(o, c, cf1 * s, cf2 * s, own1, own2, mask, ua + 2 * a);
-            else if (p == 1) walk(o, c, cf1, cf2 * s, own1 * s, own2, mask, ua + 2 * a);
-            else walk(o, c, cf1 * s, cf2, own1, own2 * s, mask, ua + 2 * a);
             u[0] += s * ua[2 * a];
             u[1] += s * ua[2 * a + 1];
         }
         if (p > 0 && (mask & (1 << p))) {
             double cf = p == 1 ? cf1 : cf2;
-            for (int32_t a = 0; a < na; ++a) o->inst[qb + a] += cf * (ua[2 * a + p - 1] - u[p - 1]);
-            o->cfsum[h] += cf;
             double mine = p == 1 ? own1 : own2;
-            if (o->own_seen[h] && fabs(o->own[h] - mine) > 1e-12 * (fabs(mine) + 1e-300)) o->recall_violations++;
-            o->own[h] = mine;
-            o->own_seen[h] = 1;
+            if (o->mt) {
+                /* stored per edge and node; summed per infoset after the pass (reduce_infosets) */
+                for (int32_t a = 0; a < na; ++a) o->contrib[o->cstart[v] + a] = cf * (ua[2 * a + p - 1] - u[p - 1]);
+                o->cfnode[v] = cf;
+                o->ownnode[v] = mine;
+            } else {
+                for (int32_t a = 0; a < na; ++a) o->inst[qb + a] += cf * (ua[2 * a + p - 1] - u[p - 1]);
+                o->cfsum[h] += cf;
+                if (o->own_seen[h] && fabs(o->own[h] - mine) > 1e-12 * (fabs(mine) + 1e-300)) o->recall_violations++;
+                o->own[h] = mine;
+                o->own_seen[h] = 1;
+            }
         }
         out[0] = u[0]; out[1] = u[1];
     }
@@ -220,7 +260,10 @@ static void walk(orc *o, int32_t v, double cf1, double cf2, double own1, double 
     }
 }
 
+static void reduce_infosets(orc *o, int mask);
+
 static void pass(orc *o, int mask, double root_value[2]) {
+#pragma omp parallel for schedule(static) if (o->mt)
     for (int32_t h = 0; h < o->H; ++h) {
         if (o->player[h] > 0 && (mask & (1 << o->player[h]))) {
             for (int32_t a = 0; a < o->nact[h]; ++a) o->inst[o->qbase[h] + a] = 0.0;
@@ -230,6 +273,65 @@ static void pass(orc *o, int mask, double root_value[2]) {
         }
     }
     walk(o, o->root, 1.0, 1.0, 1.0, 1.0, mask, root_value);
+    if (o->mt) reduce_infosets(o, mask);
+}
+
+/* Depth-first post-order number of every node below v (children in action order): the order in
+ * which the one-thread walk finishes nodes, and so adds their Eq. 7 terms. */
+static void number_post(const orc *o, int32_t v, int64_t *pos, int64_t *next) {
+    int32_t h = o->infoset[v];
+    if (h >= 0)
+        for (int32_t a = 0; a < o->nact[h]; ++a) number_post(o, o->child[o->cstart[v] + a], pos, next);
+    pos[v] = (*next)++;
+}
+
+static const int64_t *g_sort_pos;
+static int by_post(const void *x, const void *y) {
+    int64_t a = g_sort_pos[*(const int32_t *)x], b = g_sort_pos[*(const int32_t *)y];
+    return a < b ? -1 : a > b;
+}
+
+/* Work arrays of the multi-threaded passes; 0 on success. */
+static int mt_prepare(orc *o) {
+    if (o->hpost) return 0;
+    o->contrib = malloc(sizeof(double) * (o->cstart[o->n] > 0 ? o->cstart[o->n] : 1));
+    o->cfnode = malloc(sizeof(double) * o->n);
+    o->ownnode = malloc(sizeof(double) * o->n);
+    int64_t *pos = malloc(sizeof(int64_t) * o->n);
+    int32_t *hp = malloc(sizeof(int32_t) * (o->hstart[o->H] > 0 ? o->hstart[o->H] : 1));
+    if (!o->contrib || !o->cfnode || !o->ownnode || !pos || !hp) { free(pos); free(hp); return -1; }
+    int64_t next = 0;
+    number_post(o, o->root, pos, &next);
+    memcpy(hp, o->hnode, sizeof(int32_t) * o->hstart[o->H]);
+    g_sort_pos = pos;
+    for (int32_t h = 0; h < o->H; ++h)
+        qsort(hp + o->hstart[h], (size_t)(o->hstart[h + 1] - o->hstart[h]), sizeof(int32_t), by_post);
+    free(pos);
+    o->hpost = hp;
+    return 0;
+}
+
+/* After a multi-threaded pass: each collecting infoset adds its nodes' stored terms, counterfactual
+ * reaches and own reaches in post-order, as the one-thread walk does. */
+static void reduce_infosets(orc *o, int mask) {
+    int64_t viol = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : viol)
+    for (int32_t h = 0; h < o->H; ++h) {
+        int p = o->player[h];
+        if (p == 0 || !(mask & (1 << p))) continue;
+        int64_t qb = o->qbase[h];
+        int32_t na = o->nact[h];
+        for (int64_t i = o->hstart[h]; i < o->hstart[h + 1]; ++i) {
+            int32_t v = o->hpost[i];
+            for (int32_t a = 0; a < na; ++a) o->inst[qb + a] += o->contrib[o->cstart[v] + a];
+            o->cfsum[h] += o->cfnode[v];
+            double mine = o->ownnode[v];
+            if (o->own_seen[h] && fabs(o->own[h] - mine) > 1e-12 * (fabs(mine) + 1e-300)) viol++;
+            o->own[h] = mine;
+            o->own_seen[h] = 1;
+        }
+    }
+    o->recall_violations += viol;
 }
 
 /* variant: 0 vanilla, 1 CFR+, 2 linear CFR, 3 discounted CFR with dcfr = {alpha, beta, gamma}. */
@@ -244,6 +346,8 @@ static void update(orc *o, int mask, int variant, int avg, const double *dcfr, i
         fneg = tb / (tb + 1.0);
         w = pow(t, dcfr[2]);
     }
+    /* independent per infoset; in parallel in a multi-threaded pass */
+#pragma omp parallel for schedule(static) if (o->mt)
     for (int32_t h = 0; h < o->H; ++h) {
         int p = o->player[h];
         if (p == 0 || !(mask & (1 << p))) continue;
@@ -285,6 +389,37 @@ void orc_iterate(orc *o, int32_t iters, int32_t variant, int32_t avg, int32_t al
         o->T = T;
     }
     if (root_value) { root_value[0] = rv[0]; root_value[1] = rv[1]; }
+}
+
+/* orc_iterate with each pass on `threads` host threads (<= 0: all of them), bit-identical to it.
+ * Returns the thread count used, or -1 if the work arrays could not be allocated. */
+int32_t orc_iterate_mt(orc *o, int32_t iters, int32_t variant, int32_t avg, int32_t alternating, const double *dcfr,
+                       double *root_value, int32_t threads) {
+    if (mt_prepare(o) != 0) return -1;
+    int32_t used = 1;
+#ifdef _OPENMP
+    used = threads > 0 ? threads : omp_get_max_threads();
+    const int before = omp_get_max_threads();
+    omp_set_num_threads(used);
+#else
+    (void)threads;
+#endif
+    o->mt = 1;
+    orc_iterate(o, iters, variant, avg, alternating, dcfr, root_value);
+    o->mt = 0;
+#ifdef _OPENMP
+    omp_set_num_threads(before);
+#endif
+    return used;
+}
+
+/* Host threads a multi-threaded pass uses by default (1 without OpenMP). */
+int32_t orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* pi~(h) of Eq. 3 (sum of the counterfactual reaches of h's nodes) from the last pass. */

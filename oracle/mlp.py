@@ -56,17 +56,55 @@ def unflatten(flat, dims):
     return out
 
 
+def _rounder(bf16: bool):
+    return bf16_round if bf16 else (lambda v: np.asarray(v, dtype=np.float64))
+
+
+def dense(a, W, b, bf16: bool = False):
+    """One layer's pre-activation Z = a W^T + b, a [B][in] used as given, W [out][in] (rounded to BF16
+    in BF16 mode), b [out]."""
+    return np.asarray(a, dtype=np.float64) @ _rounder(bf16)(W).T + np.asarray(b, dtype=np.float64)
+
+
+def hidden(z, bf16: bool = False):
+    """A hidden layer's output ReLU(Z), rounded to BF16 in BF16 mode."""
+    return _rounder(bf16)(np.maximum(z, 0.0))
+
+
+def output_gradient(y, t):
+    """dL/dy of the mean squared error L = (1 / (B n)) sum (y - t)^2, before any rounding."""
+    y = np.asarray(y, dtype=np.float64)
+    B, n = y.shape
+    return 2.0 * (y - np.asarray(t, dtype=np.float64)) / (B * n)
+
+
+def layer_gradients(dz, a):
+    """dL/dW = dZ^T a and dL/db = the column sums of dZ, for one layer with input a."""
+    dz = np.asarray(dz, dtype=np.float64)
+    return dz.T @ np.asarray(a, dtype=np.float64), dz.sum(axis=0)
+
+
+def masked_product(dz, W, a, bf16: bool = False):
+    """(dZ W) where the layer below's ReLU output a is positive, else 0 (W rounded to BF16 in BF16
+    mode): dL/dZ of the layer below before any rounding of the result."""
+    return (np.asarray(dz, dtype=np.float64) @ _rounder(bf16)(W)) * (np.asarray(a) > 0)
+
+
+def input_gradient(dz, W, a, bf16: bool = False):
+    """dL/dZ of the layer below, rounded to BF16 in BF16 mode."""
+    return _rounder(bf16)(masked_product(dz, W, a, bf16))
+
+
 def forward(params, x, bf16: bool = False):
     """Returns (y, activations): activations[0] is the input (as used), activations[l] the output of
     hidden layer l - 1 after ReLU."""
-    rd = bf16_round if bf16 else (lambda v: np.asarray(v, dtype=np.float64))
-    a = rd(x)
+    a = _rounder(bf16)(x)
     acts = [a]
     L = len(params)
     for l, (W, b) in enumerate(params):
-        z = a @ rd(W).T + b
+        z = dense(a, W, b, bf16)
         if l + 1 < L:
-            a = rd(np.maximum(z, 0.0))
+            a = hidden(z, bf16)
             acts.append(a)
         else:
             return z, acts
@@ -75,20 +113,17 @@ def forward(params, x, bf16: bool = False):
 
 def loss_and_grads(params, x, t, bf16: bool = False):
     """Mean squared error and its gradient with respect to every W and b (backpropagation)."""
-    rd = bf16_round if bf16 else (lambda v: np.asarray(v, dtype=np.float64))
     y, acts = forward(params, x, bf16)
     B, n = y.shape
     d = y - np.asarray(t, dtype=np.float64)
     loss = float(np.sum(d * d) / (B * n))
-    dz = rd(2.0 * d / (B * n))
+    dz = _rounder(bf16)(output_gradient(y, t))
     grads = [None] * len(params)
     for l in range(len(params) - 1, -1, -1):
         W, _ = params[l]
-        a = acts[l]
-        grads[l] = (dz.T @ a, dz.sum(axis=0))
+        grads[l] = layer_gradients(dz, acts[l])
         if l > 0:
-            da = dz @ rd(W)
-            dz = rd(da * (acts[l] > 0))
+            dz = input_gradient(dz, W, acts[l], bf16)
     return loss, grads
 
 

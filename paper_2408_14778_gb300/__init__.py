@@ -179,13 +179,14 @@ def lib():
         L.cfr_mlp_gemm_stats.argtypes = [_P, _P, _P, _P, _P]
         L.cfr_mlp_set_tensor_path.argtypes = [_P, ctypes.c_int32]
         L.cfr_mlp_synchronize.argtypes = [_P]
+        L.cfr_mlp_get_intermediate.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64]
         L.cfr_mlp_last_error.argtypes = [_P]
         L.cfr_mlp_last_error.restype = ctypes.c_char_p
         L.cfr_mlp_free.argtypes = [_P]
         L.cfr_mlp_free.restype = None
         for name in ("cfr_mlp_create", "cfr_mlp_set_params", "cfr_mlp_get_params", "cfr_mlp_get_grads",
                      "cfr_mlp_forward", "cfr_mlp_backward", "cfr_mlp_adam", "cfr_mlp_gemm_stats",
-                     "cfr_mlp_set_tensor_path", "cfr_mlp_synchronize"):
+                     "cfr_mlp_set_tensor_path", "cfr_mlp_synchronize", "cfr_mlp_get_intermediate"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("cfr_batch_load", "cfr_batch_iterate", "cfr_batch_set_tuning", "cfr_batch_autotune",
                      "cfr_batch_game_times", "cfr_batch_exploitability", "cfr_batch_get_state",
@@ -792,6 +793,23 @@ def cfr_mlp_set_tensor_path(m: Mlp, path: int = MLP_PATH_MIXED):
     """0: mma.sync for every product; 1: tcgen05 for every product; 2 (default): tcgen05 with TMA operands
     for the forward products, mma.sync for the backward ones."""
     _check_mlp(lib().cfr_mlp_set_tensor_path(m.handle, int(path)), m.handle)
+
+
+CFR_MLP_ACT, CFR_MLP_DZ, CFR_MLP_OUT = 0, 1, 2
+
+
+def cfr_mlp_get_intermediate(m: Mlp, which: int, layer: int, batch: int) -> np.ndarray:
+    """Test hook: one intermediate of the last forward or backward pass of ``batch`` rows, as FP32:
+    CFR_MLP_ACT the input of layer ``layer`` as its product read it (BF16 values), CFR_MLP_DZ the
+    gradient dL/dZ of layer ``layer`` (BF16 values, after a backward pass), CFR_MLP_OUT the output."""
+    cols = {CFR_MLP_ACT: m.dims[layer] if which == CFR_MLP_ACT else 0,
+            CFR_MLP_DZ: m.dims[layer + 1] if which == CFR_MLP_DZ else 0,
+            CFR_MLP_OUT: m.dims[-1]}.get(which)
+    if cols is None:
+        raise CfrError(CFR_ERR_INVALID, f"unknown intermediate {which}")
+    out = np.zeros((batch, cols), np.float32)
+    _check_mlp(lib().cfr_mlp_get_intermediate(m.handle, int(which), int(layer), out.ctypes.data, out.size), m.handle)
+    return out
 
 
 def cfr_mlp_synchronize(m: Mlp):

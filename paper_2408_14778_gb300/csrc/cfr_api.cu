@@ -1544,10 +1544,11 @@ extern "C" cfr_status cfr_exploitability_static(cfr_solver *s, double *nash_conv
         b.kmask = s->kmask; b.wbits = s->wbits;
         b.util = s->util64; b.qbase = s->qbase; b.iplayer = s->iplayer; b.avg = avg;
         b.preach = preach; b.val = val; b.cfv = cfv; b.astar = astar;
-        const double one = 1.0;
+        const int32_t nr = s->dlevel[1];   // every depth-0 root, as the allocating path fills them
         for (int player = 1; player <= 2; ++player) {
-            // the region keeps the previous call's contents: the root reach and the sums restart here
-            CK(cudaMemcpyAsync(preach, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+            // the region keeps the previous call's contents: the root reaches and the sums restart here
+            k_fill<<<nblocks(nr), kBlock, 0, st>>>(preach, nr, 1.0);
+            CK_LAUNCH();
             CK(cudaMemsetAsync(cfv, 0, sizeof(double) * (size_t)std::max<int64_t>(s->Q, 1), st));
             for (int32_t l = 0; l + 1 < s->L; ++l) {
                 const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];

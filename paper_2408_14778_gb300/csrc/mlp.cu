@@ -613,6 +613,8 @@ struct cfr_mlp {
     int64_t cap = 0;
     std::vector<__nv_bfloat16 *> acts, grads;   // grads[l]: dL/dZ of layer l (BF16, [cap][pdims[l + 1]])
     float *yp = nullptr;
+    int64_t last_batch = 0;          // real rows of the last forward or backward pass
+    bool have_dz = false;            // grads[] hold the last backward pass's output gradients
     cudaEvent_t ev[4] = {};
     double fwd_flops = 0, bwd_flops = 0;
     bool fwd_timed = false, bwd_timed = false;
@@ -908,6 +910,8 @@ cfr_status cfr_mlp_forward(cfr_mlp *m, const float *x, int32_t batch, float *y) 
     if ((st = forward_padded(m, Bp, &m->fwd_flops)) != CFR_OK) return st;
     MCK(cudaEventRecord(m->ev[1], m->stream));
     m->fwd_timed = true;
+    m->last_batch = batch;
+    m->have_dz = false;
     k_unpack_output<<<grid_for((int64_t)batch * m->dims[(size_t)m->L]), 256, 0, m->stream>>>(
         m->yp, m->pdims[(size_t)m->L], batch, m->dims[(size_t)m->L], y);
     MCK(cudaGetLastError());
@@ -949,11 +953,53 @@ cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int
     MCK(cudaEventRecord(m->ev[3], m->stream));
     m->bwd_flops = fb;
     m->bwd_timed = true;
+    m->last_batch = batch;
+    m->have_dz = true;
     for (int l = 0; l < L; ++l) {
         const int64_t N = m->pdims[(size_t)l + 1];
         k_bias_grad<<<(unsigned)(N / 32), dim3(32, 8), 0, m->stream>>>(m->grads[(size_t)l], Bp, N, m->g + m->b_off[(size_t)l]);
         MCK(cudaGetLastError());
     }
+    return CFR_OK;
+}
+
+cfr_status cfr_mlp_get_intermediate(cfr_mlp *m, int32_t which, int32_t layer, float *out, int64_t len) {
+    cfr_status st = usable(m);
+    if (st != CFR_OK) return st;
+    if (!out) return merr(m, CFR_ERR_INVALID, "out is NULL");
+    if (m->last_batch < 1) return merr(m, CFR_ERR_STATE, "no forward or backward pass has run yet");
+    if (which == CFR_MLP_DZ && !m->have_dz) return merr(m, CFR_ERR_STATE, "the last pass was not a backward pass");
+    if (which != CFR_MLP_OUT && (layer < 0 || layer >= m->L))
+        return merr(m, CFR_ERR_INVALID, "layer %d is outside [0, %d)", layer, m->L);
+    int64_t cols = 0, ld = 0;
+    const void *src = nullptr;
+    bool bf16 = true;
+    switch (which) {
+    case CFR_MLP_ACT: cols = m->dims[(size_t)layer]; ld = m->pdims[(size_t)layer]; src = m->acts[(size_t)layer]; break;
+    case CFR_MLP_DZ: cols = m->dims[(size_t)layer + 1]; ld = m->pdims[(size_t)layer + 1]; src = m->grads[(size_t)layer]; break;
+    case CFR_MLP_OUT: cols = m->dims[(size_t)m->L]; ld = m->pdims[(size_t)m->L]; src = m->yp; bf16 = false; break;
+    default: return merr(m, CFR_ERR_INVALID, "which must be CFR_MLP_ACT, CFR_MLP_DZ or CFR_MLP_OUT");
+    }
+    const int64_t B = m->last_batch;
+    if (len < B * cols) return merr(m, CFR_ERR_INVALID, "out needs %lld entries", (long long)(B * cols));
+    MDeviceGuard dg(m->device);
+    if ((st = check_err(m)) != CFR_OK) return st;
+    const size_t esz = bf16 ? sizeof(__nv_bfloat16) : sizeof(float);
+    std::vector<unsigned char> host((size_t)(B * ld) * esz);
+    MCK(cudaMemcpyAsync(host.data(), src, host.size(), cudaMemcpyDeviceToHost, m->stream));
+    MCK(cudaStreamSynchronize(m->stream));
+    for (int64_t r = 0; r < B; ++r)
+        for (int64_t c = 0; c < cols; ++c) {
+            const size_t i = (size_t)(r * ld + c);
+            if (bf16) {
+                uint16_t h;
+                std::memcpy(&h, host.data() + 2 * i, 2);
+                const uint32_t w = (uint32_t)h << 16;   // a BF16 value is the top half of an FP32 one
+                std::memcpy(&out[r * cols + c], &w, 4);
+            } else {
+                std::memcpy(&out[r * cols + c], host.data() + 4 * i, 4);
+            }
+        }
     return CFR_OK;
 }
 

@@ -1,11 +1,20 @@
 """The value network's kernels (cfr_mlp_*) against the FP64 oracle (oracle/mlp.py) in its BF16 mode,
 which rounds at the same points as the kernels (GPU tests).
 
-Tolerances: the kernels accumulate in FP32 over K <= 1024 products, a relative error near K 2^-24 at
-worst (about 1e-4) and far less on average; a hidden activation whose FP32 value differs from the
-oracle's by that much can round to the neighbouring BF16 value (one BF16 ulp, 2^-8 relative) - a rare
-event that moves a result by about 4e-3 times one term's share.  Normwise, outputs must agree to 2e-3
-and gradients to 5e-3; Adam, elementwise FP32 arithmetic, to 1e-5.
+Element by element, layer by layer: every product is recomputed by the oracle from the kernels' own
+BF16 inputs of that layer (the test hook cfr_mlp_get_intermediate), so each output entry has a
+rigorous bound.  The products of BF16 values are exact in FP32, and the FP32 accumulation of K of them
+(tensor-core or warp-level, in any order, with round-to-nearest or truncating alignment of the
+addends) is within c K 2^-24 sum_k |a_k b_k| of the exact sum; c = 8 leaves a factor of two to four
+over the worst case of either accumulation.  The sum of absolute products (|A||B|)_ij is computed by the
+oracle on absolute values.  A result that the kernels round to BF16 (hidden activations, masked
+gradients) must lie between the roundings of exact - E and exact + E (rounding is monotone); where the
+two differ the kernels may round either way (a one-BF16-ulp flip), and such flips must stay rare
+(at most 1% of a layer's entries).  An error confined to one tile, one bias row or one column would
+break these bounds by orders of magnitude.
+
+The whole network is also compared normwise with the oracle run from the input alone: outputs within
+2e-3, gradients within 5e-3 (the flips above propagate), Adam (elementwise FP32) within 1e-5.
 """
 import numpy as np
 import pytest
@@ -16,6 +25,52 @@ from oracle import mlp
 pytestmark = pytest.mark.gpu
 
 LEAF_DIMS = [64 + 2 * 169, 1024, 1024, 1024, 2 * 169]   # public embedding + two ranges -> two value vectors
+
+
+U32 = 2.0 ** -24
+C_ACC = 8.0
+
+
+def _acc_bound(absprod, k):
+    """Bound on |FP32 accumulation - exact| for reductions of length k with absolute-value sum absprod
+    (plus one FP32 rounding of the bias addition, folded into k + 1)."""
+    return C_ACC * (k + 1) * U32 * absprod
+
+
+def _check_rounded(got, exact, err, rd, what):
+    """got must be rd(v) for some v within err of exact (rd monotone); returns the number of entries
+    where got differs from rd(exact)."""
+    lo, hi = rd(exact - err), rd(exact + err)
+    bad = ~((got >= lo) & (got <= hi))
+    assert not bad.any(), (what, int(bad.sum()), np.argwhere(bad)[:5].tolist(),
+                           got[bad][:5].tolist(), exact[bad][:5].tolist(), err[bad][:5].tolist())
+    flips = int(np.count_nonzero(got != rd(exact)))
+    assert flips <= max(3, 0.01 * got.size), (what, flips, got.size)
+    return flips
+
+
+def _check_close(got, exact, err, what):
+    bad = np.abs(got - exact) > err
+    assert not bad.any(), (what, int(bad.sum()), np.argwhere(bad)[:5].tolist(), got[bad][:5].tolist(),
+                           exact[bad][:5].tolist(), err[bad][:5].tolist())
+
+
+def _layerwise_forward(m, params, x, batch):
+    """Every layer's product and epilogue element by element, from the kernels' own layer inputs."""
+    a = cfr.cfr_mlp_get_intermediate(m, cfr.CFR_MLP_ACT, 0, batch).astype(np.float64)
+    np.testing.assert_array_equal(a, mlp.bf16_round(x))            # the packed input is bf16(x), exactly
+    L = len(params)
+    for l, (W, b) in enumerate(params):
+        z = mlp.dense(a, W, b, bf16=True)
+        err = _acc_bound(mlp.dense(np.abs(a), np.abs(W), np.abs(b), bf16=True), a.shape[1])
+        if l + 1 < L:
+            nxt = cfr.cfr_mlp_get_intermediate(m, cfr.CFR_MLP_ACT, l + 1, batch).astype(np.float64)
+            _check_rounded(nxt, z, err, lambda v: mlp.hidden(v, bf16=True), f"hidden {l}")
+            a = nxt
+        else:
+            y = cfr.cfr_mlp_get_intermediate(m, cfr.CFR_MLP_OUT, 0, batch).astype(np.float64)
+            _check_close(y, z, err + U32 * np.abs(z), "output")
+    return a
 
 
 def _rel(a, b):
@@ -48,9 +103,10 @@ def test_forward_matches_oracle(dims, batch, path):
     x = rng.normal(size=(batch, dims[0])).astype(np.float32)
     y = cfr.cfr_mlp_forward(m, torch.tensor(x, device="cuda")).cpu().numpy().astype(np.float64)
     cfr.cfr_mlp_synchronize(m)
+    _layerwise_forward(m, params, x.astype(np.float64), batch)
+    np.testing.assert_array_equal(y, cfr.cfr_mlp_get_intermediate(m, cfr.CFR_MLP_OUT, 0, batch))
     ref, _ = mlp.forward(params, x.astype(np.float64), bf16=True)
     assert _rel(y, ref) <= 2e-3
-    assert np.max(np.abs(y - ref)) <= 2e-2 * np.max(np.abs(ref)) + 1e-6
 
 
 @PATHS
@@ -64,6 +120,29 @@ def test_gradients_match_oracle(dims, batch, path):
     t = rng.normal(size=(batch, dims[-1])).astype(np.float32)
     loss = cfr.cfr_mlp_backward(m, torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")).item()
     g = mlp.unflatten(cfr.cfr_mlp_get_grads(m).astype(np.float64), dims)
+    # element by element, from the kernels' own intermediates of this backward pass
+    _layerwise_forward(m, params, x.astype(np.float64), batch)
+    y = cfr.cfr_mlp_get_intermediate(m, cfr.CFR_MLP_OUT, 0, batch).astype(np.float64)
+    dz = cfr.cfr_mlp_get_intermediate(m, cfr.CFR_MLP_DZ, len(params) - 1, batch).astype(np.float64)
+    # dL/dy: the kernels form y - t and scale it in FP32 (two roundings) before rounding to BF16
+    v = mlp.output_gradient(y, t.astype(np.float64))
+    _check_rounded(dz, v, 4 * U32 * np.abs(v), lambda u: mlp.bf16_round(u), "output gradient")
+    Bp = -(-batch // 128) * 128                                      # the kernels' padded batch
+    for l in range(len(params) - 1, -1, -1):
+        W, _ = params[l]
+        a = cfr.cfr_mlp_get_intermediate(m, cfr.CFR_MLP_ACT, l, batch).astype(np.float64)
+        rW, rb = mlp.layer_gradients(dz, a)
+        aW, ab = mlp.layer_gradients(np.abs(dz), np.abs(a))
+        _check_close(g[l][0], rW, _acc_bound(aW, Bp) + U32 * np.abs(rW), f"dW {l}")
+        _check_close(g[l][1], rb, _acc_bound(ab, Bp) + U32 * np.abs(rb), f"db {l}")
+        if l > 0:
+            prev = cfr.cfr_mlp_get_intermediate(m, cfr.CFR_MLP_DZ, l - 1, batch).astype(np.float64)
+            exact = mlp.masked_product(dz, W, a, bf16=True)
+            err = _acc_bound(mlp.masked_product(np.abs(dz), np.abs(W), a, bf16=True), W.shape[0])
+            assert not prev[~(a > 0)].any(), f"masked gradient {l - 1}"   # zero where the ReLU output was 0
+            _check_rounded(prev, exact, err, lambda u: mlp.bf16_round(u), f"masked gradient {l - 1}")
+            dz = prev
+    # and the whole network from the input alone, normwise
     ref_loss, ref = mlp.loss_and_grads(params, x.astype(np.float64), t.astype(np.float64), bf16=True)
     assert loss == pytest.approx(ref_loss, rel=1e-3)
     for l, ((gW, gb), (rW, rb)) in enumerate(zip(g, ref)):

@@ -31,6 +31,13 @@ def test_matches_allocating_entry_point_on_two_calls_in_a_row(precision):
     s = cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=precision)
     info = cfr.cfr_get_info(s)
     assert 16 * (info["num_decision"] + info["num_q"]) + 4 * info["num_infosets"] < cfr.CFR_STATIC_SCRATCH_BYTES
+    # another game's call first fills the shared region with values laid out for a different tree, so a
+    # quantity the next call failed to reset would show up in its result
+    other = cfr.cfr_load_tree(gamegen.config("bucket3_depth6", seed=3), variant=cfr.CFR_VANILLA, precision=precision)
+    cfr.cfr_iterate(other, 7)
+    want_other = cfr.cfr_exploitability(other)
+    got_other = cfr.cfr_exploitability_static(other)
+    assert abs(got_other[0] - want_other[0]) <= TOL_EXPL, (got_other, want_other)
     for iters in (5, 20):
         cfr.cfr_iterate(s, iters)
         want = cfr.cfr_exploitability(s)
@@ -39,6 +46,9 @@ def test_matches_allocating_entry_point_on_two_calls_in_a_row(precision):
         for got in (first, second):
             assert abs(got[0] - want[0]) <= TOL_EXPL and abs(got[1] - want[1]) <= TOL_EXPL, (got, want)
         assert want[0] > 0
+    got_other = cfr.cfr_exploitability_static(other)     # and back to the small game after the large one
+    assert abs(got_other[0] - want_other[0]) <= TOL_EXPL, (got_other, want_other)
+    other.close()
     s.close()
 
 
