@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--variant", choices=["plus", "vanilla"], default="plus")
     ap.add_argument("--fuse-levels", type=int, default=-1,
                     help="FP32 mode: deepest depths run by the fused kernel (-1 automatic, 0 none)")
+    ap.add_argument("--tail-slots", type=int, default=0,
+                    help="FP32 mode, last two depths: 0 per-slot loads and atomics (default), 1 slot-dense tiles "
+                         "with staged strategy entries, 2 the same with bulk-reduced regrets")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true", help="skip the error-against-the-oracle block")
@@ -587,6 +590,7 @@ def workload_config(args, g, info=None):
         c.update(decision_nodes=info["num_decision"], terminals=info["num_terminal"], infosets=info["num_infosets"],
                  infoset_actions=info["num_q"], levels=info["num_levels"], device_bytes=info["device_bytes"],
                  fused_from_depth=info["fused_from_depth"], fused_tiles=info["fused_tiles"],
+                 tail_kernel=info["tail_kernel"],
                  head_depths=info["head_depths"],
                  kernels_per_iteration=info["kernels_per_iteration"])
     return c
@@ -634,7 +638,8 @@ def run_ours(args, world, rank, local):
     variant = cfr.CFR_PLUS if args.variant == "plus" else cfr.CFR_VANILLA
     precision = cfr.CFR_FP32 if args.precision == "fp32" else cfr.CFR_FP64
     g = gamegen.config(args.workload, seed=args.seed, target_nodes=args.nodes)
-    s = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local, fuse_levels=args.fuse_levels)
+    s = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local, fuse_levels=args.fuse_levels,
+                          tail_slots=args.tail_slots)
     info = cfr.cfr_get_info(s)
     stream = torch.cuda.current_stream(local)
     cfr.cfr_iterate(s, args.warmup)
@@ -666,8 +671,10 @@ def run_ours(args, world, rank, local):
     us = np.mean([[p["us"] for p in run] for run in ph], axis=0)
     by = np.array([p["bytes"] for p in ph[0]])
     nfused = info["num_levels"] - info["fused_from_depth"]
+    tail_name = {1: "k_tail", 2: "k_tail_stream", 3: "k_tail_slots", 4: "k_tail_slots (bulk regrets)"}.get(
+        info["tail_kernel"], "k_fused")
     kernel_of = {cfr.CFR_PHASE_TOPDOWN: "k_topdown", cfr.CFR_PHASE_BOTTOMUP: "k_bottomup",
-                 cfr.CFR_PHASE_FUSED: "k_tail_stream" if nfused == 2 else "k_fused",
+                 cfr.CFR_PHASE_FUSED: tail_name if nfused == 2 else "k_fused",
                  cfr.CFR_PHASE_OWN: "k_own",
                  cfr.CFR_PHASE_UPDATE: "k_update_rows" if args.precision == "fp32" else "k_update"}
     k = int(np.argmax(us))
@@ -691,7 +698,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
-        s2 = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local, fuse_levels=args.fuse_levels)
+        s2 = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local, fuse_levels=args.fuse_levels,
+                               tail_slots=args.tail_slots)
         # each step's root value lands in page-locked memory; step t's is read while step t + 1 runs
         stream = torch.cuda.current_stream(local)
         ready = [torch.cuda.Event(), torch.cuda.Event()]

@@ -110,6 +110,12 @@ typedef struct {
     int64_t batch_split_nodes;  /* cfr_batch_load: games of at least this many nodes run as one forest
                                    through the per-depth kernels, the rest in the persistent kernel if
                                    their image fits shared memory (0 = default 4096; negative = no split) */
+    int32_t tail_slots;     /* FP32 mode, last two depths fused and streamed: 0 (default) = per-slot
+                               strategy loads and regret atomics; where the tree's tiles are slot-dense
+                               (consecutive nodes of a depth in consecutive infosets, as below one deal of
+                               a public tree): 1 = the tiles' strategy entries staged in shared memory by
+                               bulk copies, regrets by per-slot atomics; 2 = the same with the regrets
+                               added to r~ by bulk reductions.  Elsewhere 1 and 2 act as 0. */
 } cfr_config;
 
 /* Sizes and accounting of a loaded solver. */
@@ -133,6 +139,10 @@ typedef struct {
     int32_t fused_from_depth;     /* first depth run by the fused kernel (num_levels: none) */
     int32_t fused_tiles;          /* thread blocks of the fused kernel that process nodes */
     int32_t head_depths;          /* FP32 mode: leading depths run in one cluster launch per direction */
+    int32_t tail_kernel;          /* the last two depths: 0 per-depth kernels, 1 one thread per node (small
+                                     trees), 2 streamed tiles with per-slot strategy loads and regret
+                                     atomics, 3 streamed slot-dense tiles with staged strategy entries,
+                                     4 the same with bulk-reduced regrets (cfr_config.tail_slots) */
 } cfr_info;
 
 /* Fills *c with defaults: vanilla, FP32, simultaneous, default averaging, current device,

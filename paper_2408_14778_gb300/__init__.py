@@ -72,6 +72,7 @@ class _Config(ctypes.Structure):
         ("dcfr_gamma", ctypes.c_double),
         ("head_levels", ctypes.c_int32),
         ("batch_split_nodes", ctypes.c_int64),
+        ("tail_slots", ctypes.c_int32),
     ]
 
 
@@ -84,7 +85,7 @@ class _Info(ctypes.Structure):
         ("avg_weight", ctypes.c_int32), ("iteration", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
         ("bytes_per_iteration", ctypes.c_int64), ("kernels_per_iteration", ctypes.c_int32),
         ("kernel_launches", ctypes.c_int64), ("fused_from_depth", ctypes.c_int32), ("fused_tiles", ctypes.c_int32),
-        ("head_depths", ctypes.c_int32),
+        ("head_depths", ctypes.c_int32), ("tail_kernel", ctypes.c_int32),
     ]
 
 
@@ -274,10 +275,11 @@ class _TorchAllocator:
 
 def cfr_load_tree(game, variant=CFR_VANILLA, precision=CFR_FP32, update_mode=CFR_SIMULTANEOUS,
                   avg_weight=CFR_AVG_DEFAULT, device=None, stream=None, allocator: str = "torch",
-                  fuse_levels: int = -1, record_nodes: bool = False, dcfr=(1.5, 0.0, 2.0), head_levels: int = 0):
+                  fuse_levels: int = -1, record_nodes: bool = False, dcfr=(1.5, 0.0, 2.0), head_levels: int = 0,
+                  tail_slots: int = 0):
     """Loads a game and returns a Solver.  stream: None = PyTorch's current stream on the device.
-    fuse_levels / record_nodes: cfr_config's fields of the same names; dcfr: (alpha, beta, gamma) of
-    CFR_DISCOUNTED."""
+    fuse_levels / record_nodes / head_levels / tail_slots: cfr_config's fields of the same names; dcfr:
+    (alpha, beta, gamma) of CFR_DISCOUNTED."""
     import torch
 
     if not torch.cuda.is_available():
@@ -292,6 +294,7 @@ def cfr_load_tree(game, variant=CFR_VANILLA, precision=CFR_FP32, update_mode=CFR
     cfg.fuse_levels = int(fuse_levels)
     cfg.record_nodes = 1 if record_nodes else 0
     cfg.head_levels = int(head_levels)
+    cfg.tail_slots = int(tail_slots)
     cfg.dcfr_alpha, cfg.dcfr_beta, cfg.dcfr_gamma = (float(x) for x in dcfr)
     alloc = None
     if allocator == "torch":

@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["cfr_api.cu", "batch_api.cu", "mlp.cu", "layout.cpp"]
-HEADERS = ["kernels.cuh", "stream.cuh", "batch.cuh", "layout.hpp"]
+HEADERS = ["kernels.cuh", "stream.cuh", "batch.cuh", "layout.hpp", "tail_tiles.hpp"]
 
 
 def _nvcc() -> str:

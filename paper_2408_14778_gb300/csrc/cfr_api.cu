@@ -92,9 +92,12 @@ struct cfr_solver {
     // node ranges per fused depth are fuse_bounds[k][0 .. fuse_ntiles]
     int32_t fuse_r = 0, fuse_ntiles = 0;
     int32_t *fuse_bounds = nullptr;
-    bool fuse_tail = false;                               // the last two depths by k_tail / k_tail_stream
-    int32_t *tail_tiles = nullptr;                        // k_tail_stream: 8 words per tile (TailTiles::tm)
-    int32_t ntail_tiles = 0, tl_grid[3] = {0, 0, 0};
+    bool fuse_tail = false;                               // the last two depths by k_tail / k_tail_stream /
+                                                          // k_tail_slots
+    bool tail_slots = false;                              // k_tail_slots (slot-dense tiles) for them
+    int32_t *tail_tiles = nullptr;                        // 8 words per tile (TailTiles::tm), or 12
+                                                          // (SlotTailTiles::tm)
+    int32_t ntail_tiles = 0, tl_grid[3] = {0, 0, 0}, ts_grid[3] = {0, 0, 0};
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
     // FP32 mode: depths 0 .. head_n - 1 run in one cluster launch per direction (k_head_*) of head_ctas
     // blocks; head_n == 0: per-depth launches
@@ -310,6 +313,11 @@ cfr_status setup_stream_na(cfr_solver *s, int gi, int sms) {
     CK(cudaFuncSetAttribute(k_tail_stream<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, lsmem));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail_stream<NA>, kSBThreads, lsmem));
     s->tl_grid[gi] = per_sm * sms;
+    const int ssmem = (int)(sizeof(STStage) * SlotTailTiles<NA, false>::kStages);
+    for (auto k : {k_tail_slots<NA, false>, k_tail_slots<NA, true>})
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail_slots<NA, false>, 32 * (kSTWarps + 1), ssmem));
+    s->ts_grid[gi] = per_sm * sms;
     return CFR_OK;
 }
 
@@ -402,7 +410,17 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
             const int32_t j0 = s->dlevel[r], j1 = s->dlevel[r + 1];
             const int32_t rec = s->cfg.record_nodes != 0, bump = first && r == 0;
             const int gi = std::max(s->level_na[(size_t)r], s->level_na[(size_t)r + 1]);
-            if (s->ntail_tiles > 0 && s->tl_grid[gi] > 0) {
+            if (s->tail_slots && s->ntail_tiles > 0 && s->ts_grid[gi] > 0) {
+                const int grid = std::min(s->ts_grid[gi], s->ntail_tiles);
+                const size_t smem = sizeof(STStage) * SlotTailTiles<3, false>::kStages;
+                const int4 *tb = reinterpret_cast<const int4 *>(s->tail_tiles);
+                const int nth = 32 * (kSTWarps + 1);
+                const bool bulk = s->cfg.tail_slots == 2;
+                auto kern = gi == 0 ? (bulk ? k_tail_slots<kStreamNA[0], true> : k_tail_slots<kStreamNA[0], false>)
+                          : gi == 1 ? (bulk ? k_tail_slots<kStreamNA[1], true> : k_tail_slots<kStreamNA[1], false>)
+                                    : (bulk ? k_tail_slots<kStreamNA[2], true> : k_tail_slots<kStreamNA[2], false>);
+                CK(go(kern, grid, nth, smem, st, t, tb, s->ntail_tiles, rec, bump, s->d_err));
+            } else if (s->ntail_tiles > 0 && s->tl_grid[gi] > 0) {
                 const int grid = std::min(s->tl_grid[gi], s->ntail_tiles);
                 const size_t smem = sizeof(TLStage) * TailTiles<3>::kStages;
                 const int4 *tb = reinterpret_cast<const int4 *>(s->tail_tiles);
@@ -493,7 +511,8 @@ std::vector<std::pair<int32_t, int32_t>> phases(const cfr_solver *s) {
 //   bottom-up at depth l:   24 Nd(l) + 4 C(l)      node fields, reach, value write; one value per child
 //   last two depths (k_tail, r = L-2):
 //                           28 Nd(r) + 12 Nd(r+1)  node fields and reaches of depth r, value written;
-//                                                  node fields of depth r+1
+//                                                  node fields of depth r+1 (k_tail_slots: 4 Nd(r+1),
+//                                                  the packed word alone)
 //                         + 4 T(r) + 4 T(r+1)      one utility per terminal child
 //   fused depths r..L-1 (k_fused tiles):
 //                           16 Nd(>=r) + 4 T(>=r)  node fields; one utility per terminal child
@@ -517,7 +536,8 @@ std::vector<double> phase_bytes(const cfr_solver *s) {
             const double children = (double)s->level_children[l];
             b.push_back(f64 ? 40 * nd(l) + 8 * children : 24 * nd(l) + 4 * children);
         } else if (ph.first == CFR_PHASE_FUSED && s->fuse_tail) {
-            b.push_back(28 * nd(l) + 12 * nd(l + 1) + 4 * (double)(s->level_terminals[l] + s->level_terminals[l + 1]));
+            b.push_back(28 * nd(l) + (s->tail_slots ? 4 : 12) * nd(l + 1) +
+                        4 * (double)(s->level_terminals[l] + s->level_terminals[l + 1]));
         } else if (ph.first == CFR_PHASE_FUSED) {
             double x = 12 * nd(l);
             for (int32_t k = l; k < s->L; ++k) x += 16 * nd(k) + 4 * (double)s->level_terminals[k];
@@ -638,6 +658,19 @@ cfr_status sync_and_check(cfr_solver *s) {
     return CFR_OK;
 }
 
+// k_tail_slots' tiles (cut_slot_tail_tiles) uploaded for depth r; false (nothing set) where the tree's
+// tiles are not slot-dense.
+bool slot_tail_tiles(cfr_solver *s, const Layout &Lo, int32_t r) {
+    std::vector<int32_t> meta;
+    if (!cut_slot_tail_tiles(Lo, s->dlevel[r], s->dlevel[r + 1], &meta)) return false;
+    if (alloc_n(s, &s->tail_tiles, (int64_t)meta.size()) != CFR_OK || upload(s, s->tail_tiles, meta) != CFR_OK ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return false;
+    s->ntail_tiles = (int32_t)(meta.size() / 12);
+    s->tail_slots = true;
+    return true;
+}
+
 // FP32 mode: picks the fused depths r .. L-1 and cuts them into tiles for k_fused.  At most
 // cfg.fuse_levels depths (kFuseAuto when negative; none below 2) are fused, fewer where a depth-r
 // node's decision subtree exceeds kFuseCap or a depth >= r holds a node with more than 32 actions.
@@ -657,6 +690,8 @@ cfr_status plan_fusion(cfr_solver *s, const Layout &Lo) {
         const int32_t r = s->L - 2;
         s->fuse_r = r;
         s->fuse_tail = true;
+        if (s->dlevel[r + 1] - s->dlevel[r] >= kStreamMinNodes && s->cfg.tail_slots > 0 && slot_tail_tiles(s, Lo, r))
+            return CFR_OK;
         if (s->dlevel[r + 1] - s->dlevel[r] >= kStreamMinNodes) {
             // tiles for k_tail_stream: consecutive parents while every staged range fits its array
             // (4 elements of each kept free for the 16-byte widening of the copies)
@@ -968,6 +1003,7 @@ void cfr_config_init(cfr_config *c) {
     c->dcfr_beta = 0.0;
     c->dcfr_gamma = 2.0;
     c->batch_split_nodes = 0;
+    c->tail_slots = 0;
 }
 
 cfr_status cfr_validate(const cfr_game_desc *g, char *msg, size_t msg_len) {
@@ -1445,6 +1481,9 @@ cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info) {
     info->kernel_launches = s->kernel_launches;
     info->fused_from_depth = fused_from(s);
     info->head_depths = s->cfg.precision == CFR_FP64 ? 0 : s->head_n;
+    info->tail_kernel = fused_from(s) == s->L || !s->fuse_tail ? 0
+                        : s->ntail_tiles == 0 ? 1
+                        : !s->tail_slots ? 2 : s->cfg.tail_slots == 2 ? 4 : 3;
     info->fused_tiles = fused_from(s) == s->L ? 0
                         : !s->fuse_tail ? s->fuse_ntiles
                         : s->ntail_tiles > 0 ? s->ntail_tiles : nblocks(s->dlevel[s->fuse_r + 1] - s->dlevel[s->fuse_r]);

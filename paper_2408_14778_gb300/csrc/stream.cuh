@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "tail_tiles.hpp"
 
 namespace cfrgb {
 namespace {   // device code: internal to each translation unit that includes it
@@ -237,13 +238,15 @@ __device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage 
     }
 }
 
-// Named barrier 1 over the consumer threads (the producer warp does not take part).
+// Named barrier 1 over the NT consumer threads (the producer warp does not take part).
+template <int NT = kSBConsumerWarps * 32>
 __device__ __forceinline__ void consumers_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(kSBConsumerWarps * 32) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
 }
 
-// Named barrier 1 over the consumer threads that also returns, to every one of them, whether any
+// Named barrier 1 over the NT consumer threads that also returns, to every one of them, whether any
 // passed true.
+template <int NT = kSBConsumerWarps * 32>
 __device__ __forceinline__ bool consumers_any(bool v) {
     uint32_t r;
     asm volatile(
@@ -252,17 +255,17 @@ __device__ __forceinline__ bool consumers_any(bool v) {
         "bar.red.or.pred p, 1, %2, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v), "n"(kSBConsumerWarps * 32)
+        : "r"((uint32_t)v), "n"(NT)
         : "memory");
     return r != 0;
 }
 
 // ---- the producer/consumer pipeline --------------------------------------------------------------
 // P supplies the tile work: P::Stage and P::Tile (shared-memory stage and its description),
-// P::kStages, ntiles(), prefetch(tile, meta) (loads P::kMetaWords words of P::Meta describing a tile,
-// one tile ahead), issue(tile, meta, stage, tile info, full barrier) run by one producer thread, and
-// consume(stage, tile info, consumer thread index) run by each of the kSBConsumerWarps * 32 consumer
-// threads.  P::kConsumerSync: consume() synchronises the consumer threads, so they agree (one
+// P::kStages, P::kConsumerWarps, ntiles(), prefetch(tile, meta) (loads P::kMetaWords words of P::Meta
+// describing a tile, one tile ahead), issue(tile, meta, stage, tile info, full barrier) run by one
+// producer thread (the first lane of warp P::kConsumerWarps), and consume(stage, tile info, consumer
+// thread index) run by each of the P::kConsumerWarps * 32 consumer threads.  P::kConsumerSync: consume() synchronises the consumer threads, so they agree (one
 // barrier with an OR) on whether to take each tile or stop.  Block b takes tiles b, b + gridDim.x, ...  Returns true in consumer threads once their
 // tiles are done (false in the producer warp), so a kernel may continue with other consumer work.
 template <class P>
@@ -274,19 +277,20 @@ __device__ __forceinline__ bool run_pipeline(const P &p, int *err) {
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ typename P::Tile tinfo[S];
     __shared__ int abort_flag;
+    constexpr int CW = P::kConsumerWarps;
     const int32_t ntiles = p.ntiles();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kSBConsumerWarps);
+            mbar_init(&empty[s], CW);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     volatile int *abort = &abort_flag;
-    if (warp == kSBConsumerWarps) {                                   // producer warp
+    if (warp == CW) {                                                 // producer warp
         if (lane != 0) return false;
         int32_t issued = 0;
         typename P::Meta meta[2][P::kMetaWords];
@@ -315,7 +319,7 @@ __device__ __forceinline__ bool run_pipeline(const P &p, int *err) {
         if (!ok && !*abort) { atomicExch(err, 1); *abort = 1; }
         if constexpr (P::kConsumerSync) {
             // consume() synchronises the consumer threads: they must all take the tile or all stop
-            if (consumers_any(!ok || *abort)) break;
+            if (consumers_any<CW * 32>(!ok || *abort)) break;
         } else if (!ok) {
             break;
         }
@@ -331,6 +335,7 @@ template <int NA>
 struct BottomUpTiles {
     using Stage = SBStage;
     using Tile = SBTile;
+    static constexpr int kConsumerWarps = kSBConsumerWarps;
     static constexpr int kStages = kSBStages;
     static constexpr bool kConsumerSync = false;
     DevTree<float> t;
@@ -382,6 +387,7 @@ template <int NA>
 struct TopDownTiles {
     using Stage = TDStage;
     using Tile = TDTile;
+    static constexpr int kConsumerWarps = kSBConsumerWarps;
     static constexpr int kStages = 3;
     static constexpr bool kConsumerSync = true;
     DevTree<float> t;
@@ -519,6 +525,7 @@ template <int NA>
 struct TailTiles {
     using Stage = TLStage;
     using Tile = TLTile;
+    static constexpr int kConsumerWarps = kSBConsumerWarps;
     static constexpr int kStages = 2;
     static constexpr bool kConsumerSync = true;
     DevTree<float> t;
@@ -724,6 +731,283 @@ __global__ void __launch_bounds__(kSBThreads) k_tail_stream(DevTree<float> t, co
     __shared__ float q1[kTC], q2[kTC], cu[kTC];
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
     run_pipeline(TailTiles<NA>{t, tm, nt, record, q1, q2, cu}, err);
+}
+
+// ---- the last two depths with their strategy and regret slots staged (FP32 mode) ----------------------
+// k_tail_slots computes what k_tail_stream does (top-down of depth L-2, bottom-up of L-1 and L-2), for
+// trees whose tiles are slot-dense: the infoset slots of a tile's parents form one contiguous range,
+// those of its children another, and each child's terminal children sit at the same offset in the
+// terminal range as its slots in the slot range.  Breadth-first ids give this wherever consecutive
+// nodes of a depth belong to consecutive infosets - the public tree below one root outcome (deal),
+// whose nodes meet their infosets in the same order for every deal - so the host cuts tiles at every
+// break of contiguity and uses this kernel when no single parent breaks it (plan_fusion).
+// Per tile the producer bulk-copies, besides the parents' fields and reaches, the strategy entries of
+// both slot ranges and both utility ranges; a child needs only its packed word (slot base, player),
+// its action count being the distance to the next child's base.  The consumers (one thread per
+// parent) read every strategy entry from shared memory, write each slot's instantaneous regret into
+// the place of its strategy entry, and one thread adds both regret ranges to r~ with two bulk
+// reductions (cp.reduce.async.bulk .add.f32, element-wise atomic), so no per-slot atomics remain.
+// The widened ends of the ranges (16-byte copies) belong to neighbouring tiles and are zeroed before
+// the reduction.
+constexpr int kSTWarps = kSTP / 32;        // tile limits kSTP .. kSTTP: tail_tiles.hpp
+
+struct STStage {                           // + 4 / + 8: room for widening the copies to 16 bytes
+    uint32_t qp[kSTP + 4], km[kSTP + 4];
+    float r1[kSTP + 4], r2[kSTP + 4];
+    int32_t df[kSTP + 8], tf[kSTP + 8];
+    uint32_t cqp[kSTC + 4];
+    float sp[kSTSP + 4], sc[kSTSC + 4];    // strategy entries of the two slot ranges, then their regrets
+    float pu[kSTTP + 4], cu[kSTSC + 4];    // the two utility ranges
+};
+
+struct STTile {
+    int32_t j0, n, o;                      // parents [j0, j0 + n); node j0 at index o of the parent arrays
+    int32_t cs, nc, co;                    // children [cs, cs + nc); child cs at index co of cqp
+    int32_t pal;                           // global terminal index of pu[0]
+    int32_t spal, spn, scal, scn;          // global slot of sp[0] / sc[0] and their widened lengths
+    int32_t qps, qpe, qcs, qce;            // the exact slot ranges of the parents and the children
+    int32_t ushift;                        // cu index of a child's first terminal = its slot base + ushift
+};
+
+// Bulk reduction shared -> global of `bytes` (a multiple of 16, both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_add_s2g(float *dst, const float *src, uint32_t bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+
+// BULK: the regrets replace the strategy entries in shared memory and are added to r~ by two bulk
+// reductions per tile (one thread waits for the copy engine to read them before the stage is
+// released); otherwise each nonzero contribution is added with a per-slot atomic, as in
+// k_tail_stream, and contributions of zero counterfactual reach are skipped.
+template <int NA, bool BULK>
+struct SlotTailTiles {
+    using Stage = STStage;
+    using Tile = STTile;
+    static constexpr int kStages = 2;
+    static constexpr int kConsumerWarps = kSTWarps;
+    static constexpr bool kConsumerSync = true;
+    static constexpr int kN = kSTP;        // consumer threads
+    DevTree<float> t;
+    const int4 *tm;                        // per tile three int4: {j0, j1, cs, ce}, {pts, pte, cts, cte},
+                                           // {qps, qpe, qcs, qce}
+    int32_t nt, record;
+    float *q1, *q2, *cv;                   // shared memory, kSTC each: children's reaches and values
+    __device__ int32_t ntiles() const { return nt; }
+    using Meta = int4;
+    static constexpr int kMetaWords = 3;
+    __device__ void prefetch(int32_t tile, int4 *meta) const {
+        meta[0] = __ldg(tm + 3 * tile);
+        meta[1] = __ldg(tm + 3 * tile + 1);
+        meta[2] = __ldg(tm + 3 * tile + 2);
+    }
+    __device__ void issue(int32_t, const int4 *meta, Stage *st, Tile *ti, uint64_t *full) const {
+        const int32_t j0 = meta[0].x, n = meta[0].y - j0, cs = meta[0].z, ce = meta[0].w;
+        const int32_t pts = meta[1].x, pte = meta[1].y, cts = meta[1].z, cte = meta[1].w;
+        const int32_t qps = meta[2].x, qpe = meta[2].y, qcs = meta[2].z, qce = meta[2].w;
+        uint32_t bf, bd, bc, bpu, bcu, bsp, bsc;
+        const int32_t jal = widen16(j0, j0 + n, &bf);
+        widen16(j0, j0 + n + 1, &bd);
+        const int32_t cal_n = widen16(cs, ce, &bc);
+        const int32_t pal = widen16(pts, pte, &bpu);
+        const int32_t cual = widen16(cts, cte, &bcu);
+        const int32_t spal = widen16(qps, qpe, &bsp);
+        const int32_t scal = widen16(qcs, qce, &bsc);
+        ti->j0 = j0; ti->n = n; ti->o = j0 - jal;
+        ti->cs = cs; ti->nc = ce - cs; ti->co = cs - cal_n;
+        ti->pal = pal;
+        ti->spal = spal; ti->spn = (int32_t)(bsp / 4u); ti->scal = scal; ti->scn = (int32_t)(bsc / 4u);
+        ti->qps = qps; ti->qpe = qpe; ti->qcs = qcs; ti->qce = qce;
+        ti->ushift = cts - cual - qcs;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(full, 4 * bf + 2 * bd + bc + bpu + bcu + bsp + bsc);
+        bulk_g2s(st->qp, t.qp + jal, bf, full);
+        bulk_g2s(st->km, t.kmask + jal, bf, full);
+        bulk_g2s(st->r1, t.reach1 + jal, bf, full);
+        bulk_g2s(st->r2, t.reach2 + jal, bf, full);
+        bulk_g2s(st->df, t.dfirst + jal, bd, full);
+        bulk_g2s(st->tf, t.tfirst + jal, bd, full);
+        if (bc) bulk_g2s(st->cqp, t.qp + cal_n, bc, full);
+        if (bpu) bulk_g2s(st->pu, t.util + pal, bpu, full);
+        if (bcu) bulk_g2s(st->cu, t.util + cual, bcu, full);
+        if (bsp) bulk_g2s(st->sp, t.sigma + spal, bsp, full);
+        if (bsc) bulk_g2s(st->sc, t.sigma + scal, bsc, full);
+    }
+    // Thread c takes parent c (phases 0 and 2) and children c, c + kN, ... (phase 1).
+    __device__ void consume(Stage &st, const Tile &tref, int c) const {
+        const Tile ti = tref;              // the tile's description in registers
+        const bool act = c < ti.n;
+        uint32_t m = 0;
+        int32_t c0 = 0, t0 = 0, e0 = 0;
+        int na = 0, p = 0;
+        float r1 = 0.f, r2 = 0.f;
+        float s[NA];
+        if (act) {
+            const int32_t k = ti.o + c;
+            const uint32_t w = st.qp[k];
+            m = st.km[k];
+            c0 = st.df[k];
+            t0 = st.tf[k];
+            na = (st.df[k + 1] - c0) + __popc(m);
+            p = qp_player(w);
+            e0 = qp_base(w) - ti.spal;
+            r1 = st.r1[k];
+            r2 = st.r2[k];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) s[a] = a < na ? st.sp[e0 + a] : 0.f;
+            // phase 0: the top-down step, the children's reaches to shared memory
+            int32_t y = c0 - ti.cs;
+            if (na <= NA) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    if (a < na && !((m >> a) & 1u)) {
+                        q1[y] = p == 1 ? r1 : r1 * s[a];
+                        q2[y] = p == 2 ? r2 : r2 * s[a];
+                        ++y;
+                    }
+                }
+            } else {
+                for (int a = 0; a < na; ++a) {
+                    if ((m >> a) & 1u) continue;
+                    const float sv = st.sp[e0 + a];
+                    q1[y] = p == 1 ? r1 : r1 * sv;
+                    q2[y] = p == 2 ? r2 : r2 * sv;
+                    ++y;
+                }
+            }
+        }
+        if constexpr (BULK) {
+            // the widened ends of both slot ranges belong to other tiles' infosets: nothing is added there
+            if (c < 4) {
+                if (ti.spal + c < ti.qps) st.sp[c] = 0.f;
+                if (ti.spn > c && ti.spal + ti.spn - 1 - c >= ti.qpe) st.sp[ti.spn - 1 - c] = 0.f;
+                if (ti.scn > c && ti.scal + c < ti.qcs) st.sc[c] = 0.f;
+                if (ti.scn > c && ti.scal + ti.scn - 1 - c >= ti.qce) st.sc[ti.scn - 1 - c] = 0.f;
+            }
+        }
+        consumers_sync<kN>();
+        // phase 1: the children's bottom-up steps (terminal children only)
+        for (int32_t ci = c; ci < ti.nc; ci += kN) {
+            const uint32_t cw = st.cqp[ti.co + ci];
+            const int32_t cq = qp_base(cw);
+            const int cp = qp_player(cw);
+            const int32_t nx = ci + 1 < ti.nc ? qp_base(st.cqp[ti.co + ci + 1]) : ti.qce;
+            const int cna = nx - cq;
+            float *sv = st.sc + (cq - ti.scal);
+            const float *tv = st.cu + (cq + ti.ushift);
+            float ud = 0.f;
+            float v[NA];
+            if (cna <= NA) {
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    if (b < cna) {
+                        v[b] = tv[b];
+                        ud = madd(ud, sv[b], v[b]);
+                    }
+                }
+            } else {
+                for (int b = 0; b < cna; ++b) ud = madd(ud, sv[b], tv[b]);
+            }
+            cv[ci] = ud;
+            const float cq1 = q1[ci], cq2 = q2[ci];
+            if (record) {
+                const int32_t cg = ti.cs + ci;
+                t.u[cg] = ud;
+                t.reach1[cg] = cq1;
+                t.reach2[cg] = cq2;
+            }
+            const float wr = !collects(t, cp) ? 0.f : cp == 1 ? cq1 : -cq2;
+            if constexpr (BULK) {
+                if (cna <= NA) {
+#pragma unroll
+                    for (int b = 0; b < NA; ++b)
+                        if (b < cna) sv[b] = wr * (v[b] - ud);
+                } else {
+                    for (int b = 0; b < cna; ++b) sv[b] = wr * (tv[b] - ud);
+                }
+            } else {
+                if (wr == 0.f) continue;
+                if (cna <= NA) {
+#pragma unroll
+                    for (int b = 0; b < NA; ++b)
+                        if (b < cna) atomicAdd(&t.inst[cq + b], wr * (v[b] - ud));
+                } else {
+                    for (int b = 0; b < cna; ++b) atomicAdd(&t.inst[cq + b], wr * (tv[b] - ud));
+                }
+            }
+        }
+        consumers_sync<kN>();
+        // phase 2: parent c's bottom-up step
+        if (act) {
+            const float *pv = st.pu + (t0 - ti.pal);
+            const float *dv = cv + (c0 - ti.cs);
+            float *sv = st.sp + e0;
+            const int32_t qb = e0 + ti.spal;
+            const float wr = !collects(t, p) ? 0.f : p == 1 ? r1 : -r2;
+            float ud = 0.f;
+            if (na <= NA) {
+                float v[NA];
+                int kt = 0, kd = 0;
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    if (a < na) {
+                        const bool term = (m >> a) & 1u;
+                        v[a] = *(term ? pv + kt : dv + kd);
+                        kt += term;
+                        kd += !term;
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+                    if (a < na) ud = madd(ud, s[a], v[a]);
+                t.u[ti.j0 + c] = ud;
+                if constexpr (BULK) {
+#pragma unroll
+                    for (int a = 0; a < NA; ++a)
+                        if (a < na) sv[a] = wr * (v[a] - ud);
+                } else if (wr != 0.f) {
+#pragma unroll
+                    for (int a = 0; a < NA; ++a)
+                        if (a < na) atomicAdd(&t.inst[qb + a], wr * (v[a] - ud));
+                }
+            } else {
+                int kt = 0, kd = 0;
+                for (int a = 0; a < na; ++a) {
+                    const float val = ((m >> a) & 1u) ? pv[kt++] : dv[kd++];
+                    ud = madd(ud, sv[a], val);
+                }
+                t.u[ti.j0 + c] = ud;
+                kt = kd = 0;
+                for (int a = 0; a < na; ++a) {
+                    const float val = ((m >> a) & 1u) ? pv[kt++] : dv[kd++];
+                    if constexpr (BULK) sv[a] = wr * (val - ud);
+                    else if (wr != 0.f) atomicAdd(&t.inst[qb + a], wr * (val - ud));
+                }
+            }
+        }
+        if constexpr (BULK) {
+            // the regrets of both ranges into r~: visible to the bulk copy engine, then two reductions; the
+            // stage is released only after the engine has read them
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            consumers_sync<kN>();
+            if (c == 0) {
+                if (ti.spn) bulk_add_s2g(t.inst + ti.spal, st.sp, 4u * (uint32_t)ti.spn);
+                if (ti.scn) bulk_add_s2g(t.inst + ti.scal, st.sc, 4u * (uint32_t)ti.scn);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            }
+        }
+    }
+};
+
+// bump: depth L-2 is the root's, so no top-down launch precedes this one; count the iteration.
+template <int NA, bool BULK>
+__global__ void __launch_bounds__(32 * (kSTWarps + 1)) k_tail_slots(DevTree<float> t, const int4 *tm, int32_t nt,
+                                                                     int32_t record, int32_t bump, int *err) {
+    grid_dependency_wait();
+    __shared__ float q1[kSTC], q2[kSTC], cv[kSTC];
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
+    run_pipeline(SlotTailTiles<NA, BULK>{t, tm, nt, record, q1, q2, cv}, err);
 }
 
 // Unrolled action counts the streamed kernels are built for; a depth takes the smallest one that

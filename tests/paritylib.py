@@ -91,15 +91,20 @@ def fp32_regret_budget_check(g, gs, os_, depth, scale=1.0, players=(1, 2)):
     (2D + 1) eps U (U = max |utility|), the difference two of those plus one, and the sum over the n_h
     nodes of h at most n_h eps * sum |terms|.  Hence
         |r~_gpu - r~| <= (8 D + 8 + 2 n_h) eps32 U pi~(h)      (pi~(h) of Eq. 3),
-    and the same bounds the regret after one step from exact state (CFR+ clipping is 1-Lipschitz).
-    scale multiplies the bound where the step weights r~ (linear CFR: by T).
+    and the same bounds the regret after one step from exact state (CFR+ clipping is 1-Lipschitz), plus
+    the rounding of the FP64 addition R + r~ on either side (half an FP64 ulp of R each), which exceeds
+    the FP32 budget where an infoset's reach is tiny.  scale multiplies the bound where the step weights
+    r~ (linear CFR: by T).
     """
     eps = 2.0 ** -24
     U = float(np.abs(g.utility).max())
     qb = qbase(g)
     nh = np.bincount(g.infoset[g.infoset >= 0], minlength=g.num_infosets)
     budget = scale * (8 * depth + 8 + 2 * nh) * eps * U * os_["cf_reach_sum"]
-    dev = np.maximum.reduceat(np.abs(gs["cum_regret"] - os_["cum_regret"]), qb[:-1]) if qb[-1] else np.zeros(0)
+    Rg, Ro = gs["cum_regret"], os_["cum_regret"]
+    # per slot: the error above the two FP64 roundings of R, then the largest per infoset
+    excess = np.maximum(np.abs(Rg - Ro) - 2.0 ** -53 * (np.abs(Rg) + np.abs(Ro)), 0.0)
+    dev = np.maximum.reduceat(excess, qb[:-1]) if qb[-1] else np.zeros(0)
     bad = np.nonzero(np.isin(g.infoset_player, players) & (dev > budget * (1 + 1e-9) + 1e-300))[0]
     assert bad.size == 0, (f"infoset {bad[0]}: regret error {dev[bad[0]]:.3e} above the FP32 budget "
                            f"{budget[bad[0]]:.3e}")

@@ -38,7 +38,8 @@ def test_full_size_first_iteration(full):
     g, o, s = full
     info = cfr.cfr_get_info(s)
     assert info["num_nodes"] == g.num_nodes > 9e7
-    o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+    assert info["tail_kernel"] == 2                       # the last two depths streamed, per-slot atomics
+    o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR, threads=0)
     cfr.cfr_iterate(s, 1)
     _compare(s, o, g)
     rv = cfr.cfr_root_value(s)
@@ -47,10 +48,10 @@ def test_full_size_first_iteration(full):
 
 def test_full_size_step_from_oracle_state(full):
     g, o, s = full
-    o.iterate(2, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)     # oracle at T = 3
+    o.iterate(2, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR, threads=0)     # oracle at T = 3
     st = o.state()
     cfr.cfr_set_state(s, st["cum_regret"], st["strat_sum"], st["iteration"])
-    o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+    o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR, threads=0)
     cfr.cfr_iterate(s, 1)
     _compare(s, o, g)
 
@@ -80,3 +81,20 @@ def test_fp64_bit_identical_above_the_parallel_layout_threshold():
     for k in ("cum_regret", "strat_sum"):
         np.testing.assert_array_equal(gs[k], os_[k])
     s.close()
+
+
+def test_full_size_both_tail_kernels_from_oracle_state(full):
+    # the last two depths by slot-dense tiles (staged strategy entries; regrets by atomics or by bulk
+    # reductions) as well as by the default per-slot kernel: each one FP32 step from the oracle's state
+    # against the oracle's next iteration (the module's solver is not used after this test)
+    g, o, s = full
+    st = o.state()
+    others = [cfr.cfr_load_tree(g, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, tail_slots=v) for v in (1, 2)]
+    assert [cfr.cfr_get_info(x)["tail_kernel"] for x in others] == [3, 4]
+    for x in [s] + others:
+        cfr.cfr_set_state(x, st["cum_regret"], st["strat_sum"], st["iteration"])
+        cfr.cfr_iterate(x, 1)
+    o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR, threads=0)
+    for x in [s] + others:
+        _compare(x, o, g)
+        x.close()

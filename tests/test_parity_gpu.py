@@ -123,9 +123,10 @@ def test_fp32_nine_to_twelve_actions():
         compare_state(s, o, TOL32, g)
 
 
-def _step_parity(g, variant, Ts, precision, tol, nodes=False, fuse=-1):
+def _step_parity(g, variant, Ts, precision, tol, nodes=False, fuse=-1, tail_slots=-1):
     o = oracle.Oracle(g, record=nodes)
-    s = cfr.cfr_load_tree(g, variant=variant, precision=precision, fuse_levels=fuse, record_nodes=nodes)
+    s = cfr.cfr_load_tree(g, variant=variant, precision=precision, fuse_levels=fuse, record_nodes=nodes,
+                          tail_slots=tail_slots)
     done = 0
     for T in Ts:
         o.iterate(T - 1 - done, variant=variant, avg=variant)
@@ -142,14 +143,18 @@ def _step_parity(g, variant, Ts, precision, tol, nodes=False, fuse=-1):
     return s, o
 
 
-@pytest.mark.parametrize("fuse", [2, 0])
-def test_step_parity_fp32_rank13_depth10(fuse):
+@pytest.mark.parametrize("fuse,slots,kernel", [(2, 1, 3), (2, 2, 4), (2, 0, 2), (0, 0, 0)],
+                         ids=["tail_slots", "tail_slots_bulk", "tail_stream", "per_depth"])
+def test_step_parity_fp32_rank13_depth10(fuse, slots, kernel):
     # ~2e6 nodes, 156-way deal, fold/showdown payoffs, CFR+: one FP32 step from the oracle's FP64
-    # state at T = 1, 2, 10, 100 (step parity), with the last two depths fused and not.
+    # state at T = 1, 2, 10, 100 (step parity), with the last two depths fused (slot-dense tiles with
+    # staged strategy entries and bulk-reduced regrets, or per-slot loads and atomics) and not.
     g = gamegen.config("rank13_depth10", seed=1)
-    s, o = _step_parity(g, cfr.CFR_PLUS, (1, 2, 10, 100), cfr.CFR_FP32, TOL32, nodes=fuse == 2, fuse=fuse)
+    s, o = _step_parity(g, cfr.CFR_PLUS, (1, 2, 10, 100), cfr.CFR_FP32, TOL32, nodes=fuse == 2, fuse=fuse,
+                        tail_slots=slots)
     info = cfr.cfr_get_info(s)
     assert (info["fused_from_depth"] < info["num_levels"]) == (fuse == 2)
+    assert info["tail_kernel"] == kernel
     nc_g, _ = cfr.cfr_exploitability(s)
     nc_o, _ = o.exploitability()
     assert abs(nc_g - nc_o) <= 1e-5 * max(1.0, abs(nc_o))
