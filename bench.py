@@ -447,8 +447,17 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
                             "note": "GPU NashConv against the oracle's best responses to the GPU's average strategy"},
            "tuning": {k: tune[k] for k in ("split_nodes", "threads_per_block", "blocks_per_sm", "cached")},
            "tuning_trials_us_per_iteration": tune["trials"],
-           "forest_part": {"games": info["forest_games"], "nodes": info["forest_nodes"]},
+           "forest_part": {"games": info["forest_games"], "nodes": info["forest_nodes"],
+                           "algorithmic_bytes_per_iteration": info["forest_bytes_per_iteration"],
+                           "achieved_gbs_if_alone": (info["forest_bytes_per_iteration"] * K / sec / 1e9
+                                                     if info["forest_games"] == len(games) else None)},
            "host_seconds": {"generate": gen_s, "tune": tune_s, "load": load_s}}
+    # the games no shared-memory image can hold (the forest part with every other game resident)
+    bres = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=-1, update_mode=update_mode)
+    ires = cfr.cfr_batch_get_info(bres)
+    out["beyond_shared_memory"] = {"games": ires["forest_games"], "nodes": ires["forest_nodes"],
+                                   "node_share": ires["forest_nodes"] / float(nodes.sum())}
+    bres.close()
     # time until every subgame's exploitability is at most 1e-3 (evaluations included)
     if ttt:
         b2 = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"],
@@ -478,8 +487,12 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
     e1.record(stream)
     torch.cuda.synchronize()
     sec_tree = e0.elapsed_time(e1) / 1e3
+    tinfo = cfr.cfr_get_info(s)
     out["plain_full_tree_same_games"] = {"seconds": sec_tree, "iterations": K, "nodes": int(root.num_nodes),
                                          "speedup_of_batched": sec_tree / sec, "host_load_seconds": tree_load_s,
+                                         "algorithmic_bytes_per_iteration": tinfo["bytes_per_iteration"],
+                                         "achieved_gbs": tinfo["bytes_per_iteration"] * K / sec_tree / 1e9,
+                                         "bytes_per_node_iteration": tinfo["bytes_per_iteration"] / root.num_nodes,
                                          "note": "the games under one uniform chance root, cfr_load_tree + cfr_iterate"}
     s.close()
     return out

@@ -289,34 +289,58 @@ def permute_nodes(g: GameDesc, seed: int) -> GameDesc:
 def batch_subgames(count: int, seed: int = 0, min_nodes: float = 1e2, max_nodes: float = 1e5,
                    min_depth: int = 4, max_depth: int = 10) -> list:
     """Independent seeded subgames for batched solving: sizes log-uniform in [min_nodes, max_nodes],
-    depth uniform in [min_depth, max_depth], 2..5 actions per public node, the 6-deal bucket game's deal
-    and U[-2, 2] payoffs.  A size the drawn depth cannot reach (even with every child a decision node)
-    raises the depth until it can (at most max_depth + 4).  The size fit is the continuation
-    probability's bisection (+-10%; where small trees only change size in large steps, the closest size
-    on a grid of continuation probabilities)."""
+    depth uniform over the depths in [min_depth, max_depth] whose full public tree reaches the drawn
+    size (a large size rules out the shallow depths; if none reaches it, the deepest), 2..5 actions per
+    public node, the 6-deal bucket game's deal and U[-2, 2] payoffs.  The size fit is the continuation
+    probability's bisection (+-10%); where small trees only change size in large steps, the closest size
+    on a grid of continuation probabilities that is not below min_nodes, and the size is kept within
+    [min_nodes, 1.1 max_nodes]."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5B6A]))
     out = []
+    kw = dict(deal_kind=DEAL_BUCKET_PAIRS, num_buckets=3, amin=2, amax=5, payoff_kind=PAY_UNIFORM, umax=2.0,
+              p_chance=0.0, general_sum=False, first_actor=1)
     for i in range(count):
         target = int(round(float(np.exp(rng.uniform(np.log(min_nodes), np.log(max_nodes))))))
-        depth = int(rng.integers(min_depth, max_depth + 1))
         sub_seed = int(rng.integers(0, 2**62))
-        kw = dict(deal_kind=DEAL_BUCKET_PAIRS, num_buckets=3, amin=2, amax=5, payoff_kind=PAY_UNIFORM, umax=2.0,
-                  p_chance=0.0, general_sum=False, first_actor=1)
-        while public_size(seed=sub_seed, depth=depth, p_cont=1.0, **kw) < target and depth < max_depth + 4:
-            depth += 1
-        full = public_size(seed=sub_seed, depth=depth, p_cont=1.0, **kw)
-        p = 1.0
-        if full > target * 1.1:
-            try:
-                p = fit_p_cont(target, seed=sub_seed, depth=depth, **kw)
-            except ValueError:       # small trees change size in steps of whole subtrees: take the closest
-                grid = np.linspace(0.0, 1.0, 201)
-                sizes = np.array([public_size(seed=sub_seed, depth=depth, p_cont=float(q), **kw) for q in grid])
-                p = float(grid[int(np.argmin(np.abs(np.log(sizes / target))))])
-        g = public_private(seed=sub_seed, depth=depth, p_cont=p, **kw)
-        g.meta.update(config="batch_subgame", target_nodes=target, batch_index=i)
+        u = float(rng.uniform())
+        # the full tree grows with the depth: the depths that reach the size are d0 .. max_depth
+        full = {}
+        d0 = max_depth
+        for d in range(min_depth, max_depth + 1):
+            full[d] = public_size(seed=sub_seed, depth=d, p_cont=1.0, **kw)
+            if full[d] >= target:
+                d0 = d
+                break
+        ok = list(range(d0, max_depth + 1))
+        first = min(int(u * len(ok)), len(ok) - 1)
+        depth, p = ok[first], 1.0
+        for depth in ok[first:] + ok[:first][::-1]:     # the drawn depth, else the next ones that fit
+            if depth not in full:
+                full[depth] = public_size(seed=sub_seed, depth=depth, p_cont=1.0, **kw)
+            p = _fit_subgame(target, full[depth], min_nodes, max_nodes, seed=sub_seed, depth=depth, **kw)
+            if p is not None:
+                break
+        g = public_private(seed=sub_seed, depth=depth, p_cont=1.0 if p is None else p, **kw)
+        g.meta.update(config="batch_subgame", target_nodes=target, batch_index=i, depth=depth)
         out.append(g)
     return out
+
+
+def _fit_subgame(target: int, full: int, min_nodes: float, max_nodes: float, **kw):
+    """Continuation probability giving about target nodes within [min_nodes, 1.1 max_nodes] (full: the
+    size at p = 1), or None."""
+    if full <= target * 1.1:
+        return 1.0 if min_nodes <= full <= 1.1 * max_nodes else None
+    try:
+        return fit_p_cont(target, **kw)
+    except ValueError:       # small trees change size in steps of whole subtrees: the closest allowed size
+        grid = np.linspace(0.0, 1.0, 201)
+        sizes = np.array([public_size(p_cont=float(q), **kw) for q in grid])
+        allowed = (sizes >= min_nodes) & (sizes <= 1.1 * max_nodes)
+        if not allowed.any():
+            return None
+        err = np.where(allowed, np.abs(np.log(sizes / target)), np.inf)
+        return float(grid[int(np.argmin(err))])
 
 
 def with_chance_root(games: list) -> GameDesc:

@@ -322,6 +322,8 @@ typedef struct {
     int64_t forest_nodes;
     int64_t split_nodes;
     int64_t smem_bytes;         /* dynamic shared memory of a persistent block (its largest game's image) */
+    int64_t forest_bytes_per_iteration;   /* algorithmic bytes of one iteration of the forest part
+                                             (cfr_info.bytes_per_iteration of its solver) */
 } cfr_batch_info;
 
 /* Validates and lays out num_games >= 1 games (each as cfr_load_tree would; the combined size must stay

@@ -100,6 +100,7 @@ class _BatchInfo(ctypes.Structure):
         ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
         ("tuned", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("forest_games", ctypes.c_int32),
         ("forest_nodes", ctypes.c_int64), ("split_nodes", ctypes.c_int64), ("smem_bytes", ctypes.c_int64),
+        ("forest_bytes_per_iteration", ctypes.c_int64),
     ]
 
 
