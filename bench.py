@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--tail-slots", type=int, default=0,
                     help="FP32 mode, last two depths: 0 per-slot loads and atomics (default), 1 slot-dense tiles "
                          "with staged strategy entries, 2 the same with bulk-reduced regrets")
+    ap.add_argument("--head-levels", type=int, default=-1,
+                    help="FP32 mode: depths below the root run by the two head launches (-1 as many as qualify, 0 none)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true", help="skip the error-against-the-oracle block")
@@ -652,7 +654,7 @@ def run_ours(args, world, rank, local):
     precision = cfr.CFR_FP32 if args.precision == "fp32" else cfr.CFR_FP64
     g = gamegen.config(args.workload, seed=args.seed, target_nodes=args.nodes)
     s = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local, fuse_levels=args.fuse_levels,
-                          tail_slots=args.tail_slots)
+                          tail_slots=args.tail_slots, head_levels=args.head_levels)
     info = cfr.cfr_get_info(s)
     stream = torch.cuda.current_stream(local)
     cfr.cfr_iterate(s, args.warmup)
@@ -712,7 +714,7 @@ def run_ours(args, world, rank, local):
         barrier(world)
         t0 = time.perf_counter()
         s2 = cfr.cfr_load_tree(g, variant=variant, precision=precision, device=local, fuse_levels=args.fuse_levels,
-                               tail_slots=args.tail_slots)
+                               tail_slots=args.tail_slots, head_levels=args.head_levels)
         # each step's root value lands in page-locked memory; step t's is read while step t + 1 runs
         stream = torch.cuda.current_stream(local)
         ready = [torch.cuda.Event(), torch.cuda.Event()]

@@ -102,10 +102,11 @@ typedef struct {
     double dcfr_alpha;      /* CFR_DISCOUNTED: alpha, beta, gamma (defaults 1.5, 0, 2); finite */
     double dcfr_beta;
     double dcfr_gamma;
-    int32_t head_levels;    /* FP32 mode: the shallowest depths (each at most 32768 nodes) run in one
-                               thread-block-cluster launch per direction instead of one launch per depth.
-                               0 = none (default: measured slower than the per-depth launches on the 1e8-
-                               node tree), -1 = as many as qualify (at least 2), k >= 2 = at most k.
+    int32_t head_levels;    /* FP32 mode: the shallowest depths of a tree whose root has decision children
+                               only run in one launch per direction instead of one launch per depth, each
+                               block walking the subtrees of a range of root children: the root and the
+                               next k depths (each at most 2^17 nodes, none with more than 32 actions).
+                               -1 (default) = as many as qualify, 0 = none, k >= 1 = at most k.
                                Ignored in FP64 mode. */
     int64_t batch_split_nodes;  /* cfr_batch_load: games of at least this many nodes run as one forest
                                    through the per-depth kernels, the rest in the persistent kernel if
@@ -138,7 +139,8 @@ typedef struct {
     int64_t kernel_launches;      /* kernel launches made by cfr_iterate so far */
     int32_t fused_from_depth;     /* first depth run by the fused kernel (num_levels: none) */
     int32_t fused_tiles;          /* thread blocks of the fused kernel that process nodes */
-    int32_t head_depths;          /* FP32 mode: leading depths run in one cluster launch per direction */
+    int32_t head_depths;          /* FP32 mode: leading depths run by the head launches (the root and the
+                                     depths below it; cfr_config.head_levels), 0 if none */
     int32_t tail_kernel;          /* the last two depths: 0 per-depth kernels, 1 one thread per node (small
                                      trees), 2 streamed tiles with per-slot strategy loads and regret
                                      atomics, 3 streamed slot-dense tiles with staged strategy entries,

@@ -276,7 +276,7 @@ class _TorchAllocator:
 
 def cfr_load_tree(game, variant=CFR_VANILLA, precision=CFR_FP32, update_mode=CFR_SIMULTANEOUS,
                   avg_weight=CFR_AVG_DEFAULT, device=None, stream=None, allocator: str = "torch",
-                  fuse_levels: int = -1, record_nodes: bool = False, dcfr=(1.5, 0.0, 2.0), head_levels: int = 0,
+                  fuse_levels: int = -1, record_nodes: bool = False, dcfr=(1.5, 0.0, 2.0), head_levels: int = -1,
                   tail_slots: int = 0):
     """Loads a game and returns a Solver.  stream: None = PyTorch's current stream on the device.
     fuse_levels / record_nodes / head_levels / tail_slots: cfr_config's fields of the same names; dcfr:

@@ -28,7 +28,7 @@ constexpr int kBlock = 256;
 constexpr int kWideBlock = 1024;   // nodes and infosets with more than 32 actions: one block each
 constexpr int32_t kFuseAuto = 2;   // fused depths when cfr_config.fuse_levels < 0
 constexpr int32_t kStreamMinNodes = 32768;   // FP32 bottom-up depths this large use k_bottomup_stream
-constexpr int32_t kHeadMaxNodes = 32768;     // FP32: leading depths at most this large run in the cluster head
+constexpr int32_t kHeadMaxNodes = 1 << 17;   // FP32: leading depths at most this large run in the head launches
 constexpr int32_t kHeadMaxWide = 64;         // ... with at most this many nodes of more than 32 actions
 
 inline int32_t nblocks(int64_t n) { return (int32_t)((n + kBlock - 1) / kBlock); }
@@ -99,9 +99,10 @@ struct cfr_solver {
                                                           // (SlotTailTiles::tm)
     int32_t ntail_tiles = 0, tl_grid[3] = {0, 0, 0}, ts_grid[3] = {0, 0, 0};
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
-    // FP32 mode: depths 0 .. head_n - 1 run in one cluster launch per direction (k_head_*) of head_ctas
-    // blocks; head_n == 0: per-depth launches
-    int32_t head_n = 0, head_ctas = 0;
+    // FP32 mode: depths 0 .. head_n - 1 run in one launch per direction (k_head_*), head_per_block root
+    // children per block; head_n == 0: per-depth launches
+    int32_t head_n = 0, head_per_block = 0;
+    int32_t *head_done = nullptr;
     // depth-limited solving (cfr_set_range_program, cfr_set_leaves)
     int64_t rp_nseg = 0, nleaves = 0;
     int64_t *rp_dst = nullptr, *rp_ent = nullptr, *rp_prod = nullptr, *leaf_src = nullptr;
@@ -255,13 +256,14 @@ struct Launcher {
 
 HeadArgs head_args(const cfr_solver *s, bool bump) {
     HeadArgs a{};
-    a.n = s->head_n;
+    a.n = s->head_n - 1;
     a.bump = bump;
-    a.wide = s->wide;
-    for (int32_t l = 0; l <= s->head_n; ++l) {
-        a.dlevel[l] = s->dlevel[(size_t)l];
-        a.wlevel[l] = s->wlevel[(size_t)l];
-    }
+    a.d1 = s->dlevel[1];
+    a.nroot = s->dlevel[2] - s->dlevel[1];
+    a.per_block = s->head_per_block;
+    a.nblk = (a.nroot + a.per_block - 1) / a.per_block;
+    a.nown = s->hlevel[(size_t)s->head_n];
+    a.done = s->head_done;
     return a;
 }
 
@@ -365,8 +367,17 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
     if (!det && !alt) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
     if (!det && alt && s->Hp > 0) CK(go(k_zero_inst<real>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp));
     TRY(mark());
-    // own reaches, depth by depth; in the graph on a branch beside the node passes that joins before the
-    // update
+    // the shallowest depths in one launch per direction (the graph's iteration only: the phase timer
+    // keeps one launch per depth); the top-down launch also forms their infosets' own reaches
+    const int32_t head = (!det && ev == nullptr) ? s->head_n : 0;
+    if constexpr (!det) {
+        if (head > 0) {
+            const HeadArgs ha = head_args(s, first);
+            CK(go(k_head_topdown, ha.nblk + nblocks(ha.nown), kHeadThreads, 0, st, t, ha));
+        }
+    }
+    // the other own reaches, depth by depth; in the graph on a branch beside the node passes that forks
+    // after the head (whose own reaches they extend) and joins before the update
     const bool branch = ev == nullptr;
     cudaStream_t os = st;
     if (branch) {
@@ -374,7 +385,7 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         CK(cudaEventRecord(s->fork[pi], st));
         CK(cudaStreamWaitEvent(os, s->fork[pi], 0));
     }
-    for (int32_t l = 0; l < s->L; ++l) {
+    for (int32_t l = head; l < s->L; ++l) {
         const int32_t h0 = s->hlevel[l], h1 = s->hlevel[l + 1];
         if (h1 > h0) CK(go(k_own<real>, nblocks(h1 - h0), kBlock, 0, os, t, h0, h1));
     }
@@ -383,12 +394,6 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         go.cut(os);
     }
     if (s->Hp > 0) TRY(mark());
-    // the shallowest depths in one cluster launch (the graph's iteration only: the phase timer keeps
-    // one launch per depth)
-    const int32_t head = (!det && ev == nullptr) ? s->head_n : 0;
-    if constexpr (!det) {
-        if (head > 0) CK(go.cluster(k_head_topdown, s->head_ctas, kHeadThreads, st, t, head_args(s, first)));
-    }
     for (int32_t l = head; l < r; ++l) {
         if (!topdown_launches(s, l)) continue;
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
@@ -455,7 +460,10 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         TRY(mark());
     }
     if constexpr (!det) {
-        if (head > 0) CK(go.cluster(k_head_bottomup, s->head_ctas, kHeadThreads, st, t, head_args(s, false)));
+        if (head > 0) {
+            const HeadArgs ha = head_args(s, false);
+            CK(go(k_head_bottomup, ha.nblk, kHeadThreads, 0, st, t, ha));
+        }
     }
     if (branch) {
         CK(cudaStreamWaitEvent(st, s->join[pi], 0));
@@ -563,8 +571,8 @@ int32_t launches_per_pass(const cfr_solver *s) {
     const int32_t r = fused_from(s);
     const int32_t head = det ? 0 : s->head_n;
     int32_t n = (r - head) + 1 + (r < s->L);                  // bottom-up depths, fused, update
-    for (int32_t l = 0; l < s->L; ++l) n += s->hlevel[l + 1] > s->hlevel[l];   // own reaches
-    if (head > 0) n += 2;                                     // the head's two cluster launches
+    for (int32_t l = head; l < s->L; ++l) n += s->hlevel[l + 1] > s->hlevel[l];   // own reaches
+    if (head > 0) n += 2;                                     // the head's two launches
     for (int32_t l = head; l < r; ++l) {
         n += s->ddepth_children[l] || l == 0;                 // top-down
         if (!det) n += 2 * (s->wlevel[l + 1] > s->wlevel[l]);
@@ -572,49 +580,30 @@ int32_t launches_per_pass(const cfr_solver *s) {
     return n;
 }
 
-// FP32 mode: the leading depths that one cluster can run faster than one launch each (at most
-// kHeadMaxNodes nodes and kHeadMaxWide wide nodes per depth, below the fused depths); used when there
-// are at least two and a cluster of 16 (or else 8) blocks of kHeadThreads fits.
-cfr_status plan_head(cfr_solver *s) {
+// FP32 mode: the leading depths run by k_head_topdown / k_head_bottomup: depths 0 .. n (head_n = n + 1)
+// for a single root whose children are all decision nodes, n >= 1 the deepest depth below the fused ones
+// such that every depth 1 .. n holds at most kHeadMaxNodes nodes and no node of more than 32 actions
+// (at most cfg.head_levels depths below the root when that is positive; 0: none).  About two blocks per
+// SM walk the root children's subtrees.
+cfr_status plan_head(cfr_solver *s, int sms) {
     s->head_n = 0;
-    s->head_ctas = 0;
+    if (s->cfg.head_levels == 0 || s->L < 2 || s->dlevel[1] != 1) return CFR_OK;
+    const int32_t nroot = s->dlevel[2] - s->dlevel[1];
+    if (nroot < 1 || s->level_children[0] != nroot) return CFR_OK;      // a terminal child of the root
     const int32_t r = fused_from(s);
     const int32_t cap = s->cfg.head_levels < 0 ? kHeadMaxDepths : std::min(s->cfg.head_levels, (int32_t)kHeadMaxDepths);
     int32_t n = 0;
-    while (n < std::min(r, cap) && s->dlevel[(size_t)n + 1] - s->dlevel[(size_t)n] <= kHeadMaxNodes &&
-           s->wlevel[(size_t)n + 1] - s->wlevel[(size_t)n] <= kHeadMaxWide)
+    while (n + 1 <= cap && n + 1 < r && n + 1 < s->L && s->dlevel[(size_t)n + 2] - s->dlevel[(size_t)n + 1] <= kHeadMaxNodes &&
+           s->wlevel[(size_t)n + 2] == s->wlevel[(size_t)n + 1])
         ++n;
-    if (n < 2) return CFR_OK;
-    for (const void *k : {(const void *)k_head_topdown, (const void *)k_head_bottomup})
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-            cudaGetLastError();
-            return CFR_OK;
-        }
-    for (int ctas : {16, 8}) {
-        bool fits = true;
-        for (const void *k : {(const void *)k_head_topdown, (const void *)k_head_bottomup}) {
-            cudaLaunchConfig_t c = {};
-            c.gridDim = dim3((unsigned)ctas);
-            c.blockDim = dim3((unsigned)kHeadThreads);
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = (unsigned)ctas;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            c.attrs = at;
-            c.numAttrs = 1;
-            int clusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&clusters, k, &c) != cudaSuccess || clusters < 1) {
-                cudaGetLastError();
-                fits = false;
-            }
-        }
-        if (fits) {
-            s->head_n = n;
-            s->head_ctas = ctas;
-            return CFR_OK;
-        }
+    if (n < 1) return CFR_OK;
+    if (!s->head_done) {
+        TRY(alloc_n(s, &s->head_done, 1));
+        CK(cudaMemsetAsync(s->head_done, 0, sizeof(int32_t), s->stream));
     }
+    s->head_n = n + 1;
+    const int32_t nblk = std::min(nroot, 2 * std::max(sms, 1));
+    s->head_per_block = (nroot + nblk - 1) / nblk;
     return CFR_OK;
 }
 
@@ -820,7 +809,9 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     TRY(upload(s, s->wide, Lo.wide));
     if (!fp64) {
         TRY(plan_fusion(s, Lo));
-        TRY(plan_head(s));
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+        TRY(plan_head(s, sms));
         {
             std::vector<int32_t> wh;
             for (int32_t h = 0; h < s->Hp; ++h) {
@@ -998,7 +989,7 @@ void cfr_config_init(cfr_config *c) {
     c->avg_weight = CFR_AVG_DEFAULT;
     c->device = -1;
     c->fuse_levels = -1;
-    c->head_levels = 0;
+    c->head_levels = -1;
     c->dcfr_alpha = 1.5;
     c->dcfr_beta = 0.0;
     c->dcfr_gamma = 2.0;

@@ -528,52 +528,121 @@ __global__ void __launch_bounds__(1024) k_bottomup_wide(DevTree<real> t, const i
     bu_wide<real, false>(t, wide[w0 + blockIdx.x], s_red);
 }
 
-// ---- the shallowest depths in one launch, FP32 mode ------------------------------------------------
-// Depths 0 .. n-1 of a large tree hold few nodes (the deal, its first actions): one launch per depth
-// spends its time in launch and dependency latency, not in memory traffic.  k_head_topdown and
-// k_head_bottomup run them all in one launch of a single thread-block cluster, depth by depth, with a
-// cluster barrier (release / acquire at cluster scope, which orders the global writes of one depth
-// before the reads of the next) between depths.  Nodes with more than 32 actions go one per block, to
-// the block-cooperative td_wide / bu_wide.  Data written in this launch is read through L2.
+// ---- the shallowest depths in one launch per direction, FP32 mode ---------------------------------------
+// Depths 0 .. n of a large tree hold few nodes (the deal, its first actions): one launch per depth
+// spends its time in launch and dependency latency, not in memory traffic.  Below the root, the
+// subtrees of consecutive root children are consecutive at every depth (breadth-first ids), and no
+// node's step needs another subtree's, so k_head_topdown gives each block a range of root children
+// and walks their subtrees down depth by depth with block barriers only; k_head_bottomup walks them
+// back up, and the block that finishes last (a global counter, with fences) takes the root.  Both run
+// the per-node steps td_node / bu_node.  The top-down launch also computes the own reaches (Eq. 4) of
+// the infosets first seen at depths 0 .. n, each as the product of the strategy entries of its
+// player's own sequence, multiplied from the first action on - the same products in the same order
+// as k_own's depth-by-depth recursion.  The host uses these kernels for a single root whose children
+// are all decision nodes, with no node of more than 32 actions below the root in depths 1 .. n.
 constexpr int kHeadMaxDepths = 16;
-constexpr int kHeadThreads = 1024;
+constexpr int kHeadThreads = 256;
 
 struct HeadArgs {
-    int32_t n;                                 // depths 0 .. n - 1
-    int32_t bump;                              // count the iteration (first pass of an iteration)
-    const int32_t *wide;                       // nodes with more than 32 actions, by depth
-    int32_t dlevel[kHeadMaxDepths + 1];
-    int32_t wlevel[kHeadMaxDepths + 1];
+    int32_t n;                 // the top-down steps of depths 0 .. n (reaches of depths 1 .. n + 1) and the
+                               // bottom-up steps of depths n .. 0
+    int32_t bump;              // count the iteration (first pass of an iteration)
+    int32_t d1, nroot;         // the root's children: nodes d1 .. d1 + nroot - 1 (depth 1)
+    int32_t per_block, nblk;   // root children per block; blocks walking subtrees
+    int32_t nown;              // infosets 0 .. nown - 1 are first seen at depths 0 .. n
+    int32_t *done;             // k_head_bottomup: blocks that have finished (reset by the last)
 };
 
-__device__ __forceinline__ void cluster_barrier() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+// Own reach of infoset h from the strategy entries along its player's own sequence.
+__device__ __forceinline__ void own_path(const DevTree<float> &t, int32_t h) {
+    const int p = t.iplayer[h];
+    if (p == 0 || !collects(t, p)) return;
+    int32_t q[kHeadMaxDepths + 1];
+    int k = 0;
+    for (int32_t x = h; x >= 0 && t.pseq[x] >= 0 && k <= kHeadMaxDepths; x = t.pseq_h[x]) q[k++] = t.pseq[x];
+    float own = 1.f;
+    for (int i = k - 1; i >= 0; --i) own = own * t.sigma[q[i]];
+    t.own[h] = own;
 }
 
 __global__ void __launch_bounds__(kHeadThreads) k_head_topdown(DevTree<float> t, HeadArgs a) {
     grid_dependency_wait();
     if (a.bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
-    const int32_t stride = (int32_t)(gridDim.x * blockDim.x);
-    for (int l = 0; l < a.n; ++l) {
-        for (int32_t j = a.dlevel[l] + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); j < a.dlevel[l + 1]; j += stride)
-            td_node<float, true, true>(t, j);
-        for (int32_t w = a.wlevel[l] + (int32_t)blockIdx.x; w < a.wlevel[l + 1]; w += (int32_t)gridDim.x)
-            td_wide<float, true>(t, a.wide[w]);
-        cluster_barrier();
+    const int32_t tid = (int32_t)threadIdx.x, bs = (int32_t)blockDim.x;
+    if ((int32_t)blockIdx.x >= a.nblk) {                       // own reaches of the shallow infosets
+        const int32_t h = ((int32_t)blockIdx.x - a.nblk) * bs + tid;
+        if (h < a.nown) own_path(t, h);
+        return;
+    }
+    int32_t lo = a.d1 + (int32_t)blockIdx.x * a.per_block;
+    int32_t hi = min(lo + a.per_block, a.d1 + a.nroot);
+    {   // depth 0: the root's step for this block's children (all decision nodes: child d1 + a is action a)
+        const uint32_t w = t.qp[0];
+        const int32_t qb = qp_base(w);
+        const int p = qp_player(w);
+        const float r1 = t.reach1[0], r2 = t.reach2[0];
+        for (int32_t c = lo + tid; c < hi; c += bs) {
+            const float sv = t.sigma[qb + (c - a.d1)];
+            t.reach1[c] = p == 1 ? r1 : r1 * sv;
+            t.reach2[c] = p == 2 ? r2 : r2 * sv;
+        }
+    }
+    __syncthreads();
+    for (int l = 1; l <= a.n; ++l) {
+        for (int32_t j = lo + tid; j < hi; j += bs) td_node<float, false, false>(t, j);
+        __syncthreads();
+        lo = t.dfirst[lo];
+        hi = t.dfirst[hi];
     }
 }
 
 __global__ void __launch_bounds__(kHeadThreads) k_head_bottomup(DevTree<float> t, HeadArgs a) {
     grid_dependency_wait();
-    __shared__ float s_red[32];
-    const int32_t stride = (int32_t)(gridDim.x * blockDim.x);
-    for (int l = a.n - 1; l >= 0; --l) {
-        for (int32_t j = a.dlevel[l] + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); j < a.dlevel[l + 1]; j += stride)
-            bu_node<float, false, true>(t, j);
-        for (int32_t w = a.wlevel[l] + (int32_t)blockIdx.x; w < a.wlevel[l + 1]; w += (int32_t)gridDim.x)
-            bu_wide<float, true>(t, a.wide[w], s_red);   // every thread of the block takes part
-        cluster_barrier();
+    __shared__ int32_t lo_s[kHeadMaxDepths + 2], hi_s[kHeadMaxDepths + 2];
+    __shared__ int32_t last;
+    __shared__ float red[kHeadThreads / 32];
+    const int32_t tid = (int32_t)threadIdx.x, bs = (int32_t)blockDim.x;
+    if (tid == 0) {
+        int32_t lo = a.d1 + (int32_t)blockIdx.x * a.per_block;
+        int32_t hi = min(lo + a.per_block, a.d1 + a.nroot);
+        for (int l = 1; l <= a.n; ++l) {
+            lo_s[l] = lo;
+            hi_s[l] = hi;
+            lo = t.dfirst[lo];
+            hi = t.dfirst[hi];
+        }
     }
+    __syncthreads();
+    for (int l = a.n; l >= 1; --l) {
+        for (int32_t j = lo_s[l] + tid; j < hi_s[l]; j += bs) bu_node<float, false, false>(t, j);
+        __syncthreads();
+    }
+    // this block's depth-1 values are written; the last block to finish takes the root
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(a.done, 1) == a.nblk - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const uint32_t w = t.qp[0];
+    const int32_t qb = qp_base(w);
+    const int p = qp_player(w);
+    float part = 0.f;
+    for (int32_t c = tid; c < a.nroot; c += bs) part = madd(part, t.sigma[qb + c], __ldcg(t.u + a.d1 + c));
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    float ud = 0.f;
+    for (int i = 0; i < bs / 32; ++i) ud += red[i];
+    if (tid == 0) {
+        t.u[0] = ud;
+        *a.done = 0;                                           // ready for the next launch
+    }
+    if (!collects(t, p)) return;
+    const float wr = p == 1 ? t.reach1[0] : -t.reach2[0];
+    if (wr == 0.f) return;
+    for (int32_t c = tid; c < a.nroot; c += bs) atomicAdd(&t.inst[qb + c], wr * (__ldcg(t.u + a.d1 + c) - ud));
 }
 
 // ---- fused deepest depths, FP32 mode ----------------------------------------------------------------
