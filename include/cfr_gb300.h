@@ -105,7 +105,7 @@ typedef struct {
     int32_t head_levels;    /* FP32 mode: the shallowest depths of a tree whose root has decision children
                                only run in one launch per direction instead of one launch per depth, each
                                block walking the subtrees of a range of root children: the root and the
-                               next k depths (each at most 2^17 nodes, none with more than 32 actions).
+                               next k depths (each at most 2^19 nodes, none with more than 32 actions).
                                -1 (default) = as many as qualify, 0 = none, k >= 1 = at most k.
                                Ignored in FP64 mode. */
     int64_t batch_split_nodes;  /* cfr_batch_load: games of at least this many nodes run as one forest

@@ -28,8 +28,8 @@ constexpr int kBlock = 256;
 constexpr int kWideBlock = 1024;   // nodes and infosets with more than 32 actions: one block each
 constexpr int32_t kFuseAuto = 2;   // fused depths when cfr_config.fuse_levels < 0
 constexpr int32_t kStreamMinNodes = 32768;   // FP32 bottom-up depths this large use k_bottomup_stream
-constexpr int32_t kHeadMaxNodes = 1 << 17;   // FP32: leading depths at most this large run in the head launches
-constexpr int32_t kHeadMaxWide = 64;         // ... with at most this many nodes of more than 32 actions
+constexpr int32_t kHeadMaxNodes = 1 << 19;   // FP32: leading depths at most this large run in the head launches
+constexpr int32_t kHeadMaxSmem = 96 << 10;   // shared memory of a head block, at most
 
 inline int32_t nblocks(int64_t n) { return (int32_t)((n + kBlock - 1) / kBlock); }
 
@@ -101,7 +101,7 @@ struct cfr_solver {
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
     // FP32 mode: depths 0 .. head_n - 1 run in one launch per direction (k_head_*), head_per_block root
     // children per block; head_n == 0: per-depth launches
-    int32_t head_n = 0, head_per_block = 0;
+    int32_t head_n = 0, head_per_block = 0, head_cap = 0, head_na = 0;   // head_na: index into kStreamNA
     int32_t *head_done = nullptr;
     // depth-limited solving (cfr_set_range_program, cfr_set_leaves)
     int64_t rp_nseg = 0, nleaves = 0;
@@ -262,6 +262,7 @@ HeadArgs head_args(const cfr_solver *s, bool bump) {
     a.nroot = s->dlevel[2] - s->dlevel[1];
     a.per_block = s->head_per_block;
     a.nblk = (a.nroot + a.per_block - 1) / a.per_block;
+    a.cap = s->head_cap;
     a.nown = s->hlevel[(size_t)s->head_n];
     a.done = s->head_done;
     return a;
@@ -373,7 +374,10 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
     if constexpr (!det) {
         if (head > 0) {
             const HeadArgs ha = head_args(s, first);
-            CK(go(k_head_topdown, ha.nblk + nblocks(ha.nown), kHeadThreads, 0, st, t, ha));
+            auto k = s->head_na == 0 ? k_head_topdown<kStreamNA[0]>
+                   : s->head_na == 1 ? k_head_topdown<kStreamNA[1]> : k_head_topdown<kStreamNA[2]>;
+            CK(go(k, ha.nblk + (ha.nown + kHeadThreads - 1) / kHeadThreads, kHeadThreads, head_smem_topdown(ha.cap), st,
+                  t, ha));
         }
     }
     // the other own reaches, depth by depth; in the graph on a branch beside the node passes that forks
@@ -462,7 +466,9 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
     if constexpr (!det) {
         if (head > 0) {
             const HeadArgs ha = head_args(s, false);
-            CK(go(k_head_bottomup, ha.nblk, kHeadThreads, 0, st, t, ha));
+            auto k = s->head_na == 0 ? k_head_bottomup<kStreamNA[0]>
+                   : s->head_na == 1 ? k_head_bottomup<kStreamNA[1]> : k_head_bottomup<kStreamNA[2]>;
+            CK(go(k, ha.nblk, kHeadThreads, head_smem_bottomup(ha.cap), st, t, ha));
         }
     }
     if (branch) {
@@ -582,10 +588,11 @@ int32_t launches_per_pass(const cfr_solver *s) {
 
 // FP32 mode: the leading depths run by k_head_topdown / k_head_bottomup: depths 0 .. n (head_n = n + 1)
 // for a single root whose children are all decision nodes, n >= 1 the deepest depth below the fused ones
-// such that every depth 1 .. n holds at most kHeadMaxNodes nodes and no node of more than 32 actions
-// (at most cfg.head_levels depths below the root when that is positive; 0: none).  About two blocks per
-// SM walk the root children's subtrees.
-cfr_status plan_head(cfr_solver *s, int sms) {
+// such that every depth 1 .. n holds at most kHeadMaxNodes nodes and no node of more than 32 actions,
+// and the largest block's nodes of depths 1 .. n fit kHeadMaxSmem bytes of shared memory (at most
+// cfg.head_levels depths below the root when that is positive; 0: none).  About two blocks per SM walk
+// the root children's subtrees.
+cfr_status plan_head(cfr_solver *s, const Layout &Lo, int sms) {
     s->head_n = 0;
     if (s->cfg.head_levels == 0 || s->L < 2 || s->dlevel[1] != 1) return CFR_OK;
     const int32_t nroot = s->dlevel[2] - s->dlevel[1];
@@ -596,14 +603,37 @@ cfr_status plan_head(cfr_solver *s, int sms) {
     while (n + 1 <= cap && n + 1 < r && n + 1 < s->L && s->dlevel[(size_t)n + 2] - s->dlevel[(size_t)n + 1] <= kHeadMaxNodes &&
            s->wlevel[(size_t)n + 2] == s->wlevel[(size_t)n + 1])
         ++n;
+    const int32_t nblk = std::min(nroot, kHeadBlocksPerSM * std::max(sms, 1));
+    const int32_t per = (nroot + nblk - 1) / nblk;
+    // the largest block's nodes of depths 1 .. n, as head_ranges cuts them; fewer depths until they fit
+    int32_t most = 0;
+    for (; n >= 1; --n) {
+        most = 0;
+        for (int32_t lo1 = s->dlevel[1]; lo1 < s->dlevel[1] + nroot; lo1 += per) {
+            int32_t lo = lo1, hi = std::min(lo1 + per, s->dlevel[1] + nroot), tot = 0;
+            for (int32_t l = 1; l <= n; ++l) {
+                tot += hi - lo;
+                lo = Lo.dfirst[(size_t)lo];
+                hi = Lo.dfirst[(size_t)hi];
+            }
+            most = std::max(most, tot);
+        }
+        if (head_smem_bottomup(most) <= (size_t)kHeadMaxSmem && head_smem_topdown(most) <= (size_t)kHeadMaxSmem) break;
+    }
     if (n < 1) return CFR_OK;
+    for (const void *k : {(const void *)k_head_topdown<kStreamNA[0]>, (const void *)k_head_bottomup<kStreamNA[0]>,
+                          (const void *)k_head_topdown<kStreamNA[1]>, (const void *)k_head_bottomup<kStreamNA[1]>,
+                          (const void *)k_head_topdown<kStreamNA[2]>, (const void *)k_head_bottomup<kStreamNA[2]>})
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeadMaxSmem));
     if (!s->head_done) {
         TRY(alloc_n(s, &s->head_done, 1));
         CK(cudaMemsetAsync(s->head_done, 0, sizeof(int32_t), s->stream));
     }
     s->head_n = n + 1;
-    const int32_t nblk = std::min(nroot, 2 * std::max(sms, 1));
-    s->head_per_block = (nroot + nblk - 1) / nblk;
+    s->head_per_block = per;
+    s->head_cap = std::max(most, 1);
+    s->head_na = 0;
+    for (int32_t l = 1; l <= n; ++l) s->head_na = std::max(s->head_na, s->level_na[(size_t)l]);
     return CFR_OK;
 }
 
@@ -808,10 +838,20 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
     TRY(alloc_n(s, &s->wide, (int64_t)Lo.wide.size()));
     TRY(upload(s, s->wide, Lo.wide));
     if (!fp64) {
+        // per depth, the smallest unrolled action count covering its largest node of at most 32 actions
+        s->level_na.assign((size_t)s->L, 2);
+        for (int32_t l = 0; l < s->L; ++l) {
+            int32_t maxa = 0;
+            for (int32_t j = s->dlevel[l]; j < s->dlevel[l + 1]; ++j) {
+                if ((Lo.qp[(size_t)j] >> 29) & 1u) continue;
+                maxa = std::max<int32_t>(maxa, (Lo.dfirst[(size_t)j + 1] - Lo.dfirst[j]) + __builtin_popcount(Lo.kmask[j]));
+            }
+            s->level_na[(size_t)l] = maxa <= kStreamNA[0] ? 0 : maxa <= kStreamNA[1] ? 1 : 2;
+        }
         TRY(plan_fusion(s, Lo));
         int sms = 0;
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-        TRY(plan_head(s, sms));
+        TRY(plan_head(s, Lo, sms));
         {
             std::vector<int32_t> wh;
             for (int32_t h = 0; h < s->Hp; ++h) {
@@ -864,16 +904,6 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
         TRY(setup_stream_na<kStreamNA[0]>(s, 0, sms));
         TRY(setup_stream_na<kStreamNA[1]>(s, 1, sms));
         TRY(setup_stream_na<kStreamNA[2]>(s, 2, sms));
-        // per depth, the smallest unrolled action count covering its largest node of at most 32 actions
-        s->level_na.assign((size_t)s->L, 2);
-        for (int32_t l = 0; l < s->L; ++l) {
-            int32_t maxa = 0;
-            for (int32_t j = s->dlevel[l]; j < s->dlevel[l + 1]; ++j) {
-                if ((Lo.qp[(size_t)j] >> 29) & 1u) continue;
-                maxa = std::max<int32_t>(maxa, (Lo.dfirst[(size_t)j + 1] - Lo.dfirst[j]) + __builtin_popcount(Lo.kmask[j]));
-            }
-            s->level_na[(size_t)l] = maxa <= kStreamNA[0] ? 0 : maxa <= kStreamNA[1] ? 1 : 2;
-        }
     }
     // The root's counterfactual reaches are 1 (Eq. 2, v = v_0) and never change (every root's, for a
     // forest of independent games).

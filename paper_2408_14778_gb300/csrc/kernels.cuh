@@ -534,14 +534,20 @@ __global__ void __launch_bounds__(1024) k_bottomup_wide(DevTree<real> t, const i
 // subtrees of consecutive root children are consecutive at every depth (breadth-first ids), and no
 // node's step needs another subtree's, so k_head_topdown gives each block a range of root children
 // and walks their subtrees down depth by depth with block barriers only; k_head_bottomup walks them
-// back up, and the block that finishes last (a global counter, with fences) takes the root.  Both run
-// the per-node steps td_node / bu_node.  The top-down launch also computes the own reaches (Eq. 4) of
-// the infosets first seen at depths 0 .. n, each as the product of the strategy entries of its
-// player's own sequence, multiplied from the first action on - the same products in the same order
-// as k_own's depth-by-depth recursion.  The host uses these kernels for a single root whose children
-// are all decision nodes, with no node of more than 32 actions below the root in depths 1 .. n.
+// back up, and the block that finishes last (a global counter, with fences) takes the root.  A block
+// first stages the node fields of all its depths in shared memory (one round of independent loads)
+// and keeps the reaches and values of its nodes there, so a depth costs one round of strategy and
+// utility loads.  The arithmetic per node and its order are td_node's and bu_node's.  The top-down
+// launch also computes the own reaches (Eq. 4) of the infosets first seen at depths 0 .. n, each as
+// the product of the strategy entries of its player's own sequence, multiplied from the first action
+// on - the same products in the same order as k_own's depth-by-depth recursion.  The host uses these
+// kernels for a single root whose children are all decision nodes, with no node of more than 32
+// actions in depths 1 .. n, and sizes the shared memory for the largest block (HeadArgs::cap nodes).
+// NA: the unrolled action count (at least the largest of depths 1 .. n for full unrolling; nodes with more
+// actions take the general loop).
 constexpr int kHeadMaxDepths = 16;
-constexpr int kHeadThreads = 256;
+constexpr int kHeadThreads = 512;
+constexpr int kHeadBlocksPerSM = 3;
 
 struct HeadArgs {
     int32_t n;                 // the top-down steps of depths 0 .. n (reaches of depths 1 .. n + 1) and the
@@ -549,7 +555,8 @@ struct HeadArgs {
     int32_t bump;              // count the iteration (first pass of an iteration)
     int32_t d1, nroot;         // the root's children: nodes d1 .. d1 + nroot - 1 (depth 1)
     int32_t per_block, nblk;   // root children per block; blocks walking subtrees
-    int32_t nown;              // infosets 0 .. nown - 1 are first seen at depths 0 .. n
+    int32_t cap;               // nodes of depths 1 .. n in a block, at most (shared-memory arrays)
+    int32_t nown;              // infosets 0 .. nown - 1 are first seen at depths 0 .. n (own reaches)
     int32_t *done;             // k_head_bottomup: blocks that have finished (reset by the last)
 };
 
@@ -565,7 +572,38 @@ __device__ __forceinline__ void own_path(const DevTree<float> &t, int32_t h) {
     t.own[h] = own;
 }
 
-__global__ void __launch_bounds__(kHeadThreads) k_head_topdown(DevTree<float> t, HeadArgs a) {
+// The block's node ranges per depth: nodes lo[l] .. hi[l] - 1 of depth l (l = 1 .. n + 1), at offset
+// off[l] of the shared-memory arrays (l <= n); run by one thread.
+__device__ __forceinline__ void head_ranges(const DevTree<float> &t, const HeadArgs &a, int32_t *lo, int32_t *hi,
+                                            int32_t *off) {
+    lo[1] = a.d1 + (int32_t)blockIdx.x * a.per_block;
+    hi[1] = min(lo[1] + a.per_block, a.d1 + a.nroot);
+    off[1] = 0;
+    for (int l = 1; l <= a.n; ++l) {
+        lo[l + 1] = t.dfirst[lo[l]];
+        hi[l + 1] = t.dfirst[hi[l]];
+        off[l + 1] = off[l] + (hi[l] - lo[l]);
+    }
+}
+
+// Stages the fields of the block's nodes of depths 1 .. n: local index off[l] + (j - lo[l]).
+__device__ __forceinline__ void head_stage(const DevTree<float> &t, const HeadArgs &a, const int32_t *lo,
+                                           const int32_t *off, uint32_t *qp_s, uint32_t *km_s, int32_t *df_s,
+                                           int32_t *tf_s) {
+    const int32_t total = off[a.n + 1];
+    for (int32_t i = (int32_t)threadIdx.x; i < total; i += (int32_t)blockDim.x) {
+        int l = 1;
+        while (l < a.n && i >= off[l + 1]) ++l;
+        const int32_t j = lo[l] + (i - off[l]);
+        qp_s[i] = t.qp[j];
+        km_s[i] = t.kmask[j];
+        df_s[i] = t.dfirst[j];
+        if (tf_s) tf_s[i] = t.tfirst[j];
+    }
+}
+
+template <int NA>
+__global__ void __launch_bounds__(kHeadThreads, kHeadBlocksPerSM) k_head_topdown(DevTree<float> t, HeadArgs a) {
     grid_dependency_wait();
     if (a.bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
     const int32_t tid = (int32_t)threadIdx.x, bs = (int32_t)blockDim.x;
@@ -574,47 +612,144 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_topdown(DevTree<float> t,
         if (h < a.nown) own_path(t, h);
         return;
     }
-    int32_t lo = a.d1 + (int32_t)blockIdx.x * a.per_block;
-    int32_t hi = min(lo + a.per_block, a.d1 + a.nroot);
+    extern __shared__ __align__(16) unsigned char head_smem[];
+    uint32_t *qp_s = reinterpret_cast<uint32_t *>(head_smem);
+    uint32_t *km_s = qp_s + a.cap;
+    int32_t *df_s = reinterpret_cast<int32_t *>(km_s + a.cap);
+    float *r1_s = reinterpret_cast<float *>(df_s + a.cap);
+    float *r2_s = r1_s + a.cap;
+    __shared__ int32_t lo[kHeadMaxDepths + 2], hi[kHeadMaxDepths + 2], off[kHeadMaxDepths + 2];
+    if (tid == 0) head_ranges(t, a, lo, hi, off);
+    __syncthreads();
+    head_stage(t, a, lo, off, qp_s, km_s, df_s, nullptr);
     {   // depth 0: the root's step for this block's children (all decision nodes: child d1 + a is action a)
         const uint32_t w = t.qp[0];
         const int32_t qb = qp_base(w);
         const int p = qp_player(w);
         const float r1 = t.reach1[0], r2 = t.reach2[0];
-        for (int32_t c = lo + tid; c < hi; c += bs) {
+        for (int32_t c = lo[1] + tid; c < hi[1]; c += bs) {
             const float sv = t.sigma[qb + (c - a.d1)];
-            t.reach1[c] = p == 1 ? r1 : r1 * sv;
-            t.reach2[c] = p == 2 ? r2 : r2 * sv;
+            r1_s[c - lo[1]] = p == 1 ? r1 : r1 * sv;
+            r2_s[c - lo[1]] = p == 2 ? r2 : r2 * sv;
         }
     }
     __syncthreads();
     for (int l = 1; l <= a.n; ++l) {
-        for (int32_t j = lo + tid; j < hi; j += bs) td_node<float, false, false>(t, j);
+        const int32_t cnt = hi[l] - lo[l];
+        const bool deep = l == a.n;                             // children outside the block's arrays
+        for (int32_t i = tid; i < cnt; i += bs) {
+            const int32_t k = off[l] + i, j = lo[l] + i;
+            const float r1 = r1_s[k], r2 = r2_s[k];
+            t.reach1[j] = r1;
+            t.reach2[j] = r2;
+            const uint32_t w = qp_s[k], m = km_s[k];
+            const int32_t c0 = df_s[k], c1 = i + 1 < cnt ? df_s[k + 1] : hi[l + 1];
+            const int32_t nd = c1 - c0;
+            if (nd == 0) continue;
+            const int32_t qb = qp_base(w);
+            const int p = qp_player(w);
+            const int na = nd + __popc(m);
+            float *w1 = deep ? t.reach1 + c0 : r1_s + off[l + 1] + (c0 - lo[l + 1]);
+            float *w2 = deep ? t.reach2 + c0 : r2_s + off[l + 1] + (c0 - lo[l + 1]);
+            if (na <= NA) {
+                float s[NA];
+#pragma unroll
+                for (int b = 0; b < NA; ++b) s[b] = b < na ? t.sigma[qb + b] : 0.f;
+                int y = 0;
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    if (b < na && !((m >> b) & 1u)) {
+                        w1[y] = p == 1 ? r1 : r1 * s[b];
+                        w2[y] = p == 2 ? r2 : r2 * s[b];
+                        ++y;
+                    }
+                }
+            } else {
+                int y = 0;
+                for (int b = 0; b < na; ++b) {
+                    if ((m >> b) & 1u) continue;
+                    const float sv = t.sigma[qb + b];
+                    w1[y] = p == 1 ? r1 : r1 * sv;
+                    w2[y] = p == 2 ? r2 : r2 * sv;
+                    ++y;
+                }
+            }
+        }
         __syncthreads();
-        lo = t.dfirst[lo];
-        hi = t.dfirst[hi];
     }
 }
 
-__global__ void __launch_bounds__(kHeadThreads) k_head_bottomup(DevTree<float> t, HeadArgs a) {
+template <int NA>
+__global__ void __launch_bounds__(kHeadThreads, kHeadBlocksPerSM) k_head_bottomup(DevTree<float> t, HeadArgs a) {
     grid_dependency_wait();
-    __shared__ int32_t lo_s[kHeadMaxDepths + 2], hi_s[kHeadMaxDepths + 2];
+    extern __shared__ __align__(16) unsigned char head_smem[];
+    uint32_t *qp_s = reinterpret_cast<uint32_t *>(head_smem);
+    uint32_t *km_s = qp_s + a.cap;
+    int32_t *df_s = reinterpret_cast<int32_t *>(km_s + a.cap);
+    int32_t *tf_s = df_s + a.cap;
+    float *u_s = reinterpret_cast<float *>(tf_s + a.cap);
+    __shared__ int32_t lo[kHeadMaxDepths + 2], hi[kHeadMaxDepths + 2], off[kHeadMaxDepths + 2];
     __shared__ int32_t last;
     __shared__ float red[kHeadThreads / 32];
     const int32_t tid = (int32_t)threadIdx.x, bs = (int32_t)blockDim.x;
-    if (tid == 0) {
-        int32_t lo = a.d1 + (int32_t)blockIdx.x * a.per_block;
-        int32_t hi = min(lo + a.per_block, a.d1 + a.nroot);
-        for (int l = 1; l <= a.n; ++l) {
-            lo_s[l] = lo;
-            hi_s[l] = hi;
-            lo = t.dfirst[lo];
-            hi = t.dfirst[hi];
-        }
-    }
+    if (tid == 0) head_ranges(t, a, lo, hi, off);
+    __syncthreads();
+    head_stage(t, a, lo, off, qp_s, km_s, df_s, tf_s);
     __syncthreads();
     for (int l = a.n; l >= 1; --l) {
-        for (int32_t j = lo_s[l] + tid; j < hi_s[l]; j += bs) bu_node<float, false, false>(t, j);
+        const int32_t cnt = hi[l] - lo[l];
+        const bool deep = l == a.n;                             // children's values in global memory
+        for (int32_t i = tid; i < cnt; i += bs) {
+            const int32_t k = off[l] + i, j = lo[l] + i;
+            const uint32_t w = qp_s[k], m = km_s[k];
+            const int32_t c0 = df_s[k], c1 = i + 1 < cnt ? df_s[k + 1] : hi[l + 1], t0 = tf_s[k];
+            const float rr1 = t.reach1[j], rr2 = t.reach2[j];
+            const int32_t qb = qp_base(w);
+            const int p = qp_player(w);
+            const int na = (c1 - c0) + __popc(m);
+            const float *dv = deep ? t.u + c0 : u_s + off[l + 1] + (c0 - lo[l + 1]);
+            float ud = 0.f;
+            const float wr = !collects(t, p) ? 0.f : p == 1 ? rr1 : -rr2;   // u_2 = -u_1
+            if (na <= NA) {
+                float v[NA], s[NA];
+                int kt = 0, kd = 0;
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    if (b < na) {
+                        const bool term = (m >> b) & 1u;
+                        v[b] = term ? t.util[t0 + kt] : dv[kd];
+                        kt += term;
+                        kd += !term;
+                        s[b] = t.sigma[qb + b];
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < NA; ++b)
+                    if (b < na) ud = madd(ud, s[b], v[b]);
+                u_s[k] = ud;
+                t.u[j] = ud;
+                if (wr != 0.f) {
+#pragma unroll
+                    for (int b = 0; b < NA; ++b)
+                        if (b < na) atomicAdd(&t.inst[qb + b], wr * (v[b] - ud));
+                }
+            } else {
+                int kt = 0, kd = 0;
+                for (int b = 0; b < na; ++b) {
+                    const float v = ((m >> b) & 1u) ? t.util[t0 + kt++] : dv[kd++];
+                    ud = madd(ud, t.sigma[qb + b], v);
+                }
+                u_s[k] = ud;
+                t.u[j] = ud;
+                if (wr != 0.f) {
+                    kt = kd = 0;
+                    for (int b = 0; b < na; ++b) {
+                        const float v = ((m >> b) & 1u) ? t.util[t0 + kt++] : dv[kd++];
+                        atomicAdd(&t.inst[qb + b], wr * (v - ud));
+                    }
+                }
+            }
+        }
         __syncthreads();
     }
     // this block's depth-1 values are written; the last block to finish takes the root
@@ -644,6 +779,10 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_bottomup(DevTree<float> t
     if (wr == 0.f) return;
     for (int32_t c = tid; c < a.nroot; c += bs) atomicAdd(&t.inst[qb + c], wr * (__ldcg(t.u + a.d1 + c) - ud));
 }
+
+// Shared memory of the head kernels for blocks of at most cap nodes.
+inline size_t head_smem_topdown(int32_t cap) { return (size_t)cap * 20; }
+inline size_t head_smem_bottomup(int32_t cap) { return (size_t)cap * 20; }
 
 // ---- fused deepest depths, FP32 mode ----------------------------------------------------------------
 // The depths r .. L-1, which hold most of the nodes, in one launch.  Block b takes a tile of
