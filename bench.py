@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--only", choices=["network-gemm"], default=None,
+                    help="run one measurement alone (profiling): the value network's matrix products")
     ap.add_argument("--workload", default="holdem169_depth12")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--nodes", type=int, default=None,
@@ -278,6 +280,38 @@ def measured_bf16_peak():
     return 1900.0, "fallback (1.9 PFLOP/s bf16 burst, earlier GB300 measurement)"
 
 
+def network_gemm_measurement(net, local: int, batch: int = 4096, reps: int = 5) -> dict:
+    """The value network's matrix products (402 -> 3 x 1024 ReLU -> 338) at a batch of 4096: forward and
+    backward time of the last of reps passes (CUDA events around the products) against the bf16 peak."""
+    import torch
+
+    import paper_2408_14778_gb300 as cfr
+
+    xb = torch.randn(batch, 402, device=f"cuda:{local}")
+    tb = torch.randn(batch, 338, device=f"cuda:{local}")
+    for _ in range(reps):
+        cfr.cfr_mlp_forward(net, xb)
+        cfr.cfr_mlp_backward(net, xb, tb)
+    st = cfr.cfr_mlp_gemm_stats(net)
+    peak, src = measured_bf16_peak()
+    fwd, bwd = st["fwd_flops"] / st["fwd_us"] / 1e6, st["bwd_flops"] / st["bwd_us"] / 1e6
+    return {"batch": batch, "forward_tflops": fwd, "backward_tflops": bwd, "forward_us": st["fwd_us"],
+            "backward_us": st["bwd_us"], "peak_tflops": peak, "peak_source": src, "forward_frac": fwd / peak,
+            "backward_frac": bwd / peak,
+            "instruction": "forward: tcgen05.mma kind::f16 (bf16, fp32 accumulator in tensor memory, TMA operands); "
+                           "backward: mma.sync m16n8k16 bf16"}
+
+
+def run_network_gemm_only(args, local: int):
+    """--only network-gemm: the value network's products alone (for profiling), one JSON line."""
+    import paper_2408_14778_gb300 as cfr
+    from paper_2408_14778_gb300 import depth_limited as dl
+
+    cfr.build()
+    net = dl.make_network(seed=args.seed, device=local)
+    print(json.dumps({"network_gemm": network_gemm_measurement(net, local, reps=max(1, args.steps))}), flush=True)
+
+
 def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
     """Depth-limited CFR+ with the learned leaf network on the 13-rank fold/showdown game (2e6 nodes) cut
     at game depth 6: training samples from full-depth GPU CFR+ solves of the cut subgames under random
@@ -342,19 +376,7 @@ def learned_leaf_measurement(args, local: int, ttt: dict | None) -> dict:
                        "samples_trained": int(Xt.shape[0]), "samples_held_out": int(nh),
                        "seconds": time.perf_counter() - t0, "mse_first": hist[0], "mse_last": hist[-1],
                        "mse_held_out": held, "note": "mean squared error of values divided by the payoff bound"}
-    # the network's matrix products at a batch of 4096
-    xb = torch.randn(4096, 402, device=f"cuda:{local}")
-    tb = torch.randn(4096, 338, device=f"cuda:{local}")
-    for _ in range(5):
-        cfr.cfr_mlp_forward(net, xb)
-        cfr.cfr_mlp_backward(net, xb, tb)
-    st = cfr.cfr_mlp_gemm_stats(net)
-    peak, src = measured_bf16_peak()
-    fwd, bwd = st["fwd_flops"] / st["fwd_us"] / 1e6, st["bwd_flops"] / st["bwd_us"] / 1e6
-    out["network_gemm"] = {"batch": 4096, "forward_tflops": fwd, "backward_tflops": bwd, "peak_tflops": peak,
-                           "peak_source": src, "forward_frac": fwd / peak, "backward_frac": bwd / peak,
-                           "instruction": "forward: tcgen05.mma kind::f16 (bf16, fp32 accumulator in tensor memory, "
-                                          "TMA operands); backward: mma.sync m16n8k16 bf16"}
+    out["network_gemm"] = network_gemm_measurement(net, local)
     untrained = dl.make_network(seed=args.seed + 1, device=local)
     for name, model, ranges in (("trained", net, cfr.CFR_AVERAGE_STRATEGY),
                                 ("trained_current_ranges", net, cfr.CFR_CURRENT_STRATEGY),
@@ -783,7 +805,10 @@ def run_ours(args, world, rank, local):
 def main():
     args = parse()
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.only == "network-gemm":
+        if rank == 0:
+            run_network_gemm_only(args, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

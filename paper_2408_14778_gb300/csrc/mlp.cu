@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -90,21 +91,26 @@ __device__ __forceinline__ void load_tile(uint32_t s, const __nv_bfloat16 *G, in
     }
 }
 
-enum Epi { kEpiHidden = 0, kEpiOut = 1, kEpiStore = 2, kEpiMask = 3 };
+enum Epi { kEpiHidden = 0, kEpiOut = 1, kEpiStore = 2, kEpiMask = 3, kEpiAdd = 4 };
 
 // C = A B over M x N (multiples of 128), reduction K (multiple of 32).  AKM / BKM: whether A / B is
 // stored K-major.  Epilogues: kEpiHidden bf16(ReLU(acc + bias[n])); kEpiOut acc + bias[n] (FP32);
-// kEpiStore acc (FP32); kEpiMask bf16(acc if mask[m][n] > 0 else 0).
+// kEpiStore acc (FP32); kEpiMask bf16(acc if mask[m][n] > 0 else 0); kEpiAdd C += acc (FP32 atomics).
+// Split reduction: block z of gridDim.z takes the reduction steps [z ksteps, (z + 1) ksteps) of kBK
+// (ksteps <= 0: all of them), its partial sum added with kEpiAdd.
 template <bool AKM, bool BKM, int EPI>
 __global__ void __launch_bounds__(kThreads) k_gemm(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B,
                                                    int64_t ldb, void *C, int64_t ldc, int32_t K, const float *bias,
-                                                   const __nv_bfloat16 *mask) {
+                                                   const __nv_bfloat16 *mask, int32_t ksteps) {
     __shared__ __align__(128) unsigned char smem[kStages * 2 * kTileBytes];
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
     const int64_t m0 = (int64_t)blockIdx.y * kBM, n0 = (int64_t)blockIdx.x * kBN;
-    const int nk = K / kBK;
+    const int kall = K / kBK;
+    const int kz = ksteps > 0 ? (int)blockIdx.z * ksteps : 0;
+    const int nk = ksteps > 0 ? min(ksteps, kall - kz) : kall;
+    const int64_t koff = (int64_t)kz * kBK;
     float acc[4][4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -118,8 +124,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const __nv_bfloat16 *A, int64
 #pragma unroll
     for (int st = 0; st < kStages - 1; ++st) {
         if (st < nk) {
-            load_tile<AKM>(sa(st), A, lda, m0, (int64_t)st * kBK);
-            load_tile<BKM>(sb(st), B, ldb, n0, (int64_t)st * kBK);
+            load_tile<AKM>(sa(st), A, lda, m0, koff + (int64_t)st * kBK);
+            load_tile<BKM>(sb(st), B, ldb, n0, koff + (int64_t)st * kBK);
         }
         cp_commit();
     }
@@ -129,8 +135,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const __nv_bfloat16 *A, int64
         {   // prefetch kStages - 1 tiles ahead into the buffer computed on in the previous step
             const int kn = kt + kStages - 1;
             if (kn < nk) {
-                load_tile<AKM>(sa(kn % kStages), A, lda, m0, (int64_t)kn * kBK);
-                load_tile<BKM>(sb(kn % kStages), B, ldb, n0, (int64_t)kn * kBK);
+                load_tile<AKM>(sa(kn % kStages), A, lda, m0, koff + (int64_t)kn * kBK);
+                load_tile<BKM>(sb(kn % kStages), B, ldb, n0, koff + (int64_t)kn * kBK);
             }
             cp_commit();
         }
@@ -184,11 +190,15 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const __nv_bfloat16 *A, int64
                     if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
                     if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
                 }
-                if (EPI == kEpiHidden || EPI == kEpiMask)
+                if (EPI == kEpiHidden || EPI == kEpiMask) {
                     *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + m * ldc + n) =
                         __floats2bfloat162_rn(v0, v1);
-                else
+                } else if (EPI == kEpiAdd) {
+                    atomicAdd(static_cast<float *>(C) + m * ldc + n, v0);
+                    atomicAdd(static_cast<float *>(C) + m * ldc + n + 1, v1);
+                } else {
                     *reinterpret_cast<float2 *>(static_cast<float *>(C) + m * ldc + n) = make_float2(v0, v1);
+                }
             }
 }
 
@@ -482,9 +492,18 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
     __syncwarp();
     const bool done = tc_mbar_wait(accb, 0);
     if (!done && lane == 0) atomicExch(err, 1);
-    if (__all_sync(0xffffffffu, done)) {
+    // Epilogue: every product has completed (so the stages' shared memory is free), and the tile goes
+    // through it: each thread writes its row (the accumulator's lane) in 16-column pieces to a padded
+    // row-major tile, then the block stores whole rows to global memory with coalesced 16-byte stores.
+    using OutT = typename std::conditional<EPI == kEpiHidden, __nv_bfloat16, float>::type;
+    constexpr int kPadE = 16 / (int)sizeof(OutT);                       // one 16-byte chunk per row
+    constexpr int kLd = BN + kPadE;                                      // row stride in elements
+    static_assert(128 * kLd * (int)sizeof(OutT) <= S::kStages * S::kStage, "output tile exceeds the stages");
+    OutT *tile = reinterpret_cast<OutT *>(raw + (base - raw_s));
+    const bool all_done = __syncthreads_and(done);
+    if (all_done) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int64_t m = m0 + warp * 32 + lane;
+        const int row = warp * 32 + lane;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
@@ -497,18 +516,31 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
                          : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int64_t n = n0 + c0;
+            uint32_t o[16];                                              // the 16 results, packed
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
                 float v0 = __uint_as_float(r[j]) + bias[n + j], v1 = __uint_as_float(r[j + 1]) + bias[n + j + 1];
-                if (EPI == kEpiHidden) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + m * ldc + n + j) =
-                        __floats2bfloat162_rn(v0, v1);
+                if constexpr (EPI == kEpiHidden) {
+                    const __nv_bfloat162 b = __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+                    o[j / 2] = *reinterpret_cast<const uint32_t *>(&b);
                 } else {
-                    *reinterpret_cast<float2 *>(static_cast<float *>(C) + m * ldc + n + j) = make_float2(v0, v1);
+                    o[j] = __float_as_uint(v0);
+                    o[j + 1] = __float_as_uint(v1);
                 }
             }
+            int4 *dst = reinterpret_cast<int4 *>(tile + row * kLd + c0);
+            constexpr int kVec = EPI == kEpiHidden ? 2 : 4;                // 16-byte pieces of 16 results
+#pragma unroll
+            for (int q = 0; q < kVec; ++q) dst[q] = make_int4((int)o[4 * q], (int)o[4 * q + 1], (int)o[4 * q + 2], (int)o[4 * q + 3]);
+        }
+    }
+    __syncthreads();
+    if (all_done) {
+        constexpr int kChunks = BN * (int)sizeof(OutT) / 16;             // 16-byte pieces of a row
+        for (int i = tid; i < 128 * kChunks; i += kTmThreads) {
+            const int row = i / kChunks, ch = i % kChunks;
+            const int4 v = *reinterpret_cast<const int4 *>(tile + row * kLd + ch * (16 / (int)sizeof(OutT)));
+            *reinterpret_cast<int4 *>(static_cast<OutT *>(C) + (m0 + row) * ldc + n0 + ch * (16 / (int)sizeof(OutT))) = v;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -604,7 +636,7 @@ struct cfr_mlp {
     std::vector<int64_t> pdims;      // padded widths
     std::vector<int64_t> w_off, b_off;   // per layer: offsets of W [pdims[l+1]][pdims[l]] and b in the flat arrays
     int64_t P = 0, num_params = 0;   // flat padded size, real parameter count
-    int device = 0;
+    int device = 0, sms = 152;
     cudaStream_t stream = nullptr;
     float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
     __nv_bfloat16 *pb = nullptr;
@@ -700,13 +732,35 @@ cudaError_t gemm_tc(cudaStream_t st, int *err, const __nv_bfloat16 *A, int64_t l
     return cudaGetLastError();
 }
 
-// C = A B on the network's tensor path (tcgen05 or mma.sync); shapes are multiples of 128.
+// C = A B on the network's tensor path (tcgen05 or mma.sync); shapes are multiples of 128.  On the
+// warp-level path a product with fewer output tiles than two per SM and a long reduction (kEpiStore:
+// the weight gradients, reduced over the batch) splits its reduction over more blocks, which add their
+// partial sums into C (zeroed first) with FP32 atomics.
 template <bool AKM, bool BKM, int EPI>
 cudaError_t gemm(const cfr_mlp *m, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, void *C,
                  int64_t ldc, int64_t M, int64_t N, int64_t K, const float *bias, const __nv_bfloat16 *mask) {
     if (m->path == 1) return gemm_tc<AKM, BKM, EPI>(m->stream, m->d_err, A, lda, B, ldb, C, ldc, M, N, K, bias, mask);
+    const int64_t tiles = (N / kBN) * (M / kBM), steps = K / kBK;
+    int64_t split = 1;
+    if constexpr (EPI == kEpiStore) split = std::min<int64_t>((2 * m->sms + tiles - 1) / tiles, steps / 8);
+    if (split > 1) {
+        const int32_t ksteps = (int32_t)((steps + split - 1) / split);
+        split = (steps + ksteps - 1) / ksteps;
+        for (int64_t r = 0; r < M; ++r) {   // C's rows are ldc apart: zero them (one call when contiguous)
+            if (ldc == N) {
+                const cudaError_t e = cudaMemsetAsync(C, 0, sizeof(float) * (size_t)(M * N), m->stream);
+                if (e != cudaSuccess) return e;
+                break;
+            }
+            const cudaError_t e = cudaMemsetAsync(static_cast<float *>(C) + r * ldc, 0, sizeof(float) * (size_t)N, m->stream);
+            if (e != cudaSuccess) return e;
+        }
+        const dim3 grid((unsigned)(N / kBN), (unsigned)(M / kBM), (unsigned)split);
+        k_gemm<AKM, BKM, kEpiAdd><<<grid, kThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask, ksteps);
+        return cudaGetLastError();
+    }
     const dim3 grid((unsigned)(N / kBN), (unsigned)(M / kBM));
-    k_gemm<AKM, BKM, EPI><<<grid, kThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask);
+    k_gemm<AKM, BKM, EPI><<<grid, kThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask, 0);
     return cudaGetLastError();
 }
 
@@ -745,11 +799,21 @@ template <int EPI>
 cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bfloat16 *W, void *C, int64_t M, int64_t N,
                          int64_t K, const float *bias) {
     CUtensorMap ta, tb;
-    // 256-wide tiles where they still give two blocks per SM, else 128-wide
-    const int bn = (N % 256 == 0 && (N / 256) * (M / 128) >= 2 * 152) ? 256 : 128;
+    // 256-wide tiles where they still give two blocks per SM, else 128-wide (the FP32 output tile of the
+    // last layer takes the 128-wide shape, whose stages can hold it for the epilogue)
+    const int bn = (EPI == kEpiHidden && N % 256 == 0 && (N / 256) * (M / 128) >= 2 * 152) ? 256 : 128;
     if (!encode_operand(&ta, A, M, K, 128) || !encode_operand(&tb, W, N, K, bn)) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)(N / bn), (unsigned)(M / 128));
-    if (bn == 256) {
+    if constexpr (EPI != kEpiHidden) {
+        static bool attr = false;
+        if (!attr) {
+            const cudaError_t e = cudaFuncSetAttribute(k_gemm_tma<128, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       TmShape<128>::kSmem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_gemm_tma<128, EPI><<<grid, kTmThreads, TmShape<128>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, m->d_err);
+    } else if (bn == 256) {
         static bool attr = false;
         if (!attr) {
             const cudaError_t e = cudaFuncSetAttribute(k_gemm_tma<256, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -818,6 +882,10 @@ cfr_status cfr_mlp_create(const int32_t *dims, int32_t num_layers, int32_t devic
     if (!dg.ok) return merr(nullptr, CFR_ERR_CUDA, "cannot select CUDA device %d", device);
     cfr_mlp *m = new cfr_mlp();
     cudaGetDevice(&m->device);
+    if (cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess) {
+        cudaGetLastError();
+        m->sms = 152;
+    }
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     m->L = num_layers;
     m->dims.assign(dims, dims + num_layers + 1);
