@@ -795,7 +795,7 @@ MLP_PATH_MMA_SYNC, MLP_PATH_TCGEN05, MLP_PATH_MIXED = 0, 1, 2
 
 def cfr_mlp_set_tensor_path(m: Mlp, path: int = MLP_PATH_MIXED):
     """0: mma.sync for every product; 1: tcgen05 for every product; 2 (default): tcgen05 with TMA operands
-    for the forward products, mma.sync for the backward ones."""
+    for the forward and data-gradient products, mma.sync for the weight-gradient ones."""
     _check_mlp(lib().cfr_mlp_set_tensor_path(m.handle, int(path)), m.handle)
 
 

@@ -11,8 +11,10 @@
 //               operand orientation;
 //   k_gemm_tc   tcgen05.mma with operands copied by every thread with cp.async into the canonical
 //               no-swizzle layout, any orientation.
-// The default (path 2) runs the forward products on k_gemm_tma and the backward ones on k_gemm, the
-// fastest measured on GB300 for each; path 0 is k_gemm everywhere, path 1 tcgen05 everywhere.  Each operand is read from global memory in its
+// The default (path 2) runs the forward and the data-gradient products on k_gemm_tma (the latter with a
+// transposed BF16 copy of the weights as its K-major operand) and the weight-gradient products on
+// k_gemm, split over the batch where they have few output tiles; path 0 is k_gemm everywhere, path 1
+// tcgen05 everywhere.  Each operand is read from global memory in its
 // stored orientation - the reduction index contiguous ("K-major") or the output index contiguous - and
 // ldmatrix (with .trans for the second case) builds the fragments, so the three products of a layer
 // need no transposed copies:
@@ -419,7 +421,8 @@ __device__ __forceinline__ void tm_load(uint32_t dst, const CUtensorMap *map, in
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constant__ CUtensorMap ta,
                                                             const __grid_constant__ CUtensorMap tb, void *C, int64_t ldc,
-                                                            int32_t K, const float *bias, int *err) {
+                                                            int32_t K, const float *bias, const __nv_bfloat16 *mask,
+                                                            int *err) {
     using S = TmShape<BN>;
     extern __shared__ unsigned char raw[];
     const uint32_t raw_s = tc_smem_u32(raw);
@@ -495,7 +498,8 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
     // Epilogue: every product has completed (so the stages' shared memory is free), and the tile goes
     // through it: each thread writes its row (the accumulator's lane) in 16-column pieces to a padded
     // row-major tile, then the block stores whole rows to global memory with coalesced 16-byte stores.
-    using OutT = typename std::conditional<EPI == kEpiHidden, __nv_bfloat16, float>::type;
+    constexpr bool kBf16 = EPI == kEpiHidden || EPI == kEpiMask;
+    using OutT = typename std::conditional<kBf16, __nv_bfloat16, float>::type;
     constexpr int kPadE = 16 / (int)sizeof(OutT);                       // one 16-byte chunk per row
     constexpr int kLd = BN + kPadE;                                      // row stride in elements
     static_assert(128 * kLd * (int)sizeof(OutT) <= S::kStages * S::kStage, "output tile exceeds the stages");
@@ -519,9 +523,17 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
             uint32_t o[16];                                              // the 16 results, packed
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
-                float v0 = __uint_as_float(r[j]) + bias[n + j], v1 = __uint_as_float(r[j + 1]) + bias[n + j + 1];
+                float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+                if constexpr (EPI != kEpiMask) {
+                    v0 += bias[n + j];
+                    v1 += bias[n + j + 1];
+                }
                 if constexpr (EPI == kEpiHidden) {
-                    const __nv_bfloat162 b = __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                if constexpr (kBf16) {
+                    const __nv_bfloat162 b = __floats2bfloat162_rn(v0, v1);
                     o[j / 2] = *reinterpret_cast<const uint32_t *>(&b);
                 } else {
                     o[j] = __float_as_uint(v0);
@@ -529,7 +541,7 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
                 }
             }
             int4 *dst = reinterpret_cast<int4 *>(tile + row * kLd + c0);
-            constexpr int kVec = EPI == kEpiHidden ? 2 : 4;                // 16-byte pieces of 16 results
+            constexpr int kVec = kBf16 ? 2 : 4;                          // 16-byte pieces of 16 results
 #pragma unroll
             for (int q = 0; q < kVec; ++q) dst[q] = make_int4((int)o[4 * q], (int)o[4 * q + 1], (int)o[4 * q + 2], (int)o[4 * q + 3]);
         }
@@ -539,8 +551,19 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
         constexpr int kChunks = BN * (int)sizeof(OutT) / 16;             // 16-byte pieces of a row
         for (int i = tid; i < 128 * kChunks; i += kTmThreads) {
             const int row = i / kChunks, ch = i % kChunks;
-            const int4 v = *reinterpret_cast<const int4 *>(tile + row * kLd + ch * (16 / (int)sizeof(OutT)));
-            *reinterpret_cast<int4 *>(static_cast<OutT *>(C) + (m0 + row) * ldc + n0 + ch * (16 / (int)sizeof(OutT))) = v;
+            int4 v = *reinterpret_cast<const int4 *>(tile + row * kLd + ch * (16 / (int)sizeof(OutT)));
+            const int64_t at = (m0 + row) * ldc + n0 + ch * (16 / (int)sizeof(OutT));
+            if constexpr (EPI == kEpiMask) {                             // zero where the ReLU output was 0
+                const int4 mk = *reinterpret_cast<const int4 *>(mask + at);
+                uint32_t *vw = reinterpret_cast<uint32_t *>(&v);
+                const __nv_bfloat162 *mw = reinterpret_cast<const __nv_bfloat162 *>(&mk);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool keep0 = __bfloat162float(mw[q].x) > 0.f, keep1 = __bfloat162float(mw[q].y) > 0.f;
+                    vw[q] &= (keep0 ? 0x0000FFFFu : 0u) | (keep1 ? 0xFFFF0000u : 0u);
+                }
+            }
+            *reinterpret_cast<int4 *>(static_cast<OutT *>(C) + at) = v;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -621,6 +644,15 @@ __global__ void k_adam(float *p, const float *g, float *m1, float *m2, __nv_bflo
     }
 }
 
+// wt [cols][rows] = w [rows][cols] (BF16, both dimensions multiples of 32), through 32 x 32 tiles.
+__global__ void k_transpose_w(const __nv_bfloat16 *w, int64_t rows, int64_t cols, __nv_bfloat16 *wt) {
+    __shared__ __nv_bfloat16 t[32][34];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int i = (int)threadIdx.y; i < 32; i += (int)blockDim.y) t[i][threadIdx.x] = w[(r0 + i) * cols + c0 + threadIdx.x];
+    __syncthreads();
+    for (int i = (int)threadIdx.y; i < 32; i += (int)blockDim.y) wt[(c0 + i) * rows + r0 + threadIdx.x] = t[threadIdx.x][i];
+}
+
 __global__ void k_to_bf16(const float *p, __nv_bfloat16 *pb, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         pb[i] = __float2bfloat16_rn(p[i]);
@@ -640,6 +672,8 @@ struct cfr_mlp {
     cudaStream_t stream = nullptr;
     float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
     __nv_bfloat16 *pb = nullptr;
+    __nv_bfloat16 *pbt = nullptr;    // each layer's BF16 weights transposed ([in][out] at w_off): the K-major
+                                     // operand of the data-gradient products on the TMA path
     int64_t steps = 0;
     // activations for the largest batch seen: acts[0] input, acts[l] hidden output of layer l - 1
     int64_t cap = 0;
@@ -797,14 +831,14 @@ bool encode_operand(CUtensorMap *map, const __nv_bfloat16 *g, int64_t rows, int6
 // The forward product on tcgen05 with TMA operands: BN = 256 where N allows, else 128.
 template <int EPI>
 cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bfloat16 *W, void *C, int64_t M, int64_t N,
-                         int64_t K, const float *bias) {
+                         int64_t K, const float *bias, const __nv_bfloat16 *mask = nullptr) {
     CUtensorMap ta, tb;
     // 256-wide tiles where they still give two blocks per SM, else 128-wide (the FP32 output tile of the
     // last layer takes the 128-wide shape, whose stages can hold it for the epilogue)
-    const int bn = (EPI == kEpiHidden && N % 256 == 0 && (N / 256) * (M / 128) >= 2 * 152) ? 256 : 128;
+    const int bn = (EPI != kEpiOut && N % 256 == 0 && (N / 256) * (M / 128) >= 2 * 152) ? 256 : 128;
     if (!encode_operand(&ta, A, M, K, 128) || !encode_operand(&tb, W, N, K, bn)) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)(N / bn), (unsigned)(M / 128));
-    if constexpr (EPI != kEpiHidden) {
+    if constexpr (EPI == kEpiOut) {
         static bool attr = false;
         if (!attr) {
             const cudaError_t e = cudaFuncSetAttribute(k_gemm_tma<128, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -812,7 +846,7 @@ cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bf
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_gemm_tma<128, EPI><<<grid, kTmThreads, TmShape<128>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, m->d_err);
+        k_gemm_tma<128, EPI><<<grid, kTmThreads, TmShape<128>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, mask, m->d_err);
     } else if (bn == 256) {
         static bool attr = false;
         if (!attr) {
@@ -821,7 +855,7 @@ cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bf
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_gemm_tma<256, EPI><<<grid, kTmThreads, TmShape<256>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, m->d_err);
+        k_gemm_tma<256, EPI><<<grid, kTmThreads, TmShape<256>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, mask, m->d_err);
     } else {
         static bool attr = false;
         if (!attr) {
@@ -830,7 +864,17 @@ cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bf
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_gemm_tma<128, EPI><<<grid, kTmThreads, TmShape<128>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, m->d_err);
+        k_gemm_tma<128, EPI><<<grid, kTmThreads, TmShape<128>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, mask, m->d_err);
+    }
+    return cudaGetLastError();
+}
+
+// The transposed BF16 weights of every layer from the BF16 mirror.
+cudaError_t refresh_transposes(const cfr_mlp *m) {
+    for (int l = 0; l < m->L; ++l) {
+        const int64_t out = m->pdims[(size_t)l + 1], in = m->pdims[(size_t)l];
+        k_transpose_w<<<dim3((unsigned)(in / 32), (unsigned)(out / 32)), dim3(32, 8), 0, m->stream>>>(
+            m->pb + m->w_off[(size_t)l], out, in, m->pbt + m->w_off[(size_t)l]);
     }
     return cudaGetLastError();
 }
@@ -908,9 +952,11 @@ cfr_status cfr_mlp_create(const int32_t *dims, int32_t num_layers, int32_t devic
     for (float **a : {&m->p, &m->g, &m->m1, &m->m2})
         if (e == cudaSuccess) e = cudaMalloc(a, sizeof(float) * (size_t)m->P);
     if (e == cudaSuccess) e = cudaMalloc(&m->pb, sizeof(__nv_bfloat16) * (size_t)m->P);
+    if (e == cudaSuccess) e = cudaMalloc(&m->pbt, sizeof(__nv_bfloat16) * (size_t)m->P);
     for (float *a : {m->p, m->g, m->m1, m->m2})
         if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, sizeof(float) * (size_t)m->P, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->pb, 0, sizeof(__nv_bfloat16) * (size_t)m->P, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->pbt, 0, sizeof(__nv_bfloat16) * (size_t)m->P, m->stream);
     for (cudaEvent_t &ev : m->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
@@ -937,6 +983,7 @@ cfr_status cfr_mlp_set_params(cfr_mlp *m, const float *params, int64_t len) {
     MCK(cudaMemcpyAsync(m->p, flat.data(), sizeof(float) * flat.size(), cudaMemcpyHostToDevice, m->stream));
     k_to_bf16<<<grid_for(m->P), 256, 0, m->stream>>>(m->p, m->pb, m->P);
     MCK(cudaGetLastError());
+    MCK(refresh_transposes(m));
     for (float *a : {m->m1, m->m2}) MCK(cudaMemsetAsync(a, 0, sizeof(float) * (size_t)m->P, m->stream));
     m->steps = 0;
     MCK(cudaStreamSynchronize(m->stream));
@@ -1013,8 +1060,12 @@ cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int
                                            nullptr, nullptr)));
         fb += 2.0 * (double)N * K * Bp;
         if (l > 0) {   // dZ of layer l - 1 = (dZ W) masked where its ReLU output was 0
-            MCK((gemm<true, false, kEpiMask>(m, dz, N, m->pb + m->w_off[(size_t)l], K, m->grads[(size_t)l - 1], K, Bp, K,
-                                             N, nullptr, m->acts[(size_t)l])));
+            if (m->path == 2)   // tcgen05 with TMA operands: dZ [batch][out] and W^T [in][out], both K-major
+                MCK(gemm_fwd_tma<kEpiMask>(m, dz, m->pbt + m->w_off[(size_t)l], m->grads[(size_t)l - 1], Bp, K, N, nullptr,
+                                           m->acts[(size_t)l]));
+            else
+                MCK((gemm<true, false, kEpiMask>(m, dz, N, m->pb + m->w_off[(size_t)l], K, m->grads[(size_t)l - 1], K, Bp,
+                                                 K, N, nullptr, m->acts[(size_t)l])));
             fb += 2.0 * (double)Bp * K * N;
         }
     }
@@ -1082,6 +1133,7 @@ cfr_status cfr_mlp_adam(cfr_mlp *m, float lr, float beta1, float beta2, float ep
     const float c2 = (float)(1.0 - std::pow((double)beta2, (double)m->steps));
     k_adam<<<grid_for(m->P), 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, m->pb, m->P, lr, beta1, beta2, eps, c1, c2);
     MCK(cudaGetLastError());
+    MCK(refresh_transposes(m));
     return CFR_OK;
 }
 
@@ -1121,7 +1173,8 @@ void cfr_mlp_free(cfr_mlp *m) {
     if (!m) return;
     MDeviceGuard dg(m->device);
     cudaStreamSynchronize(m->stream);
-    for (void *a : {(void *)m->p, (void *)m->g, (void *)m->m1, (void *)m->m2, (void *)m->pb, (void *)m->yp, (void *)m->d_err})
+    for (void *a : {(void *)m->p, (void *)m->g, (void *)m->m1, (void *)m->m2, (void *)m->pb, (void *)m->pbt, (void *)m->yp,
+                    (void *)m->d_err})
         if (a) cudaFree(a);
     for (auto *a : m->acts) if (a) cudaFree(a);
     for (auto *a : m->grads) if (a) cudaFree(a);
