@@ -366,11 +366,14 @@ def cfr_set_state(s: "Solver", cum_regret, strat_sum, iteration: int):
     _check(lib().cfr_set_state(s.handle, R.ctypes.data, S.ctypes.data, R.shape[0], int(iteration)), s.handle)
 
 
-def cfr_get_nodes(s: "Solver") -> dict:
+def cfr_get_nodes(s: "Solver", values_only: bool = False) -> dict:
+    """Per node of the last iteration: u1 (Eq. 1) and, unless values_only, the counterfactual reaches."""
     n = s.num_nodes
-    u, r1, r2 = np.empty(n), np.empty(n), np.empty(n)
-    _check(lib().cfr_get_nodes(s.handle, u.ctypes.data, r1.ctypes.data, r2.ctypes.data, n), s.handle)
-    return dict(u1=u, cf_reach1=r1, cf_reach2=r2)
+    u = np.empty(n)
+    r1, r2 = (None, None) if values_only else (np.empty(n), np.empty(n))
+    _check(lib().cfr_get_nodes(s.handle, u.ctypes.data, None if r1 is None else r1.ctypes.data,
+                               None if r2 is None else r2.ctypes.data, n), s.handle)
+    return dict(u1=u) if values_only else dict(u1=u, cf_reach1=r1, cf_reach2=r2)
 
 
 def cfr_root_value(s: "Solver") -> float:

@@ -313,7 +313,7 @@ def generate_samples(cut: Cut, per_node: int, iterations: int = 300, seed: int =
         st = cfr_get_state(s)
         cfr_set_state(s, st["strat_sum"], st["strat_sum"], st["iteration"])   # sigma := the average strategy
         cfr_iterate(s, 1)
-        u1 = cfr_get_nodes(s)["u1"]
+        u1 = cfr_get_nodes(s, values_only=True)["u1"]
         s.close()
         for j in range(i0, i1):
             r, c, r1, r2 = jobs[j]
@@ -426,7 +426,7 @@ def blueprint_leaf_values(cut: Cut, strat_sum: np.ndarray, device=None):
     S = np.asarray(strat_sum, dtype=np.float64)
     cfr_set_state(s, S, S, 1)                  # sigma := the average strategy
     cfr_iterate(s, 1)
-    u1 = cfr_get_nodes(s)["u1"]
+    u1 = cfr_get_nodes(s, values_only=True)["u1"]
     s.close()
     umax = float(np.max(np.abs(g.utility))) or 1.0
     rows = cut.cut_nodes.size
