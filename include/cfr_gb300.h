@@ -106,6 +106,8 @@ typedef struct {
                                only run in one launch per direction instead of one launch per depth, each
                                block walking the subtrees of a range of root children: the root and the
                                next k depths (each at most 2^19 nodes, none with more than 32 actions).
+                               The forest part of a batch (cfr_batch_load) does the same with blocks
+                               walking ranges of its games' roots (no root of more than 32 actions).
                                -1 (default) = as many as qualify, 0 = none, k >= 1 = at most k.
                                Ignored in FP64 mode. */
     int64_t batch_split_nodes;  /* cfr_batch_load: games of at least this many nodes run as one forest
@@ -326,6 +328,7 @@ typedef struct {
     int64_t smem_bytes;         /* dynamic shared memory of a persistent block (its largest game's image) */
     int64_t forest_bytes_per_iteration;   /* algorithmic bytes of one iteration of the forest part
                                              (cfr_info.bytes_per_iteration of its solver) */
+    int32_t forest_head_depths; /* cfr_info.head_depths of the forest part's solver */
 } cfr_batch_info;
 
 /* Validates and lays out num_games >= 1 games (each as cfr_load_tree would; the combined size must stay

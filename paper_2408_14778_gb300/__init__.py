@@ -100,7 +100,7 @@ class _BatchInfo(ctypes.Structure):
         ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
         ("tuned", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("forest_games", ctypes.c_int32),
         ("forest_nodes", ctypes.c_int64), ("split_nodes", ctypes.c_int64), ("smem_bytes", ctypes.c_int64),
-        ("forest_bytes_per_iteration", ctypes.c_int64),
+        ("forest_bytes_per_iteration", ctypes.c_int64), ("forest_head_depths", ctypes.c_int32),
     ]
 
 
@@ -515,9 +515,10 @@ class Batch:
 
 def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=None, stream=None,
                    allocator: str = "torch", dcfr=(1.5, 0.0, 2.0), split_nodes: int = 0,
-                   update_mode=CFR_SIMULTANEOUS) -> Batch:
+                   update_mode=CFR_SIMULTANEOUS, head_levels: int = -1) -> Batch:
     """Loads a list of games for batched solving (FP32 mode).  split_nodes: cfr_config.batch_split_nodes
-    (0 default, negative: every game whose image fits shared memory in the persistent kernel)."""
+    (0 default, negative: every game whose image fits shared memory in the persistent kernel);
+    head_levels: cfr_config.head_levels of the forest part."""
     import torch
 
     if not torch.cuda.is_available():
@@ -531,6 +532,7 @@ def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=N
     cfg.dcfr_alpha, cfg.dcfr_beta, cfg.dcfr_gamma = (float(x) for x in dcfr)
     cfg.batch_split_nodes = int(split_nodes)
     cfg.update_mode = int(update_mode)
+    cfg.head_levels = int(head_levels)
     alloc = None
     if allocator == "torch":
         alloc = _TorchAllocator(dev, st_handle)

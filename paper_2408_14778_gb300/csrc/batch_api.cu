@@ -904,6 +904,7 @@ cfr_status cfr_batch_get_info(const cfr_batch *b, cfr_batch_info *info) {
     info->split_nodes = b->split_nodes;
     info->smem_bytes = b->smem_bytes;
     info->forest_bytes_per_iteration = fi.bytes_per_iteration;
+    info->forest_head_depths = fi.head_depths;
     info->device_bytes = b->device_bytes + fi.device_bytes;
     info->iteration = b->iteration;
     info->threads_per_block = b->threads;

@@ -258,8 +258,9 @@ HeadArgs head_args(const cfr_solver *s, bool bump) {
     HeadArgs a{};
     a.n = s->head_n - 1;
     a.bump = bump;
-    a.d1 = s->dlevel[1];
-    a.nroot = s->dlevel[2] - s->dlevel[1];
+    a.forest = s->dlevel[1] > 1;
+    a.d1 = a.forest ? 0 : s->dlevel[1];
+    a.nroot = a.forest ? s->dlevel[1] : s->dlevel[2] - s->dlevel[1];
     a.per_block = s->head_per_block;
     a.nblk = (a.nroot + a.per_block - 1) / a.per_block;
     a.cap = s->head_cap;
@@ -267,6 +268,10 @@ HeadArgs head_args(const cfr_solver *s, bool bump) {
     a.done = s->head_done;
     return a;
 }
+
+// Whether the head top-down of this pass clears r~ (instead of the memset before it): simultaneous
+// updates, in the graph's iteration.
+bool head_clears(const cfr_solver *s, bool timed_phases, bool alt) { return s->head_n > 0 && !timed_phases && !alt; }
 
 // Whether the top-down step from depth l launches anything: a depth whose nodes have no decision
 // children (the last one) has none, except depth 0, whose first thread counts the iteration, and
@@ -365,7 +370,7 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         }
         return CFR_OK;
     };
-    if (!det && !alt) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
+    if (!det && !alt && !head_clears(s, ev != nullptr, alt)) CK(cudaMemsetAsync(s->inst, 0, sizeof(real) * (size_t)s->Q, st));
     if (!det && alt && s->Hp > 0) CK(go(k_zero_inst<real>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp));
     TRY(mark());
     // the shallowest depths in one launch per direction (the graph's iteration only: the phase timer
@@ -373,7 +378,11 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
     const int32_t head = (!det && ev == nullptr) ? s->head_n : 0;
     if constexpr (!det) {
         if (head > 0) {
-            const HeadArgs ha = head_args(s, first);
+            HeadArgs ha = head_args(s, first);
+            if (head_clears(s, ev != nullptr, alt)) {
+                ha.zero = reinterpret_cast<float *>(s->inst);
+                ha.nzero = s->Q;
+            }
             auto k = s->head_na == 0 ? k_head_topdown<kStreamNA[0]>
                    : s->head_na == 1 ? k_head_topdown<kStreamNA[1]> : k_head_topdown<kStreamNA[2]>;
             CK(go(k, ha.nblk + (ha.nown + kHeadThreads - 1) / kHeadThreads, kHeadThreads, head_smem_topdown(ha.cap), st,
@@ -587,16 +596,21 @@ int32_t launches_per_pass(const cfr_solver *s) {
 }
 
 // FP32 mode: the leading depths run by k_head_topdown / k_head_bottomup: depths 0 .. n (head_n = n + 1)
-// for a single root whose children are all decision nodes, n >= 1 the deepest depth below the fused ones
+// for a single root whose children are all decision nodes, or for a forest whose roots have at most 32
+// actions, n >= 1 the deepest depth below the fused ones
 // such that every depth 1 .. n holds at most kHeadMaxNodes nodes and no node of more than 32 actions,
 // and the largest block's nodes of depths 1 .. n fit kHeadMaxSmem bytes of shared memory (at most
 // cfg.head_levels depths below the root when that is positive; 0: none).  About two blocks per SM walk
 // the root children's subtrees.
 cfr_status plan_head(cfr_solver *s, const Layout &Lo, int sms) {
     s->head_n = 0;
-    if (s->cfg.head_levels == 0 || s->L < 2 || s->dlevel[1] != 1) return CFR_OK;
-    const int32_t nroot = s->dlevel[2] - s->dlevel[1];
-    if (nroot < 1 || s->level_children[0] != nroot) return CFR_OK;      // a terminal child of the root
+    if (s->cfg.head_levels == 0 || s->L < 2) return CFR_OK;
+    const bool forest = s->dlevel[1] > 1;
+    // the nodes blocks take ranges of: the roots of a forest (none of more than 32 actions), else the root's
+    // children (all decision nodes)
+    const int32_t first = forest ? 0 : 1;
+    const int32_t nroot = forest ? s->dlevel[1] : s->dlevel[2] - s->dlevel[1];
+    if (forest ? s->wlevel[1] > s->wlevel[0] : (nroot < 1 || s->level_children[0] != nroot)) return CFR_OK;
     const int32_t r = fused_from(s);
     const int32_t cap = s->cfg.head_levels < 0 ? kHeadMaxDepths : std::min(s->cfg.head_levels, (int32_t)kHeadMaxDepths);
     int32_t n = 0;
@@ -609,9 +623,9 @@ cfr_status plan_head(cfr_solver *s, const Layout &Lo, int sms) {
     int32_t most = 0;
     for (; n >= 1; --n) {
         most = 0;
-        for (int32_t lo1 = s->dlevel[1]; lo1 < s->dlevel[1] + nroot; lo1 += per) {
-            int32_t lo = lo1, hi = std::min(lo1 + per, s->dlevel[1] + nroot), tot = 0;
-            for (int32_t l = 1; l <= n; ++l) {
+        for (int32_t lo1 = s->dlevel[(size_t)first]; lo1 < s->dlevel[(size_t)first] + nroot; lo1 += per) {
+            int32_t lo = lo1, hi = std::min(lo1 + per, s->dlevel[(size_t)first] + nroot), tot = 0;
+            for (int32_t l = first; l <= n; ++l) {
                 tot += hi - lo;
                 lo = Lo.dfirst[(size_t)lo];
                 hi = Lo.dfirst[(size_t)hi];
@@ -633,7 +647,7 @@ cfr_status plan_head(cfr_solver *s, const Layout &Lo, int sms) {
     s->head_per_block = per;
     s->head_cap = std::max(most, 1);
     s->head_na = 0;
-    for (int32_t l = 1; l <= n; ++l) s->head_na = std::max(s->head_na, s->level_na[(size_t)l]);
+    for (int32_t l = first; l <= n; ++l) s->head_na = std::max(s->head_na, s->level_na[(size_t)l]);
     return CFR_OK;
 }
 

@@ -542,7 +542,9 @@ __global__ void __launch_bounds__(1024) k_bottomup_wide(DevTree<real> t, const i
 // the product of the strategy entries of its player's own sequence, multiplied from the first action
 // on - the same products in the same order as k_own's depth-by-depth recursion.  The host uses these
 // kernels for a single root whose children are all decision nodes, with no node of more than 32
-// actions in depths 1 .. n, and sizes the shared memory for the largest block (HeadArgs::cap nodes).
+// actions in depths 1 .. n, or for a forest of independent games (blocks then take ranges of roots,
+// and no node of depths 0 .. n may have more than 32 actions), and sizes the shared memory for the
+// largest block (HeadArgs::cap nodes).
 // NA: the unrolled action count (at least the largest of depths 1 .. n for full unrolling; nodes with more
 // actions take the general loop).
 constexpr int kHeadMaxDepths = 16;
@@ -553,12 +555,30 @@ struct HeadArgs {
     int32_t n;                 // the top-down steps of depths 0 .. n (reaches of depths 1 .. n + 1) and the
                                // bottom-up steps of depths n .. 0
     int32_t bump;              // count the iteration (first pass of an iteration)
-    int32_t d1, nroot;         // the root's children: nodes d1 .. d1 + nroot - 1 (depth 1)
+    int32_t forest;            // several roots (independent games): blocks take ranges of roots, and depth 0
+                               // is a level like the others; else blocks take ranges of the root's children
+    int32_t d1, nroot;         // the nodes blocks take ranges of: d1 .. d1 + nroot - 1 (the root's children at
+                               // depth 1, or the roots at depth 0)
     int32_t per_block, nblk;   // root children per block; blocks walking subtrees
     int32_t cap;               // nodes of depths 1 .. n in a block, at most (shared-memory arrays)
     int32_t nown;              // infosets 0 .. nown - 1 are first seen at depths 0 .. n (own reaches)
     int32_t *done;             // k_head_bottomup: blocks that have finished (reset by the last)
+    float *zero;               // k_head_topdown: r~ to clear (nzero floats; nullptr: cleared elsewhere),
+    int64_t nzero;             // in slices by the subtree blocks - no kernel before the bottom-up reads it
 };
+
+// This block's slice of r~ (zero[0 .. nzero)) cleared with 16-byte stores where the slice allows.
+__device__ __forceinline__ void head_clear(const HeadArgs &a) {
+    if (!a.zero) return;
+    const int64_t per = ((a.nzero + a.nblk - 1) / a.nblk + 3) & ~(int64_t)3;   // a multiple of 4 floats
+    const int64_t b0 = per * blockIdx.x, b1 = min(b0 + per, a.nzero);
+    if (b0 >= b1) return;
+    const bool aligned = (reinterpret_cast<uintptr_t>(a.zero) & 15u) == 0;
+    const int64_t v1 = aligned ? b0 + ((b1 - b0) & ~(int64_t)3) : b0;   // b0 is a multiple of 4
+    float4 *z4 = reinterpret_cast<float4 *>(a.zero + b0);
+    for (int64_t i = threadIdx.x; i < (v1 - b0) / 4; i += blockDim.x) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t i = v1 + threadIdx.x; i < b1; i += blockDim.x) a.zero[i] = 0.f;
+}
 
 // Own reach of infoset h from the strategy entries along its player's own sequence.
 __device__ __forceinline__ void own_path(const DevTree<float> &t, int32_t h) {
@@ -572,14 +592,16 @@ __device__ __forceinline__ void own_path(const DevTree<float> &t, int32_t h) {
     t.own[h] = own;
 }
 
-// The block's node ranges per depth: nodes lo[l] .. hi[l] - 1 of depth l (l = 1 .. n + 1), at offset
-// off[l] of the shared-memory arrays (l <= n); run by one thread.
+// The block's node ranges per depth: nodes lo[l] .. hi[l] - 1 of depth l (l = f .. n + 1, f the first
+// depth the blocks split: 0 for a forest, else 1), at offset off[l] of the shared-memory arrays (l <= n);
+// run by one thread.
 __device__ __forceinline__ void head_ranges(const DevTree<float> &t, const HeadArgs &a, int32_t *lo, int32_t *hi,
                                             int32_t *off) {
-    lo[1] = a.d1 + (int32_t)blockIdx.x * a.per_block;
-    hi[1] = min(lo[1] + a.per_block, a.d1 + a.nroot);
-    off[1] = 0;
-    for (int l = 1; l <= a.n; ++l) {
+    const int f = a.forest ? 0 : 1;
+    lo[f] = a.d1 + (int32_t)blockIdx.x * a.per_block;
+    hi[f] = min(lo[f] + a.per_block, a.d1 + a.nroot);
+    off[f] = 0;
+    for (int l = f; l <= a.n; ++l) {
         lo[l + 1] = t.dfirst[lo[l]];
         hi[l + 1] = t.dfirst[hi[l]];
         off[l + 1] = off[l] + (hi[l] - lo[l]);
@@ -592,7 +614,7 @@ __device__ __forceinline__ void head_stage(const DevTree<float> &t, const HeadAr
                                            int32_t *tf_s) {
     const int32_t total = off[a.n + 1];
     for (int32_t i = (int32_t)threadIdx.x; i < total; i += (int32_t)blockDim.x) {
-        int l = 1;
+        int l = a.forest ? 0 : 1;
         while (l < a.n && i >= off[l + 1]) ++l;
         const int32_t j = lo[l] + (i - off[l]);
         qp_s[i] = t.qp[j];
@@ -622,7 +644,14 @@ __global__ void __launch_bounds__(kHeadThreads, kHeadBlocksPerSM) k_head_topdown
     if (tid == 0) head_ranges(t, a, lo, hi, off);
     __syncthreads();
     head_stage(t, a, lo, off, qp_s, km_s, df_s, nullptr);
-    {   // depth 0: the root's step for this block's children (all decision nodes: child d1 + a is action a)
+    head_clear(a);
+    const int f = a.forest ? 0 : 1;
+    if (a.forest) {   // depth 0: the roots' reaches (1, set at load)
+        for (int32_t j = lo[0] + tid; j < hi[0]; j += bs) {
+            r1_s[j - lo[0]] = t.reach1[j];
+            r2_s[j - lo[0]] = t.reach2[j];
+        }
+    } else {          // depth 0: the root's step for this block's children (all decision nodes: child d1 + a is action a)
         const uint32_t w = t.qp[0];
         const int32_t qb = qp_base(w);
         const int p = qp_player(w);
@@ -634,7 +663,7 @@ __global__ void __launch_bounds__(kHeadThreads, kHeadBlocksPerSM) k_head_topdown
         }
     }
     __syncthreads();
-    for (int l = 1; l <= a.n; ++l) {
+    for (int l = f; l <= a.n; ++l) {
         const int32_t cnt = hi[l] - lo[l];
         const bool deep = l == a.n;                             // children outside the block's arrays
         for (int32_t i = tid; i < cnt; i += bs) {
@@ -696,7 +725,7 @@ __global__ void __launch_bounds__(kHeadThreads, kHeadBlocksPerSM) k_head_bottomu
     __syncthreads();
     head_stage(t, a, lo, off, qp_s, km_s, df_s, tf_s);
     __syncthreads();
-    for (int l = a.n; l >= 1; --l) {
+    for (int l = a.n; l >= (a.forest ? 0 : 1); --l) {
         const int32_t cnt = hi[l] - lo[l];
         const bool deep = l == a.n;                             // children's values in global memory
         for (int32_t i = tid; i < cnt; i += bs) {
@@ -752,6 +781,7 @@ __global__ void __launch_bounds__(kHeadThreads, kHeadBlocksPerSM) k_head_bottomu
         }
         __syncthreads();
     }
+    if (a.forest) return;                                       // every root is its own game's
     // this block's depth-1 values are written; the last block to finish takes the root
     if (tid == 0) {
         __threadfence();

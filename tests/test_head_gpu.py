@@ -1,5 +1,6 @@
 """The shallowest depths in one launch per direction (k_head_topdown / k_head_bottomup, FP32 mode: each
-block walks the subtrees of a range of root children; the last block to finish takes the root) against
+block walks the subtrees of a range of root children, the last block to finish taking the root, or, in a
+batch's forest part, the subtrees of a range of games' roots) against
 the oracle: a first iteration and a step from the oracle's state at T = 3 (FP32 step parity; two FP32
 runs' trajectories part after a few iterations whatever their kernels, since the atomics' order differs
 and regret matching amplifies it) (GPU tests)."""
@@ -9,7 +10,7 @@ import pytest
 import gamegen
 import oracle
 import paper_2408_14778_gb300 as cfr
-from paritylib import TOL32, compare_nodes, compare_state, normwise
+from paritylib import TOL32, compare_nodes, compare_state, fp32_regret_budget_check, normwise
 
 pytestmark = pytest.mark.gpu
 
@@ -104,3 +105,47 @@ def test_head_converges_like_the_oracle():
             assert nc_g <= 1.1 * nc_o + 1e-4, (T, nc_g, nc_o)
             nc_chk, _ = o.exploitability(cfr.cfr_average_strategy(x))
             assert abs(nc_chk - nc_g) <= 1e-6
+
+
+@pytest.mark.parametrize("variant,alt", [(cfr.CFR_PLUS, False), (cfr.CFR_VANILLA, False), (cfr.CFR_PLUS, True)],
+                         ids=["cfr+", "vanilla", "cfr+_alternating"])
+def test_forest_head_matches_oracle_game_by_game(variant, alt):
+    # A batch's forest part (every game at split 1): blocks take ranges of the games' roots, and depth 0 is
+    # walked like the others (no root step).  Games of 1e2-3e4 nodes and depths 4-10 (chance roots), so that
+    # blocks hold subtrees of unequal sizes and depths, and two matrix games (player roots).
+    rng = np.random.default_rng(21)
+    games = gamegen.batch_subgames(30, seed=21, max_nodes=3e4)
+    games[3:3] = [gamegen.matrix_game(rng.uniform(-1, 1, size=(8, 3)))]
+    games.append(gamegen.matrix_game(rng.uniform(-1, 1, size=(32, 5))))
+    mode = cfr.CFR_ALTERNATING if alt else cfr.CFR_SIMULTANEOUS
+    runs = {}
+    for levels in (-1, 0):
+        b = cfr.cfr_batch_load(games, variant=variant, split_nodes=1, update_mode=mode, head_levels=levels)
+        info = cfr.cfr_batch_get_info(b)
+        assert info["forest_games"] == len(games)
+        assert (info["forest_head_depths"] >= 2) if levels else info["forest_head_depths"] == 0
+        cfr.cfr_batch_iterate(b, 1)
+        runs[levels] = [cfr.cfr_batch_get_state(b, i) for i in range(len(games))]
+    avg = oracle.AVG_LINEAR if variant == cfr.CFR_PLUS else oracle.AVG_UNIFORM
+    for i, g in enumerate(games):
+        o = oracle.Oracle(g)
+        o.iterate(1, variant=variant, avg=avg, alternating=alt)
+        os_ = o.state()
+        p1 = np.repeat(g.infoset_player == 1, g.infoset_num_actions)
+        sel = p1 if alt else np.ones_like(p1)
+        for levels, states in runs.items():
+            gs = states[i]
+            for k in ("cum_regret", "strat_sum"):
+                assert normwise(gs[k][sel], os_[k][sel]) <= TOL32, (i, levels, k)
+            if not alt:
+                fp32_regret_budget_check(g, gs, os_, _max_depth(g))
+
+
+def _max_depth(g):
+    d = np.full(g.num_nodes, -1)
+    d[g.parent < 0] = 0
+    while (d < 0).any():
+        todo = np.nonzero(d < 0)[0]
+        ok = d[g.parent[todo]] >= 0
+        d[todo[ok]] = d[g.parent[todo[ok]]] + 1
+    return int(d.max())
