@@ -688,6 +688,18 @@ struct cfr_mlp {
     int *d_err = nullptr;            // set by a tcgen05 kernel whose mbarrier wait gave up
     std::string err;
     bool poisoned = false;
+    // The products of a forward pass and of a backward pass (after the loss gradient), replayed from a
+    // CUDA graph: the host's per-launch work (tensor-map encoding, launch) then no longer sits between the
+    // kernels.  A graph is captured (on cap_stream, a stream of its own) the second time a pass runs with the same
+    // key; the first run of a key is launched directly.
+    cudaStream_t cap_stream = nullptr;
+    struct PassGraph {
+        cudaGraphExec_t exec = nullptr;
+        int64_t bp = 0, cap = 0;     // the key: padded batch, buffer capacity, tensor path
+        int32_t path = -1;
+        bool seen = false;           // the key has run once directly
+        double flops = 0;            // the pass's multiply-add work, times two
+    } gfwd, gbwd;
 };
 
 namespace {
@@ -891,7 +903,8 @@ cfr_status check_err(cfr_mlp *m) {
     return CFR_OK;
 }
 
-// The forward pass over Bp padded rows (input already packed into acts[0]); output in yp.
+// The forward pass over Bp padded rows (input already packed into acts[0]); output in yp.  Launches on
+// m->stream.
 cfr_status forward_padded(cfr_mlp *m, int64_t Bp, double *flops) {
     double f = 0;
     for (int l = 0; l < m->L; ++l) {
@@ -910,6 +923,72 @@ cfr_status forward_padded(cfr_mlp *m, int64_t Bp, double *flops) {
     }
     *flops = f;
     return CFR_OK;
+}
+
+// The backward products over Bp padded rows (the output gradient already in grads[L - 1]): every weight
+// gradient and every masked data gradient.  Launches on m->stream.
+cfr_status backward_products(cfr_mlp *m, int64_t Bp, double *flops) {
+    double fb = 0;
+    for (int l = m->L - 1; l >= 0; --l) {
+        const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
+        const __nv_bfloat16 *dz = m->grads[(size_t)l];
+        // dW[o][i] = sum_b dZ[b][o] X[b][i]
+        MCK((gemm<false, false, kEpiStore>(m, dz, N, m->acts[(size_t)l], K, m->g + m->w_off[(size_t)l], K, N, K, Bp,
+                                           nullptr, nullptr)));
+        fb += 2.0 * (double)N * K * Bp;
+        if (l > 0) {   // dZ of layer l - 1 = (dZ W) masked where its ReLU output was 0
+            if (m->path == 2)   // tcgen05 with TMA operands: dZ [batch][out] and W^T [in][out], both K-major
+                MCK(gemm_fwd_tma<kEpiMask>(m, dz, m->pbt + m->w_off[(size_t)l], m->grads[(size_t)l - 1], Bp, K, N, nullptr,
+                                           m->acts[(size_t)l]));
+            else
+                MCK((gemm<true, false, kEpiMask>(m, dz, N, m->pb + m->w_off[(size_t)l], K, m->grads[(size_t)l - 1], K, Bp,
+                                                 K, N, nullptr, m->acts[(size_t)l])));
+            fb += 2.0 * (double)Bp * K * N;
+        }
+    }
+    *flops = fb;
+    return CFR_OK;
+}
+
+// Runs pass (forward_padded or backward_products) for Bp rows on m->stream: directly the first time a key
+// (Bp, buffers, tensor path) is seen, from the pass's graph after that.
+cfr_status run_pass(cfr_mlp *m, cfr_mlp::PassGraph *g, cfr_status (*pass)(cfr_mlp *, int64_t, double *), int64_t Bp,
+                    double *flops) {
+    const bool same = g->bp == Bp && g->cap == m->cap && g->path == m->path;
+    if (!same) {                         // a new key: run directly first (this also sets kernel attributes)
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+        g->bp = Bp;
+        g->cap = m->cap;
+        g->path = m->path;
+        g->seen = false;
+    }
+    if (!g->exec && g->seen && m->cap_stream) {
+        MCK(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaStream_t user = m->stream;
+        m->stream = m->cap_stream;
+        const cfr_status st = pass(m, Bp, &g->flops);
+        m->stream = user;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(m->cap_stream, &graph);
+        if (st != CFR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        MCK(e);
+        const cudaError_t ei = cudaGraphInstantiate(&g->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        MCK(ei);
+    }
+    if (g->exec) {
+        MCK(cudaGraphLaunch(g->exec, m->stream));
+        *flops = g->flops;
+        return CFR_OK;
+    }
+    g->seen = true;
+    const cfr_status st = pass(m, Bp, &g->flops);
+    *flops = g->flops;
+    return st;
 }
 
 }  // namespace
@@ -959,6 +1038,7 @@ cfr_status cfr_mlp_create(const int32_t *dims, int32_t num_layers, int32_t devic
     if (e == cudaSuccess) e = cudaMemsetAsync(m->pbt, 0, sizeof(__nv_bfloat16) * (size_t)m->P, m->stream);
     for (cudaEvent_t &ev : m->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return fail(e);
     *out = m;
@@ -1022,7 +1102,7 @@ cfr_status cfr_mlp_forward(cfr_mlp *m, const float *x, int32_t batch, float *y) 
     k_pack_input<<<grid_for(Bp * m->pdims[0]), 256, 0, m->stream>>>(x, batch, m->dims[0], m->acts[0], Bp, m->pdims[0]);
     MCK(cudaGetLastError());
     MCK(cudaEventRecord(m->ev[0], m->stream));
-    if ((st = forward_padded(m, Bp, &m->fwd_flops)) != CFR_OK) return st;
+    if ((st = run_pass(m, &m->gfwd, forward_padded, Bp, &m->fwd_flops)) != CFR_OK) return st;
     MCK(cudaEventRecord(m->ev[1], m->stream));
     m->fwd_timed = true;
     m->last_batch = batch;
@@ -1044,7 +1124,7 @@ cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int
     k_pack_input<<<grid_for(Bp * m->pdims[0]), 256, 0, m->stream>>>(x, batch, m->dims[0], m->acts[0], Bp, m->pdims[0]);
     MCK(cudaGetLastError());
     double f = 0;
-    if ((st = forward_padded(m, Bp, &f)) != CFR_OK) return st;
+    if ((st = run_pass(m, &m->gfwd, forward_padded, Bp, &f)) != CFR_OK) return st;
     if (loss) MCK(cudaMemsetAsync(loss, 0, sizeof(double), m->stream));
     const int64_t nL = m->pdims[(size_t)L];
     k_mse<<<grid_for(Bp * nL), 256, 0, m->stream>>>(m->yp, nL, target, batch, m->dims[(size_t)L], Bp,
@@ -1052,23 +1132,7 @@ cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int
     MCK(cudaGetLastError());
     MCK(cudaEventRecord(m->ev[2], m->stream));
     double fb = 0;
-    for (int l = L - 1; l >= 0; --l) {
-        const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
-        const __nv_bfloat16 *dz = m->grads[(size_t)l];
-        // dW[o][i] = sum_b dZ[b][o] X[b][i]
-        MCK((gemm<false, false, kEpiStore>(m, dz, N, m->acts[(size_t)l], K, m->g + m->w_off[(size_t)l], K, N, K, Bp,
-                                           nullptr, nullptr)));
-        fb += 2.0 * (double)N * K * Bp;
-        if (l > 0) {   // dZ of layer l - 1 = (dZ W) masked where its ReLU output was 0
-            if (m->path == 2)   // tcgen05 with TMA operands: dZ [batch][out] and W^T [in][out], both K-major
-                MCK(gemm_fwd_tma<kEpiMask>(m, dz, m->pbt + m->w_off[(size_t)l], m->grads[(size_t)l - 1], Bp, K, N, nullptr,
-                                           m->acts[(size_t)l]));
-            else
-                MCK((gemm<true, false, kEpiMask>(m, dz, N, m->pb + m->w_off[(size_t)l], K, m->grads[(size_t)l - 1], K, Bp,
-                                                 K, N, nullptr, m->acts[(size_t)l])));
-            fb += 2.0 * (double)Bp * K * N;
-        }
-    }
+    if ((st = run_pass(m, &m->gbwd, backward_products, Bp, &fb)) != CFR_OK) return st;
     MCK(cudaEventRecord(m->ev[3], m->stream));
     m->bwd_flops = fb;
     m->bwd_timed = true;
@@ -1180,6 +1244,9 @@ void cfr_mlp_free(cfr_mlp *m) {
     for (auto *a : m->grads) if (a) cudaFree(a);
     for (cudaEvent_t ev : m->ev)
         if (ev) cudaEventDestroy(ev);
+    for (cfr_mlp::PassGraph *g : {&m->gfwd, &m->gbwd})
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     delete m;
 }
 
