@@ -405,7 +405,8 @@ template <int BN>
 struct TmShape {
     static constexpr int kStages = BN == 256 ? 2 : 3;
     static constexpr int kA = 128 * kTmK * 2, kB = BN * kTmK * 2, kStage = kA + kB;
-    static constexpr int kSmem = kStages * kStage + 1024 + 128;   // + alignment slack, barriers
+    static constexpr int kBias = BN * 4;                          // the tile's bias values
+    static constexpr int kSmem = kStages * kStage + 1024 + 128 + kBias;   // + alignment slack, barriers
 };
 
 __device__ __forceinline__ uint64_t tm_desc_sw128(uint32_t saddr) {
@@ -429,6 +430,7 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
     const uint32_t base = (raw_s + 1023u) & ~1023u;              // swizzled tiles: 1024-byte aligned
     const uint32_t bars = base + S::kStages * S::kStage;           // full[stages], empty[stages], acc
     uint32_t *tslot = reinterpret_cast<uint32_t *>(raw + (bars - raw_s) + (2 * S::kStages + 1) * 8);
+    float *bias_s = reinterpret_cast<float *>(raw + (bars - raw_s) + 128);   // after the barriers and tslot
     auto full = [&](int st) { return bars + 8u * st; };
     auto empty = [&](int st) { return bars + 8u * (S::kStages + st); };
     const uint32_t accb = bars + 8u * (2 * S::kStages);
@@ -492,6 +494,23 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accb) : "memory");
         if (!ok) atomicExch(err, 1);
     }
+    // While the products run: warps 2 and 3 stage the tile's bias values in shared memory, and every
+    // thread loads the ReLU mask of its accumulator row (kEpiMask), so that the epilogue waits on no
+    // global load.  (The copy and MMA lanes get here once their loops are done.)
+    if constexpr (EPI != kEpiMask) {
+        if (warp >= 2)
+            for (int c = tid - 64; c < BN; c += kTmThreads - 64) bias_s[c] = __ldg(bias + n0 + c);
+    }
+    constexpr int kMaskHalf = BN / 16 > 8 ? 8 : BN / 16;                 // chunks of 16 columns held at once
+    int4 mreg[kMaskHalf][2];
+    const int64_t mrow = (int64_t)(m0 + warp * 32 + lane) * ldc + n0;
+    if constexpr (EPI == kEpiMask) {
+#pragma unroll
+        for (int q = 0; q < kMaskHalf; ++q) {
+            mreg[q][0] = __ldg(reinterpret_cast<const int4 *>(mask + mrow + 16 * q));
+            mreg[q][1] = __ldg(reinterpret_cast<const int4 *>(mask + mrow + 16 * q + 8));
+        }
+    }
     __syncwarp();
     const bool done = tc_mbar_wait(accb, 0);
     if (!done && lane == 0) atomicExch(err, 1);
@@ -508,8 +527,17 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
     if (all_done) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = warp * 32 + lane;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {                            // unrolled: the mask chunks stay in registers
+            if constexpr (EPI == kEpiMask) {
+                if (c0 > 0 && (c0 / 16) % kMaskHalf == 0) {                 // BN = 256: the second half
+#pragma unroll
+                    for (int q = 0; q < kMaskHalf; ++q) {
+                        mreg[q][0] = __ldg(reinterpret_cast<const int4 *>(mask + mrow + c0 + 16 * q));
+                        mreg[q][1] = __ldg(reinterpret_cast<const int4 *>(mask + mrow + c0 + 16 * q + 8));
+                    }
+                }
+            }
             uint32_t r[16];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
@@ -519,14 +547,25 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
                            "=r"(r[14]), "=r"(r[15])
                          : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int64_t n = n0 + c0;
             uint32_t o[16];                                              // the 16 results, packed
+            uint32_t mk[8] = {};                                         // this chunk's 16 mask values
+            if constexpr (EPI == kEpiMask) {
+                const int q = (c0 / 16) % kMaskHalf;
+                const int4 a = mreg[q][0], b = mreg[q][1];
+                mk[0] = (uint32_t)a.x; mk[1] = (uint32_t)a.y; mk[2] = (uint32_t)a.z; mk[3] = (uint32_t)a.w;
+                mk[4] = (uint32_t)b.x; mk[5] = (uint32_t)b.y; mk[6] = (uint32_t)b.z; mk[7] = (uint32_t)b.w;
+            }
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
                 float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
                 if constexpr (EPI != kEpiMask) {
-                    v0 += bias[n + j];
-                    v1 += bias[n + j + 1];
+                    v0 += bias_s[c0 + j];
+                    v1 += bias_s[c0 + j + 1];
+                }
+                if constexpr (EPI == kEpiMask) {                             // zero where the ReLU output was 0
+                    const __nv_bfloat162 mw = *reinterpret_cast<const __nv_bfloat162 *>(&mk[j / 2]);
+                    if (!(__bfloat162float(mw.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(mw.y) > 0.f)) v1 = 0.f;
                 }
                 if constexpr (EPI == kEpiHidden) {
                     v0 = fmaxf(v0, 0.f);
@@ -553,16 +592,6 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
             const int row = i / kChunks, ch = i % kChunks;
             int4 v = *reinterpret_cast<const int4 *>(tile + row * kLd + ch * (16 / (int)sizeof(OutT)));
             const int64_t at = (m0 + row) * ldc + n0 + ch * (16 / (int)sizeof(OutT));
-            if constexpr (EPI == kEpiMask) {                             // zero where the ReLU output was 0
-                const int4 mk = *reinterpret_cast<const int4 *>(mask + at);
-                uint32_t *vw = reinterpret_cast<uint32_t *>(&v);
-                const __nv_bfloat162 *mw = reinterpret_cast<const __nv_bfloat162 *>(&mk);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const bool keep0 = __bfloat162float(mw[q].x) > 0.f, keep1 = __bfloat162float(mw[q].y) > 0.f;
-                    vw[q] &= (keep0 ? 0x0000FFFFu : 0u) | (keep1 ? 0xFFFF0000u : 0u);
-                }
-            }
             *reinterpret_cast<int4 *>(static_cast<OutT *>(C) + at) = v;
         }
     }
