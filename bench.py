@@ -298,9 +298,9 @@ def network_gemm_measurement(net, local: int, batch: int = 4096, reps: int = 5) 
     return {"batch": batch, "forward_tflops": fwd, "backward_tflops": bwd, "forward_us": st["fwd_us"],
             "backward_us": st["bwd_us"], "peak_tflops": peak, "peak_source": src, "forward_frac": fwd / peak,
             "backward_frac": bwd / peak,
-            "instruction": "forward and data-gradient products: tcgen05.mma kind::f16 (bf16, fp32 accumulator in "
-                           "tensor memory, TMA operands); weight-gradient products: mma.sync m16n8k16 bf16, split "
-                           "over the batch"}
+            "instruction": "every product: tcgen05.mma kind::f16 (bf16, fp32 accumulator in tensor memory, TMA "
+                           "operands); weight gradients from transposed copies of the layer inputs and output "
+                           "gradients, split over the batch with fp32 vector atomics"}
 
 
 def run_network_gemm_only(args, local: int):

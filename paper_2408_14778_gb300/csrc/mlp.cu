@@ -423,7 +423,7 @@ template <int BN, int EPI>
 __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constant__ CUtensorMap ta,
                                                             const __grid_constant__ CUtensorMap tb, void *C, int64_t ldc,
                                                             int32_t K, const float *bias, const __nv_bfloat16 *mask,
-                                                            int *err) {
+                                                            __nv_bfloat16 *Ct, int64_t ldt, int32_t ksteps, int *err) {
     using S = TmShape<BN>;
     extern __shared__ unsigned char raw[];
     const uint32_t raw_s = tc_smem_u32(raw);
@@ -436,7 +436,9 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
     const uint32_t accb = bars + 8u * (2 * S::kStages);
     const int tid = (int)threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int32_t m0 = (int32_t)blockIdx.y * 128, n0 = (int32_t)blockIdx.x * BN;
-    const int nk = K / kTmK;
+    // reduction steps kt0 .. kt0 + nk - 1: all of them, or (ksteps > 0) block z's share of a split reduction
+    const int kt0 = ksteps > 0 ? (int)blockIdx.z * ksteps : 0;
+    const int nk = ksteps > 0 ? min(ksteps, K / kTmK - kt0) : K / kTmK;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(tslot)),
@@ -455,6 +457,11 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((128u >> 4) << 24);
+    // Launched as a programmatic dependent of the previous product (the host sets the attribute only
+    // there): the set-up above overlaps that kernel's end; nothing global is touched before it completes.
+    // The next product may launch as soon as this one's blocks are all running.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == 0 && lane == 0) {                       // the copier
         int issued = 0;
@@ -465,8 +472,8 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"((uint32_t)S::kStage)
                          : "memory");
             const uint32_t sa = base + (uint32_t)(st * S::kStage);
-            tm_load(sa, &ta, kt * kTmK, m0, full(st));
-            tm_load(sa + S::kA, &tb, kt * kTmK, n0, full(st));
+            tm_load(sa, &ta, (kt0 + kt) * kTmK, m0, full(st));
+            tm_load(sa + S::kA, &tb, (kt0 + kt) * kTmK, n0, full(st));
             ++issued;
         }
         // no copy may still be landing when the block exits
@@ -497,7 +504,7 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
     // While the products run: warps 2 and 3 stage the tile's bias values in shared memory, and every
     // thread loads the ReLU mask of its accumulator row (kEpiMask), so that the epilogue waits on no
     // global load.  (The copy and MMA lanes get here once their loops are done.)
-    if constexpr (EPI != kEpiMask) {
+    if constexpr (EPI == kEpiHidden || EPI == kEpiOut) {
         if (warp >= 2)
             for (int c = tid - 64; c < BN; c += kTmThreads - 64) bias_s[c] = __ldg(bias + n0 + c);
     }
@@ -558,7 +565,7 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
                 float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
-                if constexpr (EPI != kEpiMask) {
+                if constexpr (EPI == kEpiHidden || EPI == kEpiOut) {
                     v0 += bias_s[c0 + j];
                     v1 += bias_s[c0 + j + 1];
                 }
@@ -579,6 +586,13 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
                     o[j + 1] = __float_as_uint(v1);
                 }
             }
+            if constexpr (kBf16) {
+                if (Ct) {                                                // the transposed copy: Ct[n][m]
+                    uint16_t *ct = reinterpret_cast<uint16_t *>(Ct) + (int64_t)(n0 + c0) * ldt + m0 + row;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) ct[j * ldt] = (uint16_t)((j & 1) ? (o[j / 2] >> 16) : (o[j / 2] & 0xFFFFu));
+                }
+            }
             int4 *dst = reinterpret_cast<int4 *>(tile + row * kLd + c0);
             constexpr int kVec = kBf16 ? 2 : 4;                          // 16-byte pieces of 16 results
 #pragma unroll
@@ -592,7 +606,11 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
             const int row = i / kChunks, ch = i % kChunks;
             int4 v = *reinterpret_cast<const int4 *>(tile + row * kLd + ch * (16 / (int)sizeof(OutT)));
             const int64_t at = (m0 + row) * ldc + n0 + ch * (16 / (int)sizeof(OutT));
-            *reinterpret_cast<int4 *>(static_cast<OutT *>(C) + at) = v;
+            if constexpr (EPI == kEpiAdd)                                // a split reduction's partial sum
+                atomicAdd(reinterpret_cast<float4 *>(static_cast<float *>(C) + at),
+                          make_float4(__int_as_float(v.x), __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w)));
+            else
+                *reinterpret_cast<int4 *>(static_cast<OutT *>(C) + at) = v;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -601,12 +619,14 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_gemm_tma(const __grid_constan
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
 }
 
-// x [B][n] FP32 -> xp [Bp][np] BF16, zero outside.
-__global__ void k_pack_input(const float *x, int32_t B, int32_t n, __nv_bfloat16 *xp, int64_t Bp, int64_t np) {
+// x [B][n] FP32 -> xp [Bp][np] BF16, zero outside (and its transpose xpt [np][Bp] unless NULL).
+__global__ void k_pack_input(const float *x, int32_t B, int32_t n, __nv_bfloat16 *xp, int64_t Bp, int64_t np,
+                             __nv_bfloat16 *xpt) {
     const int64_t total = Bp * np;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / np, c = i % np;
         xp[i] = __float2bfloat16_rn(r < B && c < n ? x[r * n + c] : 0.f);
+        if (xpt) xpt[c * Bp + r] = xp[i];
     }
 }
 
@@ -620,7 +640,7 @@ __global__ void k_unpack_output(const float *yp, int64_t np, int32_t B, int32_t 
 // Mean squared error: dY = bf16(2 (y - t) / (B n)) on the real entries, 0 elsewhere; *loss += sum (y - t)^2
 // / (B n) (zeroed beforehand).
 __global__ void k_mse(const float *yp, int64_t np, const float *t, int32_t B, int32_t n, int64_t Bp,
-                      __nv_bfloat16 *dy, double *loss) {
+                      __nv_bfloat16 *dy, __nv_bfloat16 *dyt, double *loss) {
     __shared__ double red[32];
     const int64_t total = Bp * np;
     const double scale = 1.0 / ((double)B * n);
@@ -633,6 +653,7 @@ __global__ void k_mse(const float *yp, int64_t np, const float *t, int32_t B, in
             part += (double)d * d;
         }
         dy[i] = __float2bfloat16_rn((float)(2.0 * scale) * d);
+        if (dyt) dyt[c * Bp + r] = dy[i];                     // the transpose [np][Bp], unless NULL
     }
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
@@ -644,17 +665,20 @@ __global__ void k_mse(const float *yp, int64_t np, const float *t, int32_t B, in
     }
 }
 
-// db[c] = sum over the Bp rows of dz[r][c] (one thread per column; rows strided over blockDim.y).
+// db[c] += sum over rows [blockIdx.y * kBiasRows, + kBiasRows) of dz[r][c] (db zeroed beforehand): 32
+// columns per block, the rows strided over blockDim.y = 8, the partial sums added with FP32 atomics.
+constexpr int kBiasRows = 256;
 __global__ void k_bias_grad(const __nv_bfloat16 *dz, int64_t Bp, int64_t np, float *db) {
     __shared__ float red[8][32];
     const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * kBiasRows, r1 = r0 + kBiasRows < Bp ? r0 + kBiasRows : Bp;
     float s = 0.f;
-    for (int64_t r = threadIdx.y; r < Bp; r += blockDim.y) s += __bfloat162float(dz[r * np + c]);
+    for (int64_t r = r0 + threadIdx.y; r < r1; r += blockDim.y) s += __bfloat162float(dz[r * np + c]);
     red[threadIdx.y][threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.y == 0) {
         for (int k = 1; k < (int)blockDim.y; ++k) s += red[k][threadIdx.x];
-        db[c] = s;
+        atomicAdd(db + c, s);
     }
 }
 
@@ -707,6 +731,9 @@ struct cfr_mlp {
     // activations for the largest batch seen: acts[0] input, acts[l] hidden output of layer l - 1
     int64_t cap = 0;
     std::vector<__nv_bfloat16 *> acts, grads;   // grads[l]: dL/dZ of layer l (BF16, [cap][pdims[l + 1]])
+    // their transposes ([pdims[l]][Bp] and [pdims[l + 1]][Bp], row length the padded batch of the pass),
+    // written in training passes on the TMA path: the K-major operands of the weight gradients
+    std::vector<__nv_bfloat16 *> acts_t, grads_t;
     float *yp = nullptr;
     int64_t last_batch = 0;          // real rows of the last forward or backward pass
     bool have_dz = false;            // grads[] hold the last backward pass's output gradients
@@ -714,6 +741,7 @@ struct cfr_mlp {
     double fwd_flops = 0, bwd_flops = 0;
     bool fwd_timed = false, bwd_timed = false;
     int32_t path = 2;                // cfr_mlp_set_tensor_path: 0 mma.sync, 1 tcgen05, 2 (default) mixed
+    mutable bool pdl_next = false;   // the last operation queued by a pass was a product kernel
     int *d_err = nullptr;            // set by a tcgen05 kernel whose mbarrier wait gave up
     std::string err;
     bool poisoned = false;
@@ -728,7 +756,7 @@ struct cfr_mlp {
         int32_t path = -1;
         bool seen = false;           // the key has run once directly
         double flops = 0;            // the pass's multiply-add work, times two
-    } gfwd, gbwd;
+    } gfwd, gfwd_train, gbwd;
 };
 
 namespace {
@@ -777,16 +805,17 @@ int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 1
 
 cfr_status ensure_batch(cfr_mlp *m, int64_t Bp) {
     if (Bp <= m->cap) return CFR_OK;
-    for (auto *a : m->acts) cudaFree(a);
-    for (auto *a : m->grads) cudaFree(a);
+    for (auto *v : {&m->acts, &m->grads, &m->acts_t, &m->grads_t})
+        for (auto *a : *v) cudaFree(a);
     cudaFree(m->yp);
-    m->acts.assign((size_t)m->L, nullptr);
-    m->grads.assign((size_t)m->L, nullptr);
+    for (auto *v : {&m->acts, &m->grads, &m->acts_t, &m->grads_t}) v->assign((size_t)m->L, nullptr);
     m->yp = nullptr;
     m->cap = 0;
     for (int l = 0; l < m->L; ++l) {
         MCK(cudaMalloc(&m->acts[(size_t)l], sizeof(__nv_bfloat16) * (size_t)(Bp * m->pdims[(size_t)l])));
         MCK(cudaMalloc(&m->grads[(size_t)l], sizeof(__nv_bfloat16) * (size_t)(Bp * m->pdims[(size_t)l + 1])));
+        MCK(cudaMalloc(&m->acts_t[(size_t)l], sizeof(__nv_bfloat16) * (size_t)(Bp * m->pdims[(size_t)l])));
+        MCK(cudaMalloc(&m->grads_t[(size_t)l], sizeof(__nv_bfloat16) * (size_t)(Bp * m->pdims[(size_t)l + 1])));
     }
     MCK(cudaMalloc(&m->yp, sizeof(float) * (size_t)(Bp * m->pdims[(size_t)m->L])));
     m->cap = Bp;
@@ -814,13 +843,17 @@ cudaError_t gemm_tc(cudaStream_t st, int *err, const __nv_bfloat16 *A, int64_t l
 template <bool AKM, bool BKM, int EPI>
 cudaError_t gemm(const cfr_mlp *m, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, void *C,
                  int64_t ldc, int64_t M, int64_t N, int64_t K, const float *bias, const __nv_bfloat16 *mask) {
-    if (m->path == 1) return gemm_tc<AKM, BKM, EPI>(m->stream, m->d_err, A, lda, B, ldb, C, ldc, M, N, K, bias, mask);
+    if (m->path == 1) {
+        m->pdl_next = true;
+        return gemm_tc<AKM, BKM, EPI>(m->stream, m->d_err, A, lda, B, ldb, C, ldc, M, N, K, bias, mask);
+    }
     const int64_t tiles = (N / kBN) * (M / kBM), steps = K / kBK;
     int64_t split = 1;
     if constexpr (EPI == kEpiStore) split = std::min<int64_t>((2 * m->sms + tiles - 1) / tiles, steps / 8);
     if (split > 1) {
         const int32_t ksteps = (int32_t)((steps + split - 1) / split);
         split = (steps + ksteps - 1) / ksteps;
+        m->pdl_next = false;                // a memset comes next: the product after it waits in full
         for (int64_t r = 0; r < M; ++r) {   // C's rows are ldc apart: zero them (one call when contiguous)
             if (ldc == N) {
                 const cudaError_t e = cudaMemsetAsync(C, 0, sizeof(float) * (size_t)(M * N), m->stream);
@@ -832,10 +865,12 @@ cudaError_t gemm(const cfr_mlp *m, const __nv_bfloat16 *A, int64_t lda, const __
         }
         const dim3 grid((unsigned)(N / kBN), (unsigned)(M / kBM), (unsigned)split);
         k_gemm<AKM, BKM, kEpiAdd><<<grid, kThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask, ksteps);
+        m->pdl_next = true;
         return cudaGetLastError();
     }
     const dim3 grid((unsigned)(N / kBN), (unsigned)(M / kBM));
     k_gemm<AKM, BKM, EPI><<<grid, kThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, (int32_t)K, bias, mask, 0);
+    m->pdl_next = true;
     return cudaGetLastError();
 }
 
@@ -869,10 +904,31 @@ bool encode_operand(CUtensorMap *map, const __nv_bfloat16 *g, int64_t rows, int6
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// k_gemm_tma launched on m->stream, as a programmatic dependent of the previous launch when that was a
+// product kernel of the same pass (m->pdl_next).
+template <int BN, int EPI>
+cudaError_t launch_tma(const cfr_mlp *m, dim3 grid, const CUtensorMap &ta, const CUtensorMap &tb, void *C, int64_t ldc,
+                       int32_t K, const float *bias, const __nv_bfloat16 *mask, __nv_bfloat16 *Ct = nullptr,
+                       int64_t ldt = 0, int32_t ksteps = 0) {
+    cudaLaunchConfig_t c = {};
+    c.gridDim = grid;
+    c.blockDim = dim3(kTmThreads);
+    c.dynamicSmemBytes = TmShape<BN>::kSmem;
+    c.stream = m->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = at;
+    c.numAttrs = m->pdl_next ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&c, k_gemm_tma<BN, EPI>, ta, tb, C, ldc, K, bias, mask, Ct, ldt, ksteps, m->d_err);
+    m->pdl_next = true;
+    return e;
+}
+
 // The forward product on tcgen05 with TMA operands: BN = 256 where N allows, else 128.
 template <int EPI>
 cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bfloat16 *W, void *C, int64_t M, int64_t N,
-                         int64_t K, const float *bias, const __nv_bfloat16 *mask = nullptr) {
+                         int64_t K, const float *bias, const __nv_bfloat16 *mask = nullptr, __nv_bfloat16 *Ct = nullptr) {
     CUtensorMap ta, tb;
     // 256-wide tiles where they still give two blocks per SM, else 128-wide (the FP32 output tile of the
     // last layer takes the 128-wide shape, whose stages can hold it for the epilogue)
@@ -887,7 +943,7 @@ cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bf
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_gemm_tma<128, EPI><<<grid, kTmThreads, TmShape<128>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, mask, m->d_err);
+        return launch_tma<128, EPI>(m, grid, ta, tb, C, N, (int32_t)K, bias, mask, Ct, M);
     } else if (bn == 256) {
         static bool attr = false;
         if (!attr) {
@@ -896,7 +952,7 @@ cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bf
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_gemm_tma<256, EPI><<<grid, kTmThreads, TmShape<256>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, mask, m->d_err);
+        return launch_tma<256, EPI>(m, grid, ta, tb, C, N, (int32_t)K, bias, mask, Ct, M);
     } else {
         static bool attr = false;
         if (!attr) {
@@ -905,9 +961,34 @@ cudaError_t gemm_fwd_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bf
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_gemm_tma<128, EPI><<<grid, kTmThreads, TmShape<128>::kSmem, m->stream>>>(ta, tb, C, N, (int32_t)K, bias, mask, m->d_err);
+        return launch_tma<128, EPI>(m, grid, ta, tb, C, N, (int32_t)K, bias, mask, Ct, M);
     }
-    return cudaGetLastError();
+}
+
+// A weight gradient on tcgen05 with TMA operands: C [M][N] (FP32) = A [M][K] B [N][K]^T with both operands
+// K-major (the transposed output gradient [out][batch] and the transposed layer input [in][batch]), the
+// reduction over the batch split over enough blocks for two per SM, each adding its partial tile into C
+// (zeroed first) with FP32 vector atomics.
+cudaError_t gemm_dw_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int64_t M, int64_t N,
+                        int64_t K) {
+    CUtensorMap ta, tb;
+    if (!encode_operand(&ta, A, M, K, 128) || !encode_operand(&tb, B, N, K, 128)) return cudaErrorInvalidValue;
+    const int64_t tiles = (N / 128) * (M / 128), steps = K / kTmK;
+    int64_t split = std::max<int64_t>(1, std::min<int64_t>((2 * m->sms + tiles - 1) / tiles, steps));
+    const int64_t ksteps = (steps + split - 1) / split;
+    split = (steps + ksteps - 1) / ksteps;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gemm_tma<128, kEpiAdd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   TmShape<128>::kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaError_t e = cudaMemsetAsync(C, 0, sizeof(float) * (size_t)(M * N), m->stream);
+    if (e != cudaSuccess) return e;
+    m->pdl_next = false;
+    const dim3 grid((unsigned)(N / 128), (unsigned)(M / 128), (unsigned)split);
+    return launch_tma<128, kEpiAdd>(m, grid, ta, tb, C, N, (int32_t)K, nullptr, nullptr, nullptr, 0, (int32_t)ksteps);
 }
 
 // The transposed BF16 weights of every layer from the BF16 mirror.
@@ -933,15 +1014,18 @@ cfr_status check_err(cfr_mlp *m) {
 }
 
 // The forward pass over Bp padded rows (input already packed into acts[0]); output in yp.  Launches on
-// m->stream.
-cfr_status forward_padded(cfr_mlp *m, int64_t Bp, double *flops) {
+// m->stream.  train (TMA path): the hidden outputs' transposes too.
+cfr_status forward_impl(cfr_mlp *m, int64_t Bp, double *flops, bool train) {
     double f = 0;
+    m->pdl_next = false;
     for (int l = 0; l < m->L; ++l) {
         const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
         const __nv_bfloat16 *W = m->pb + m->w_off[(size_t)l];
         const float *b = m->p + m->b_off[(size_t)l];
         if (m->path != 0) {   // tcgen05 with TMA operands
-            if (l + 1 < m->L) MCK(gemm_fwd_tma<kEpiHidden>(m, m->acts[(size_t)l], W, m->acts[(size_t)l + 1], Bp, N, K, b));
+            if (l + 1 < m->L)
+                MCK(gemm_fwd_tma<kEpiHidden>(m, m->acts[(size_t)l], W, m->acts[(size_t)l + 1], Bp, N, K, b, nullptr,
+                                             train && m->path == 2 ? m->acts_t[(size_t)l + 1] : nullptr));
             else MCK(gemm_fwd_tma<kEpiOut>(m, m->acts[(size_t)l], W, m->yp, Bp, N, K, b));
         } else if (l + 1 < m->L) {
             MCK((gemm<true, true, kEpiHidden>(m, m->acts[(size_t)l], K, W, K, m->acts[(size_t)l + 1], N, Bp, N, K, b, nullptr)));
@@ -953,22 +1037,28 @@ cfr_status forward_padded(cfr_mlp *m, int64_t Bp, double *flops) {
     *flops = f;
     return CFR_OK;
 }
+cfr_status forward_padded(cfr_mlp *m, int64_t Bp, double *flops) { return forward_impl(m, Bp, flops, false); }
+cfr_status forward_train(cfr_mlp *m, int64_t Bp, double *flops) { return forward_impl(m, Bp, flops, true); }
 
 // The backward products over Bp padded rows (the output gradient already in grads[L - 1]): every weight
 // gradient and every masked data gradient.  Launches on m->stream.
 cfr_status backward_products(cfr_mlp *m, int64_t Bp, double *flops) {
     double fb = 0;
+    m->pdl_next = false;
     for (int l = m->L - 1; l >= 0; --l) {
         const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
         const __nv_bfloat16 *dz = m->grads[(size_t)l];
         // dW[o][i] = sum_b dZ[b][o] X[b][i]
-        MCK((gemm<false, false, kEpiStore>(m, dz, N, m->acts[(size_t)l], K, m->g + m->w_off[(size_t)l], K, N, K, Bp,
-                                           nullptr, nullptr)));
+        if (m->path == 2)   // tcgen05 with TMA operands: the transposes dZ^T [out][batch] and X^T [in][batch]
+            MCK(gemm_dw_tma(m, m->grads_t[(size_t)l], m->acts_t[(size_t)l], m->g + m->w_off[(size_t)l], N, K, Bp));
+        else
+            MCK((gemm<false, false, kEpiStore>(m, dz, N, m->acts[(size_t)l], K, m->g + m->w_off[(size_t)l], K, N, K, Bp,
+                                               nullptr, nullptr)));
         fb += 2.0 * (double)N * K * Bp;
         if (l > 0) {   // dZ of layer l - 1 = (dZ W) masked where its ReLU output was 0
             if (m->path == 2)   // tcgen05 with TMA operands: dZ [batch][out] and W^T [in][out], both K-major
                 MCK(gemm_fwd_tma<kEpiMask>(m, dz, m->pbt + m->w_off[(size_t)l], m->grads[(size_t)l - 1], Bp, K, N, nullptr,
-                                           m->acts[(size_t)l]));
+                                           m->acts[(size_t)l], m->grads_t[(size_t)l - 1]));
             else
                 MCK((gemm<true, false, kEpiMask>(m, dz, N, m->pb + m->w_off[(size_t)l], K, m->grads[(size_t)l - 1], K, Bp,
                                                  K, N, nullptr, m->acts[(size_t)l])));
@@ -1128,7 +1218,8 @@ cfr_status cfr_mlp_forward(cfr_mlp *m, const float *x, int32_t batch, float *y) 
     MDeviceGuard dg(m->device);
     const int64_t Bp = pad_to(batch, kPad);
     if ((st = ensure_batch(m, Bp)) != CFR_OK) return st;
-    k_pack_input<<<grid_for(Bp * m->pdims[0]), 256, 0, m->stream>>>(x, batch, m->dims[0], m->acts[0], Bp, m->pdims[0]);
+    k_pack_input<<<grid_for(Bp * m->pdims[0]), 256, 0, m->stream>>>(x, batch, m->dims[0], m->acts[0], Bp, m->pdims[0],
+                                                                   nullptr);
     MCK(cudaGetLastError());
     MCK(cudaEventRecord(m->ev[0], m->stream));
     if ((st = run_pass(m, &m->gfwd, forward_padded, Bp, &m->fwd_flops)) != CFR_OK) return st;
@@ -1150,14 +1241,17 @@ cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int
     const int64_t Bp = pad_to(batch, kPad);
     if ((st = ensure_batch(m, Bp)) != CFR_OK) return st;
     const int L = m->L;
-    k_pack_input<<<grid_for(Bp * m->pdims[0]), 256, 0, m->stream>>>(x, batch, m->dims[0], m->acts[0], Bp, m->pdims[0]);
+    const bool tr = m->path == 2;                         // the weight gradients read transposed operands
+    k_pack_input<<<grid_for(Bp * m->pdims[0]), 256, 0, m->stream>>>(x, batch, m->dims[0], m->acts[0], Bp, m->pdims[0],
+                                                                   tr ? m->acts_t[0] : nullptr);
     MCK(cudaGetLastError());
     double f = 0;
-    if ((st = run_pass(m, &m->gfwd, forward_padded, Bp, &f)) != CFR_OK) return st;
+    if ((st = run_pass(m, &m->gfwd_train, forward_train, Bp, &f)) != CFR_OK) return st;
     if (loss) MCK(cudaMemsetAsync(loss, 0, sizeof(double), m->stream));
     const int64_t nL = m->pdims[(size_t)L];
-    k_mse<<<grid_for(Bp * nL), 256, 0, m->stream>>>(m->yp, nL, target, batch, m->dims[(size_t)L], Bp,
-                                                    m->grads[(size_t)L - 1], loss);
+    // few blocks: each adds its part of the loss with one FP64 atomic
+    k_mse<<<std::min(grid_for(Bp * nL), 2 * m->sms), 256, 0, m->stream>>>(m->yp, nL, target, batch, m->dims[(size_t)L], Bp,
+                                                    m->grads[(size_t)L - 1], tr ? m->grads_t[(size_t)L - 1] : nullptr, loss);
     MCK(cudaGetLastError());
     MCK(cudaEventRecord(m->ev[2], m->stream));
     double fb = 0;
@@ -1169,7 +1263,9 @@ cfr_status cfr_mlp_backward(cfr_mlp *m, const float *x, const float *target, int
     m->have_dz = true;
     for (int l = 0; l < L; ++l) {
         const int64_t N = m->pdims[(size_t)l + 1];
-        k_bias_grad<<<(unsigned)(N / 32), dim3(32, 8), 0, m->stream>>>(m->grads[(size_t)l], Bp, N, m->g + m->b_off[(size_t)l]);
+        MCK(cudaMemsetAsync(m->g + m->b_off[(size_t)l], 0, sizeof(float) * (size_t)N, m->stream));
+        k_bias_grad<<<dim3((unsigned)(N / 32), (unsigned)((Bp + kBiasRows - 1) / kBiasRows)), dim3(32, 8), 0, m->stream>>>(
+            m->grads[(size_t)l], Bp, N, m->g + m->b_off[(size_t)l]);
         MCK(cudaGetLastError());
     }
     return CFR_OK;
@@ -1269,11 +1365,11 @@ void cfr_mlp_free(cfr_mlp *m) {
     for (void *a : {(void *)m->p, (void *)m->g, (void *)m->m1, (void *)m->m2, (void *)m->pb, (void *)m->pbt, (void *)m->yp,
                     (void *)m->d_err})
         if (a) cudaFree(a);
-    for (auto *a : m->acts) if (a) cudaFree(a);
-    for (auto *a : m->grads) if (a) cudaFree(a);
+    for (auto *v : {&m->acts, &m->grads, &m->acts_t, &m->grads_t})
+        for (auto *a : *v) if (a) cudaFree(a);
     for (cudaEvent_t ev : m->ev)
         if (ev) cudaEventDestroy(ev);
-    for (cfr_mlp::PassGraph *g : {&m->gfwd, &m->gbwd})
+    for (cfr_mlp::PassGraph *g : {&m->gfwd, &m->gfwd_train, &m->gbwd})
         if (g->exec) cudaGraphExecDestroy(g->exec);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     delete m;
