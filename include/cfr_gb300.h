@@ -422,12 +422,12 @@ cfr_status cfr_mlp_adam(cfr_mlp *m, float lr, float beta1, float beta2, float ep
  * skip.  Synchronises. */
 cfr_status cfr_mlp_gemm_stats(cfr_mlp *m, double *fwd_us, double *fwd_flops, double *bwd_us, double *bwd_flops);
 
-/* The instructions the products run on: 2 (default) the forward and the data-gradient products on
- * tcgen05.mma (accumulator in tensor memory, TMA-loaded operands; the data gradients read a transposed
- * BF16 copy of the weights) and the weight-gradient products on the warp-level mma.sync kernel, split over
- * the batch where their output tiles are few - the fastest measured for each; 0 mma.sync for every product;
- * 1 tcgen05.mma for every product (with per-thread operand copies).  Results agree within the rounding of
- * FP32 accumulation.  Takes effect for later calls. */
+/* The instructions the products run on: 2 (default) every product on tcgen05.mma (accumulator in tensor
+ * memory, TMA-loaded operands; the data gradients read a transposed BF16 copy of the weights, the weight
+ * gradients transposed copies of the layer inputs and output gradients written by the training pass, their
+ * batch reduction split over blocks); 0 mma.sync for every product; 1 tcgen05.mma for every product with
+ * per-thread operand copies.  Results agree within the rounding of FP32 accumulation.  Takes effect for
+ * later calls. */
 cfr_status cfr_mlp_set_tensor_path(cfr_mlp *m, int32_t path);
 
 /* Waits for the network's queued work; CFR_ERR_TIMEOUT if a tensor-core kernel gave up waiting for its

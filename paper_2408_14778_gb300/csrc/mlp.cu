@@ -3,24 +3,24 @@
 //
 // Matrix products: C[M][N] = sum_k A(m, k) B(k, n), BF16 operands and FP32 accumulation, by three
 // kernels (cfr_mlp_set_tensor_path chooses):
-//   k_gemm_tma  forward products on the 5th-generation tensor cores (tcgen05.mma, accumulator in tensor
-//               memory) with TMA-loaded, 128-byte-swizzled operands and warp-specialised copy / MMA
-//               issue (both operands of the forward product are K-major);
+//   k_gemm_tma  the 5th-generation tensor cores (tcgen05.mma, accumulator in tensor memory) with
+//               TMA-loaded, 128-byte-swizzled, K-major operands and warp-specialised copy / MMA issue;
 //   k_gemm      the warp-level kernel (mma.sync m16n8k16, 128 x 128 x 32 block tiles staged through
 //               shared memory by cp.async in a three-stage pipeline, eight warps of 64 x 32), any
 //               operand orientation;
 //   k_gemm_tc   tcgen05.mma with operands copied by every thread with cp.async into the canonical
 //               no-swizzle layout, any orientation.
-// The default (path 2) runs the forward and the data-gradient products on k_gemm_tma (the latter with a
-// transposed BF16 copy of the weights as its K-major operand) and the weight-gradient products on
-// k_gemm, split over the batch where they have few output tiles; path 0 is k_gemm everywhere, path 1
-// tcgen05 everywhere.  Each operand is read from global memory in its
-// stored orientation - the reduction index contiguous ("K-major") or the output index contiguous - and
-// ldmatrix (with .trans for the second case) builds the fragments, so the three products of a layer
-// need no transposed copies:
+// The three products of a layer:
 //   forward        Z[b][o]  = sum_i X[b][i] W[o][i]      A K-major, B K-major ([o][i])
 //   weight grad    dW[o][i] = sum_b dZ[b][o] X[b][i]     A and B with the output index contiguous
 //   data grad      dX[b][i] = sum_o dZ[b][o] W[o][i]     A K-major, B with the output index contiguous
+// The default (path 2) runs all three on k_gemm_tma, whose TMA boxes need K-major operands: the data
+// gradient reads a transposed BF16 copy of the weights (kept by cfr_mlp_set_params and Adam), and the
+// weight gradient reads transposed copies of the layer input and of the output gradient [feature][batch],
+// which a training pass writes beside the row-major ones (the input packing, the loss gradient and the
+// products' epilogues); its reduction over the batch is split over blocks that add their partial tiles
+// with FP32 vector atomics.  Paths 0 and 1 read every operand in its stored orientation (ldmatrix with
+// .trans, or the tcgen05 descriptor's major bits) and need no transposed copies.
 // Every dimension is padded to a multiple of 128 (the batch too): padded weights and inputs are zero and
 // padded rows of the output gradient are zero, so padding never reaches a real result.
 #include <cuda.h>   // CUtensorMap and its enums; the encoder is fetched through the runtime's entry point
