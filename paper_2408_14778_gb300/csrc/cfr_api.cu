@@ -56,6 +56,9 @@ struct cfr_solver {
     cudaStream_t cap = nullptr;      // private, for graph capture
     cudaStream_t side = nullptr;     // private: the own-reach branch of the captured iteration
     cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr};   // per pass of an iteration
+    cudaEvent_t deep[2] = {nullptr, nullptr};             // split update: the deep infosets' regrets are complete
+    cudaEvent_t upd[2] = {nullptr, nullptr};              // split update: the deep infosets' update is done
+    int prio_least = 0, prio_greatest = 0;                // the device's stream priority range
     double *wts = nullptr;                                // linear / discounted CFR weights (k_weights)
     // sizes
     int64_t N = 0, Nd = 0, Nt = 0, Q = 0;
@@ -205,6 +208,7 @@ DevTree<real> dev_tree(cfr_solver *s) {
 // operation on the stream (a memset, an event) ends the chain (`cut`).
 struct Launcher {
     bool pdl = false;
+    int prio = 0;                                        // launch priority (cudaLaunchAttributePriority) if nonzero
     cudaStream_t chained[2] = {nullptr, nullptr};   // streams whose last operation was a kernel
     int nchained = 0;
     bool follows_kernel(cudaStream_t st) const {
@@ -223,11 +227,18 @@ struct Launcher {
         c.blockDim = dim3((unsigned)block);
         c.dynamicSmemBytes = smem;
         c.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchAttribute at[2];
+        unsigned n = 0;
+        if (pdl && follows_kernel(st)) {
+            at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[n++].val.programmaticStreamSerializationAllowed = 1;
+        }
+        if (prio != 0) {
+            at[n].id = cudaLaunchAttributePriority;
+            at[n++].val.priority = prio;
+        }
         c.attrs = at;
-        c.numAttrs = pdl && follows_kernel(st) ? 1 : 0;
+        c.numAttrs = n;
         const cudaError_t e = cudaLaunchKernelEx(&c, k, args...);
         if (!follows_kernel(st) && nchained < 2) chained[nchained++] = st;
         return e;
@@ -331,16 +342,28 @@ cfr_status setup_stream_na(cfr_solver *s, int gi, int sms) {
 
 // FP32 update of variant V: one thread per infoset (k_update_rows, instantiated for the largest action
 // count) and one block per infoset of more than 32 actions.
+// The update of the player infosets [h0, h1) (up to 32 actions) and, with wide, of the wider ones.
 template <int V>
-cfr_status launch_update(Launcher &go, cfr_solver *s, const DevTree<float> &t, cudaStream_t st, int32_t linear) {
-    if (s->Hp > 0) {
-        const int g = nblocks(s->Hp);
-        if (s->hp_na <= 3) CK(go(k_update_rows<3, V>, g, kBlock, 0, st, t, s->Hp, linear));
-        else if (s->hp_na <= 5) CK(go(k_update_rows<5, V>, g, kBlock, 0, st, t, s->Hp, linear));
-        else CK(go(k_update_rows<8, V>, g, kBlock, 0, st, t, s->Hp, linear));
+cfr_status launch_update(Launcher &go, cfr_solver *s, const DevTree<float> &t, cudaStream_t st, int32_t linear,
+                         int32_t h0, int32_t h1, bool wide) {
+    if (h1 > h0) {
+        const int g = nblocks(h1 - h0);
+        if (s->hp_na <= 3) CK(go(k_update_rows<3, V>, g, kBlock, 0, st, t, h0, h1, linear));
+        else if (s->hp_na <= 5) CK(go(k_update_rows<5, V>, g, kBlock, 0, st, t, h0, h1, linear));
+        else CK(go(k_update_rows<8, V>, g, kBlock, 0, st, t, h0, h1, linear));
     }
-    if (s->nwide_h > 0) CK(go(k_update_list<V>, s->nwide_h, kWideBlock, 0, st, t, (const int32_t *)s->wide_h, linear));
+    if (wide && s->nwide_h > 0)
+        CK(go(k_update_list<V>, s->nwide_h, kWideBlock, 0, st, t, (const int32_t *)s->wide_h, linear));
     return CFR_OK;
+}
+cfr_status launch_update_any(Launcher &go, cfr_solver *s, const DevTree<float> &t, cudaStream_t st, int32_t linear,
+                             int32_t h0, int32_t h1, bool wide) {
+    switch (s->cfg.variant) {
+    case CFR_VANILLA: return launch_update<CFRV_VANILLA>(go, s, t, st, linear, h0, h1, wide);
+    case CFR_PLUS: return launch_update<CFRV_PLUS>(go, s, t, st, linear, h0, h1, wide);
+    case CFR_LINEAR: return launch_update<CFRV_LINEAR>(go, s, t, st, linear, h0, h1, wide);
+    default: return launch_update<CFRV_DISCOUNTED>(go, s, t, st, linear, h0, h1, wide);
+    }
 }
 
 // One full-tree iteration, queued on `st` (captured into the solver's graph).  FP64 mode reduces
@@ -392,6 +415,28 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
     // the other own reaches, depth by depth; in the graph on a branch beside the node passes that forks
     // after the head (whose own reaches they extend) and joins before the update
     const bool branch = ev == nullptr;
+    // Split update (the graph's simultaneous pass with a head): the regrets of the infosets first seen
+    // below the head are complete when the deep bottom-up passes end, so their update runs on the branch
+    // beside the head's bottom-up launch (latency-bound: few bytes, block barriers); the head's infosets'
+    // update follows it.  (Starting the fused depths' infosets right after the fused kernel, beside the
+    // bandwidth-bound bottom-up passes, measured slower.)
+    const bool split = branch && head > 0 && !alt && s->Hp > 0;
+    const int32_t hsplit = split ? s->hlevel[(size_t)head] : 0;
+    const int32_t linear = s->cfg.avg_weight == CFR_AVG_LINEAR, variant = s->cfg.variant;
+    // the deep infosets' update on the branch, after its own reaches and the event below
+    auto deep_update = [&]() -> cfr_status {
+        if (first && variant == CFR_DISCOUNTED)
+            CK(go(k_weights, 1, 1, 0, st, (const int64_t *)s->d_iter, s->wts, s->cfg.dcfr_alpha, s->cfg.dcfr_beta,
+                  s->cfg.dcfr_gamma));
+        CK(cudaEventRecord(s->deep[pi], st));
+        CK(cudaStreamWaitEvent(s->side, s->deep[pi], 0));
+        go.cut(s->side);
+        if constexpr (!det) TRY(launch_update_any(go, s, t, s->side, linear, hsplit, s->Hp, false));
+        CK(cudaEventRecord(s->upd[pi], s->side));
+        go.cut(s->side);
+        go.prio = s->prio_greatest;                      // the head's blocks go ahead of its blocks
+        return CFR_OK;
+    };
     cudaStream_t os = st;
     if (branch) {
         os = s->side;
@@ -473,6 +518,7 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         TRY(mark());
     }
     if constexpr (!det) {
+        if (split) TRY(deep_update());
         if (head > 0) {
             const HeadArgs ha = head_args(s, false);
             auto k = s->head_na == 0 ? k_head_bottomup<kStreamNA[0]>
@@ -484,17 +530,18 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         CK(cudaStreamWaitEvent(st, s->join[pi], 0));
         go.cut(st);
     }
-    const int32_t linear = s->cfg.avg_weight == CFR_AVG_LINEAR, variant = s->cfg.variant;
-    if (first && variant == CFR_DISCOUNTED)
+    if (first && variant == CFR_DISCOUNTED && !split)
         CK(go(k_weights, 1, 1, 0, st, (const int64_t *)s->d_iter, s->wts, s->cfg.dcfr_alpha, s->cfg.dcfr_beta,
               s->cfg.dcfr_gamma));
     if constexpr (det) {
         if (s->Hp > 0) CK(go(k_update<real, det>, nblocks(s->Hp), kBlock, 0, st, t, s->Hp, variant, linear));
     } else {
-        if (variant == CFR_VANILLA) TRY(launch_update<CFRV_VANILLA>(go, s, t, st, linear));
-        else if (variant == CFR_PLUS) TRY(launch_update<CFRV_PLUS>(go, s, t, st, linear));
-        else if (variant == CFR_LINEAR) TRY(launch_update<CFRV_LINEAR>(go, s, t, st, linear));
-        else TRY(launch_update<CFRV_DISCOUNTED>(go, s, t, st, linear));
+        go.prio = 0;
+        TRY(launch_update_any(go, s, t, st, linear, 0, split ? hsplit : s->Hp, true));
+        if (split) {
+            CK(cudaStreamWaitEvent(st, s->upd[pi], 0));
+            go.cut(st);
+        }
     }
     TRY(mark());
     return CFR_OK;
@@ -588,6 +635,9 @@ int32_t launches_per_pass(const cfr_solver *s) {
     int32_t n = (r - head) + 1 + (r < s->L);                  // bottom-up depths, fused, update
     for (int32_t l = head; l < s->L; ++l) n += s->hlevel[l + 1] > s->hlevel[l];   // own reaches
     if (head > 0) n += 2;                                     // the head's two launches
+    if (head > 0 && s->cfg.update_mode != CFR_ALTERNATING && s->hlevel[(size_t)head] > 0 &&
+        s->hlevel[(size_t)head] < s->Hp)
+        n += 1;                                               // the update split in two (enqueue_pass)
     for (int32_t l = head; l < r; ++l) {
         n += s->ddepth_children[l] || l == 0;                 // top-down
         if (!det) n += 2 * (s->wlevel[l + 1] > s->wlevel[l]);
@@ -1119,9 +1169,12 @@ cfr_status cfrgb::load_tree_impl(const cfr_game_desc *g, const cfr_config *c, bo
     s->stream = static_cast<cudaStream_t>(cfg.cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&s->prio_least, &s->prio_greatest);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaEventCreateWithFlags(&s->fork[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->deep[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->upd[i], cudaEventDisableTiming);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1544,6 +1597,8 @@ void cfr_free(cfr_solver *s) {
     for (int i = 0; i < 2; ++i) {
         if (s->fork[i]) cudaEventDestroy(s->fork[i]);
         if (s->join[i]) cudaEventDestroy(s->join[i]);
+        if (s->deep[i]) cudaEventDestroy(s->deep[i]);
+        if (s->upd[i]) cudaEventDestroy(s->upd[i]);
     }
     delete s;
 }

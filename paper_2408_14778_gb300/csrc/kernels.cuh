@@ -470,10 +470,10 @@ __device__ __forceinline__ void update_row(const DevTree<float> &t, int32_t h, c
 }
 
 template <int NA, int V>
-__global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t Hp, int32_t linear) {
+__global__ void __launch_bounds__(256) k_update_rows(DevTree<float> t, int32_t h0, int32_t h1, int32_t linear) {
     grid_dependency_wait();
-    const int32_t h = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (h >= Hp) return;
+    const int32_t h = h0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (h >= h1) return;
     if (t.pmask != 6 && !collects(t, t.iplayer[h])) return;      // alternating: the other player's pass
     if (t.qbase[h + 1] - t.qbase[h] > 32) return;
     update_row<NA, V, false>(t, h, update_weights(t, V, linear != 0));
