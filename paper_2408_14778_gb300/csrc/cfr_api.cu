@@ -114,6 +114,8 @@ struct cfr_solver {
     int64_t iteration = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph2 = nullptr;                         // two iterations back to back: no graph-launch gap
+    cudaGraphExec_t graph_exec2 = nullptr;                // between them
     std::vector<std::pair<void *, size_t>> blocks;
     int64_t device_bytes = 0;
     std::string err;
@@ -712,6 +714,15 @@ cfr_status build_graph(cfr_solver *s) {
     if (e != cudaSuccess) { s->poisoned = true; return set_err(s, CFR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)); }
     s->graph = g;
     CK(cudaGraphInstantiate(&s->graph_exec, g, 0));
+    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < 2 && st == CFR_OK; ++i)
+        st = s->cfg.precision == CFR_FP64 ? enqueue_iteration<double>(s, s->cap) : enqueue_iteration<float>(s, s->cap);
+    g = nullptr;
+    e = cudaStreamEndCapture(s->cap, &g);
+    if (st != CFR_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) { s->poisoned = true; return set_err(s, CFR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)); }
+    s->graph2 = g;
+    CK(cudaGraphInstantiate(&s->graph_exec2, g, 0));
     return CFR_OK;
 }
 
@@ -1216,9 +1227,11 @@ cfr_status cfr_iterate(cfr_solver *s, int32_t n) {
     TRY(check_usable(s));
     if (n < 0) return set_err(s, CFR_ERR_INVALID, "n must be >= 0");
     DeviceGuard dg(s->device);
-    for (int32_t i = 0; i < n && s->graph_exec; ++i) {
-        CK(cudaGraphLaunch(s->graph_exec, s->stream));
-        s->kernel_launches += launches_per_iteration(s);
+    for (int32_t i = 0; i < n && s->graph_exec;) {
+        const bool two = i + 1 < n && s->graph_exec2;
+        CK(cudaGraphLaunch(two ? s->graph_exec2 : s->graph_exec, s->stream));
+        s->kernel_launches += (two ? 2 : 1) * launches_per_iteration(s);
+        i += two ? 2 : 1;
     }
     s->iteration += n;
     return CFR_OK;
@@ -1587,6 +1600,8 @@ void cfr_free(cfr_solver *s) {
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
     if (s->br_exec) cudaGraphExecDestroy(s->br_exec);
     if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->graph_exec2) cudaGraphExecDestroy(s->graph_exec2);
+    if (s->graph2) cudaGraphDestroy(s->graph2);
     for (auto &b : s->blocks) {
         if (s->cfg.dev_free) s->cfg.dev_free(b.first, s->cfg.alloc_ctx);
         else cudaFree(b.first);
