@@ -974,7 +974,8 @@ cudaError_t gemm_dw_tma(const cfr_mlp *m, const __nv_bfloat16 *A, const __nv_bfl
     CUtensorMap ta, tb;
     if (!encode_operand(&ta, A, M, K, 128) || !encode_operand(&tb, B, N, K, 128)) return cudaErrorInvalidValue;
     const int64_t tiles = (N / 128) * (M / 128), steps = K / kTmK;
-    int64_t split = std::max<int64_t>(1, std::min<int64_t>((2 * m->sms + tiles - 1) / tiles, steps));
+    // at most two blocks per SM in all (one wave of the two that fit): a block more starts a second wave
+    int64_t split = std::max<int64_t>(1, std::min<int64_t>((2 * m->sms) / tiles, steps));
     const int64_t ksteps = (steps + split - 1) / split;
     split = (steps + ksteps - 1) / ksteps;
     static bool attr = false;
