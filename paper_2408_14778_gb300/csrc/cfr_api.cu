@@ -25,6 +25,7 @@ namespace {
 thread_local std::string g_thread_err;
 
 constexpr int kBlock = 256;
+constexpr int kGraphIters = 4;   // iterations captured in the solver's second graph (cfr_iterate replays it first)
 constexpr int kWideBlock = 1024;   // nodes and infosets with more than 32 actions: one block each
 constexpr int32_t kFuseAuto = 2;   // fused depths when cfr_config.fuse_levels < 0
 constexpr int32_t kStreamMinNodes = 32768;   // FP32 bottom-up depths this large use k_bottomup_stream
@@ -114,8 +115,8 @@ struct cfr_solver {
     int64_t iteration = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
-    cudaGraph_t graph2 = nullptr;                         // two iterations back to back: no graph-launch gap
-    cudaGraphExec_t graph_exec2 = nullptr;                // between them
+    cudaGraph_t graph2 = nullptr;                         // kGraphIters iterations back to back: no graph-launch
+    cudaGraphExec_t graph_exec2 = nullptr;                // gap between them
     std::vector<std::pair<void *, size_t>> blocks;
     int64_t device_bytes = 0;
     std::string err;
@@ -715,7 +716,7 @@ cfr_status build_graph(cfr_solver *s) {
     s->graph = g;
     CK(cudaGraphInstantiate(&s->graph_exec, g, 0));
     CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < 2 && st == CFR_OK; ++i)
+    for (int i = 0; i < kGraphIters && st == CFR_OK; ++i)
         st = s->cfg.precision == CFR_FP64 ? enqueue_iteration<double>(s, s->cap) : enqueue_iteration<float>(s, s->cap);
     g = nullptr;
     e = cudaStreamEndCapture(s->cap, &g);
@@ -1228,10 +1229,10 @@ cfr_status cfr_iterate(cfr_solver *s, int32_t n) {
     if (n < 0) return set_err(s, CFR_ERR_INVALID, "n must be >= 0");
     DeviceGuard dg(s->device);
     for (int32_t i = 0; i < n && s->graph_exec;) {
-        const bool two = i + 1 < n && s->graph_exec2;
-        CK(cudaGraphLaunch(two ? s->graph_exec2 : s->graph_exec, s->stream));
-        s->kernel_launches += (two ? 2 : 1) * launches_per_iteration(s);
-        i += two ? 2 : 1;
+        const bool many = i + kGraphIters <= n && s->graph_exec2;
+        CK(cudaGraphLaunch(many ? s->graph_exec2 : s->graph_exec, s->stream));
+        s->kernel_launches += (many ? kGraphIters : 1) * launches_per_iteration(s);
+        i += many ? kGraphIters : 1;
     }
     s->iteration += n;
     return CFR_OK;
