@@ -629,7 +629,7 @@ def workload_config(args, g, info=None):
                  infoset_actions=info["num_q"], levels=info["num_levels"], device_bytes=info["device_bytes"],
                  fused_from_depth=info["fused_from_depth"], fused_tiles=info["fused_tiles"],
                  tail_kernel=info["tail_kernel"],
-                 head_depths=info["head_depths"],
+                 head_depths=info["head_depths"], pair_depth=info["pair_depth"],
                  kernels_per_iteration=info["kernels_per_iteration"])
     return c
 
@@ -713,7 +713,8 @@ def run_ours(args, world, rank, local):
         info["tail_kernel"], "k_fused")
     kernel_of = {cfr.CFR_PHASE_TOPDOWN: "k_topdown", cfr.CFR_PHASE_BOTTOMUP: "k_bottomup",
                  cfr.CFR_PHASE_FUSED: tail_name if nfused == 2 else "k_fused",
-                 cfr.CFR_PHASE_OWN: "k_own",
+                 cfr.CFR_PHASE_OWN: "k_own", cfr.CFR_PHASE_TOPDOWN_PAIR: "k_pair_topdown",
+                 cfr.CFR_PHASE_BOTTOMUP_PAIR: "k_pair_bottomup",
                  cfr.CFR_PHASE_UPDATE: "k_update_rows" if args.precision == "fp32" else "k_update"}
     k = int(np.argmax(us))
     peak, peak_src = measured_hbm_peak()

@@ -60,7 +60,8 @@ enum { CFR_SIMULTANEOUS = 0, CFR_ALTERNATING = 1 };
  * and LINEAR for CFR+.  Linear and discounted CFR fix their own weights (T, T^gamma). */
 enum { CFR_AVG_DEFAULT = -1, CFR_AVG_UNIFORM = 0, CFR_AVG_LINEAR = 1 };
 /* Phases of one iteration reported by cfr_phase_times. */
-enum { CFR_PHASE_TOPDOWN = 0, CFR_PHASE_BOTTOMUP = 1, CFR_PHASE_FUSED = 2, CFR_PHASE_UPDATE = 3, CFR_PHASE_OWN = 4 };
+enum { CFR_PHASE_TOPDOWN = 0, CFR_PHASE_BOTTOMUP = 1, CFR_PHASE_FUSED = 2, CFR_PHASE_UPDATE = 3, CFR_PHASE_OWN = 4,
+       CFR_PHASE_TOPDOWN_PAIR = 5, CFR_PHASE_BOTTOMUP_PAIR = 6 };
 
 typedef struct cfr_solver cfr_solver;   /* opaque; owned by the library */
 
@@ -78,7 +79,9 @@ typedef struct {
     const double *utility;              /* [num_nodes x 2] u(t, 1), u(t, 2) row-major; read at terminals */
 } cfr_game_desc;
 
-typedef void *(*cfr_alloc_fn)(size_t bytes, void *ctx);   /* returns NULL on failure */
+/* Returns NULL on failure, else memory aligned to 256 bytes as cudaMalloc's is (the kernels' bulk copies
+ * need 16-byte aligned arrays; a block that is not 256-byte aligned fails the call with CFR_ERR_INVALID). */
+typedef void *(*cfr_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*cfr_free_fn)(void *ptr, void *ctx);
 
 typedef struct {
@@ -93,9 +96,13 @@ typedef struct {
     void *alloc_ctx;
     int32_t fuse_levels;    /* FP32 mode: the deepest depths run as one kernel, tile by tile in shared
                                memory, with their reaches and values kept on chip.  -1 = automatic
-                               (default), 0 or 1 = none (one kernel per depth and pass), k >= 2 = at
-                               most k depths (fewer where a subtree exceeds a tile or a node has more
-                               than 32 actions).  Ignored in FP64 mode. */
+                               (default): the last two depths in one streamed pass, and the two depths
+                               above them as a pair (one top-down and one bottom-up launch for both, see
+                               cfr_info.pair_depth) where they lie below the head launches, hold no node
+                               of more than 32 actions and the upper one has at least 8192 decision
+                               nodes; 0 or 1 = none (one kernel per depth and pass); k >= 2 = at most k
+                               depths (fewer where a subtree exceeds a tile or a node has more than 32
+                               actions), no pair.  Ignored in FP64 mode. */
     int32_t record_nodes;   /* 1: fused depths also write every node's value and reaches to device
                                memory, so that cfr_get_nodes can return them; 0 (default): they do
                                not, and cfr_get_nodes returns CFR_ERR_STATE when depths are fused. */
@@ -147,6 +154,9 @@ typedef struct {
                                      trees), 2 streamed tiles with per-slot strategy loads and regret
                                      atomics, 3 streamed slot-dense tiles with staged strategy entries,
                                      4 the same with bulk-reduced regrets (cfr_config.tail_slots) */
+    int32_t pair_depth;           /* FP32 mode: m when depths m and m+1 (just above the fused last two
+                                     depths) run as a pair, one top-down and one bottom-up launch for both
+                                     with depth m+1's reaches and values kept on chip; -1 if not */
 } cfr_info;
 
 /* Fills *c with defaults: vanilla, FP32, simultaneous, default averaging, current device,
@@ -277,11 +287,14 @@ cfr_status cfr_root_value_async(cfr_solver *s, double *u1);
 /* Runs ONE iteration (it counts: T advances by 1) as individually launched kernels on the solver's
  * stream with CUDA events between its phases, and returns per phase the elapsed time in
  * microseconds (us), the phase's algorithmic bytes (bytes), its kind (CFR_PHASE_*) and depth (depth;
- * the first fused depth for CFR_PHASE_FUSED, -1 for the own reaches and the update).  Phases in order:
- * the own reaches of all infosets (Eq. 4; if there are player infosets - cfr_iterate runs them beside
- * the node passes), top-down from depth 0, 1, ..., f-1, the fused depths f .. num_levels-1 (if any;
- * f = cfr_info.fused_from_depth), bottom-up at depth f-1, ..., 0, then the per-infoset update (no phase
- * at all for a game without decision nodes).  The bytes add up to cfr_info.bytes_per_iteration.
+ * the first fused depth for CFR_PHASE_FUSED, the upper depth m for CFR_PHASE_TOPDOWN_PAIR and
+ * CFR_PHASE_BOTTOMUP_PAIR, -1 for the own reaches and the update).  Phases in order: the own reaches of
+ * all infosets (Eq. 4; if there are player infosets - cfr_iterate runs them beside the node passes),
+ * top-down from depth 0, 1, ..., f-1 (depths m and m+1 in one CFR_PHASE_TOPDOWN_PAIR phase when
+ * cfr_info.pair_depth = m >= 0), the fused depths f .. num_levels-1 (if any; f =
+ * cfr_info.fused_from_depth), bottom-up at depth f-1, ..., 0 (depths m+1 and m in one
+ * CFR_PHASE_BOTTOMUP_PAIR phase), then the per-infoset update (no phase at all for a game without
+ * decision nodes).  The bytes add up to cfr_info.bytes_per_iteration.
  * *nphases receives the count; with us, bytes, kind and depth all NULL only the count is returned (no
  * iteration runs), otherwise len must be at least the count (NULL arrays are skipped).  Tracing hook. */
 cfr_status cfr_phase_times(cfr_solver *s, double *us, double *bytes, int32_t *kind, int32_t *depth, int32_t len,

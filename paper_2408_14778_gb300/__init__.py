@@ -24,6 +24,7 @@ CFR_FP32, CFR_FP64 = 0, 1
 CFR_SIMULTANEOUS, CFR_ALTERNATING = 0, 1
 CFR_AVG_DEFAULT, CFR_AVG_UNIFORM, CFR_AVG_LINEAR = -1, 0, 1
 CFR_PHASE_TOPDOWN, CFR_PHASE_BOTTOMUP, CFR_PHASE_FUSED, CFR_PHASE_UPDATE, CFR_PHASE_OWN = 0, 1, 2, 3, 4
+CFR_PHASE_TOPDOWN_PAIR, CFR_PHASE_BOTTOMUP_PAIR = 5, 6
 
 _STATUS_NAMES = {0: "CFR_OK", 1: "CFR_ERR_INVALID", 2: "CFR_ERR_CUDA", 3: "CFR_ERR_OOM", 4: "CFR_ERR_TIMEOUT",
                  5: "CFR_ERR_STATE", 6: "CFR_ERR_UNSUPPORTED"}
@@ -85,7 +86,7 @@ class _Info(ctypes.Structure):
         ("avg_weight", ctypes.c_int32), ("iteration", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
         ("bytes_per_iteration", ctypes.c_int64), ("kernels_per_iteration", ctypes.c_int32),
         ("kernel_launches", ctypes.c_int64), ("fused_from_depth", ctypes.c_int32), ("fused_tiles", ctypes.c_int32),
-        ("head_depths", ctypes.c_int32), ("tail_kernel", ctypes.c_int32),
+        ("head_depths", ctypes.c_int32), ("tail_kernel", ctypes.c_int32), ("pair_depth", ctypes.c_int32),
     ]
 
 
@@ -402,8 +403,9 @@ def cfr_phase_times(s: "Solver") -> list:
     _check(lib().cfr_phase_times(s.handle, us.ctypes.data, by.ctypes.data, kind.ctypes.data, depth.ctypes.data,
                                  n.value, ctypes.byref(n)), s.handle)
     names = {CFR_PHASE_TOPDOWN: "top-down depth {}", CFR_PHASE_BOTTOMUP: "bottom-up depth {}",
-             CFR_PHASE_FUSED: "fused depths {}+", CFR_PHASE_UPDATE: "update", CFR_PHASE_OWN: "own reaches"}
-    return [dict(name=names[int(k)].format(int(d)), kind=int(k), depth=int(d), us=float(u), bytes=float(b))
+             CFR_PHASE_FUSED: "fused depths {}+", CFR_PHASE_UPDATE: "update", CFR_PHASE_OWN: "own reaches",
+             CFR_PHASE_TOPDOWN_PAIR: "top-down depths {}-{}", CFR_PHASE_BOTTOMUP_PAIR: "bottom-up depths {}-{}"}
+    return [dict(name=names[int(k)].format(int(d), int(d) + 1), kind=int(k), depth=int(d), us=float(u), bytes=float(b))
             for k, d, u, b in zip(kind, depth, us, by)]
 
 

@@ -28,6 +28,7 @@ constexpr int kBlock = 256;
 constexpr int kGraphIters = 4;   // iterations captured in the solver's second graph (cfr_iterate replays it first)
 constexpr int kWideBlock = 1024;   // nodes and infosets with more than 32 actions: one block each
 constexpr int32_t kFuseAuto = 2;   // fused depths when cfr_config.fuse_levels < 0
+constexpr int32_t kPairMinNodes = 8192;      // FP32: fewest decision nodes at the upper depth of a pair
 constexpr int32_t kStreamMinNodes = 32768;   // FP32 bottom-up depths this large use k_bottomup_stream
 constexpr int32_t kHeadMaxNodes = 1 << 19;   // FP32: leading depths at most this large run in the head launches
 constexpr int32_t kHeadMaxSmem = 96 << 10;   // shared memory of a head block, at most
@@ -102,6 +103,10 @@ struct cfr_solver {
     int32_t *tail_tiles = nullptr;                        // 8 words per tile (TailTiles::tm), or 12
                                                           // (SlotTailTiles::tm)
     int32_t ntail_tiles = 0, tl_grid[3] = {0, 0, 0}, ts_grid[3] = {0, 0, 0};
+    // FP32 mode: depths pair_m and pair_m + 1 (just above the fused tail) in one top-down and one bottom-up
+    // launch (k_pair_*), over npair_tiles tiles of 12 words (PairTopDownTiles::tm); pair_m < 0: none
+    int32_t pair_m = -1, npair_tiles = 0, pt_grid[3] = {0, 0, 0}, pb_grid[3] = {0, 0, 0};
+    int32_t *pair_tiles = nullptr;
     int32_t Hp = 0;                                       // player infosets: internal ids [0, Hp)
     // FP32 mode: depths 0 .. head_n - 1 run in one launch per direction (k_head_*), head_per_block root
     // children per block; head_n == 0: per-depth launches
@@ -157,6 +162,10 @@ cfr_status dev_alloc(cfr_solver *s, void **p, size_t bytes) {
     if (s->cfg.dev_alloc) {
         ptr = s->cfg.dev_alloc(bytes, s->cfg.alloc_ctx);
         if (!ptr) return set_err(s, CFR_ERR_OOM, "device allocator returned NULL for %zu bytes", bytes);
+        if (reinterpret_cast<uintptr_t>(ptr) & 255u) {
+            s->cfg.dev_free(ptr, s->cfg.alloc_ctx);
+            return set_err(s, CFR_ERR_INVALID, "device allocator returned %p: not 256-byte aligned", ptr);
+        }
     } else {
         cudaError_t e = cudaMalloc(&ptr, bytes);
         if (e != cudaSuccess) {
@@ -340,6 +349,44 @@ cfr_status setup_stream_na(cfr_solver *s, int gi, int sms) {
         CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail_slots<NA, false>, 32 * (kSTWarps + 1), ssmem));
     s->ts_grid[gi] = per_sm * sms;
+    const int ptsmem = (int)(sizeof(PTStage) * PairTopDownTiles<NA>::kStages);
+    CK(cudaFuncSetAttribute(k_pair_topdown<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, ptsmem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_topdown<NA>, kSBThreads, ptsmem));
+    s->pt_grid[gi] = per_sm * sms;
+    const int pbsmem = (int)(sizeof(PBStage) * PairBottomUpTiles<NA>::kStages);
+    CK(cudaFuncSetAttribute(k_pair_bottomup<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbsmem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_bottomup<NA>, kSBThreads, pbsmem));
+    s->pb_grid[gi] = per_sm * sms;
+    return CFR_OK;
+}
+
+// Whether depths l and l + 1 run as the pair (k_pair_topdown / k_pair_bottomup) in a pass whose first
+// per-depth launch is at depth head.
+bool pair_at(const cfr_solver *s, int32_t l, int32_t head) {
+    return s->pair_m >= head && l == s->pair_m && s->npair_tiles > 0;
+}
+
+// The paired launches of depths pair_m and pair_m + 1, in the instantiation for their largest action
+// count; bump: depth pair_m is the root's (the top-down launch counts the iteration).
+cfr_status launch_pair(Launcher &go, cfr_solver *s, const DevTree<float> &t, cudaStream_t st, bool bottom_up,
+                       int32_t bump) {
+    const int32_t m = s->pair_m;
+    const int gi = std::max(s->level_na[(size_t)m], s->level_na[(size_t)m + 1]);
+    const int4 *tb = reinterpret_cast<const int4 *>(s->pair_tiles);
+    const int32_t rec = s->cfg.record_nodes != 0, nt = s->npair_tiles;
+    if (bottom_up) {
+        const int grid = std::min(s->pb_grid[gi], nt);
+        const size_t smem = sizeof(PBStage) * PairBottomUpTiles<3>::kStages;
+        if (gi == 0) CK(go(k_pair_bottomup<kStreamNA[0]>, grid, kSBThreads, smem, st, t, tb, nt, rec, s->d_err));
+        else if (gi == 1) CK(go(k_pair_bottomup<kStreamNA[1]>, grid, kSBThreads, smem, st, t, tb, nt, rec, s->d_err));
+        else CK(go(k_pair_bottomup<kStreamNA[2]>, grid, kSBThreads, smem, st, t, tb, nt, rec, s->d_err));
+    } else {
+        const int grid = std::min(s->pt_grid[gi], nt);
+        const size_t smem = sizeof(PTStage) * PairTopDownTiles<3>::kStages;
+        if (gi == 0) CK(go(k_pair_topdown<kStreamNA[0]>, grid, kSBThreads, smem, st, t, tb, nt, rec, bump, s->d_err));
+        else if (gi == 1) CK(go(k_pair_topdown<kStreamNA[1]>, grid, kSBThreads, smem, st, t, tb, nt, rec, bump, s->d_err));
+        else CK(go(k_pair_topdown<kStreamNA[2]>, grid, kSBThreads, smem, st, t, tb, nt, rec, bump, s->d_err));
+    }
     return CFR_OK;
 }
 
@@ -456,6 +503,14 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
     }
     if (s->Hp > 0) TRY(mark());
     for (int32_t l = head; l < r; ++l) {
+        if constexpr (!det) {
+            if (pair_at(s, l, head)) {                   // the top-down steps of depths l and l + 1
+                TRY(launch_pair(go, s, t, st, false, (int32_t)(first && l == 0)));
+                TRY(mark());
+                ++l;
+                continue;
+            }
+        }
         if (!topdown_launches(s, l)) continue;
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         if (s->ddepth_children[l] || l == 0) {
@@ -509,6 +564,14 @@ cfr_status enqueue_pass(cfr_solver *s, cudaStream_t st, cudaEvent_t *ev, int32_t
         }
     }
     for (int32_t l = r - 1; l >= head; --l) {
+        if constexpr (!det) {
+            if (l >= 1 && pair_at(s, l - 1, head)) {     // the bottom-up steps of depths l and l - 1
+                TRY(launch_pair(go, s, t, st, true, 0));
+                TRY(mark());
+                --l;
+                continue;
+            }
+        }
         const int32_t j0 = s->dlevel[l], j1 = s->dlevel[l + 1];
         bool streamed = false;
         if constexpr (!det) {
@@ -569,10 +632,21 @@ std::vector<std::pair<int32_t, int32_t>> phases(const cfr_solver *s) {
     if (s->L == 0) return p;
     const int32_t r = fused_from(s);
     if (s->Hp > 0) p.push_back({CFR_PHASE_OWN, -1});
-    for (int32_t l = 0; l < r; ++l)
+    for (int32_t l = 0; l < r; ++l) {
+        if (r < s->L && pair_at(s, l, 0)) {
+            p.push_back({CFR_PHASE_TOPDOWN_PAIR, l++});
+            continue;
+        }
         if (topdown_launches(s, l)) p.push_back({CFR_PHASE_TOPDOWN, l});
+    }
     if (r < s->L) p.push_back({CFR_PHASE_FUSED, r});
-    for (int32_t l = r - 1; l >= 0; --l) p.push_back({CFR_PHASE_BOTTOMUP, l});
+    for (int32_t l = r - 1; l >= 0; --l) {
+        if (r < s->L && l >= 1 && pair_at(s, l - 1, 0)) {
+            p.push_back({CFR_PHASE_BOTTOMUP_PAIR, --l});
+            continue;
+        }
+        p.push_back({CFR_PHASE_BOTTOMUP, l});
+    }
     p.push_back({CFR_PHASE_UPDATE, -1});
     return p;
 }
@@ -587,6 +661,12 @@ std::vector<std::pair<int32_t, int32_t>> phases(const cfr_solver *s) {
 //                                                  node fields of depth r+1 (k_tail_slots: 4 Nd(r+1),
 //                                                  the packed word alone)
 //                         + 4 T(r) + 4 T(r+1)      one utility per terminal child
+//   depths m, m+1 paired (k_pair_topdown, k_pair_bottomup; m = r-2 below the fused tail):
+//     top-down              20 Nd(m) + 12 Nd(m+1)  fields and reaches of depth m, fields of depth m+1
+//                         + 8 Nd(m+2)             the reaches of depth m+2 written
+//     bottom-up             28 Nd(m) + 16 Nd(m+1)  as k_tail's, with the children's first decision child
+//                         + 4 T(m) + 4 T(m+1)     one utility per terminal child
+//                         + 4 Nd(m+2)             one value per decision grandchild
 //   fused depths r..L-1 (k_fused tiles):
 //                           16 Nd(>=r) + 4 T(>=r)  node fields; one utility per terminal child
 //                         + 12 Nd(r)               the tile roots' reaches read and values written
@@ -608,6 +688,11 @@ std::vector<double> phase_bytes(const cfr_solver *s) {
         } else if (ph.first == CFR_PHASE_BOTTOMUP) {
             const double children = (double)s->level_children[l];
             b.push_back(f64 ? 40 * nd(l) + 8 * children : 24 * nd(l) + 4 * children);
+        } else if (ph.first == CFR_PHASE_TOPDOWN_PAIR) {
+            b.push_back(20 * nd(l) + 12 * nd(l + 1) + 8 * nd(l + 2));
+        } else if (ph.first == CFR_PHASE_BOTTOMUP_PAIR) {
+            b.push_back(28 * nd(l) + 16 * nd(l + 1) + 4 * nd(l + 2) +
+                        4 * (double)(s->level_terminals[l] + s->level_terminals[l + 1]));
         } else if (ph.first == CFR_PHASE_FUSED && s->fuse_tail) {
             b.push_back(28 * nd(l) + (s->tail_slots ? 4 : 12) * nd(l + 1) +
                         4 * (double)(s->level_terminals[l] + s->level_terminals[l + 1]));
@@ -645,6 +730,7 @@ int32_t launches_per_pass(const cfr_solver *s) {
         n += s->ddepth_children[l] || l == 0;                 // top-down
         if (!det) n += 2 * (s->wlevel[l + 1] > s->wlevel[l]);
     }
+    if (!det && r < s->L && s->pair_m >= head && s->npair_tiles > 0) n -= 2;   // two depths per launch
     return n;
 }
 
@@ -655,6 +741,58 @@ int32_t launches_per_pass(const cfr_solver *s) {
 // and the largest block's nodes of depths 1 .. n fit kHeadMaxSmem bytes of shared memory (at most
 // cfg.head_levels depths below the root when that is positive; 0: none).  About two blocks per SM walk
 // the root children's subtrees.
+// Tiles of the depth-m parents [jb, je) for k_pair_topdown / k_pair_bottomup: consecutive parents while
+// every staged range (their decision children, both terminal ranges, the decision grandchildren) fits
+// its array, 4 elements of each kept free for the 16-byte widening of the copies.  Appends 12 words per
+// tile: {j0, j1, cs, ce}, {pts, pte, cts, cte}, {gs, ge, 0, 0}.  False if one parent alone exceeds a range.
+bool cut_pair_tiles(const Layout &Lo, int32_t jb, int32_t je, std::vector<int32_t> *meta) {
+    const auto df = [&](int32_t j) { return Lo.dfirst[(size_t)j]; };
+    const auto tf = [&](int32_t j) { return Lo.tfirst[(size_t)j]; };
+    std::vector<int32_t> tb{jb};
+    int32_t n = 0, nc = 0, npt = 0, nct = 0, ng = 0;
+    for (int32_t j = jb; j < je; ++j) {
+        const int32_t d0 = df(j), d1 = df(j + 1);
+        const int32_t ndj = d1 - d0, ptj = tf(j + 1) - tf(j), ctj = tf(d1) - tf(d0), gj = df(d1) - df(d0);
+        if (ndj > kPC - 4 || ptj > kPPT - 4 || ctj > kPCT - 4 || gj > kPG - 4) return false;
+        if (n + 1 > kPP || nc + ndj > kPC - 4 || npt + ptj > kPPT - 4 || nct + ctj > kPCT - 4 || ng + gj > kPG - 4) {
+            tb.push_back(j);
+            n = nc = npt = nct = ng = 0;
+        }
+        ++n; nc += ndj; npt += ptj; nct += ctj; ng += gj;
+    }
+    tb.push_back(je);
+    meta->clear();
+    meta->reserve((size_t)12 * (tb.size() - 1));
+    for (size_t i = 0; i + 1 < tb.size(); ++i) {
+        const int32_t j0 = tb[i], j1 = tb[i + 1], cs = df(j0), ce = df(j1);
+        const int32_t v[12] = {j0, j1, cs, ce, tf(j0), tf(j1), tf(cs), tf(ce), df(cs), df(ce), 0, 0};
+        meta->insert(meta->end(), v, v + 12);
+    }
+    return true;
+}
+
+// FP32 mode with automatic fusion, after plan_fusion and plan_head: the two depths m = fuse_r - 2 and
+// m + 1 above the streamed tail run as a pair (one top-down and one bottom-up launch) when both lie below
+// the head, hold decision children and no node of more than 32 actions, and depth m holds at least
+// kPairMinNodes decision nodes.
+cfr_status plan_pair(cfr_solver *s, const Layout &Lo) {
+    s->pair_m = -1;
+    s->npair_tiles = 0;
+    if (s->cfg.fuse_levels >= 0 || !s->fuse_tail || s->ntail_tiles == 0) return CFR_OK;
+    const int32_t m = s->fuse_r - 2;
+    if (m < 0 || m < s->head_n || s->dlevel[m + 1] - s->dlevel[m] < kPairMinNodes) return CFR_OK;
+    if (s->wlevel[(size_t)m + 2] > s->wlevel[(size_t)m] || !s->ddepth_children[m] || !s->ddepth_children[m + 1])
+        return CFR_OK;
+    std::vector<int32_t> meta;
+    if (!cut_pair_tiles(Lo, s->dlevel[m], s->dlevel[m + 1], &meta)) return CFR_OK;
+    TRY(alloc_n(s, &s->pair_tiles, (int64_t)meta.size()));
+    TRY(upload(s, s->pair_tiles, meta));
+    CK(cudaStreamSynchronize(s->stream));
+    s->npair_tiles = (int32_t)(meta.size() / 12);
+    s->pair_m = m;
+    return CFR_OK;
+}
+
 cfr_status plan_head(cfr_solver *s, const Layout &Lo, int sms) {
     s->head_n = 0;
     if (s->cfg.head_levels == 0 || s->L < 2) return CFR_OK;
@@ -928,6 +1066,7 @@ cfr_status load(cfr_solver *s, Layout &Lo) {
         int sms = 0;
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
         TRY(plan_head(s, Lo, sms));
+        TRY(plan_pair(s, Lo));
         {
             std::vector<int32_t> wh;
             for (int32_t h = 0; h < s->Hp; ++h) {
@@ -1586,6 +1725,7 @@ cfr_status cfr_get_info(const cfr_solver *s, cfr_info *info) {
     info->tail_kernel = fused_from(s) == s->L || !s->fuse_tail ? 0
                         : s->ntail_tiles == 0 ? 1
                         : !s->tail_slots ? 2 : s->cfg.tail_slots == 2 ? 4 : 3;
+    info->pair_depth = fused_from(s) < s->L && s->npair_tiles > 0 ? s->pair_m : -1;
     info->fused_tiles = fused_from(s) == s->L ? 0
                         : !s->fuse_tail ? s->fuse_ntiles
                         : s->ntail_tiles > 0 ? s->ntail_tiles : nblocks(s->dlevel[s->fuse_r + 1] - s->dlevel[s->fuse_r]);

@@ -1010,6 +1010,418 @@ __global__ void __launch_bounds__(32 * (kSTWarps + 1)) k_tail_slots(DevTree<floa
     run_pipeline(SlotTailTiles<NA, BULK>{t, tm, nt, record, q1, q2, cv}, err);
 }
 
+// ---- two depths above the fused tail, paired (FP32 mode) ----------------------------------------------
+// The top-down steps of depths m and m+1 in one launch, and their bottom-up steps in another, over
+// tiles of consecutive depth-m nodes ("parents") cut on the host so that every range below fits its
+// stage array (cut_pair_tiles in the host code).  A tile's decision children (depth m+1, "children")
+// and their decision children (depth m+2, "grandchildren") are contiguous ranges in breadth-first
+// order.  Depth m+1's reaches and values stay on chip:
+//   top-down:  phase 0, one thread per parent: td_node's arithmetic, the children's reaches to shared
+//              memory; phase 1, one thread per child: the same for the child, the grandchildren's
+//              reaches to a shared-memory buffer, stored afterwards as one coalesced range;
+//   bottom-up: phase 0 as above (the same products, so the children's reaches are those the top-down
+//              launch formed); phase 1, one thread per child: bu_node's arithmetic on the staged
+//              grandchildren's values and terminal utilities, value to shared memory; phase 2, one
+//              thread per parent: its bottom-up step.
+// With record set both launches also store depth m+1's reaches and values.  Nodes with more than 32
+// actions are not handled (the host keeps such depths off these kernels).
+constexpr int kPP = 256;                   // parents per tile, at most (one per consumer thread)
+constexpr int kPC = 640;                   // children per tile, at most
+constexpr int kPPT = 640;                  // parents' terminal children per tile, at most
+constexpr int kPCT = 1344;                 // children's terminal children per tile, at most
+constexpr int kPG = 1664;                  // grandchildren per tile, at most
+constexpr int kPCPer = (kPC + kSBConsumerWarps * 32 - 1) / (kSBConsumerWarps * 32);
+
+struct PTStage {                           // top-down stage; + 4 / + 8: room for widening the copies
+    uint32_t qp[kPP + 4], km[kPP + 4];
+    float r1[kPP + 4], r2[kPP + 4];
+    int32_t df[kPP + 8];
+    uint32_t cqp[kPC + 4], ckm[kPC + 4];
+    int32_t cdf[kPC + 8];
+};
+
+struct PBStage {                           // bottom-up stage
+    uint32_t qp[kPP + 4], km[kPP + 4];
+    float r1[kPP + 4], r2[kPP + 4];
+    int32_t df[kPP + 8], tf[kPP + 8];
+    uint32_t cqp[kPC + 4], ckm[kPC + 4];
+    int32_t cdf[kPC + 8], ctf[kPC + 8];
+    float pu[kPPT + 4], cu[kPCT + 4], gu[kPG + 4];
+};
+
+struct PRTile {
+    int32_t j0, n, o;                      // parents [j0, j0 + n); node j0 at index o of the parent arrays
+    int32_t cs, nc, co;                    // children [cs, cs + nc); child cs at index co of the child arrays
+    int32_t gs, ng, gal;                   // grandchildren [gs, gs + ng); global index of gu[0]
+    int32_t pal, cal;                      // global terminal index of pu[0] / cu[0]
+};
+
+// Phase 0 of both launches: parent c's decision children's reaches into q1/q2 (indexed from the tile's
+// first child), as td_node forms them; s: the parent's strategy entries (its first NA).
+template <int NA>
+__device__ __forceinline__ void pair_parent_topdown(const DevTree<float> &t, int32_t c0, int na, uint32_t m, int p,
+                                                    float r1, float r2, int32_t qb, const float (&s)[NA], float *q1,
+                                                    float *q2) {
+    int32_t y = c0;
+    if (na <= NA) {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            if (a < na && !((m >> a) & 1u)) {
+                q1[y] = p == 1 ? r1 : r1 * s[a];
+                q2[y] = p == 2 ? r2 : r2 * s[a];
+                ++y;
+            }
+        }
+    } else {
+        for (int a = 0; a < na; ++a) {
+            if ((m >> a) & 1u) continue;
+            const float sv = __ldg(t.sigma + qb + a);
+            q1[y] = p == 1 ? r1 : r1 * sv;
+            q2[y] = p == 2 ? r2 : r2 * sv;
+            ++y;
+        }
+    }
+}
+
+template <int NA>
+struct PairTopDownTiles {
+    using Stage = PTStage;
+    using Tile = PRTile;
+    static constexpr int kConsumerWarps = kSBConsumerWarps;
+    static constexpr int kStages = 2;
+    static constexpr bool kConsumerSync = true;
+    DevTree<float> t;
+    const int4 *tm;                        // per tile three int4: {j0, j1, cs, ce}, {pts, pte, cts, cte}, {gs, ge, -, -}
+    int32_t nt, record;
+    float *q1, *q2;                        // shared memory, kPC each: the children's reaches
+    float *o1, *o2;                        // shared memory, kPG each: the grandchildren's reaches
+    __device__ int32_t ntiles() const { return nt; }
+    using Meta = int4;
+    static constexpr int kMetaWords = 3;
+    __device__ void prefetch(int32_t tile, int4 *meta) const {
+        meta[0] = __ldg(tm + 3 * tile);
+        meta[1] = __ldg(tm + 3 * tile + 1);
+        meta[2] = __ldg(tm + 3 * tile + 2);
+    }
+    __device__ void issue(int32_t, const int4 *meta, Stage *st, Tile *ti, uint64_t *full) const {
+        const int32_t j0 = meta[0].x, n = meta[0].y - j0, cs = meta[0].z, ce = meta[0].w;
+        uint32_t bf, bd, bc, bcd;
+        const int32_t jal = widen16(j0, j0 + n, &bf);
+        widen16(j0, j0 + n + 1, &bd);
+        const int32_t cal_n = widen16(cs, ce, &bc);
+        widen16(cs, ce + 1, &bcd);
+        ti->j0 = j0; ti->n = n; ti->o = j0 - jal;
+        ti->cs = cs; ti->nc = ce - cs; ti->co = cs - cal_n;
+        ti->gs = meta[2].x; ti->ng = meta[2].y - meta[2].x; ti->gal = 0;
+        ti->pal = 0; ti->cal = 0;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(full, 4 * bf + bd + 2 * bc + bcd);
+        bulk_g2s(st->qp, t.qp + jal, bf, full);
+        bulk_g2s(st->km, t.kmask + jal, bf, full);
+        bulk_g2s(st->r1, t.reach1 + jal, bf, full);
+        bulk_g2s(st->r2, t.reach2 + jal, bf, full);
+        bulk_g2s(st->df, t.dfirst + jal, bd, full);
+        if (bc) {
+            bulk_g2s(st->cqp, t.qp + cal_n, bc, full);
+            bulk_g2s(st->ckm, t.kmask + cal_n, bc, full);
+        }
+        bulk_g2s(st->cdf, t.dfirst + cal_n, bcd, full);
+    }
+    // Thread c takes parent c and children c, c + 256, c + 512; the strategy entries of all of them are
+    // loaded in one round before phase 0.
+    __device__ void consume(const Stage &st, const Tile &ti, int c) const {
+        constexpr int kC = kSBConsumerWarps * 32;
+        const int32_t k = ti.o + c;
+        uint32_t m = 0;
+        int32_t c0 = 0, qb = 0;
+        int na = 0, p = 0;
+        float r1 = 0.f, r2 = 0.f;
+        float s[NA];
+        bool act = false;
+        if (c < ti.n) {
+            c0 = st.df[k];
+            const int32_t nd = st.df[k + 1] - c0;
+            act = nd > 0;
+            if (act) {
+                const uint32_t w = st.qp[k];
+                m = st.km[k];
+                na = nd + __popc(m);
+                r1 = st.r1[k];
+                r2 = st.r2[k];
+                qb = qp_base(w);
+                p = qp_player(w);
+#pragma unroll
+                for (int a = 0; a < NA; ++a) s[a] = a < na ? __ldg(t.sigma + qb + a) : 0.f;
+            }
+        }
+        uint32_t cm[kPCPer];
+        int32_t cw[kPCPer], cd0[kPCPer];
+        float sc[kPCPer][NA];
+#pragma unroll
+        for (int r = 0; r < kPCPer; ++r) {               // cd0 < 0: no child, or one without decision children
+            const int32_t ci = c + r * kC;
+            cm[r] = 0;
+            cw[r] = 0;
+            cd0[r] = -1;
+            if (ci < ti.nc) {
+                const int32_t cd = st.cdf[ti.co + ci], cnd = st.cdf[ti.co + ci + 1] - cd;
+                if (cnd > 0) {
+                    cw[r] = (int32_t)st.cqp[ti.co + ci];
+                    cm[r] = st.ckm[ti.co + ci];
+                    cd0[r] = cd;
+                    const int cna = cnd + __popc(cm[r]);
+                    const int32_t cq = qp_base((uint32_t)cw[r]);
+#pragma unroll
+                    for (int b = 0; b < NA; ++b) sc[r][b] = b < cna ? __ldg(t.sigma + cq + b) : 0.f;
+                }
+            }
+        }
+        // phase 0: parent c's top-down step, the children's reaches to shared memory
+        if (act) pair_parent_topdown<NA>(t, c0 - ti.cs, na, m, p, r1, r2, qb, s, q1, q2);
+        consumers_sync();
+        // phase 1: the children's top-down steps, the grandchildren's reaches to the output buffers
+#pragma unroll
+        for (int r = 0; r < kPCPer; ++r) {
+            const int32_t ci = c + r * kC;
+            if (ci >= ti.nc) continue;
+            const float cr1 = q1[ci], cr2 = q2[ci];
+            if (record) {
+                t.reach1[ti.cs + ci] = cr1;
+                t.reach2[ti.cs + ci] = cr2;
+            }
+            if (cd0[r] < 0) continue;
+            const int32_t cnd = st.cdf[ti.co + ci + 1] - cd0[r];
+            const int cna = cnd + __popc(cm[r]);
+            pair_parent_topdown<NA>(t, cd0[r] - ti.gs, cna, cm[r], qp_player((uint32_t)cw[r]), cr1, cr2,
+                                    qp_base((uint32_t)cw[r]), sc[r], o1, o2);
+        }
+        consumers_sync();                              // the tile's grandchildren's reaches are in o1/o2
+        for (int32_t i = c; i < ti.ng; i += kC) {
+            t.reach1[ti.gs + i] = o1[i];
+            t.reach2[ti.gs + i] = o2[i];
+        }
+    }
+};
+
+// bump: depth m is the root's, so no top-down launch precedes this one; count the iteration.
+template <int NA>
+__global__ void __launch_bounds__(kSBThreads) k_pair_topdown(DevTree<float> t, const int4 *tm, int32_t nt,
+                                                             int32_t record, int32_t bump, int *err) {
+    grid_dependency_wait();
+    __shared__ float q1[kPC], q2[kPC], o1[kPG], o2[kPG];
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *t.iter += 1;
+    run_pipeline(PairTopDownTiles<NA>{t, tm, nt, record, q1, q2, o1, o2}, err);
+}
+
+template <int NA>
+struct PairBottomUpTiles {
+    using Stage = PBStage;
+    using Tile = PRTile;
+    static constexpr int kConsumerWarps = kSBConsumerWarps;
+    static constexpr int kStages = 2;
+    static constexpr bool kConsumerSync = true;
+    DevTree<float> t;
+    const int4 *tm;
+    int32_t nt, record;
+    float *q1, *q2, *cv;                   // shared memory, kPC each: the children's reaches and values
+    __device__ int32_t ntiles() const { return nt; }
+    using Meta = int4;
+    static constexpr int kMetaWords = 3;
+    __device__ void prefetch(int32_t tile, int4 *meta) const {
+        meta[0] = __ldg(tm + 3 * tile);
+        meta[1] = __ldg(tm + 3 * tile + 1);
+        meta[2] = __ldg(tm + 3 * tile + 2);
+    }
+    __device__ void issue(int32_t, const int4 *meta, Stage *st, Tile *ti, uint64_t *full) const {
+        const int32_t j0 = meta[0].x, n = meta[0].y - j0, cs = meta[0].z, ce = meta[0].w;
+        const int32_t pts = meta[1].x, pte = meta[1].y, cts = meta[1].z, cte = meta[1].w;
+        const int32_t gs = meta[2].x, ge = meta[2].y;
+        uint32_t bf, bd, bc, bcd, bpu, bcu, bgu;
+        const int32_t jal = widen16(j0, j0 + n, &bf);
+        widen16(j0, j0 + n + 1, &bd);
+        const int32_t cal_n = widen16(cs, ce, &bc);
+        widen16(cs, ce + 1, &bcd);
+        const int32_t pal = widen16(pts, pte, &bpu);
+        const int32_t cal = widen16(cts, cte, &bcu);
+        const int32_t gal = widen16(gs, ge, &bgu);
+        ti->j0 = j0; ti->n = n; ti->o = j0 - jal;
+        ti->cs = cs; ti->nc = ce - cs; ti->co = cs - cal_n;
+        ti->gs = gs; ti->ng = ge - gs; ti->gal = gal;
+        ti->pal = pal; ti->cal = cal;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(full, 4 * bf + 2 * bd + 2 * bc + 2 * bcd + bpu + bcu + bgu);
+        bulk_g2s(st->qp, t.qp + jal, bf, full);
+        bulk_g2s(st->km, t.kmask + jal, bf, full);
+        bulk_g2s(st->r1, t.reach1 + jal, bf, full);
+        bulk_g2s(st->r2, t.reach2 + jal, bf, full);
+        bulk_g2s(st->df, t.dfirst + jal, bd, full);
+        bulk_g2s(st->tf, t.tfirst + jal, bd, full);
+        if (bc) {
+            bulk_g2s(st->cqp, t.qp + cal_n, bc, full);
+            bulk_g2s(st->ckm, t.kmask + cal_n, bc, full);
+        }
+        bulk_g2s(st->cdf, t.dfirst + cal_n, bcd, full);
+        bulk_g2s(st->ctf, t.tfirst + cal_n, bcd, full);
+        if (bpu) bulk_g2s(st->pu, t.util + pal, bpu, full);
+        if (bcu) bulk_g2s(st->cu, t.util + cal, bcu, full);
+        if (bgu) bulk_g2s(st->gu, t.u + gal, bgu, full);
+    }
+    // Thread c takes parent c and children c, c + 256, c + 512; the strategy entries of all of them are
+    // loaded in one round before phase 0.
+    __device__ void consume(const Stage &st, const Tile &ti, int c) const {
+        constexpr int kC = kSBConsumerWarps * 32;
+        const bool act = c < ti.n;
+        const int32_t k = ti.o + c;
+        uint32_t m = 0;
+        int32_t c0 = 0, t0 = 0, qb = 0;
+        int na = 0, p = 0;
+        float r1 = 0.f, r2 = 0.f;
+        float s[NA];
+        if (act) {
+            const uint32_t w = st.qp[k];
+            m = st.km[k];
+            c0 = st.df[k];
+            na = (st.df[k + 1] - c0) + __popc(m);
+            t0 = st.tf[k];
+            r1 = st.r1[k];
+            r2 = st.r2[k];
+            qb = qp_base(w);
+            p = qp_player(w);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) s[a] = a < na ? __ldg(t.sigma + qb + a) : 0.f;
+        }
+        uint32_t cm[kPCPer];
+        int32_t cw[kPCPer];
+        float sc[kPCPer][NA];
+#pragma unroll
+        for (int r = 0; r < kPCPer; ++r) {
+            const int32_t ci = c + r * kC;
+            cm[r] = 0;
+            cw[r] = 0;
+            if (ci < ti.nc) {
+                cw[r] = (int32_t)st.cqp[ti.co + ci];
+                cm[r] = st.ckm[ti.co + ci];
+                const int cna = (st.cdf[ti.co + ci + 1] - st.cdf[ti.co + ci]) + __popc(cm[r]);
+                const int32_t cq = qp_base((uint32_t)cw[r]);
+#pragma unroll
+                for (int b = 0; b < NA; ++b) sc[r][b] = b < cna ? __ldg(t.sigma + cq + b) : 0.f;
+            }
+        }
+        // phase 0: parent c's top-down step, the children's reaches to shared memory
+        if (act) pair_parent_topdown<NA>(t, c0 - ti.cs, na, m, p, r1, r2, qb, s, q1, q2);
+        consumers_sync();
+        // phase 1: the children's bottom-up steps (grandchildren's values and terminal utilities staged)
+#pragma unroll
+        for (int r = 0; r < kPCPer; ++r) {
+            const int32_t ci = c + r * kC;
+            if (ci >= ti.nc) continue;
+            const uint32_t w = (uint32_t)cw[r];
+            const int32_t cq = qp_base(w);
+            const int cp = qp_player(w);
+            const int32_t cd = st.cdf[ti.co + ci];
+            const int cna = (st.cdf[ti.co + ci + 1] - cd) + __popc(cm[r]);
+            const float *tv = st.cu + (st.ctf[ti.co + ci] - ti.cal);
+            const float *dv = st.gu + (cd - ti.gal);
+            const uint32_t mm = cm[r];
+            float ud = 0.f;
+            float v[NA];
+            if (cna <= NA) {
+                int kt = 0, kd = 0;
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    if (b < cna) {
+                        const bool term = (mm >> b) & 1u;
+                        v[b] = term ? tv[kt] : dv[kd];
+                        kt += term;
+                        kd += !term;
+                        ud = madd(ud, sc[r][b], v[b]);
+                    }
+                }
+            } else {
+                int kt = 0, kd = 0;
+                for (int b = 0; b < cna; ++b) {
+                    const float val = ((mm >> b) & 1u) ? tv[kt++] : dv[kd++];
+                    ud = madd(ud, __ldg(t.sigma + cq + b), val);
+                }
+            }
+            cv[ci] = ud;
+            const float cq1 = q1[ci], cq2 = q2[ci];
+            if (record) {
+                const int32_t cg = ti.cs + ci;
+                t.u[cg] = ud;
+                t.reach1[cg] = cq1;
+                t.reach2[cg] = cq2;
+            }
+            if (!collects(t, cp)) continue;
+            const float wr = cp == 1 ? cq1 : -cq2;
+            if (wr == 0.f) continue;
+            if (cna <= NA) {
+#pragma unroll
+                for (int b = 0; b < NA; ++b)
+                    if (b < cna) atomicAdd(&t.inst[cq + b], wr * (v[b] - ud));
+            } else {
+                int kt = 0, kd = 0;
+                for (int b = 0; b < cna; ++b) {
+                    const float val = ((mm >> b) & 1u) ? tv[kt++] : dv[kd++];
+                    atomicAdd(&t.inst[cq + b], wr * (val - ud));
+                }
+            }
+        }
+        consumers_sync();
+        // phase 2: parent c's bottom-up step
+        if (!act) return;
+        const float *pv = st.pu + (t0 - ti.pal);
+        const float *dv = cv + (c0 - ti.cs);
+        float ud = 0.f;
+        if (na <= NA) {
+            float v[NA];
+            int kt = 0, kd = 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                if (a < na) {
+                    const bool term = (m >> a) & 1u;
+                    v[a] = term ? pv[kt] : dv[kd];
+                    kt += term;
+                    kd += !term;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                if (a < na) ud = madd(ud, s[a], v[a]);
+            t.u[ti.j0 + c] = ud;
+            if (!collects(t, p)) return;
+            const float wr = p == 1 ? r1 : -r2;
+            if (wr == 0.f) return;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                if (a < na) atomicAdd(&t.inst[qb + a], wr * (v[a] - ud));
+            return;
+        }
+        int kt = 0, kd = 0;
+        for (int a = 0; a < na; ++a) {
+            const float val = ((m >> a) & 1u) ? pv[kt++] : dv[kd++];
+            ud = madd(ud, __ldg(t.sigma + qb + a), val);
+        }
+        t.u[ti.j0 + c] = ud;
+        if (!collects(t, p)) return;
+        const float wr = p == 1 ? r1 : -r2;
+        if (wr == 0.f) return;
+        kt = kd = 0;
+        for (int a = 0; a < na; ++a) {
+            const float val = ((m >> a) & 1u) ? pv[kt++] : dv[kd++];
+            atomicAdd(&t.inst[qb + a], wr * (val - ud));
+        }
+    }
+};
+
+template <int NA>
+__global__ void __launch_bounds__(kSBThreads) k_pair_bottomup(DevTree<float> t, const int4 *tm, int32_t nt,
+                                                              int32_t record, int *err) {
+    grid_dependency_wait();
+    __shared__ float q1[kPC], q2[kPC], cv[kPC];
+    run_pipeline(PairBottomUpTiles<NA>{t, tm, nt, record, q1, q2, cv}, err);
+}
+
 // Unrolled action counts the streamed kernels are built for; a depth takes the smallest one that
 // covers its largest (non-wide) node.
 constexpr int kStreamNA[3] = {3, 5, 8};

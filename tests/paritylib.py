@@ -144,3 +144,25 @@ def compare_nodes(s, o, tol, g):
     assert normwise(gn["cf_reach2"][dec], on["cf2"][dec]) <= tol
     assert np.all(np.isnan(gn["cf_reach1"][~dec]))
     return gn, on
+
+
+def compare_step(s, o, g, alt, nodes=True):
+    """One FP32 step (simultaneous or alternating updates) against the oracle's step from the same state;
+    nodes: also the node values and reaches (the solver records them)."""
+    if not alt:
+        compare_state(s, o, TOL32, g)
+        if nodes:
+            compare_nodes(s, o, TOL32, g)
+        return
+    # Alternating: player 1's half of the step is checked like a simultaneous step.  Player 2's pass runs
+    # under player 1's new FP32 strategy: where regret matching is ill-conditioned (a regret sum of exactly
+    # 0 in FP64 against a rounding residue in FP32) the two sides legitimately decide player 1's strategy
+    # differently, and player 2's regrets follow (whatever the kernels).  Player 2 is compared (normwise)
+    # when the two new player-1 strategies agree to FP32 rounding.
+    compare_state(s, o, TOL32, g, players=(1,))
+    gs, os_ = cfr.cfr_get_state(s), o.state()
+    p1 = np.repeat(g.infoset_player == 1, g.infoset_num_actions)
+    p2 = np.repeat(g.infoset_player == 2, g.infoset_num_actions)
+    if np.abs(cfr.cfr_current_strategy(s)[p1] - os_["sigma"][p1]).max() <= 4 * 2.0 ** -24:
+        for k in ("cum_regret", "strat_sum", "inst_regret"):
+            assert normwise(gs[k][p2], os_[k][p2]) <= TOL32, k

@@ -10,7 +10,7 @@ import pytest
 import gamegen
 import oracle
 import paper_2408_14778_gb300 as cfr
-from paritylib import TOL32, compare_nodes, compare_state, fp32_regret_budget_check, normwise
+from paritylib import TOL32, compare_nodes, compare_state, compare_step, fp32_regret_budget_check, normwise
 
 pytestmark = pytest.mark.gpu
 
@@ -31,33 +31,14 @@ def test_head_matches_oracle(name, nodes, levels, fuse, variant, alt):
     avg = oracle.AVG_LINEAR if variant == cfr.CFR_PLUS else oracle.AVG_UNIFORM
     o.iterate(1, variant=variant, avg=avg, alternating=alt)
     cfr.cfr_iterate(s, 1)
-    _compare_step(s, o, g, alt)
+    compare_step(s, o, g, alt)
     o.iterate(2, variant=variant, avg=avg, alternating=alt)
     st = o.state()
     cfr.cfr_set_state(s, st["cum_regret"], st["strat_sum"], st["iteration"])
     o.iterate(1, variant=variant, avg=avg, alternating=alt)
     cfr.cfr_iterate(s, 1)
-    _compare_step(s, o, g, alt)
+    compare_step(s, o, g, alt)
     assert np.isfinite(cfr.cfr_root_value(s))
-
-
-def _compare_step(s, o, g, alt):
-    if not alt:
-        compare_state(s, o, TOL32, g)
-        compare_nodes(s, o, TOL32, g)
-        return
-    # Alternating: player 1's half of the step is checked like a simultaneous step.  Player 2's pass runs
-    # under player 1's new FP32 strategy: where regret matching is ill-conditioned (a regret sum of exactly
-    # 0 in FP64 against a rounding residue in FP32) the two sides legitimately decide player 1's strategy
-    # differently, and player 2's regrets follow (the same holds with the head off).  Player 2 is compared
-    # (normwise) when the two new player-1 strategies agree to FP32 rounding.
-    compare_state(s, o, TOL32, g, players=(1,))
-    gs, os_ = cfr.cfr_get_state(s), o.state()
-    p1 = np.repeat(g.infoset_player == 1, g.infoset_num_actions)
-    p2 = np.repeat(g.infoset_player == 2, g.infoset_num_actions)
-    if np.abs(cfr.cfr_current_strategy(s)[p1] - os_["sigma"][p1]).max() <= 4 * 2.0 ** -24:
-        for k in ("cum_regret", "strat_sum", "inst_regret"):
-            assert normwise(gs[k][p2], os_[k][p2]) <= TOL32, k
 
 
 def test_head_levels_and_eligibility():
