@@ -112,6 +112,7 @@ struct cfr_solver {
     // children per block; head_n == 0: per-depth launches
     int32_t head_n = 0, head_per_block = 0, head_cap = 0, head_na = 0;   // head_na: index into kStreamNA
     int32_t *head_done = nullptr;
+    int32_t *head_rng = nullptr;                          // per head block kHeadRangeWords words (head_ranges)
     // depth-limited solving (cfr_set_range_program, cfr_set_leaves)
     int64_t rp_nseg = 0, nleaves = 0;
     int64_t *rp_dst = nullptr, *rp_ent = nullptr, *rp_prod = nullptr, *leaf_src = nullptr;
@@ -289,6 +290,7 @@ HeadArgs head_args(const cfr_solver *s, bool bump) {
     a.cap = s->head_cap;
     a.nown = s->hlevel[(size_t)s->head_n];
     a.done = s->head_done;
+    a.rng = s->head_rng;
     return a;
 }
 
@@ -833,6 +835,27 @@ cfr_status plan_head(cfr_solver *s, const Layout &Lo, int sms) {
     if (!s->head_done) {
         TRY(alloc_n(s, &s->head_done, 1));
         CK(cudaMemsetAsync(s->head_done, 0, sizeof(int32_t), s->stream));
+    }
+    // each block's node ranges per depth (head_ranges in kernels.cuh): lo, hi and shared-memory offsets
+    {
+        constexpr int K = kHeadMaxDepths + 2;
+        const int32_t d1 = s->dlevel[(size_t)first];
+        const int32_t nblocks_head = (nroot + per - 1) / per;
+        std::vector<int32_t> rng((size_t)nblocks_head * kHeadRangeWords, 0);
+        for (int32_t b = 0; b < nblocks_head; ++b) {
+            int32_t *lo = rng.data() + (size_t)b * kHeadRangeWords, *hi = lo + K, *off = hi + K;
+            lo[first] = d1 + b * per;
+            hi[first] = std::min(lo[first] + per, d1 + nroot);
+            off[first] = 0;
+            for (int32_t l = first; l <= n; ++l) {
+                lo[l + 1] = Lo.dfirst[(size_t)lo[l]];
+                hi[l + 1] = Lo.dfirst[(size_t)hi[l]];
+                off[l + 1] = off[l] + (hi[l] - lo[l]);
+            }
+        }
+        TRY(alloc_n(s, &s->head_rng, (int64_t)rng.size()));
+        TRY(upload(s, s->head_rng, rng));
+        CK(cudaStreamSynchronize(s->stream));
     }
     s->head_n = n + 1;
     s->head_per_block = per;

@@ -563,6 +563,7 @@ struct HeadArgs {
     int32_t cap;               // nodes of depths 1 .. n in a block, at most (shared-memory arrays)
     int32_t nown;              // infosets 0 .. nown - 1 are first seen at depths 0 .. n (own reaches)
     int32_t *done;             // k_head_bottomup: blocks that have finished (reset by the last)
+    const int32_t *rng;        // per block kHeadRangeWords words: lo, hi, off of head_ranges (set at load)
     float *zero;               // k_head_topdown: r~ to clear (nzero floats; nullptr: cleared elsewhere),
     int64_t nzero;             // in slices by the subtree blocks - no kernel before the bottom-up reads it
 };
@@ -593,19 +594,16 @@ __device__ __forceinline__ void own_path(const DevTree<float> &t, int32_t h) {
 }
 
 // The block's node ranges per depth: nodes lo[l] .. hi[l] - 1 of depth l (l = f .. n + 1, f the first
-// depth the blocks split: 0 for a forest, else 1), at offset off[l] of the shared-memory arrays (l <= n);
-// run by one thread.
-__device__ __forceinline__ void head_ranges(const DevTree<float> &t, const HeadArgs &a, int32_t *lo, int32_t *hi,
-                                            int32_t *off) {
-    const int f = a.forest ? 0 : 1;
-    lo[f] = a.d1 + (int32_t)blockIdx.x * a.per_block;
-    hi[f] = min(lo[f] + a.per_block, a.d1 + a.nroot);
-    off[f] = 0;
-    for (int l = f; l <= a.n; ++l) {
-        lo[l + 1] = t.dfirst[lo[l]];
-        hi[l + 1] = t.dfirst[hi[l]];
-        off[l + 1] = off[l] + (hi[l] - lo[l]);
-    }
+// depth the blocks split: 0 for a forest, else 1), at offset off[l] of the shared-memory arrays (l <= n).
+// The host computes them once at load (head_block_ranges: lo[f] = d1 + block * per_block, hi[f] = lo[f] +
+// per_block capped at d1 + nroot, lo[l + 1] = dfirst[lo[l]], hi[l + 1] = dfirst[hi[l]], off[f] = 0,
+// off[l + 1] = off[l] + hi[l] - lo[l]), so a block reads them in one round instead of a chain of dependent
+// loads per depth.  rng: the three arrays, kHeadMaxDepths + 2 words each; its threads load them.
+constexpr int kHeadRangeWords = 3 * (kHeadMaxDepths + 2);
+__device__ __forceinline__ void head_ranges(const HeadArgs &a, int32_t (*rng)[kHeadMaxDepths + 2]) {
+    const int32_t *src = a.rng + (size_t)blockIdx.x * kHeadRangeWords;
+    for (int i = (int)threadIdx.x; i < kHeadRangeWords; i += (int)blockDim.x)
+        rng[i / (kHeadMaxDepths + 2)][i % (kHeadMaxDepths + 2)] = src[i];
 }
 
 // Stages the fields of the block's nodes of depths 1 .. n: local index off[l] + (j - lo[l]).
@@ -640,8 +638,9 @@ __global__ void __launch_bounds__(kHeadThreads, kHeadBlocksPerSM) k_head_topdown
     int32_t *df_s = reinterpret_cast<int32_t *>(km_s + a.cap);
     float *r1_s = reinterpret_cast<float *>(df_s + a.cap);
     float *r2_s = r1_s + a.cap;
-    __shared__ int32_t lo[kHeadMaxDepths + 2], hi[kHeadMaxDepths + 2], off[kHeadMaxDepths + 2];
-    if (tid == 0) head_ranges(t, a, lo, hi, off);
+    __shared__ int32_t rng[3][kHeadMaxDepths + 2];
+    const int32_t *lo = rng[0], *hi = rng[1], *off = rng[2];
+    head_ranges(a, rng);
     __syncthreads();
     head_stage(t, a, lo, off, qp_s, km_s, df_s, nullptr);
     head_clear(a);
@@ -717,11 +716,12 @@ __global__ void __launch_bounds__(kHeadThreads, kHeadBlocksPerSM) k_head_bottomu
     int32_t *df_s = reinterpret_cast<int32_t *>(km_s + a.cap);
     int32_t *tf_s = df_s + a.cap;
     float *u_s = reinterpret_cast<float *>(tf_s + a.cap);
-    __shared__ int32_t lo[kHeadMaxDepths + 2], hi[kHeadMaxDepths + 2], off[kHeadMaxDepths + 2];
+    __shared__ int32_t rng[3][kHeadMaxDepths + 2];
+    const int32_t *lo = rng[0], *hi = rng[1], *off = rng[2];
     __shared__ int32_t last;
     __shared__ float red[kHeadThreads / 32];
     const int32_t tid = (int32_t)threadIdx.x, bs = (int32_t)blockDim.x;
-    if (tid == 0) head_ranges(t, a, lo, hi, off);
+    head_ranges(a, rng);
     __syncthreads();
     head_stage(t, a, lo, off, qp_s, km_s, df_s, tf_s);
     __syncthreads();
