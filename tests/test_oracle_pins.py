@@ -239,7 +239,7 @@ def test_cfr_plus_regret_and_linear_average_by_definition():
         for h in range(tr.H):
             if tr.player[h] != 0:
                 player_q[tr.qbase[h]:tr.qbase[h] + tr.nact[h]] = True
-        for T in range(1, 7):
+        for T in range(1, 11):
             prof = o.current_strategy().copy()
             inst = tr.inst_regret(prof)
             R = np.where(player_q, np.maximum(R + inst, 0.0), 0.0)             # regret-matching+
@@ -253,6 +253,17 @@ def test_cfr_plus_regret_and_linear_average_by_definition():
             np.testing.assert_allclose(st["cum_regret"], R, atol=1e-12)
             np.testing.assert_allclose(st["strat_sum"], S, atol=1e-12)
             assert np.all(st["cum_regret"] >= 0.0)
+            # the next strategy: regret matching (Eq. 9) of these regrets, uniform where none is positive, so
+            # that every iterate of the trajectory (not only its sums) follows from the definitions
+            nxt = o.current_strategy()
+            for h in range(tr.H):
+                sl = slice(tr.qbase[h], tr.qbase[h] + tr.nact[h])
+                if tr.player[h] == 0:
+                    np.testing.assert_array_equal(nxt[sl], prof[sl])                    # chance keeps sigma_0
+                    continue
+                pos = np.maximum(R[sl], 0.0)
+                want = pos / pos.sum() if pos.sum() > 0 else np.full(tr.nact[h], 1.0 / tr.nact[h])
+                np.testing.assert_allclose(nxt[sl], want, atol=1e-12)
 
 
 def test_cfr_plus_first_iteration_equals_vanilla():
