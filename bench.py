@@ -466,7 +466,10 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
            "node_updates_per_s": float(nodes.sum()) * K / sec,
            "per_subgame_us_per_iteration": {"p50": float(np.percentile(per_game, 50)),
                                             "p99": float(np.percentile(per_game, 99)),
-                                            "max": float(per_game.max())},
+                                            "max": float(per_game.max()),
+                                            "note": "a resident subgame's own block time; a subgame of the forest "
+                                                    "part advances with the forest, so its iteration time is the "
+                                                    "forest's"},
            "exploitability_after": {"median": float(np.median(nc) / 2), "max": float(nc.max() / 2)},
            "oracle_error": {"games_checked": len(checked), "nash_conv_abs_max": float(max(dev)),
                             "note": "GPU NashConv against the oracle's best responses to the GPU's average strategy"},
@@ -489,15 +492,33 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
                                 update_mode=update_mode)
         cfr.cfr_batch_set_tuning(b2, tune["threads_per_block"], tune["blocks_per_sm"])
         t0, it, worst = time.perf_counter(), 0, float("inf")
+        first_s = np.full(len(games), np.nan)                 # per game: the first check at or below 1e-3
+        first_it = np.full(len(games), -1, dtype=np.int64)
         while it < 20000 and time.perf_counter() - t0 < 60.0:
             cfr.cfr_batch_iterate(b2, 100)
             it += 100
-            worst = float(cfr.cfr_batch_exploitability(b2).max() / 2)
+            ex = cfr.cfr_batch_exploitability(b2) / 2
+            now = (ex <= TTT_TARGET) & (first_it < 0)
+            first_it[now] = it
+            first_s[now] = time.perf_counter() - t0
+            worst = float(ex.max())
             if worst <= TTT_TARGET:
                 break
+        done = first_it >= 0
         out["time_to_exploitability_1e-3_all"] = {"reached": worst <= TTT_TARGET,
                                                   "seconds": time.perf_counter() - t0, "iterations": it,
                                                   "worst_exploitability": worst, "check_every": 100}
+        # every subgame advances with the batch, so its own time to the target is when the batch's evaluation
+        # first finds it at or below 1e-3: a per-subgame distribution (evaluations included)
+        out["per_subgame_time_to_exploitability_1e-3"] = {
+            "games_reached": int(done.sum()),
+            "seconds": {"p50": float(np.percentile(first_s[done], 50)) if done.any() else None,
+                        "p99": float(np.percentile(first_s[done], 99)) if done.any() else None,
+                        "max": float(first_s[done].max()) if done.any() else None},
+            "iterations": {"p50": float(np.percentile(first_it[done], 50)) if done.any() else None,
+                           "p99": float(np.percentile(first_it[done], 99)) if done.any() else None,
+                           "max": int(first_it[done].max()) if done.any() else None},
+            "note": "first evaluation (every 100 iterations) at which the subgame's exploitability is at most 1e-3"}
         b2.close()
     b.close()
     # the plain full-tree solver on the same games as one tree
