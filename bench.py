@@ -437,8 +437,9 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
     tune = cfr.cfr_batch_tune(games, variant=cfr.CFR_PLUS, device=local, cache_path=cache, update_mode=update_mode)
     tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
+    fuse = tune.get("fuse_levels", -1)
     b = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"],
-                           update_mode=update_mode)
+                           update_mode=update_mode, fuse_levels=fuse)
     cfr.cfr_batch_set_tuning(b, tune["threads_per_block"], tune["blocks_per_sm"])
     load_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(local)
@@ -473,7 +474,8 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
            "exploitability_after": {"median": float(np.median(nc) / 2), "max": float(nc.max() / 2)},
            "oracle_error": {"games_checked": len(checked), "nash_conv_abs_max": float(max(dev)),
                             "note": "GPU NashConv against the oracle's best responses to the GPU's average strategy"},
-           "tuning": {k: tune[k] for k in ("split_nodes", "threads_per_block", "blocks_per_sm", "cached")},
+           "tuning": {k: tune.get(k, -1) for k in ("split_nodes", "threads_per_block", "blocks_per_sm", "fuse_levels",
+                                                   "cached")},
            "tuning_trials_us_per_iteration": tune["trials"],
            "forest_part": {"games": info["forest_games"], "nodes": info["forest_nodes"],
                            "algorithmic_bytes_per_iteration": info["forest_bytes_per_iteration"],
@@ -489,7 +491,7 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
     # time until every subgame's exploitability is at most 1e-3 (evaluations included)
     if ttt:
         b2 = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, device=local, split_nodes=tune["split_nodes"],
-                                update_mode=update_mode)
+                                update_mode=update_mode, fuse_levels=fuse)
         cfr.cfr_batch_set_tuning(b2, tune["threads_per_block"], tune["blocks_per_sm"])
         t0, it, worst = time.perf_counter(), 0, float("inf")
         first_s = np.full(len(games), np.nan)                 # per game: the first check at or below 1e-3
@@ -524,7 +526,8 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
     # the plain full-tree solver on the same games as one tree
     t0 = time.perf_counter()
     root = gamegen.with_chance_root(games)
-    s = cfr.cfr_load_tree(root, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, device=local, update_mode=update_mode)
+    s = cfr.cfr_load_tree(root, variant=cfr.CFR_PLUS, precision=cfr.CFR_FP32, device=local, update_mode=update_mode,
+                          fuse_levels=fuse)
     tree_load_s = time.perf_counter() - t0
     cfr.cfr_iterate(s, 3)
     torch.cuda.synchronize()
@@ -539,7 +542,9 @@ def _batched_run(args, local: int, games_gen, label: str, ttt: bool = True, upda
                                          "algorithmic_bytes_per_iteration": tinfo["bytes_per_iteration"],
                                          "achieved_gbs": tinfo["bytes_per_iteration"] * K / sec_tree / 1e9,
                                          "bytes_per_node_iteration": tinfo["bytes_per_iteration"] / root.num_nodes,
-                                         "note": "the games under one uniform chance root, cfr_load_tree + cfr_iterate"}
+                                         "fuse_levels": fuse,
+                                         "note": "the games under one uniform chance root, cfr_load_tree + cfr_iterate, "
+                                                 "with the batch's tuned fusion setting"}
     s.close()
     return out
 

@@ -517,10 +517,10 @@ class Batch:
 
 def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=None, stream=None,
                    allocator: str = "torch", dcfr=(1.5, 0.0, 2.0), split_nodes: int = 0,
-                   update_mode=CFR_SIMULTANEOUS, head_levels: int = -1) -> Batch:
+                   update_mode=CFR_SIMULTANEOUS, head_levels: int = -1, fuse_levels: int = -1) -> Batch:
     """Loads a list of games for batched solving (FP32 mode).  split_nodes: cfr_config.batch_split_nodes
     (0 default, negative: every game whose image fits shared memory in the persistent kernel);
-    head_levels: cfr_config.head_levels of the forest part."""
+    head_levels and fuse_levels: cfr_config.head_levels and cfr_config.fuse_levels of the forest part."""
     import torch
 
     if not torch.cuda.is_available():
@@ -535,6 +535,7 @@ def cfr_batch_load(games, variant=CFR_PLUS, avg_weight=CFR_AVG_DEFAULT, device=N
     cfg.batch_split_nodes = int(split_nodes)
     cfg.update_mode = int(update_mode)
     cfg.head_levels = int(head_levels)
+    cfg.fuse_levels = int(fuse_levels)
     alloc = None
     if allocator == "torch":
         alloc = _TorchAllocator(dev, st_handle)
@@ -644,20 +645,22 @@ def cfr_batch_get_info(b: Batch) -> dict:
 
 def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 512, 2048, -1), trial_iterations: int = 10,
                    device=None, cache_path: str | None = None, dcfr=(1.5, 0.0, 2.0),
-                   update_mode=CFR_SIMULTANEOUS) -> dict:
+                   update_mode=CFR_SIMULTANEOUS, fuse_candidates=(-1, 2)) -> dict:
     """The batch's size split (which games run as one forest through the per-depth kernels, which in the
-    persistent kernel) and the persistent launch shape: for each candidate split the batch is loaded,
-    the launch shape measured (cfr_batch_autotune), and trial_iterations timed; the fastest is kept and
-    cached per GPU and size bucket (in memory, and in the JSON file cache_path when given).  split 1 runs
-    every game as one forest, -1 every game whose image fits shared memory in the persistent kernel.
-    Returns {split_nodes, threads_per_block, blocks_per_sm, us_per_iteration (None if cached), cached,
-    trials}."""
+    persistent kernel), the persistent launch shape and the forest part's fusion: for each candidate split
+    the batch is loaded, the launch shape measured (cfr_batch_autotune), and trial_iterations timed; then
+    the fastest split is timed again with each other fusion setting of fuse_candidates (cfr_config.fuse_levels
+    of the forest part: -1 the last two depths and the pair above them, 2 the last two only).  The fastest is
+    kept and cached per GPU and size bucket (in memory, and in the JSON file cache_path when given).  split 1
+    runs every game as one forest, -1 every game whose image fits shared memory in the persistent kernel.
+    Returns {split_nodes, threads_per_block, blocks_per_sm, fuse_levels, us_per_iteration (None if cached),
+    cached, trials}."""
     import json
 
     import torch
 
     probe = Batch(None, None, games)
-    key = f"{torch.cuda.get_device_name()}|{_size_bucket(probe)}|variant={int(variant)}|mode={int(update_mode)}|split"
+    key = f"{torch.cuda.get_device_name()}|{_size_bucket(probe)}|variant={int(variant)}|mode={int(update_mode)}|split+fuse"
     disk = {}
     if cache_path and os.path.exists(cache_path):
         try:
@@ -666,13 +669,17 @@ def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 512, 2048, -1), trial_ite
             disk = {}
     hit = _TUNE_CACHE.get(key) or disk.get(key)
     if hit:
-        return dict(hit, us_per_iteration=None, cached=True, trials=None, key=key)
-    trials = []
-    for split in splits:
-        b = cfr_batch_load(games, variant=variant, device=device, dcfr=dcfr, split_nodes=split, update_mode=update_mode)
-        t = _BatchTuning()                               # measured for this split (no cache lookup)
-        _check_batch(lib().cfr_batch_autotune(b.handle, 2, ctypes.byref(t), None), b.handle)
-        shape = {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm}
+        return dict({"fuse_levels": -1}, **hit, us_per_iteration=None, cached=True, trials=None, key=key)
+
+    def trial(split, fuse, shape=None):
+        b = cfr_batch_load(games, variant=variant, device=device, dcfr=dcfr, split_nodes=split, update_mode=update_mode,
+                           fuse_levels=fuse)
+        if shape is None:
+            t = _BatchTuning()                           # measured for this split (no cache lookup)
+            _check_batch(lib().cfr_batch_autotune(b.handle, 2, ctypes.byref(t), None), b.handle)
+            shape = {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm}
+        else:
+            cfr_batch_set_tuning(b, shape["threads_per_block"], shape["blocks_per_sm"])
         cfr_batch_iterate(b, 2)                       # warm-up (graph capture)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -681,11 +688,16 @@ def cfr_batch_tune(games, variant=CFR_PLUS, splits=(1, 512, 2048, -1), trial_ite
         e1.record()
         torch.cuda.synchronize()
         us = 1e3 * e0.elapsed_time(e1) / trial_iterations
-        trials.append({"split_nodes": split, "threads_per_block": shape["threads_per_block"],
-                       "blocks_per_sm": shape["blocks_per_sm"], "us_per_iteration": us})
         b.close()
+        return {"split_nodes": split, "threads_per_block": shape["threads_per_block"],
+                "blocks_per_sm": shape["blocks_per_sm"], "fuse_levels": fuse, "us_per_iteration": us}
+
+    trials = [trial(split, fuse_candidates[0]) for split in splits]
     best = min(trials, key=lambda r: r["us_per_iteration"])
-    rec = {k: best[k] for k in ("split_nodes", "threads_per_block", "blocks_per_sm")}
+    for fuse in fuse_candidates[1:]:
+        trials.append(trial(best["split_nodes"], fuse, {k: best[k] for k in ("threads_per_block", "blocks_per_sm")}))
+    best = min(trials, key=lambda r: r["us_per_iteration"])
+    rec = {k: best[k] for k in ("split_nodes", "threads_per_block", "blocks_per_sm", "fuse_levels")}
     _TUNE_CACHE[key] = rec
     if cache_path:
         disk[key] = rec

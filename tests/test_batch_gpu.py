@@ -184,3 +184,27 @@ def test_size_split_runs_both_parts_like_the_oracle():
     t = cfr.cfr_batch_game_times(b)
     assert np.all(t > 0)
     assert len(set(np.round(t[sizes >= 1500], 6))) == 1          # the forest part advances together
+
+
+@pytest.mark.parametrize("fuse", [-1, 2], ids=["tail_and_pair", "tail_only"])
+def test_forest_fusion_settings_match_oracle(fuse):
+    # The batch autotuner also chooses the forest part's fusion (cfr_config.fuse_levels): -1 fuses the last two
+    # depths and runs the two above them as a pair, 2 fuses the last two only.  Games large enough that the pair
+    # applies (checked on the same games under one chance root), all in the forest part, first iteration and a
+    # step from the oracle's T = 3 state game by game.
+    # (the head limited to a few depths, so that the pair's depths lie below it)
+    games = gamegen.batch_subgames(48, seed=17, min_nodes=2e3, max_nodes=6e4)
+    root = gamegen.with_chance_root(games)
+    info = cfr.cfr_get_info(cfr.cfr_load_tree(root, precision=cfr.CFR_FP32, fuse_levels=fuse, head_levels=3))
+    assert info["pair_depth"] == (-1 if fuse == 2 else info["fused_from_depth"] - 2)
+    b = cfr.cfr_batch_load(games, variant=cfr.CFR_PLUS, split_nodes=1, fuse_levels=fuse, head_levels=3)
+    assert cfr.cfr_batch_get_info(b)["forest_games"] == len(games)
+    cfr.cfr_batch_iterate(b, 1)
+    for i, g in enumerate(games):
+        o = oracle.Oracle(g)
+        o.iterate(1, variant=oracle.CFR_PLUS, avg=oracle.AVG_LINEAR)
+        gs, os_ = cfr.cfr_batch_get_state(b, i), o.state()
+        for k in ("cum_regret", "strat_sum"):
+            assert normwise(gs[k], os_[k]) <= TOL32, (i, k)
+        fp32_regret_budget_check(g, gs, os_, _max_depth(g))
+    b.close()
