@@ -102,7 +102,8 @@ typedef struct {
                                of more than 32 actions and the upper one has at least 8192 decision
                                nodes; 0 or 1 = none (one kernel per depth and pass); k >= 2 = at most k
                                depths (fewer where a subtree exceeds a tile or a node has more than 32
-                               actions), no pair.  Ignored in FP64 mode. */
+                               actions), no pair.  The forest part of a batch (cfr_batch_load) is
+                               loaded with this setting too.  Ignored in FP64 mode. */
     int32_t record_nodes;   /* 1: fused depths also write every node's value and reaches to device
                                memory, so that cfr_get_nodes can return them; 0 (default): they do
                                not, and cfr_get_nodes returns CFR_ERR_STATE when depths are fused. */
