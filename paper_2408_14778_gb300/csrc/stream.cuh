@@ -210,14 +210,12 @@ __device__ __forceinline__ void sb_nodes(const DevTree<float> &t, const SBStage 
             }
         } else {
             const float *dv = ti.staged ? st.dval + (c0[x] - ti.dal) : t.u + c0[x];
-            int kt = 0, kd = 0;
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 if (a < na[x]) {
-                    const bool term = (m[x] >> a) & 1u;
-                    v[x][a] = term ? tv[kt] : dv[kd];
-                    kt += term;
-                    kd += !term;
+                    const int kt = __popc(m[x] & ((1u << a) - 1u));   // terminal children before action a
+                    const float *src = ((m[x] >> a) & 1u) ? tv + kt : dv + (a - kt);
+                    v[x][a] = *src;
                     s[x][a] = __ldg(t.sigma + qb[x] + a);
                 }
             }
@@ -687,14 +685,12 @@ struct TailTiles {
         float ud = 0.f;
         if (na <= NA) {
             float v[NA];
-            int kt = 0, kd = 0;
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 if (a < na) {
-                    const bool term = (m >> a) & 1u;
-                    v[a] = term ? pv[kt] : dv[kd];
-                    kt += term;
-                    kd += !term;
+                    const int kt = __popc(m & ((1u << a) - 1u));   // terminal children before action a
+                    const float *src = ((m >> a) & 1u) ? pv + kt : dv + (a - kt);
+                    v[a] = *src;
                 }
             }
 #pragma unroll
@@ -1329,14 +1325,12 @@ struct PairBottomUpTiles {
             float ud = 0.f;
             float v[NA];
             if (cna <= NA) {
-                int kt = 0, kd = 0;
 #pragma unroll
                 for (int b = 0; b < NA; ++b) {
                     if (b < cna) {
-                        const bool term = (mm >> b) & 1u;
-                        v[b] = term ? tv[kt] : dv[kd];
-                        kt += term;
-                        kd += !term;
+                        const int kt = __popc(mm & ((1u << b) - 1u));
+                        const float *src = ((mm >> b) & 1u) ? tv + kt : dv + (b - kt);
+                        v[b] = *src;
                         ud = madd(ud, sc[r][b], v[b]);
                     }
                 }
@@ -1378,14 +1372,12 @@ struct PairBottomUpTiles {
         float ud = 0.f;
         if (na <= NA) {
             float v[NA];
-            int kt = 0, kd = 0;
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 if (a < na) {
-                    const bool term = (m >> a) & 1u;
-                    v[a] = term ? pv[kt] : dv[kd];
-                    kt += term;
-                    kd += !term;
+                    const int kt = __popc(m & ((1u << a) - 1u));   // terminal children before action a
+                    const float *src = ((m >> a) & 1u) ? pv + kt : dv + (a - kt);
+                    v[a] = *src;
                 }
             }
 #pragma unroll
