@@ -404,3 +404,34 @@ def test_phase_times_run_a_real_iteration(precision, fuse):
         assert info["bytes_per_iteration"] == want
     else:
         assert precision == cfr.CFR_FP32 and info["fused_tiles"] > 0
+
+
+def test_unaligned_device_allocator_is_rejected():
+    # A caller's allocator must return 256-byte aligned blocks, as cudaMalloc does: the kernels' bulk copies
+    # need 16-byte aligned arrays.  One that returns blocks 16 bytes off fails the load with CFR_ERR_INVALID
+    # and gets every block it handed out back.
+    import ctypes
+
+    import torch
+
+    lib = cfr.lib()
+    d = cfr._Desc(gamegen.config("bucket3_depth6", seed=1))
+    c = cfr._Config()
+    lib.cfr_config_init(ctypes.byref(c))
+    c.precision, c.device = cfr.CFR_FP32, torch.cuda.current_device()
+    held = {}
+
+    def alloc(nbytes, ctx):
+        p = int(torch.cuda.caching_allocator_alloc(int(nbytes) + 256, c.device))
+        held[p + 16] = p
+        return p + 16
+
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(held.pop(int(ptr)))
+
+    a, f = cfr._ALLOC_FN(alloc), cfr._FREE_FN(free)
+    c.dev_alloc, c.dev_free = a, f
+    h = ctypes.c_void_p()
+    st = lib.cfr_load_tree(ctypes.byref(d.c), ctypes.byref(c), ctypes.byref(h))
+    assert st == cfr.CFR_ERR_INVALID and b"256-byte" in lib.cfr_last_error(None)
+    assert not held and not h.value
