@@ -750,6 +750,11 @@ struct cfr_mlp {
     // kernels.  A graph is captured (on cap_stream, a stream of its own) the second time a pass runs with the same
     // key; the first run of a key is launched directly.
     cudaStream_t cap_stream = nullptr;
+    // Path 2's backward pass runs each layer's weight gradient on side (forked from the pass's stream once
+    // that layer's output gradient exists, joined at the end) beside the data-gradient chain.
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> fork_ev;
+    cudaEvent_t join_ev = nullptr;
     struct PassGraph {
         cudaGraphExec_t exec = nullptr;
         int64_t bp = 0, cap = 0;     // the key: padded batch, buffer capacity, tensor path
@@ -1050,9 +1055,19 @@ cfr_status backward_products(cfr_mlp *m, int64_t Bp, double *flops) {
         const int64_t K = m->pdims[(size_t)l], N = m->pdims[(size_t)l + 1];
         const __nv_bfloat16 *dz = m->grads[(size_t)l];
         // dW[o][i] = sum_b dZ[b][o] X[b][i]
-        if (m->path == 2)   // tcgen05 with TMA operands: the transposes dZ^T [out][batch] and X^T [in][batch]
-            MCK(gemm_dw_tma(m, m->grads_t[(size_t)l], m->acts_t[(size_t)l], m->g + m->w_off[(size_t)l], N, K, Bp));
-        else
+        if (m->path == 2) {  // tcgen05 with TMA operands: the transposes dZ^T [out][batch] and X^T [in][batch]
+            // on the side stream, beside the data gradients, once this layer's output gradient is written
+            MCK(cudaEventRecord(m->fork_ev[(size_t)l], m->stream));
+            MCK(cudaStreamWaitEvent(m->side, m->fork_ev[(size_t)l], 0));
+            cudaStream_t main = m->stream;
+            const bool pdl = m->pdl_next;
+            m->stream = m->side;
+            const cudaError_t e = gemm_dw_tma(m, m->grads_t[(size_t)l], m->acts_t[(size_t)l], m->g + m->w_off[(size_t)l],
+                                              N, K, Bp);
+            m->stream = main;
+            m->pdl_next = pdl;
+            MCK(e);
+        } else
             MCK((gemm<false, false, kEpiStore>(m, dz, N, m->acts[(size_t)l], K, m->g + m->w_off[(size_t)l], K, N, K, Bp,
                                                nullptr, nullptr)));
         fb += 2.0 * (double)N * K * Bp;
@@ -1065,6 +1080,11 @@ cfr_status backward_products(cfr_mlp *m, int64_t Bp, double *flops) {
                                                  K, N, nullptr, m->acts[(size_t)l])));
             fb += 2.0 * (double)Bp * K * N;
         }
+    }
+    if (m->path == 2) {              // the weight gradients are done before the pass ends
+        MCK(cudaEventRecord(m->join_ev, m->side));
+        MCK(cudaStreamWaitEvent(m->stream, m->join_ev, 0));
+        m->pdl_next = false;
     }
     *flops = fb;
     return CFR_OK;
@@ -1159,6 +1179,11 @@ cfr_status cfr_mlp_create(const int32_t *dims, int32_t num_layers, int32_t devic
     for (cudaEvent_t &ev : m->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);
+    m->fork_ev.assign((size_t)m->L, nullptr);
+    for (cudaEvent_t &ev : m->fork_ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->join_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return fail(e);
     *out = m;
@@ -1373,6 +1398,10 @@ void cfr_mlp_free(cfr_mlp *m) {
     for (cfr_mlp::PassGraph *g : {&m->gfwd, &m->gfwd_train, &m->gbwd})
         if (g->exec) cudaGraphExecDestroy(g->exec);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->side) cudaStreamDestroy(m->side);
+    for (cudaEvent_t ev : m->fork_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (m->join_ev) cudaEventDestroy(m->join_ev);
     delete m;
 }
 
